@@ -1,0 +1,318 @@
+"""Plain FP64 CPU oracle: truncated CPQR, column/row/two-sided ID, CUR-ID and
+the randomized sketch of Voronin & Martinsson (arXiv:1412.8447).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  Everything is float64
+numpy, one step at a time, in the order the paper states the method.  Library
+primitives (matrix product, Householder QR of a tall matrix, triangular
+solve) serve as single steps; nothing is blocked, fused or reordered.
+
+Conventions fixed here (the paper leaves them open):
+  * indices are 0-based; ``J[:k]`` are the pivots in selection order and
+    ``J[k:]`` are the unselected columns in ascending index order;
+  * among exactly equal pivot norms the smallest column index wins;
+  * ``T`` is k x (n-k), its columns follow ``J[k:]``;
+  * ``orth`` returns the row-orthonormal Q with Y = L Q, L lower triangular
+    with a positive diagonal (unique for full row rank);
+  * the adaptive rank is the smallest j with ||A - C V*||_F <= tol ||A||_F.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg
+
+__all__ = [
+    "as_f64", "CPQR", "cpqr", "interpolation_matrix", "vstar", "wmat",
+    "IDResult", "id_col", "id_row", "TSIDResult", "tsid", "CURResult",
+    "cur_middle", "cur", "orth_rows", "sketch", "randomized_id_col",
+    "randomized_cur", "rel_err_fro", "OK", "RANK_DEFICIENT",
+    "rank_threshold",
+]
+
+OK = 0
+RANK_DEFICIENT = 2
+
+
+def as_f64(A):
+    """Exact upcast of a stored matrix (float32, float64, or bfloat16 values
+    already held as float32) to a float64 numpy array."""
+    if hasattr(A, "detach"):  # torch tensor
+        A = A.detach().to("cpu")
+        if str(A.dtype) == "torch.bfloat16":
+            A = A.float()
+        A = A.numpy()
+    return np.array(A, dtype=np.float64, copy=True)
+
+
+def rank_threshold(shape, nu_first, eps=np.finfo(np.float64).eps):
+    """Pivot norm at or below which the factorization is declared rank
+    deficient (the case of Section 2.3 where S11 is singular): a pivot norm
+    no larger than 10 * max(m, n) * eps times the first pivot norm."""
+    return 10.0 * max(shape) * eps * nu_first
+
+
+@dataclass
+class CPQR:
+    """Result of k steps of column-pivoted QR, Eq. (2.4)-(2.5):
+    Y(:, J) = Q1 S1 + Q2 S2 with S1 = [S11 S12] upper trapezoidal.
+
+    J       : full permutation (int64, length n); J[:k] pivots in order.
+    S1      : k x n, columns in the order J (S1[:, :k] = S11 upper triangular).
+    Q1      : l x k with orthonormal columns.
+    k       : number of steps taken.
+    k_eff   : numerical rank found (== k unless rank deficient).
+    nu      : pivot norms, nu[j] = |S(j, j)|.
+    gaps    : relative gap (nu_(1) - nu_(2)) / nu_(1) between the two largest
+              candidate norms at every step (inf when only one candidate).
+    resid   : ||Y - Q1 Q1^T Y||_F after 0, 1, ..., k steps.
+    """
+    J: np.ndarray
+    S1: np.ndarray
+    Q1: np.ndarray
+    k: int
+    k_eff: int
+    nu: np.ndarray
+    gaps: np.ndarray
+    resid: np.ndarray
+    status: int = OK
+
+
+def cpqr(Y, k=None, tol=None, eps=np.finfo(np.float64).eps):
+    """Truncated column-pivoted QR by pivoted Gram-Schmidt (Section 2.2,
+    Eq. (2.4)-(2.5); the first step of Algorithm 1; the Gram-Schmidt reading
+    of Remark 2.1 and Section 2.4).
+
+    Each step j: (1) recompute the norm of every unselected residual column
+    from the vector itself; (2) pick the largest (smallest index on exact
+    ties); (3) normalise it to q_j and re-orthogonalise once against
+    q_1..q_{j-1}; (4) project q_j out of every unselected residual column.
+    Stops after ``k`` steps, or (``tol`` given) at the first j with
+    ||residual||_F <= tol * ||Y||_F, or at min(l, n).
+    Finally S1 = Q1^T Y(:, J), whose strictly lower part in the first k columns
+    is zero in exact arithmetic and is set to zero.
+    """
+    Y = as_f64(Y)
+    l, n = Y.shape
+    kmax = min(l, n)
+    if k is not None:
+        kmax = min(kmax, int(k))
+    Rres = Y.copy()
+    active = np.ones(n, dtype=bool)
+    Q = np.zeros((l, kmax))
+    J, nus, gaps = [], [], []
+    normY = np.sqrt(np.sum(Y * Y))
+    resid = [normY]
+    k_eff = None
+    nu_first = None
+    for j in range(kmax):
+        if tol is not None and resid[-1] <= tol * normY:
+            break
+        nu = np.sqrt(np.sum(Rres * Rres, axis=0))            # (1)
+        cand = np.where(active, nu, -1.0)
+        p = int(np.argmax(cand))                               # (2) first max
+        srt = np.sort(cand[active])[::-1]
+        if srt.size > 1 and srt[0] > 0:
+            gaps.append((srt[0] - srt[1]) / srt[0])
+        else:
+            gaps.append(np.inf)
+        if nu_first is None:
+            nu_first = nu[p]
+        if k_eff is None and (nu[p] == 0.0 or
+                              nu[p] <= rank_threshold((l, n), nu_first, eps)):
+            k_eff = j
+        if nu[p] > 0.0:
+            q = Rres[:, p] / nu[p]                              # (3)
+            q = q - Q[:, :j] @ (Q[:, :j].T @ q)
+            nq = np.linalg.norm(q)
+            q = q / nq if nq > 0 else q
+        else:
+            q = np.zeros(l)
+        Q[:, j] = q
+        nus.append(nu[p])
+        J.append(p)
+        active[p] = False
+        Rres[:, p] = 0.0
+        Rres[:, active] -= np.outer(q, q @ Rres[:, active])     # (4)
+        resid.append(np.sqrt(np.sum(Rres[:, active] ** 2)))
+    kk = len(J)
+    Jfull = np.array(J + [i for i in range(n) if active[i]], dtype=np.int64)
+    Q1 = Q[:, :kk]
+    S1 = Q1.T @ Y[:, Jfull]
+    S1[:, :kk] = np.triu(S1[:, :kk])
+    status = OK
+    if k_eff is None:
+        k_eff = kk
+    else:
+        status = RANK_DEFICIENT
+    return CPQR(J=Jfull, S1=S1, Q1=Q1, k=kk, k_eff=k_eff,
+                nu=np.array(nus), gaps=np.array(gaps), resid=np.array(resid),
+                status=status)
+
+
+def interpolation_matrix(S1, k, k_eff=None):
+    """T solving S11 T = S12 by back substitution (Eq. (2.8), Section 4.1).
+    S1 is k x n in pivot order.  When S11 is singular (numerical rank
+    k_eff < k) the bottom k - k_eff rows of T are zero and the top rows solve
+    the leading k_eff x k_eff system, as Section 2.3 allows."""
+    S1 = np.asarray(S1, dtype=np.float64)
+    n = S1.shape[1]
+    if k_eff is None:
+        k_eff = k
+    T = np.zeros((k, n - k))
+    if k_eff > 0:
+        T[:k_eff] = scipy.linalg.solve_triangular(
+            S1[:k_eff, :k_eff], S1[:k_eff, k:], lower=False)
+    return T
+
+
+def vstar(J, T, n):
+    """V* = [I_k T] P^* as an explicit k x n matrix (Eq. (2.9)):
+    V*(:, J[:k]) = I and V*(:, J[k:]) = T."""
+    k = T.shape[0]
+    V = np.zeros((k, n))
+    V[np.arange(k), J[:k]] = 1.0
+    V[:, J[k:]] = T
+    return V
+
+
+def wmat(I, TW, m):
+    """W = P [I; T_W^*] as an explicit m x k matrix (Eq. (3.11)):
+    W(I[:k], :) = I and W(I[k:], :) = T_W^T."""
+    k = TW.shape[0]
+    W = np.zeros((m, k))
+    W[I[:k], np.arange(k)] = 1.0
+    W[I[k:], :] = TW.T
+    return W
+
+
+@dataclass
+class IDResult:
+    """Column ID A ~ A(:, J[:k]) V*, V* = [I T] P^* (Algorithm 1)."""
+    J: np.ndarray
+    T: np.ndarray
+    k: int
+    qr: CPQR
+    status: int = OK
+
+
+def id_col(A, k=None, tol=None, eps=np.finfo(np.float64).eps):
+    """Rank-k column ID (Algorithm 1, Section 2.3): CPQR of A, then
+    T = S11^{-1} S12."""
+    res = cpqr(A, k=k, tol=tol, eps=eps)
+    T = interpolation_matrix(res.S1, res.k, res.k_eff)
+    return IDResult(J=res.J, T=T, k=res.k, qr=res, status=res.status)
+
+
+def id_row(A, k=None, tol=None, eps=np.finfo(np.float64).eps):
+    """Row ID A ~ W A(I[:k], :) by the column ID of A^* (Remark 2.1)."""
+    return id_col(as_f64(A).T, k=k, tol=tol, eps=eps)
+
+
+@dataclass
+class TSIDResult:
+    """Two-sided ID A ~ W A(I[:k], J[:k]) V* (Algorithm 2, Eq. (2.12))."""
+    J: np.ndarray
+    T: np.ndarray
+    I: np.ndarray
+    TW: np.ndarray
+    k: int
+    col: IDResult
+    row: IDResult
+    status: int = OK
+
+
+def tsid(A, k=None, tol=None, Y=None, eps=np.finfo(np.float64).eps):
+    """Algorithm 2: a column ID (of A, or of a sketch Y of A when given, as in
+    Algorithm 4), then a full rank-k ID of C^* with C = A(:, J[:k])
+    (Eq. (2.11)), which is exact."""
+    A = as_f64(A)
+    col = id_col(A if Y is None else Y, k=k, tol=tol, eps=eps)
+    kk = col.k
+    C = A[:, col.J[:kk]]
+    row = id_col(C.T, k=kk, eps=eps)
+    status = col.status if col.status != OK else row.status
+    return TSIDResult(J=col.J, T=col.T, I=row.J, TW=row.T, k=kk, col=col,
+                      row=row, status=status)
+
+
+def cur_middle(R, Vs):
+    """U = V* R^+ (Eq. (3.5)) as the least-squares solution of U R = V*
+    (Eq. (4.2)) through the Householder QR of R^T: R^T = Q_R S_R, then
+    U^T = S_R^{-1} Q_R^T V with V = (V*)^T."""
+    Qr, Sr = np.linalg.qr(np.asarray(R, dtype=np.float64).T)
+    Ut = scipy.linalg.solve_triangular(Sr, Qr.T @ np.asarray(Vs).T,
+                                       lower=False)
+    return Ut.T
+
+
+@dataclass
+class CURResult:
+    """CUR-ID A ~ C U R (Algorithm 3)."""
+    J: np.ndarray
+    I: np.ndarray
+    T: np.ndarray
+    TW: np.ndarray
+    U: np.ndarray
+    C: np.ndarray
+    R: np.ndarray
+    k: int
+    ts: TSIDResult
+    status: int = OK
+
+
+def cur(A, k=None, tol=None, Y=None, eps=np.finfo(np.float64).eps):
+    """Algorithm 3: two-sided ID, C = A(:, J[:k]), R = A(I[:k], :),
+    U = V* R^+ (Eq. (3.1), (3.5))."""
+    A = as_f64(A)
+    ts = tsid(A, k=k, tol=tol, Y=Y, eps=eps)
+    kk = ts.k
+    n = A.shape[1]
+    C = A[:, ts.J[:kk]]
+    R = A[ts.I[:kk], :]
+    U = cur_middle(R, vstar(ts.J, ts.T, n))
+    return CURResult(J=ts.J, I=ts.I, T=ts.T, TW=ts.TW, U=U, C=C, R=R, k=kk,
+                     ts=ts, status=ts.status)
+
+
+def orth_rows(Y):
+    """Row orthonormalisation without pivoting (Section 5.3): the unique
+    row-orthonormal Q with Y = L Q, L lower triangular with positive
+    diagonal, from the Householder QR of Y^T with the signs fixed."""
+    Qt, Rt = np.linalg.qr(as_f64(Y).T)
+    s = np.sign(np.diag(Rt))
+    s[s == 0] = 1.0
+    return (Qt * s).T
+
+
+def sketch(A, Omega, q=0, orth=True):
+    """Sample matrix of Algorithm 4 with the power scheme of Section 5.3:
+    (2a) Y = Omega A; (2b) for i = 1..q: (2c) Y <- orth(Y) A^*,
+    (2d) Y <- orth(Y) A.  ``orth=False`` gives the un-orthonormalised
+    variant, Eq. (5.3)."""
+    A = as_f64(A)
+    Y = as_f64(Omega) @ A
+    for _ in range(q):
+        Y = (orth_rows(Y) if orth else Y) @ A.T
+        Y = (orth_rows(Y) if orth else Y) @ A
+    return Y
+
+
+def randomized_id_col(A, Omega, k, q=0, orth=True,
+                      eps=np.finfo(np.float64).eps):
+    """Algorithm 4: Y from ``sketch``, k steps of CPQR on Y (the first k
+    pivots of the full pivoted QR the algorithm states), T from S of Y."""
+    Y = sketch(A, Omega, q=q, orth=orth)
+    return id_col(Y, k=k, eps=eps), Y
+
+
+def randomized_cur(A, Omega, k, q=0, orth=True,
+                   eps=np.finfo(np.float64).eps):
+    """CUR-ID (Algorithm 3) with its column ID taken from Algorithm 4."""
+    Y = sketch(A, Omega, q=q, orth=orth)
+    return cur(A, k=k, Y=Y, eps=eps), Y
+
+
+def rel_err_fro(A, C, U, R):
+    """||A - C U R||_F / ||A||_F in float64."""
+    A = as_f64(A)
+    E = A - as_f64(C) @ as_f64(U) @ as_f64(R)
+    return float(np.sqrt(np.sum(E * E)) / np.sqrt(np.sum(A * A)))

@@ -1,0 +1,289 @@
+"""Pins for the FP64 oracle: checks against values fixed by the paper's
+identities, by library routines (LAPACK dgeqp3 via scipy, lstsq, pinv, SVD,
+Cholesky), by closed forms, by a hand-derived example and by brute force.
+No check re-types the oracle's own formula."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import torch
+
+import oracle as O
+import synthetic as syn
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def f64(t):
+    return t.numpy().astype(np.float64) if hasattr(t, "numpy") else np.asarray(t, np.float64)
+
+
+def fro(X):
+    return float(np.sqrt(np.sum(np.asarray(X) ** 2)))
+
+
+# --- hand-derived example ---------------------------------------------------
+
+def test_handworked_example():
+    g = json.load(open(os.path.join(GOLDEN, "handworked_2x3.json")))
+    A = np.array(g["A"])
+    for key, k in (("k1", 1), ("k2", 2)):
+        r = O.id_col(A, k=k)
+        assert list(r.J) == g[key]["J"]
+        np.testing.assert_allclose(r.T, np.array(g[key]["T"]), rtol=0, atol=1e-15)
+        np.testing.assert_allclose(r.qr.nu, g[key]["nu"], rtol=1e-15)
+        assert abs(r.qr.resid[-1] - g[key]["resid_fro"]) <= 1e-15
+    r = O.id_col(A, k=2)
+    np.testing.assert_allclose(np.abs(r.qr.S1[:, :2]), np.array(g["k2"]["S11_abs"]), atol=1e-15)
+
+
+# --- CPQR against LAPACK and against the planted order ---------------------
+
+@pytest.mark.parametrize("m,n,k,seed", [(60, 40, 12, 1), (40, 70, 20, 2),
+                                        (128, 96, 33, 3), (33, 257, 30, 4)])
+def test_cpqr_planted_and_lapack(m, n, k, seed):
+    A, perm = syn.planted_pivots(m, n, k, seed)
+    A = f64(A)
+    r = O.cpqr(A, k=k)
+    assert list(r.J[:k]) == list(perm[:k])
+    # LAPACK dgeqp3 (Householder with norm downdating): a different algorithm
+    R, P = scipy.linalg.qr(A, mode="r", pivoting=True)
+    assert list(P[:k]) == list(r.J[:k])
+    # rows of S agree with LAPACK's R up to sign, column by column
+    S_by_col = np.zeros((k, n))
+    S_by_col[:, r.J] = r.S1
+    R_by_col = np.zeros((k, n))
+    R_by_col[:, P] = R[:k]
+    sgn = np.sign(np.diag(R[:k, :k])) * np.sign(np.diag(r.S1[:, :k]))
+    np.testing.assert_allclose(S_by_col, sgn[:, None] * R_by_col,
+                               atol=1e-12 * np.abs(R).max())
+    # residual columns are ascending
+    assert list(r.J[k:]) == sorted(r.J[k:])
+    assert sorted(r.J) == list(range(n))
+
+
+def _brute_force_greedy(A, k):
+    """Independent greedy: at each step pick the column with the largest
+    least-squares residual against the columns already picked."""
+    m, n = A.shape
+    sel = []
+    for _ in range(k):
+        best, bi = -1.0, None
+        for c in range(n):
+            if c in sel:
+                continue
+            if sel:
+                x, *_ = np.linalg.lstsq(A[:, sel], A[:, c], rcond=None)
+                res = np.linalg.norm(A[:, c] - A[:, sel] @ x)
+            else:
+                res = np.linalg.norm(A[:, c])
+            if res > best * (1 + 1e-12):
+                best, bi = res, c
+        sel.append(bi)
+    return sel
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_cpqr_brute_force_tiny(seed):
+    g = np.random.default_rng(100 + seed)
+    m, n = g.integers(3, 9), g.integers(3, 10)
+    A = g.standard_normal((m, n)) * g.uniform(0.1, 3, n)
+    k = min(m, n) - 1
+    r = O.cpqr(A, k=k)
+    assert list(r.J[:k]) == _brute_force_greedy(A, k)
+
+
+def test_cpqr_ties_take_smallest_index():
+    g = np.random.default_rng(7)
+    A = g.standard_normal((8, 6))
+    A[:, 4] = A[:, 1] = 10 * g.standard_normal(8)  # exact tie, largest norm
+    r = O.cpqr(A, k=3)
+    assert r.J[0] == 1
+
+
+def test_cpqr_decay_property():
+    """|S(j,j)| >= ||S(j:k, l)|| for l after j (Section 2.2)."""
+    A = f64(syn.spectrum_matrix(80, 60, syn.exp_decay(60, 5.0), 11))
+    r = O.cpqr(A, k=30)
+    S = r.S1
+    for j in range(30):
+        col_norms = np.sqrt(np.sum(S[j:, j + 1:] ** 2, axis=0))
+        assert np.all(abs(S[j, j]) >= col_norms * (1 - 1e-12))
+
+
+def test_cpqr_residual_matches_projection():
+    """resid[j] = ||A - Q_j Q_j^T A||_F with Q_j from numpy's QR of the
+    selected columns (Eq. (2.5), (2.10))."""
+    A = f64(syn.spectrum_matrix(50, 70, syn.exp_decay(50, 8.0), 12))
+    r = O.cpqr(A, k=20)
+    for j in (1, 5, 20):
+        Qj, _ = np.linalg.qr(A[:, r.J[:j]])
+        assert abs(fro(A - Qj @ (Qj.T @ A)) - r.resid[j]) <= 1e-12 * fro(A)
+
+
+# --- column ID ---------------------------------------------------------------
+
+def test_id_identities():
+    A = f64(syn.spectrum_matrix(90, 70, syn.exp_decay(70), 21))
+    k = 25
+    r = O.id_col(A, k=k)
+    V = O.vstar(r.J, r.T, A.shape[1])
+    # V*(:, J[:k]) is exactly the identity (Eq. (2.9))
+    assert np.array_equal(V[:, r.J[:k]], np.eye(k))
+    C = A[:, r.J[:k]]
+    # A - C V* = Q2 S22: its Frobenius norm is the CPQR residual (Eq. (2.10))
+    assert abs(fro(A - C @ V) - r.qr.resid[k]) <= 1e-12 * fro(A)
+    # T closed form: least-squares coefficients of the residual columns
+    Tls, *_ = np.linalg.lstsq(C, A[:, r.J[k:]], rcond=None)
+    np.testing.assert_allclose(r.T, Tls, atol=1e-9 * np.abs(Tls).max())
+    # Eckart-Young: the ID error is at least sigma_{k+1} (Section 2.2)
+    s = np.linalg.svd(A, compute_uv=False)
+    assert np.linalg.norm(A - C @ V, 2) >= s[k] * (1 - 1e-12)
+
+
+def test_exact_rank_reconstruction():
+    A = f64(syn.exact_rank(120, 90, 15, 31))
+    res = O.cur(A, k=15)
+    assert O.rel_err_fro(A, res.C, res.U, res.R) <= 1e-13
+    V = O.vstar(res.J, res.T, 90)
+    assert fro(A - res.C @ V) <= 1e-13 * fro(A)
+
+
+def test_rank_deficient_status_and_zero_rows():
+    A = f64(syn.exact_rank(40, 30, 6, 32))
+    r = O.id_col(A, k=10)
+    assert r.status == O.RANK_DEFICIENT and r.qr.k_eff == 6
+    assert np.all(r.T[6:] == 0)
+    C = A[:, r.J[:10]]
+    assert fro(A - C @ O.vstar(r.J, r.T, 30)) <= 1e-12 * fro(A)
+
+
+def test_adaptive_rank():
+    A = f64(syn.spectrum_matrix(100, 80, syn.exp_decay(80, 6.0), 41))
+    tol = 1e-6
+    r = O.id_col(A, tol=tol)
+    k = r.k
+    nA = fro(A)
+    # residual at k meets the tolerance; at k - 1 (recomputed independently) it does not
+    assert r.qr.resid[k] <= tol * nA
+    rk1 = O.id_col(A, k=k - 1)
+    C = A[:, rk1.J[:k - 1]]
+    assert fro(A - C @ O.vstar(rk1.J, rk1.T, 80)) > tol * nA
+
+
+# --- row ID, two-sided ID, CUR -------------------------------------------------
+
+def test_row_id_and_tsid():
+    A = f64(syn.spectrum_matrix(70, 110, syn.exp_decay(70), 51))
+    k = 20
+    ts = O.tsid(A, k=k)
+    C = A[:, ts.J[:k]]
+    W = O.wmat(ts.I, ts.TW, 70)
+    V = O.vstar(ts.J, ts.T, 110)
+    # C = W C(I, :) exactly up to rounding (Eq. (2.11), full-rank ID)
+    assert fro(C - W @ C[ts.I[:k]]) <= 1e-12 * fro(C)
+    # W(I[:k], :) is the identity
+    assert np.array_equal(W[ts.I[:k]], np.eye(k))
+    # the two-sided ID adds no error to the column ID (Section 2.4)
+    E1 = fro(A - C @ V)
+    E2 = fro(A - W @ A[np.ix_(ts.I[:k], ts.J[:k])] @ V)
+    assert abs(E1 - E2) <= 1e-12 * fro(A)
+    # row ID via the transpose: id_row(A) is id_col(A^T)
+    rr = O.id_row(A, k=k)
+    Rl, P = scipy.linalg.qr(A.T, mode="r", pivoting=True)
+    assert list(rr.J[:k]) == list(P[:k]) or min(rr.qr.gaps) < 1e-8
+
+
+def test_cur_middle_closed_form_and_bounds():
+    A = f64(syn.spectrum_matrix(90, 120, syn.exp_decay(90, 7.0), 61))
+    k = 18
+    res = O.cur(A, k=k)
+    V = O.vstar(res.J, res.T, 120)
+    # U = V* R^+ (Eq. (3.5)) against numpy's pinv (SVD based)
+    Up = V @ np.linalg.pinv(res.R)
+    np.testing.assert_allclose(res.U, Up, atol=1e-8 * np.abs(Up).max())
+    # Lemma 3.1, Lemma 3.2 and Corollary 3.3 in the spectral norm
+    E = A - res.C @ V
+    W = O.wmat(res.I, res.TW, 90)
+    Et = A - W @ res.R
+    nE, nEt = np.linalg.norm(E, 2), np.linalg.norm(Et, 2)
+    ncur = np.linalg.norm(A - res.C @ res.U @ res.R, 2)
+    assert ncur <= (nE + nEt) * (1 + 1e-10)
+    assert nEt <= (1 + np.linalg.norm(res.TW, 2)) * nE * (1 + 1e-10)
+    assert ncur <= (2 + np.linalg.norm(res.TW, 2)) * nE * (1 + 1e-10)
+    # Eq. (3.14): E~ = P [0; F E], with F = [-T_W^* I] P^* (Eq. (3.13))
+    Ires, Isk = res.I[k:], res.I[:k]
+    FE = E[Ires] - res.TW.T @ E[Isk]
+    np.testing.assert_allclose(Et[Ires], FE, atol=1e-11 * fro(A))
+    assert fro(Et[Isk]) <= 1e-12 * fro(A)
+    # F W = 0
+    FW = W[Ires] - res.TW.T @ W[Isk]
+    assert fro(FW) <= 1e-13
+
+
+# --- randomized front end ------------------------------------------------------
+
+def test_orth_rows_against_cholesky():
+    g = np.random.default_rng(71)
+    Y = g.standard_normal((12, 50)) * np.logspace(0, -3, 12)[:, None]
+    Q = O.orth_rows(Y)
+    np.testing.assert_allclose(Q @ Q.T, np.eye(12), atol=1e-13)
+    L = np.linalg.cholesky(Y @ Y.T)          # Y Y^T = L L^T, L with positive diagonal
+    np.testing.assert_allclose(Q, np.linalg.solve(L, Y), atol=1e-9)
+
+
+def _proj(M):
+    Qm, _ = np.linalg.qr(M.T)
+    return Qm @ Qm.T
+
+
+def test_sketch_power_spans_closed_form():
+    """The orthonormalised scheme (Section 5.3) spans the same row space as
+    Omega A (A^* A)^q evaluated directly (Eq. (5.3))."""
+    A = f64(syn.spectrum_matrix(60, 45, np.linspace(1, 0.3, 45), 81))
+    Om = f64(syn.gaussian(10, 60, 82))
+    for q in (0, 1, 2):
+        Y = O.sketch(A, Om, q=q, orth=True)
+        Yd = Om @ A @ np.linalg.matrix_power(A.T @ A, q)
+        assert fro(_proj(Y) - _proj(Yd)) <= 1e-10
+        Yn = O.sketch(A, Om, q=q, orth=False)
+        np.testing.assert_allclose(Yn, Yd, rtol=1e-10, atol=1e-12 * np.abs(Yd).max())
+
+
+def test_randomized_exact_rank():
+    A = f64(syn.exact_rank(200, 150, 12, 91))
+    Om = f64(syn.gaussian(17, 200, 92))
+    res, Y = O.randomized_cur(A, Om, k=12, q=1)
+    assert O.rel_err_fro(A, res.C, res.U, res.R) <= 1e-12
+
+
+def test_randomized_close_to_deterministic():
+    """With p = 10 and q = 1 the randomized CUR error is within a small
+    factor of the optimal rank-k error (Section 5)."""
+    A = f64(syn.spectrum_matrix(300, 200, syn.power_decay(200), 93))
+    Om = f64(syn.gaussian(30, 300, 94))
+    res, _ = O.randomized_cur(A, Om, k=20, q=1)
+    s = np.linalg.svd(A, compute_uv=False)
+    opt = np.sqrt(np.sum(s[20:] ** 2)) / np.sqrt(np.sum(s ** 2))
+    e = O.rel_err_fro(A, res.C, res.U, res.R)
+    assert opt <= e <= 10 * opt
+
+
+def test_exhaustive_best_subset():
+    """The greedy skeleton is never better than the best k-subset and is
+    within a small factor of it on a tiny input."""
+    g = np.random.default_rng(95)
+    A = g.standard_normal((7, 9)) @ np.diag(np.logspace(0, -2, 9))
+    k = 3
+    best = np.inf
+    for sub in itertools.combinations(range(9), k):
+        C = A[:, sub]
+        Qc, _ = np.linalg.qr(C)
+        best = min(best, fro(A - Qc @ (Qc.T @ A)))
+    r = O.id_col(A, k=k)
+    e = fro(A - A[:, r.J[:k]] @ O.vstar(r.J, r.T, 9))
+    assert best <= e * (1 + 1e-12)
+    assert e <= 3 * best
