@@ -45,9 +45,12 @@ def as_f64(A):
 
 def rank_threshold(shape, nu_first, eps=np.finfo(np.float64).eps):
     """Pivot norm at or below which the factorization is declared rank
-    deficient (the case of Section 2.3 where S11 is singular): a pivot norm
-    no larger than 10 * max(m, n) * eps times the first pivot norm."""
-    return 10.0 * max(shape) * eps * nu_first
+    deficient (the case of Section 2.3 where S11 is singular; the paper gives
+    no numerical threshold): 2 sqrt(l) eps times the first pivot norm, l the
+    column length.  After an exact rank-r part is removed, rounding leaves
+    residual columns of relative norm about sqrt(l) eps / 4 or less, while a
+    genuine trailing singular value above this level keeps its pivot."""
+    return 2.0 * np.sqrt(shape[0]) * eps * nu_first
 
 
 @dataclass
