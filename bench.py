@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput of randomized CUR-ID (Algorithms 3 + 4) on one GB300.
+
+Workload (seeded, synthetic, resident in HBM): dense float32 A of
+8000 x 6000 = U_a diag(sigma) V_a^T with sigma_j = j^-2 and Haar factors;
+rank k = 200, oversampling p = 10, one power step (q = 1); a fresh Gaussian
+Omega (210 x 8000) is drawn on the device every step from the step's seed.
+One step = Omega, the three products with A, two row orthonormalisations,
+CPQR of Y (210 x 6000), T, the gather of C, the full CPQR of C^T
+(200 x 8000), the gather of R and U = V* R^+ -- the whole decomposition.
+A (192 MB) is larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (the reference arm of this comparison).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "rank-k CUR/ID decompositions/sec at stated rel. error; % of HBM/TC roofline"
+UNIT = "decompositions/s"
+M, N, K, P, Q = 8000, 6000, 200, 10, 1
+BASE_SEED = 1413
+FP32_FMA_PER_SM_CLK = 128          # FP32 lanes per SM
+NUM_SMS = 152
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m", type=int, default=M)
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--k", type=int, default=K)
+    ap.add_argument("--p", type=int, default=P)
+    ap.add_argument("--q", type=int, default=Q)
+    ap.add_argument("--tf32", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, device):
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms during a region."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.remove(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def phase_work(args, l):
+    """Algorithmic flops / bytes per launch of the main phases (float32)."""
+    m, n, k = args.m, args.n, args.k
+    return {
+        # one product with A: 2 l m n flops, A read once (m n floats)
+        "sketch": {"flops": 2.0 * l * m * n, "bytes": 4.0 * (m * n + l * max(m, n) * 2)},
+        # CPQR of Y (l x n): Y read once, S (k x n) and J written
+        "cpqr_col": {"flops": 4.0 * l * n * k, "bytes": 4.0 * (l * n + k * n + n)},
+        # CPQR of C^T (k x m), full k steps
+        "cpqr_row": {"flops": 4.0 * k * m * k, "bytes": 4.0 * (2 * k * m + m)},
+    }
+
+
+def run_ours(args, ws, rank, local):
+    import paper_1412_8447_gb300 as curid
+    from paper_1412_8447_gb300.build import build
+    import synthetic as syn
+
+    if rank == 0:
+        build()
+    barrier(ws)
+    if ws > 1:
+        build()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    l = args.k + args.p
+    A = syn.spectrum_matrix(args.m, args.n, syn.power_decay(min(args.m, args.n)),
+                            BASE_SEED + rank, torch.float32, dev)
+    out = curid.cur_outputs(A, args.k)
+    tf32 = bool(args.tf32)
+
+    def step(i, Adev=A):
+        return curid.cur(Adev, args.k, p=args.p, q=args.q, seed=BASE_SEED * 1000 + i, tf32=tf32,
+                         out=out, check=False)
+
+    for i in range(args.warmup):
+        step(i)
+    st, kout = curid.last_status(local)
+    if st not in (0, 2):
+        raise RuntimeError(f"device status {curid.STATUS_NAMES[st]} in warm-up")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    curid.profile(True, local)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    elapsed_ms = e0.elapsed_time(e1)
+    phase_ms, phase_calls, launches = curid.profile_read(local)
+    curid.profile(False, local)
+    clk = clocks.stop()
+    st, kout = curid.last_status(local)
+    if st not in (0, 2):
+        raise RuntimeError(f"device status {curid.STATUS_NAMES[st]} in timed region")
+    elapsed_ms = max_over_ranks(elapsed_ms, ws, dev)
+    value = args.steps * ws / (elapsed_ms / 1e3)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        A_host = A.cpu().pin_memory()
+        A2 = torch.empty_like(A)
+        Jh = torch.empty(args.n, dtype=torch.int32).pin_memory()
+        Ih = torch.empty(args.m, dtype=torch.int32).pin_memory()
+        Uh = torch.empty((args.k, args.k), dtype=torch.float64).pin_memory()
+        ke = max(3, min(args.steps, 10))
+
+        def e2e_step(i):
+            A2.copy_(A_host, non_blocking=True)
+            step(i, A2)
+            Jh.copy_(out.J, non_blocking=True)
+            Ih.copy_(out.I, non_blocking=True)
+            Uh.copy_(out.U, non_blocking=True)
+
+        e2e_step(0)
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+        e0.record(stream)
+        for i in range(ke):
+            e2e_step(i + 1)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+        e2e = {"value": ke * ws / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": A.numel() * 4,
+               "d2h_bytes_per_step": (args.n + args.m) * 4 + args.k * args.k * 8}
+
+    pk, pk_kind = peaks()
+    work = phase_work(args, l)
+    per_step = {p: phase_ms[p] / args.steps for p in phase_ms}
+    total_phase = sum(phase_ms.values()) or 1.0
+    dominant = max(("sketch", "cpqr_col", "cpqr_row", "orth", "u_solve"),
+                   key=lambda p: phase_ms[p])
+    roof = None
+    if dominant in work and phase_calls[dominant]:
+        dur_s = phase_ms[dominant] / phase_calls[dominant] / 1e3
+        w = work[dominant]
+        if dominant == "sketch" and not tf32:
+            sm_mhz = pk.get("sm_max_mhz", 2070.0)
+            peak = NUM_SMS * FP32_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+            ach = w["flops"] / dur_s / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None, "kernel": "gemm_simt_kernel (FP32 FMA)",
+                    "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
+        elif dominant == "sketch":
+            peak = pk["bf16_tflops_sustained"] / 2
+            ach = w["flops"] / dur_s / 1e12
+            roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None, "kernel": "gemm_tf32 (tcgen05)",
+                    "peak_source": f"{pk_kind} bf16 sustained x 1/2 (TF32 nominal ratio)"}
+        else:
+            ach = w["bytes"] / dur_s / 1e9
+            peak = pk["hbm_gbs"]
+            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": None, "kernel": f"cpqr_kernel ({dominant})",
+                    "peak_source": f"{pk_kind} hbm_gbs"}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, A, curid)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "tf32+f32" if tf32 else "f32",
+        "data": "synthetic (seeded; sigma_j = j^-2, Haar factors; Omega drawn on device)",
+        "config": {"workload": f"randomized CUR-ID, float32 A {args.m}x{args.n}, k={args.k}, "
+                               f"p={args.p}, q={args.q}, Omega {l}x{args.m}",
+                   "m": args.m, "n": args.n, "k": args.k, "p": args.p, "q": args.q,
+                   "l2": "inputs larger than L2 (A is %.0f MB), no flush" % (A.numel() * 4 / 1e6),
+                   "parallelism": f"replicas x{ws}"},
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                   "reasons": clk["reasons"], "samples": clk["samples"]},
+        "e2e": e2e, "gpu_launches": launches,
+        "roofline": roof,
+        "phases_ms_per_step": {p: round(v, 4) for p, v in per_step.items()},
+        "phase_share": {p: round(phase_ms[p] / total_phase, 4) for p in phase_ms},
+        "cpu_baseline": cpu,
+        "status": curid.STATUS_NAMES[st], "k_out": kout,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def cpu_baseline(args, A, curid):
+    """The FP64 oracle on the host cores, one full decomposition of the same
+    workload with the Omega the device drew for seed BASE_SEED*1000."""
+    import oracle as O
+    l = args.k + args.p
+    Om = curid.gaussian(l, args.m, BASE_SEED * 1000, dtype=torch.float32,
+                        device=A.device.index).cpu().numpy()
+    Ah = A.cpu().numpy()
+    t = time.perf_counter()
+    O.randomized_cur(Ah, Om, args.k, q=args.q)
+    dt = time.perf_counter() - t
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one full randomized CUR-ID of the same {args.m}x{args.n} float32 A "
+                      f"(numpy float64, OpenBLAS threads = all {os.cpu_count()} cores), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, ws, rank, local):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import oracle as O
+    import synthetic as syn
+    from oracle.philox import gaussian as philox_gaussian
+    dev = "cuda:0" if torch.cuda.is_available() else "cpu"
+    A = syn.spectrum_matrix(args.m, args.n, syn.power_decay(min(args.m, args.n)), BASE_SEED,
+                            torch.float32, dev).cpu().numpy()
+    l = args.k + args.p
+    oms = {}
+
+    def step(i):
+        seed = BASE_SEED * 1000 + i
+        if seed not in oms:
+            oms[seed] = philox_gaussian(l, args.m, seed).astype(np.float32)
+        O.randomized_cur(A, oms[seed], args.k, q=args.q)
+
+    t0 = time.perf_counter()
+    step(0)                                   # one warm-up decomposition
+    t_one = time.perf_counter() - t0
+    k_steps = max(1, min(args.steps, int(120.0 / max(t_one, 1e-3))))
+    for i in range(k_steps):                  # Omega generation outside the timed region
+        seed = BASE_SEED * 1000 + 1 + i
+        oms[seed] = philox_gaussian(l, args.m, seed).astype(np.float32)
+    t0 = time.perf_counter()
+    for i in range(k_steps):
+        step(1 + i)
+    dt = time.perf_counter() - t0
+    value = k_steps / dt
+    sample = (f"{k_steps} full randomized CUR-ID decompositions of the {args.m}x{args.n} "
+              f"workload after 1 warm-up (numpy float64 oracle, {os.cpu_count()} cores)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": k_steps, "warmup": 1, "ms_per_step": dt / k_steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": f"randomized CUR-ID, float32 A {args.m}x{args.n}, k={args.k}, "
+                               f"p={args.p}, q={args.q}, Omega {l}x{args.m}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank, local)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

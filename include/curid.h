@@ -1,0 +1,204 @@
+/*
+ * curid.h -- C ABI of the GB300 (sm_103a) CUR / interpolative decomposition
+ * library.  Method: Voronin & Martinsson, "Efficient Algorithms for CUR and
+ * Interpolative Matrix Decompositions" (arXiv:1412.8447).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Matrices are dense, row-major, real (float64 or float32), with an
+ *    explicit leading dimension (elements between consecutive rows).  The
+ *    paper's A^* is the transpose.
+ *  - Every matrix / index pointer passed to a compute entry point is DEVICE
+ *    memory on the handle's device, owned by the caller; the library never
+ *    frees or keeps it after the call's work has finished on the stream.
+ *  - Indices are 0-based int32.  A pivot vector J of length n lists the k
+ *    skeleton columns in selection order, then the other n-k columns in
+ *    ascending index order.  Among exactly equal pivot norms the smallest
+ *    column index wins.
+ *  - T (k x (n-k), leading dimension ldt) holds the interpolation
+ *    coefficients; its column c belongs to original column J[k + c].
+ *  - Work is enqueued on the handle's stream and runs asynchronously.  A
+ *    compute call returns CURID_OK once its work is enqueued, or an error
+ *    found on the host (bad argument, workspace too small, launch failure).
+ *    Conditions found on the device (rank deficiency, non-finite input, a
+ *    timed-out inter-block wait, Cholesky breakdown) are recorded in the
+ *    handle's device status word and read with curid_last_status().
+ *  - The library allocates no device memory: scratch comes from the
+ *    workspace the caller attaches with curid_set_workspace(), sized by
+ *    curid_workspace_size().
+ *  - Errors are returned, never trapped; no kernel of this library faults
+ *    or spins without a bound.
+ */
+#ifndef CURID_H
+#define CURID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CURID_OK = 0,
+  CURID_INVALID_ARG = 1,     /* a size, pointer or leading dimension is invalid */
+  CURID_RANK_DEFICIENT = 2,  /* S11 numerically singular: k_out < k (Section 2.3) */
+  CURID_BREAKDOWN = 3,       /* row orthonormalisation failed (non-positive Gram pivot) */
+  CURID_NONFINITE = 4,       /* NaN or Inf found in the input */
+  CURID_TIMEOUT = 5,         /* an inter-block wait exceeded its bound */
+  CURID_CUDA_ERROR = 6,      /* a CUDA runtime call failed */
+  CURID_NO_WORKSPACE = 7,    /* attached workspace smaller than required */
+  CURID_UNSUPPORTED = 8      /* valid request outside what this build implements */
+} curid_status;
+
+typedef enum { CURID_F64 = 0, CURID_F32 = 1 } curid_dtype;
+
+/* Randomized front end (Section 5, Algorithm 4 and the power scheme of
+ * Section 5.3).
+ *   p < 0 : deterministic method, CPQR runs on A itself (Algorithms 1-3).
+ *   p >= 0: randomized method with l = k + p sample rows,
+ *           Y = Omega A (A^* A)^q, with row orthonormalisation between the
+ *           products (Section 5.3, steps 2a-2e).
+ *   omega : optional DEVICE matrix l x m (row-major, leading dimension m,
+ *           same dtype as A) used as Omega; when NULL the library draws
+ *           Omega from its Philox4x32-10 + Box-Muller generator with `seed`.
+ *   tf32  : for CURID_F32 only: 1 = the three kinds of sketch product run on
+ *           the tensor cores in TF32 with FP32 accumulation; 0 = FP32 FMA. */
+typedef struct {
+  int p;
+  int q;
+  uint64_t seed;
+  const void* omega;
+  int tf32;
+} curid_sketch;
+
+typedef struct curid_handle curid_handle;
+
+/* Handle: binds a device, a stream (default: the legacy default stream) and
+ * a caller-owned workspace.  create/destroy are not thread safe with respect
+ * to the same handle; one handle serves one stream at a time. */
+curid_status curid_create(curid_handle** handle, int device);
+curid_status curid_destroy(curid_handle* handle);
+/* stream: a cudaStream_t passed as void* (NULL = default stream). */
+curid_status curid_set_stream(curid_handle* handle, void* stream);
+/* ptr: device memory of `bytes` bytes, 256-byte aligned, owned by the
+ * caller and kept alive while work that uses it is in flight. */
+curid_status curid_set_workspace(curid_handle* handle, void* ptr, size_t bytes);
+
+/* Workspace bytes needed by curid_cur / curid_tsid / curid_id_col /
+ * curid_id_row for an m x n matrix of dtype `dtype` at rank k (fixed) or
+ * k_max (adaptive) with sketch parameters `sk`.  Host-only. */
+curid_status curid_workspace_size(curid_handle* handle, curid_dtype dtype,
+                                  int64_t m, int64_t n,
+                                  int k, curid_sketch sk, size_t* bytes);
+
+/* Synchronises the handle's stream and returns the status recorded on the
+ * device by the last compute call (CURID_OK, CURID_RANK_DEFICIENT,
+ * CURID_NONFINITE, CURID_TIMEOUT, CURID_BREAKDOWN), or CURID_CUDA_ERROR.
+ * *k_out (may be NULL) receives the rank actually produced. */
+curid_status curid_last_status(curid_handle* handle, int* k_out);
+
+/* ----- profiling -------------------------------------------------------
+ * With profiling enabled, every compute call records a CUDA event pair on
+ * the handle's stream around each phase below and counts the kernels it
+ * launches.  curid_profile_read() synchronises the stream, returns the
+ * summed milliseconds and the number of timed intervals per phase (arrays
+ * of CURID_NUM_PHASES entries, either may be NULL) and the launch count
+ * since the last read, then resets them.  Events come from a pool owned by
+ * the handle (no device memory is allocated). */
+enum {
+  CURID_PHASE_OMEGA = 0,     /* Gaussian Omega (Algorithm 4 line 1) */
+  CURID_PHASE_SKETCH = 1,    /* products with A: Omega A, Q A^T, Q A (Section 5.3) */
+  CURID_PHASE_ORTH = 2,      /* row orthonormalisation between power steps */
+  CURID_PHASE_CPQR_COL = 3,  /* truncated CPQR of Y (or A) */
+  CURID_PHASE_T = 4,         /* T = S11^{-1} S12 */
+  CURID_PHASE_GATHER = 5,    /* C = A(:, J), R = A(I, :) */
+  CURID_PHASE_CPQR_ROW = 6,  /* full-rank CPQR of C^T (row ID of C) */
+  CURID_PHASE_U = 7,         /* T_W and U = V* R^+ */
+  CURID_NUM_PHASES = 8
+};
+curid_status curid_profile(curid_handle* handle, int enable);
+curid_status curid_profile_read(curid_handle* handle, double* ms, int* calls,
+                                long long* launches);
+
+/* ----- building blocks ----------------------------------------------- */
+
+/* i.i.d. N(0,1) matrix (Algorithm 4, line 1): rows x cols, row-major,
+ * leading dimension cols, dtype `dtype`, written to device `out`.
+ * Element e = r*cols + c comes from Philox4x32-10 (Salmon et al., SC'11)
+ * with key (seed low 32 bits, seed high 32 bits) and counter
+ * (e/4, 0, 0, 0), word e%4, mapped to (0,1] and paired by Box-Muller. */
+curid_status curid_gaussian(curid_handle* handle, curid_dtype dtype,
+                            int64_t rows, int64_t cols, uint64_t seed,
+                            void* out);
+
+/* Sample matrix Y = Omega A (A^* A)^q (Eq. (5.1); Section 5.3 with orth):
+ * A m x n (lda), omega l x m (leading dimension m, device, required),
+ * Y l x n written with leading dimension n. */
+curid_status curid_sketch_matrix(curid_handle* handle, curid_dtype dtype,
+                                 const void* A, int64_t m, int64_t n,
+                                 int64_t lda, int l, int q, int tf32,
+                                 const void* omega, void* Y);
+
+/* Truncated column-pivoted QR (Section 2.2, Eq. (2.4)-(2.5)) of Y (l x n,
+ * leading dimension ldy): k > 0 steps, or (k == 0, tol > 0) until the
+ * residual ||Y(:,J) - Q1 S1||_F <= tol ||Y||_F.
+ * Outputs: J (n), S (k_max x n, leading dimension n, row i = S1(i, :) with
+ * columns in ORIGINAL column order, i.e. S[i*n + J[t]] = S1(i, t)).  Only
+ * the first k_out rows of S are written. */
+curid_status curid_cpqr(curid_handle* handle, curid_dtype dtype,
+                        const void* Y, int64_t l, int64_t n, int64_t ldy,
+                        int k, double tol, int32_t* J, void* S);
+
+/* ----- the decompositions -------------------------------------------- */
+
+/* Rank selection of the decompositions below: k > 0 is a fixed rank
+ * (1 <= k <= min(m, n); randomized: k + p <= min(m, n)).  The adaptive
+ * rank (k == 0, tol > 0) is available through curid_cpqr only; the
+ * decompositions return CURID_UNSUPPORTED for it. */
+
+/* Column ID (Algorithm 1; randomized: Algorithm 4):
+ * A ~ A(:, J[:k]) [I T] P^*.  A m x n (lda).  Outputs J (n) and
+ * T (k x (n-k), leading dimension ldt >= n-k; rows at and after k_out are
+ * zero when rank deficient). */
+curid_status curid_id_col(curid_handle* handle, curid_dtype dtype,
+                          const void* A, int64_t m, int64_t n, int64_t lda,
+                          int k, double tol, curid_sketch sk, int32_t* J,
+                          void* T, int64_t ldt);
+
+/* Row ID (Remark 2.1): A ~ W A(I[:k], :), W = P [I; T_W^*], computed as
+ * the column ID of A^*.  Outputs I (m), TW (k x (m-k), leading dimension
+ * ldtw). */
+curid_status curid_id_row(curid_handle* handle, curid_dtype dtype,
+                          const void* A, int64_t m, int64_t n, int64_t lda,
+                          int k, double tol, curid_sketch sk, int32_t* I,
+                          void* TW, int64_t ldtw);
+
+/* Two-sided ID (Algorithm 2, Eq. (2.12)): column ID of A (or of its sketch),
+ * then the full rank-k ID of C^* (Eq. (2.11)).  Outputs J, T, I, TW as in
+ * curid_id_col / curid_id_row. */
+curid_status curid_tsid(curid_handle* handle, curid_dtype dtype,
+                        const void* A, int64_t m, int64_t n, int64_t lda,
+                        int k, double tol, curid_sketch sk, int32_t* J,
+                        void* T, int64_t ldt, int32_t* I, void* TW,
+                        int64_t ldtw);
+
+/* CUR-ID (Algorithm 3): C = A(:, J[:k]), R = A(I[:k], :), U = V* R^+
+ * (Eq. (3.1), (3.5)).  Outputs J (n), I (m) and U (k x k, leading
+ * dimension k, ALWAYS float64: U carries the conditioning of the skeleton,
+ * its entries reach 1/sigma_k, and rounding U alone to float32 moves
+ * ||A - CUR||_F / ||A||_F by about 1e-5 on the 8000 x 6000, k = 200
+ * workload); optional (NULL = not written): C (m x k, leading dimension k),
+ * R (k x n, leading dimension n), T (k x (n-k), ldt), TW (k x (m-k), ldtw),
+ * in the dtype of A. */
+curid_status curid_cur(curid_handle* handle, curid_dtype dtype,
+                       const void* A, int64_t m, int64_t n, int64_t lda,
+                       int k, double tol, curid_sketch sk, int32_t* J,
+                       int32_t* I, double* U, void* C, void* R, void* T,
+                       int64_t ldt, void* TW, int64_t ldtw);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CURID_H */

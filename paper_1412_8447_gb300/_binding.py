@@ -1,0 +1,321 @@
+"""ctypes binding of libcurid.so: argument marshalling only.
+
+Every function here takes torch tensors that live on a CUDA device, passes
+their device pointers and the current torch stream to the C ABI declared in
+``include/curid.h``, and returns torch tensors the C library wrote.  No step
+of the decomposition runs in Python.  The library allocates nothing itself:
+the workspace is a torch uint8 tensor owned by the per-device handle here.
+"""
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcurid.so")
+
+OK, INVALID_ARG, RANK_DEFICIENT, BREAKDOWN, NONFINITE, TIMEOUT, CUDA_ERROR, NO_WORKSPACE, \
+    UNSUPPORTED = range(9)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "RANK_DEFICIENT", 3: "BREAKDOWN",
+                4: "NONFINITE", 5: "TIMEOUT", 6: "CUDA_ERROR", 7: "NO_WORKSPACE",
+                8: "UNSUPPORTED"}
+F64, F32 = 0, 1
+
+
+class CuridError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: curid status {STATUS_NAMES.get(status, status)}")
+
+
+class Sketch(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("q", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("omega", ctypes.c_void_p), ("tf32", ctypes.c_int)]
+
+
+_vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+SIGNATURES = {
+    "curid_create": [ctypes.POINTER(_vp), _int],
+    "curid_destroy": [_vp],
+    "curid_set_stream": [_vp, _vp],
+    "curid_set_workspace": [_vp, _vp, ctypes.c_size_t],
+    "curid_workspace_size": [_vp, _int, _i64, _i64, _int, Sketch, ctypes.POINTER(ctypes.c_size_t)],
+    "curid_last_status": [_vp, ctypes.POINTER(_int)],
+    "curid_profile": [_vp, _int],
+    "curid_profile_read": [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_int),
+                           ctypes.POINTER(ctypes.c_longlong)],
+    "curid_gaussian": [_vp, _int, _i64, _i64, ctypes.c_uint64, _vp],
+    "curid_sketch_matrix": [_vp, _int, _vp, _i64, _i64, _i64, _int, _int, _int, _vp, _vp],
+    "curid_cpqr": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, _vp, _vp],
+    "curid_id_col": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _i64],
+    "curid_id_row": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _i64],
+    "curid_tsid": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _i64, _vp,
+                   _vp, _i64],
+    "curid_cur": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _vp, _vp, _vp,
+                  _vp, _i64, _vp, _i64],
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library():
+    """Load libcurid.so (raises if it has not been built: there is no
+    fallback implementation)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing; build it with "
+                                  "`python -m paper_1412_8447_gb300.build`")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, args in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _dtype_code(t):
+    if t == torch.float64:
+        return F64
+    if t == torch.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {t}; use float32 or float64")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _check(st, where):
+    if st != OK:
+        raise CuridError(st, where)
+
+
+class _Handle:
+    """One library handle per CUDA device, with a growable workspace."""
+
+    def __init__(self, device):
+        self.lib = load_library()
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(self.lib.curid_create(ctypes.byref(h), device), "curid_create")
+        self.h = h
+        self.ws = None
+
+    def prepare(self, nbytes):
+        if self.ws is None or self.ws.numel() < nbytes:
+            self.ws = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8,
+                                  device=f"cuda:{self.device}")
+            _check(self.lib.curid_set_workspace(self.h, _ptr(self.ws), self.ws.numel()),
+                   "curid_set_workspace")
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        _check(self.lib.curid_set_stream(self.h, ctypes.c_void_p(stream)), "curid_set_stream")
+
+    def status(self):
+        k = ctypes.c_int(0)
+        st = self.lib.curid_last_status(self.h, ctypes.byref(k))
+        return st, k.value
+
+
+_handles = {}
+
+
+def handle(device):
+    if device not in _handles:
+        _handles[device] = _Handle(device)
+    return _handles[device]
+
+
+def _dev(t):
+    if not t.is_cuda:
+        raise ValueError("tensors must be on a CUDA device")
+    return t.device.index if t.device.index is not None else torch.cuda.current_device()
+
+
+def _mat(A):
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("expected a 2-D row-major tensor (stride(1) == 1)")
+    return A
+
+
+def _sketch(p, q, seed, omega, tf32):
+    return Sketch(int(p), int(q), int(seed) & ((1 << 64) - 1),
+                  ctypes.c_void_p(omega.data_ptr()) if omega is not None else None,
+                  1 if tf32 else 0)
+
+
+def workspace_bytes(h, dt, m, n, k, sk):
+    b = ctypes.c_size_t(0)
+    _check(h.lib.curid_workspace_size(h.h, dt, m, n, k, sk, ctypes.byref(b)),
+           "curid_workspace_size")
+    return b.value
+
+
+class Result:
+    """Outputs of one call; ``status`` is the device status (0 = OK,
+    2 = RANK_DEFICIENT) and ``k`` the rank produced, both filled when the
+    call ran with ``check=True``."""
+
+    def __init__(self, **kw):
+        self.status = None
+        self.k = None
+        self.__dict__.update(kw)
+
+    def __repr__(self):
+        keys = ", ".join(k for k in self.__dict__)
+        return f"Result({keys})"
+
+
+def _finish(h, res, check, where):
+    if check:
+        st, k = h.status()
+        if st not in (OK, RANK_DEFICIENT):
+            raise CuridError(st, where)
+        res.status, res.k = st, k
+    return res
+
+
+PHASES = ["omega", "sketch", "orth", "cpqr_col", "t_solve", "gather", "cpqr_row", "u_solve"]
+
+
+def profile(enable=True, device=0):
+    """Turn per-phase CUDA-event timing and launch counting on or off."""
+    h = handle(device)
+    _check(h.lib.curid_profile(h.h, 1 if enable else 0), "curid_profile")
+
+
+def profile_read(device=0):
+    """({phase: ms}, {phase: intervals}, launches) since the last read."""
+    h = handle(device)
+    n = len(PHASES)
+    ms = (ctypes.c_double * n)()
+    calls = (ctypes.c_int * n)()
+    launches = ctypes.c_longlong(0)
+    _check(h.lib.curid_profile_read(h.h, ms, calls, ctypes.byref(launches)), "curid_profile_read")
+    return ({p: ms[i] for i, p in enumerate(PHASES)},
+            {p: calls[i] for i, p in enumerate(PHASES)}, launches.value)
+
+
+def last_status(device=0):
+    """(status, k) recorded by the last call on ``device`` (synchronises)."""
+    return handle(device).status()
+
+
+def gaussian(rows, cols, seed, dtype=torch.float32, device=None):
+    """N(0, 1) rows x cols matrix from the library's Philox4x32-10 generator."""
+    device = torch.cuda.current_device() if device is None else device
+    h = handle(device)
+    h.prepare(0)
+    out = torch.empty((rows, cols), dtype=dtype, device=f"cuda:{device}")
+    _check(h.lib.curid_gaussian(h.h, _dtype_code(dtype), rows, cols, int(seed) & ((1 << 64) - 1),
+                                _ptr(out)), "curid_gaussian")
+    return out
+
+
+def sketch_matrix(A, omega, q=0, tf32=False):
+    """Y = Omega A (A^T A)^q with row orthonormalisation between products."""
+    A = _mat(A)
+    dev = _dev(A)
+    h = handle(dev)
+    m, n = A.shape
+    l = omega.shape[0]
+    dt = _dtype_code(A.dtype)
+    h.prepare(workspace_bytes(h, dt, m, n, max(1, min(l, m, n)),
+                              _sketch(max(0, l - 1), q, 0, omega, tf32)))
+    Y = torch.empty((l, n), dtype=A.dtype, device=A.device)
+    _check(h.lib.curid_sketch_matrix(h.h, dt, _ptr(A), m, n, A.stride(0), l, q,
+                                     1 if tf32 else 0, _ptr(omega.contiguous()), _ptr(Y)),
+           "curid_sketch_matrix")
+    return Y
+
+
+def cpqr(Y, k=0, tol=0.0, check=True):
+    """Truncated column-pivoted QR of Y: J (int32, n) and S (k_max x n,
+    original column order)."""
+    Y = _mat(Y)
+    dev = _dev(Y)
+    h = handle(dev)
+    l, n = Y.shape
+    k_max = k if k > 0 else min(l, n)
+    dt = _dtype_code(Y.dtype)
+    h.prepare(workspace_bytes(h, dt, max(l, 1), n, min(k_max, l, n), _sketch(-1, 0, 0, None, 0))
+              if l >= 1 else 1 << 20)
+    J = torch.empty(n, dtype=torch.int32, device=Y.device)
+    S = torch.zeros((k_max, n), dtype=Y.dtype, device=Y.device)
+    _check(h.lib.curid_cpqr(h.h, dt, _ptr(Y), l, n, Y.stride(0), k, float(tol), _ptr(J), _ptr(S)),
+           "curid_cpqr")
+    return _finish(h, Result(J=J, S=S), check, "curid_cpqr")
+
+
+def _prep(A, k, p, q, seed, omega, tf32):
+    A = _mat(A)
+    dev = _dev(A)
+    h = handle(dev)
+    m, n = A.shape
+    dt = _dtype_code(A.dtype)
+    sk = _sketch(p, q, seed, omega, tf32)
+    h.prepare(workspace_bytes(h, dt, m, n, k, sk))
+    return A, h, m, n, dt, sk
+
+
+def id_col(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, check=True):
+    """Column ID A ~ A(:, J[:k]) [I T] P^T (Algorithm 1; p >= 0: Algorithm 4)."""
+    A, h, m, n, dt, sk = _prep(A, k, p, q, seed, omega, tf32)
+    J = torch.empty(n, dtype=torch.int32, device=A.device)
+    T = torch.empty((k, max(n - k, 1)), dtype=A.dtype, device=A.device)
+    _check(h.lib.curid_id_col(h.h, dt, _ptr(A), m, n, A.stride(0), k, 0.0, sk, _ptr(J), _ptr(T),
+                              T.stride(0)), "curid_id_col")
+    return _finish(h, Result(J=J, T=T[:, :n - k]), check, "curid_id_col")
+
+
+def id_row(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, check=True):
+    """Row ID A ~ W A(I[:k], :) (the column ID of A^T)."""
+    A, h, m, n, dt, sk = _prep(A, k, p, q, seed, omega, tf32)
+    I = torch.empty(m, dtype=torch.int32, device=A.device)
+    TW = torch.empty((k, max(m - k, 1)), dtype=A.dtype, device=A.device)
+    _check(h.lib.curid_id_row(h.h, dt, _ptr(A), m, n, A.stride(0), k, 0.0, sk, _ptr(I),
+                              _ptr(TW), TW.stride(0)), "curid_id_row")
+    return _finish(h, Result(I=I, TW=TW[:, :m - k]), check, "curid_id_row")
+
+
+def tsid(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, check=True):
+    """Two-sided ID A ~ W A(I[:k], J[:k]) V* (Algorithm 2)."""
+    A, h, m, n, dt, sk = _prep(A, k, p, q, seed, omega, tf32)
+    J = torch.empty(n, dtype=torch.int32, device=A.device)
+    I = torch.empty(m, dtype=torch.int32, device=A.device)
+    T = torch.empty((k, max(n - k, 1)), dtype=A.dtype, device=A.device)
+    TW = torch.empty((k, max(m - k, 1)), dtype=A.dtype, device=A.device)
+    _check(h.lib.curid_tsid(h.h, dt, _ptr(A), m, n, A.stride(0), k, 0.0, sk, _ptr(J), _ptr(T),
+                            T.stride(0), _ptr(I), _ptr(TW), TW.stride(0)), "curid_tsid")
+    return _finish(h, Result(J=J, T=T[:, :n - k], I=I, TW=TW[:, :m - k]), check, "curid_tsid")
+
+
+def cur_outputs(A, k, want_c=False, want_r=False, want_t=False, want_tw=False):
+    """Preallocated output tensors for ``cur(..., out=...)``."""
+    m, n = A.shape
+    dev = A.device
+    return Result(
+        J=torch.empty(n, dtype=torch.int32, device=dev),
+        I=torch.empty(m, dtype=torch.int32, device=dev),
+        U=torch.empty((k, k), dtype=torch.float64, device=dev),
+        C=torch.empty((m, k), dtype=A.dtype, device=dev) if want_c else None,
+        R=torch.empty((k, n), dtype=A.dtype, device=dev) if want_r else None,
+        T=torch.empty((k, max(n - k, 1)), dtype=A.dtype, device=dev) if want_t else None,
+        TW=torch.empty((k, max(m - k, 1)), dtype=A.dtype, device=dev) if want_tw else None)
+
+
+def cur(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, want_c=False, want_r=False,
+        want_t=False, want_tw=False, out=None, check=True):
+    """CUR-ID A ~ C U R (Algorithm 3); U is float64 (k x k)."""
+    A, h, m, n, dt, sk = _prep(A, k, p, q, seed, omega, tf32)
+    o = out if out is not None else cur_outputs(A, k, want_c, want_r, want_t, want_tw)
+    st = h.lib.curid_cur(h.h, dt, _ptr(A), m, n, A.stride(0), k, 0.0, sk, _ptr(o.J), _ptr(o.I),
+                         _ptr(o.U), _ptr(o.C), _ptr(o.R), _ptr(o.T),
+                         o.T.stride(0) if o.T is not None else 0, _ptr(o.TW),
+                         o.TW.stride(0) if o.TW is not None else 0)
+    _check(st, "curid_cur")
+    return _finish(h, o, check, "curid_cur")

@@ -1,0 +1,433 @@
+// Truncated column-pivoted Householder QR (Section 2.2, Eq. (2.4)-(2.5); the
+// first line of Algorithms 1 and 4; the full-rank ID of C^* in Algorithm 2).
+//
+// GB300 design: one persistent CTA per SM (cooperative launch, so all CTAs
+// are co-resident).  CTA b owns a contiguous slab of columns, held in shared
+// memory for the whole factorization, column-major with an odd stride so a
+// warp walking down a column is bank-conflict free.  A step j is:
+//   1. every CTA reads the G candidate records of step j (one per CTA: its
+//      largest residual column norm, that column's index, the sum of its
+//      squared residual norms) and picks the global pivot (largest norm,
+//      smallest index on ties) -- the records double as the grid barrier;
+//   2. every CTA reads the pivot column (rows j..l-1) that its owner
+//      published and forms the same Householder reflector
+//      H = I - tau v v^T (v(j) = 1), mapping it to beta e_j;
+//   3. each warp applies H to one of the CTA's unselected columns and
+//      recomputes that column's residual norm from rows j+1..l-1 (no norm
+//      downdating, hence no cancellation to guard against);
+//   4. the CTA publishes its new local candidate for step j+1.
+// One grid-wide exchange per pivot step; no host round trip until the end.
+// After the last step row i of S holds S1(i, c) for every original column c,
+// J lists the pivots and then the unselected columns in ascending order.
+#include "kernels.cuh"
+
+namespace curid {
+
+namespace {
+
+template <typename real>
+struct Slot {
+  unsigned long long tag;  // (epoch << 32) | column (0xffffffff: no candidate)
+  real norm;
+  real sumsq;
+  int nonfinite;
+  int count;
+};
+
+template <typename real>
+struct CpqrParams {
+  const real* Y;
+  int64_t ldy;
+  int l, n, k_max, nc, ldl;
+  real tol;
+  real rank_rtol;
+  int32_t* J;
+  real* S;
+  int64_t lds;
+  Slot<real>* slots;
+  real* slot_data;
+  int* abort_flag;
+  StatusBlock* status;
+  int which;
+};
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr unsigned kNoCol = 0xffffffffu;
+
+template <typename real>
+__device__ __forceinline__ bool better(real na, unsigned ca, real nb, unsigned cb) {
+  // (na, ca) beats (nb, cb): larger norm, then smaller column; kNoCol loses.
+  if (ca == kNoCol) return false;
+  if (cb == kNoCol) return true;
+  if (na > nb) return true;
+  if (na < nb) return false;
+  return ca < cb;
+}
+
+// Poll the G records of buffer `bf` until all carry `epoch` (warp 0 only).
+// Returns false on timeout or abort.
+template <typename real>
+__device__ bool wait_epoch(const CpqrParams<real>& P, int bf, unsigned epoch) {
+  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x;
+  bool ok = true;
+  const long long t0 = clock64();
+  for (int s = lane; s < G && ok; s += 32) {
+    const unsigned long long* tp = &P.slots[bf * G + s].tag;
+    while (true) {
+      const unsigned long long t = ld_volatile_u64(tp);
+      if ((unsigned)(t >> 32) == epoch) break;
+      if (ld_volatile_i32(P.abort_flag)) { ok = false; break; }
+      if (clock64() - t0 > kSpinBudget) {
+        atomicExch(P.abort_flag, 1);
+        ok = false;
+        break;
+      }
+    }
+  }
+  ok = __all_sync(0xffffffffu, ok);
+  __threadfence();
+  return ok;
+}
+
+template <typename real>
+__device__ void publish(const CpqrParams<real>& P, const real* ys, const real* nrm,
+                        const int* active, int ncl, int c0, int r0, int bf, unsigned epoch,
+                        int* s_best, real* s_red, int* s_redi, int count) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = gridDim.x;
+  // local argmax over active columns; tie -> smallest index
+  real bn = real(-1);
+  int bi = -1;
+  real ss = real(0);
+  int nf = 0;
+  for (int lc = tid; lc < ncl; lc += kThreads) {
+    if (!active[lc]) continue;
+    const real v = nrm[lc];
+    if (!isfinite(v)) nf = 1;
+    ss += v * v;
+    if (bi < 0 || v > bn) { bn = v; bi = lc; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const real on = __shfl_xor_sync(0xffffffffu, bn, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (oi >= 0 && (bi < 0 || on > bn || (on == bn && oi < bi))) { bn = on; bi = oi; }
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    nf |= __shfl_xor_sync(0xffffffffu, nf, o);
+  }
+  if (lane == 0) {
+    s_red[warp] = bn;
+    s_red[kWarps + warp] = ss;
+    s_redi[warp] = bi;
+    s_redi[kWarps + warp] = nf;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    real b = real(-1), s = real(0);
+    int i = -1, f = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      const int wi = s_redi[w];
+      if (wi >= 0 && (i < 0 || s_red[w] > b || (s_red[w] == b && wi < i))) { b = s_red[w]; i = wi; }
+      s += s_red[kWarps + w];
+      f |= s_redi[kWarps + w];
+    }
+    s_best[0] = i;
+    s_red[0] = b;
+    s_red[1] = s;
+    s_redi[0] = f;
+  }
+  __syncthreads();
+  const int best = s_best[0];
+  if (best >= 0) {
+    real* dst = P.slot_data + ((int64_t)bf * G + blockIdx.x) * P.l;
+    const real* src = ys + (int64_t)best * P.ldl;
+    for (int r = r0 + tid; r < P.l; r += kThreads) dst[r] = src[r];
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    Slot<real>* sl = &P.slots[bf * G + blockIdx.x];
+    sl->norm = best >= 0 ? s_red[0] : real(0);
+    sl->sumsq = s_red[1];
+    sl->nonfinite = s_redi[0];
+    sl->count = count;
+    __threadfence();
+    const unsigned col = best >= 0 ? (unsigned)(c0 + best) : kNoCol;
+    st_volatile_u64(&sl->tag, ((unsigned long long)epoch << 32) | col);
+  }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int nc = P.nc, ldl = P.ldl, l = P.l;
+  real* ys = reinterpret_cast<real*>(smem_raw);
+  real* v = ys + (int64_t)nc * ldl;
+  real* nrm = v + ldl;
+  int* active = reinterpret_cast<int*>(nrm + nc);
+
+  __shared__ int s_best[2];
+  __shared__ real s_red[2 * kWarps];
+  __shared__ int s_redi[2 * kWarps];
+  __shared__ int s_stop, s_owner, s_col, s_prefix;
+  __shared__ real s_nu, s_total;
+
+  const int c0 = b * nc;
+  const int ncl = max(0, min(nc, P.n - c0));
+
+  // load the slab
+  for (int64_t e = tid; e < (int64_t)l * ncl; e += kThreads) {
+    const int r = (int)(e / ncl), lc = (int)(e % ncl);
+    ys[(int64_t)lc * ldl + r] = P.Y[(int64_t)r * P.ldy + c0 + lc];
+  }
+  for (int lc = tid; lc < nc; lc += kThreads) active[lc] = lc < ncl ? 1 : 0;
+  __syncthreads();
+  for (int lc = warp; lc < ncl; lc += kWarps) {
+    const real* y = ys + (int64_t)lc * ldl;
+    real s2 = real(0);
+    for (int r = lane; r < l; r += 32) s2 += y[r] * y[r];
+    s2 = warp_sum(s2);
+    if (lane == 0) nrm[lc] = sqrt(s2);
+  }
+  __syncthreads();
+  publish(P, ys, nrm, active, ncl, c0, 0, 0, 1u, s_best, s_red, s_redi, 0);
+
+  real normY = real(-1), nu_first = real(0);
+  int k_eff = -1;
+  int j = 0;
+  for (;; ++j) {
+    const int bf = j & 1;
+    if (warp == 0) {
+      const bool ok = wait_epoch(P, bf, (unsigned)(j + 1));
+      // global pivot and totals, identical in every CTA
+      real bn = real(-1), tot = real(0);
+      unsigned bc = kNoCol;
+      int bo = -1, nf = 0;
+      if (ok) {
+        for (int s = lane; s < G; s += 32) {
+          const Slot<real>* sl = &P.slots[bf * G + s];
+          const unsigned col = (unsigned)(ld_volatile_u64(&sl->tag) & 0xffffffffull);
+          const real nn = *reinterpret_cast<const volatile real*>(&sl->norm);
+          tot += *reinterpret_cast<const volatile real*>(&sl->sumsq);
+          nf |= *reinterpret_cast<const volatile int*>(&sl->nonfinite);
+          if (better(nn, col, bn, bc)) { bn = nn; bc = col; bo = s; }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const real on = __shfl_xor_sync(0xffffffffu, bn, o);
+        const unsigned oc = __shfl_xor_sync(0xffffffffu, bc, o);
+        const int oo = __shfl_xor_sync(0xffffffffu, bo, o);
+        if (better(on, oc, bn, bc)) { bn = on; bc = oc; bo = oo; }
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        nf |= __shfl_xor_sync(0xffffffffu, nf, o);
+      }
+      if (lane == 0) {
+        int stop = 0;
+        if (!ok) {
+          stop = 2;
+          set_flag(&P.status->flags, FLAG_TIMEOUT);
+        } else if (nf) {
+          stop = 1;
+          if (b == 0) set_flag(&P.status->flags, FLAG_NONFINITE);
+        } else if (j >= P.k_max || bc == kNoCol) {
+          stop = 1;
+        } else {
+          if (normY < real(0)) normY = sqrt(tot);
+          if (P.tol > real(0) && sqrt(tot) <= P.tol * normY) stop = 1;
+        }
+        s_stop = stop;
+        s_owner = bo;
+        s_col = (int)bc;
+        s_nu = bn;
+        s_total = tot;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int owner = s_owner, pcol = s_col;
+    const real nu = s_nu;
+    if (j == 0) nu_first = nu;
+    if (k_eff < 0 && (nu == real(0) || nu <= P.rank_rtol * nu_first)) {
+      k_eff = j;
+      if (b == 0 && tid == 0) set_flag(&P.status->flags, FLAG_RANK_DEFICIENT);
+    }
+    // pivot column rows j..l-1 from its owner
+    const real* src = P.slot_data + ((int64_t)bf * G + owner) * l;
+    for (int r = j + tid; r < l; r += kThreads) v[r] = __ldcg(src + r);
+    __syncthreads();
+    const real alpha = v[j];
+    const real beta = alpha >= real(0) ? -nu : nu;
+    real tau = real(0), scale = real(0);
+    if (nu > real(0)) {
+      tau = (beta - alpha) / beta;
+      scale = real(1) / (alpha - beta);
+    }
+    __syncthreads();
+    for (int r = j + 1 + tid; r < l; r += kThreads) v[r] *= scale;
+    if (tid == 0) v[j] = real(1);
+    if (b == owner) {
+      const int lc = pcol - c0;
+      real* y = ys + (int64_t)lc * ldl;
+      for (int r = j + tid; r < l; r += kThreads) y[r] = r == j ? beta : real(0);
+      if (tid == 0) {
+        active[lc] = 0;
+        P.J[j] = pcol;
+      }
+    }
+    __syncthreads();
+    // apply H to every unselected local column, recompute its residual norm
+    for (int lc = warp; lc < ncl; lc += kWarps) {
+      if (!active[lc]) continue;
+      real* y = ys + (int64_t)lc * ldl;
+      real d = real(0);
+      for (int r = j + lane; r < l; r += 32) d += v[r] * y[r];
+      d = warp_sum(d);
+      const real w = tau * d;
+      real s2 = real(0);
+      for (int r = j + lane; r < l; r += 32) {
+        const real yr = y[r] - w * v[r];
+        y[r] = yr;
+        if (r > j) s2 += yr * yr;
+      }
+      s2 = warp_sum(s2);
+      if (lane == 0) nrm[lc] = sqrt(s2);
+    }
+    __syncthreads();
+    publish(P, ys, nrm, active, ncl, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2), s_best, s_red,
+            s_redi, 0);
+  }
+  const int k_done = j;
+  if (s_stop == 2) return;  // timed out: leave without further waits
+  // S rows 0..k_done-1 in original column order
+  for (int64_t e = tid; e < (int64_t)k_done * ncl; e += kThreads) {
+    const int i = (int)(e / ncl), lc = (int)(e % ncl);
+    P.S[(int64_t)i * P.lds + c0 + lc] = ys[(int64_t)lc * ldl + i];
+  }
+  // unselected columns in ascending order after the pivots: exchange counts
+  int cnt = 0;
+  if (tid == 0)
+    for (int lc = 0; lc < ncl; ++lc) cnt += active[lc];
+  const int fbf = (j + 1) & 1;
+  if (tid == 0) {
+    Slot<real>* sl = &P.slots[fbf * G + b];
+    sl->count = cnt;
+    __threadfence();
+    st_volatile_u64(&sl->tag, ((unsigned long long)(j + 2) << 32) | kNoCol);
+  }
+  if (warp == 0) {
+    const bool ok = wait_epoch(P, fbf, (unsigned)(j + 2));
+    int pre = 0;
+    if (ok)
+      for (int s = lane; s < b; s += 32)
+        pre += *reinterpret_cast<const volatile int*>(&P.slots[fbf * G + s].count);
+    pre = warp_sum(pre);
+    if (lane == 0) {
+      s_prefix = pre;
+      s_stop = ok ? 0 : 1;
+      if (!ok) set_flag(&P.status->flags, FLAG_TIMEOUT);
+    }
+  }
+  __syncthreads();
+  if (s_stop) return;
+  if (tid == 0) {
+    int pos = k_done + s_prefix;
+    for (int lc = 0; lc < ncl; ++lc)
+      if (active[lc]) P.J[pos++] = c0 + lc;
+    if (b == 0) {
+      if (P.which == 0) {
+        P.status->k_done = k_done;
+        P.status->k_eff = k_eff < 0 ? k_done : k_eff;
+      } else {
+        P.status->k_row = k_eff < 0 ? k_done : k_eff;
+      }
+    }
+  }
+}
+
+template <typename real>
+size_t cpqr_smem_bytes(int nc, int ldl) {
+  return (size_t)nc * ldl * sizeof(real) + (size_t)ldl * sizeof(real) + (size_t)nc * sizeof(real) +
+         (size_t)nc * sizeof(int) + 64;
+}
+
+}  // namespace
+
+template <typename real>
+curid_status cpqr_plan(const Ctx& ctx, int64_t l, int64_t n, int* grid, size_t* smem) {
+  if (l <= 0 || n <= 0) return CURID_INVALID_ARG;
+  int G = (int)std::min<int64_t>(ctx.num_sms, n);
+  const int nc = (int)((n + G - 1) / G);
+  G = (int)((n + nc - 1) / nc);
+  const int ldl = (int)(l | 1);
+  const size_t bytes = cpqr_smem_bytes<real>(nc, ldl);
+  *grid = G;
+  *smem = bytes;
+  if (bytes > ctx.smem_optin) return CURID_UNSUPPORTED;
+  return CURID_OK;
+}
+
+template <typename real>
+void cpqr_carve(Carver& cv, int grid, int64_t l, CpqrScratch* s) {
+  s->grid = grid;
+  s->slots = cv.take<Slot<real>>(2 * (size_t)grid);
+  s->slot_data = cv.take<real>(2 * (size_t)grid * l);
+  s->counts = cv.take<int>(grid);
+  s->abort_flag = cv.take<int>(1);
+}
+
+template <typename real>
+curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64_t ldy, int k_max,
+                      double tol, int32_t* J, real* S, int64_t lds, const CpqrScratch& s,
+                      int which) {
+  int G;
+  size_t smem;
+  CURID_TRY(cpqr_plan<real>(ctx, l, n, &G, &smem));
+  if (G != s.grid) return CURID_INVALID_ARG;
+  CpqrParams<real> P;
+  P.Y = Y;
+  P.ldy = ldy;
+  P.l = (int)l;
+  P.n = (int)n;
+  P.k_max = k_max;
+  P.nc = (int)((n + G - 1) / G);
+  P.ldl = (int)(l | 1);
+  P.tol = (real)tol;
+  // a pivot norm at or below 2 sqrt(l) eps nu_1 is rounding noise (Section 2.3's
+  // singular S11): k_eff stops there
+  P.rank_rtol = real(2) * (real)std::sqrt((double)l) *
+                (sizeof(real) == 8 ? (real)2.220446049250313e-16 : (real)1.1920929e-07);
+  P.J = J;
+  P.S = S;
+  P.lds = lds;
+  P.slots = static_cast<Slot<real>*>(s.slots);
+  P.slot_data = static_cast<real*>(s.slot_data);
+  P.abort_flag = s.abort_flag;
+  P.status = ctx.status;
+  P.which = which;
+  CURID_CUDA(cudaMemsetAsync(s.slots, 0, 2 * (size_t)G * sizeof(Slot<real>), ctx.stream));
+  CURID_CUDA(cudaMemsetAsync(s.abort_flag, 0, sizeof(int), ctx.stream));
+  auto fn = cpqr_kernel<real>;
+  CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  void* args[] = {&P};
+  CURID_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(G), dim3(kThreads), args, smem,
+                                         ctx.stream));
+  if (ctx.launches) ++*ctx.launches;
+  return CURID_OK;
+}
+
+template curid_status cpqr_plan<float>(const Ctx&, int64_t, int64_t, int*, size_t*);
+template curid_status cpqr_plan<double>(const Ctx&, int64_t, int64_t, int*, size_t*);
+template void cpqr_carve<float>(Carver&, int, int64_t, CpqrScratch*);
+template void cpqr_carve<double>(Carver&, int, int64_t, CpqrScratch*);
+template curid_status cpqr_run<float>(const Ctx&, const float*, int64_t, int64_t, int64_t, int,
+                                      double, int32_t*, float*, int64_t, const CpqrScratch&, int);
+template curid_status cpqr_run<double>(const Ctx&, const double*, int64_t, int64_t, int64_t, int,
+                                       double, int32_t*, double*, int64_t, const CpqrScratch&,
+                                       int);
+
+}  // namespace curid

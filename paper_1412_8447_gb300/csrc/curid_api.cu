@@ -1,0 +1,711 @@
+// C-ABI entry points: argument checks, workspace layout and the order of
+// kernels for CPQR -> column ID -> row ID of C -> CUR (Algorithms 1-4).
+// Every step of the method runs in this library's kernels; the host only
+// validates, carves the caller's workspace and enqueues launches.
+#include <cstring>
+#include <new>
+
+#include "kernels.cuh"
+
+using namespace curid;
+
+namespace {
+
+enum class Op { IdCol, Tsid, Cur };
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+cudaEvent_t take_event(curid_handle* h) {
+  if (h->pool_used < h->pool.size()) return h->pool[h->pool_used++];
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  h->pool.push_back(e);
+  h->pool_used = h->pool.size();
+  return e;
+}
+
+// Records CUDA events around one phase of a call when profiling is on.
+struct PhaseScope {
+  curid_handle* h;
+  int phase;
+  cudaEvent_t start = nullptr;
+  PhaseScope(curid_handle* hh, int ph) : h(hh), phase(ph) {
+    if (h && h->profiling) {
+      start = take_event(h);
+      if (start) cudaEventRecord(start, h->stream);
+    }
+  }
+  ~PhaseScope() {
+    if (!start) return;
+    cudaEvent_t stop = take_event(h);
+    if (!stop) return;
+    cudaEventRecord(stop, h->stream);
+    h->recs.push_back({phase, start, stop});
+  }
+};
+
+Ctx make_ctx(curid_handle* h) {
+  Ctx c{h->stream, h->num_sms, h->smem_optin, nullptr};
+  c.launches = h->profiling ? &h->launches : nullptr;
+  return c;
+}
+
+// All buffers of one decomposition, carved from the workspace in a fixed
+// order.  With a null base the carver only counts bytes.
+template <typename real>
+struct Plan {
+  StatusBlock* status = nullptr;
+  // randomized front end
+  real* omega = nullptr;  // l x m (when generated)
+  real* B[3] = {nullptr, nullptr, nullptr};  // sample-matrix buffers, l x max(m, n)
+  real* G = nullptr;      // l x l  (Gram)
+  real* Linv = nullptr;   // l x l
+  // column CPQR and T
+  CpqrScratch cs{};
+  real* S = nullptr;      // k x n
+  real* S11 = nullptr;    // k x k
+  real* S12 = nullptr;    // k x (n - k)
+  real* Sinv = nullptr;   // k x k
+  real* T = nullptr;      // k x (n - k)
+  // row ID of C
+  real* Ct = nullptr;     // k x m
+  CpqrScratch rs{};
+  int32_t* I = nullptr;   // m (when the caller passes none)
+  real* SW = nullptr;     // k x m
+  real* SW11 = nullptr;   // k x k
+  real* SW12 = nullptr;   // k x (m - k)
+  real* SWinv = nullptr;  // k x k
+  // U = V* R^+
+  real* R = nullptr;      // k x n
+  real* Rt = nullptr;     // k x n
+  real* Q = nullptr;      // k x n
+  real* Gu = nullptr;     // k x k
+  real* L1 = nullptr;     // k x k
+  real* L2 = nullptr;     // k x k
+  real* Qsk = nullptr;    // k x k
+  real* Qres = nullptr;   // k x (n - k)
+  real* M = nullptr;      // k x k
+  real* Uh = nullptr;     // k x k
+  real* partial = nullptr;
+  size_t partial_cap = 0;
+  size_t bytes = 0;
+};
+
+struct Dims {
+  int64_t m, n, lda;
+  int k, l;
+  bool randomized;
+  int q;
+};
+
+template <typename real>
+curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, bool need_I,
+                       void* base, Plan<real>* P) {
+  Carver cv(base);
+  const int64_t m = d.m, n = d.n;
+  const int k = d.k, l = d.l;
+  P->status = cv.take<StatusBlock>(1);
+  size_t part = 0;
+  auto upd = [&](int64_t M, int64_t N, int64_t K) {
+    part = std::max(part, gemm_partial_elems<real>(M, N, K, ctx.num_sms));
+  };
+  if (d.randomized) {
+    if (gen_omega) P->omega = cv.take<real>((size_t)l * m);
+    upd(l, n, m);
+    if (d.q == 0) {
+      P->B[0] = cv.take<real>((size_t)l * n);
+    } else {
+      for (int b = 0; b < 3; ++b) P->B[b] = cv.take<real>((size_t)l * std::max(m, n));
+      P->G = cv.take<real>((size_t)l * l);
+      P->Linv = cv.take<real>((size_t)l * l);
+      upd(l, l, n);
+      upd(l, l, m);
+      upd(l, n, l);
+      upd(l, m, l);
+      upd(l, m, n);
+    }
+  }
+  const int64_t ly = d.randomized ? l : m;
+  int grid;
+  size_t smem;
+  CURID_TRY(cpqr_plan<real>(ctx, ly, n, &grid, &smem));
+  cpqr_carve<real>(cv, grid, ly, &P->cs);
+  P->S = cv.take<real>((size_t)k * n);
+  P->S11 = cv.take<real>((size_t)k * k);
+  P->S12 = cv.take<real>((size_t)k * std::max<int64_t>(1, n - k));
+  P->Sinv = cv.take<real>((size_t)k * k);
+  P->T = cv.take<real>((size_t)k * std::max<int64_t>(1, n - k));
+  upd(k, n - k, k);
+  if (!upper_tri_inverse_fits<real>(ctx, k)) return CURID_UNSUPPORTED;
+  if (d.randomized && d.q > 0 && !chol_inverse_fits<real>(ctx, l)) return CURID_UNSUPPORTED;
+  if (op == Op::Tsid || op == Op::Cur) {
+    P->Ct = cv.take<real>((size_t)k * m);
+    CURID_TRY(cpqr_plan<real>(ctx, k, m, &grid, &smem));
+    cpqr_carve<real>(cv, grid, k, &P->rs);
+    if (need_I) P->I = cv.take<int32_t>(m);
+    P->SW = cv.take<real>((size_t)k * m);
+    P->SW11 = cv.take<real>((size_t)k * k);
+    P->SW12 = cv.take<real>((size_t)k * std::max<int64_t>(1, m - k));
+    P->SWinv = cv.take<real>((size_t)k * k);
+    upd(k, m - k, k);
+  }
+  if (op == Op::Cur) {
+    P->R = cv.take<real>((size_t)k * n);
+    P->Rt = cv.take<real>((size_t)k * n);
+    P->Q = cv.take<real>((size_t)k * n);
+    P->Gu = cv.take<real>((size_t)k * k);
+    P->L1 = cv.take<real>((size_t)k * k);
+    P->L2 = cv.take<real>((size_t)k * k);
+    P->Qsk = cv.take<real>((size_t)k * k);
+    P->Qres = cv.take<real>((size_t)k * std::max<int64_t>(1, n - k));
+    P->M = cv.take<real>((size_t)k * k);
+    P->Uh = cv.take<real>((size_t)k * k);
+    upd(k, n, k);
+    upd(k, k, n);
+    upd(k, k, n - k);
+    upd(k, k, k);
+  }
+  P->partial_cap = part;
+  P->partial = part ? cv.take<real>(part) : nullptr;
+  P->bytes = cv.used + 256;
+  return CURID_OK;
+}
+
+// Products that read A (Y = Omega A, Z = Q A^T, Y = Q A): FP32 FMA, FP64 FMA,
+// or TF32 tensor cores when requested.
+template <typename real>
+curid_status a_product(const Ctx& ctx, bool tf32, bool tb, int64_t M, int64_t N, int64_t K,
+                       const real* X, int64_t ldx, const real* A, int64_t lda, real* out,
+                       int64_t ldo, const Plan<real>& P) {
+  if constexpr (sizeof(real) == 4) {
+    if (tf32)
+      return gemm_tf32(ctx, false, tb, M, N, K, X, ldx, A, lda, out, ldo, P.partial,
+                       P.partial_cap);
+  }
+  return gemm<real>(ctx, false, tb, M, N, K, real(1), X, ldx, A, lda, real(0), out, ldo,
+                    P.partial, P.partial_cap);
+}
+
+// Row orthonormalisation without pivoting (Section 5.3): X (r x c) is
+// replaced by orth(X), computed by repeated Cholesky QR: G = X X^T,
+// G + shift I = L L^T, X <- L^{-1} X.  The first pass is shifted (FP32:
+// 1e-5 trace(G)) so the factorization exists at condition numbers near
+// 1/eps; the later passes restore orthonormality.  Each pass writes out of
+// place; on return *X points at the result and *tmp at the other buffer.
+template <typename real>
+curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c,
+                       const Plan<real>& P) {
+  const int passes = 3;
+  const double shift = sizeof(real) == 4 ? 1e-5 : 1e-13;
+  for (int pass = 0; pass < passes; ++pass) {
+    CURID_TRY(gemm<real>(ctx, false, true, r, r, c, real(1), *X, c, *X, c, real(0), P.G, r,
+                         P.partial, P.partial_cap));
+    CURID_TRY(chol_inverse<real>(ctx, P.G, (int)r, pass == 0 ? shift : 0.0, P.Linv));
+    CURID_TRY(gemm<real>(ctx, false, false, r, c, r, real(1), P.Linv, r, *X, c, real(0), *tmp, c,
+                         P.partial, P.partial_cap));
+    std::swap(*X, *tmp);
+  }
+  return CURID_OK;
+}
+
+// Sample matrix of Algorithm 4 with the power scheme of Section 5.3:
+// (2a) Y = Omega A; for i = 1..q: (2c) Y <- orth(Y) A^*, (2d) Y <- orth(Y) A.
+// Returns the buffer holding the final Y (l x n, leading dimension n).
+template <typename real>
+curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const real* A,
+                    int64_t m, int64_t n, int64_t lda, int l, int q, bool tf32, const real* Om,
+                    real** Yout) {
+  auto other = [&](const real* a, const real* b) -> real* {
+    for (int i = 0; i < 3; ++i)
+      if (P.B[i] != a && P.B[i] != b) return P.B[i];
+    return nullptr;
+  };
+  real* cur = P.B[0];
+  {
+    PhaseScope ps(h, CURID_PHASE_SKETCH);
+    CURID_TRY(a_product<real>(ctx, tf32, false, l, n, m, Om, m, A, lda, cur, n, P));
+  }
+  for (int i = 0; i < q; ++i) {
+    real* t = other(cur, nullptr);
+    {
+      PhaseScope ps(h, CURID_PHASE_ORTH);
+      CURID_TRY(orth_rows<real>(ctx, &cur, &t, l, n, P));
+    }
+    real* z = other(cur, nullptr);
+    {
+      PhaseScope ps(h, CURID_PHASE_SKETCH);
+      CURID_TRY(a_product<real>(ctx, tf32, true, l, m, n, cur, n, A, lda, z, m, P));
+    }
+    real* zt = other(z, nullptr);
+    {
+      PhaseScope ps(h, CURID_PHASE_ORTH);
+      CURID_TRY(orth_rows<real>(ctx, &z, &zt, l, m, P));
+    }
+    real* y = other(z, nullptr);
+    {
+      PhaseScope ps(h, CURID_PHASE_SKETCH);
+      CURID_TRY(a_product<real>(ctx, tf32, false, l, n, m, z, m, A, lda, y, n, P));
+    }
+    cur = y;
+  }
+  *Yout = cur;
+  return CURID_OK;
+}
+
+// T = S11^{-1} S12 (Eq. (2.8)) from S (k x n, original column order) and J.
+template <typename real>
+curid_status t_solve(const Ctx& ctx, const real* S, int64_t n, const int32_t* J, int k,
+                     const int* k_eff, real* S11, real* S12, real* Sinv, real* T, int64_t ldt,
+                     const Plan<real>& P) {
+  CURID_TRY(split_s<real>(ctx, S, n, J, k, n, S11, S12));
+  CURID_TRY(upper_tri_inverse<real>(ctx, S11, k, k_eff, Sinv));
+  if (n - k > 0)
+    CURID_TRY(gemm<real>(ctx, false, false, k, n - k, k, real(1), Sinv, k, S12, n - k, real(0),
+                         T, ldt, P.partial, P.partial_cap));
+  return CURID_OK;
+}
+
+struct Outputs {
+  int32_t* J;
+  void* T;
+  int64_t ldt;
+  int32_t* I;
+  void* TW;
+  int64_t ldtw;
+  double* U;
+  void* C;
+  void* R;
+};
+
+template <typename real>
+curid_status run(curid_handle* h, Op op, const real* A, const Dims& d, double tol,
+                 const curid_sketch& sk, const Outputs& o, char* ws, size_t ws_bytes) {
+  Ctx ctx = make_ctx(h);
+  Plan<real> P;
+  const bool gen_omega = d.randomized && sk.omega == nullptr;
+  const bool need_I = o.I == nullptr;
+  CURID_TRY(make_plan<real>(ctx, op, d, gen_omega, need_I, nullptr, &P));
+  if (ws == nullptr || P.bytes > ws_bytes) return CURID_NO_WORKSPACE;
+  CURID_TRY(make_plan<real>(ctx, op, d, gen_omega, need_I, ws, &P));
+  ctx.status = P.status;
+  const int64_t m = d.m, n = d.n, lda = d.lda;
+  const int k = d.k, l = d.l;
+  CURID_CUDA(cudaMemsetAsync(P.status, 0, sizeof(StatusBlock), ctx.stream));
+
+  // ---- sample matrix (Algorithm 4 lines 1-2; Section 5.3 steps 2a-2e) ----
+  const real* Y = A;
+  int64_t ly = m, ldy = lda;
+  if (d.randomized) {
+    const real* Om = static_cast<const real*>(sk.omega);
+    if (gen_omega) {
+      PhaseScope ps(h, CURID_PHASE_OMEGA);
+      CURID_TRY(gaussian_fill<real>(ctx, l, m, sk.seed, P.omega));
+      Om = P.omega;
+    }
+    real* Yr;
+    CURID_TRY(sketch<real>(h, ctx, P, A, m, n, lda, l, d.q, sk.tf32 != 0, Om, &Yr));
+    Y = Yr;
+    ly = l;
+    ldy = n;
+  }
+
+  // ---- truncated CPQR and T (Algorithm 1 / 4) ----
+  {
+    PhaseScope ps(h, CURID_PHASE_CPQR_COL);
+    CURID_TRY(cpqr_run<real>(ctx, Y, ly, n, ldy, k, tol, o.J, P.S, n, P.cs, 0));
+  }
+  real* T = (o.T && op != Op::Cur) ? static_cast<real*>(o.T) : P.T;
+  int64_t ldt = (T == P.T) ? std::max<int64_t>(1, n - k) : o.ldt;
+  {
+    PhaseScope ps(h, CURID_PHASE_T);
+    CURID_TRY(t_solve<real>(ctx, P.S, n, o.J, k, &P.status->k_eff, P.S11, P.S12, P.Sinv, T, ldt,
+                            P));
+    if (o.T && T == P.T)
+      CURID_TRY(copy2d<real>(ctx, P.T, ldt, static_cast<real*>(o.T), o.ldt, k, n - k));
+  }
+  if (op == Op::IdCol) return CURID_OK;
+
+  // ---- row ID of C (Algorithm 2, Eq. (2.11)): full k-step CPQR of C^T ----
+  int32_t* I = o.I ? o.I : P.I;
+  {
+    PhaseScope ps(h, CURID_PHASE_GATHER);
+    CURID_TRY(gather_cols<real>(ctx, A, m, lda, o.J, k, P.Ct, m, true));
+    if (o.C)
+      CURID_TRY(gather_cols<real>(ctx, A, m, lda, o.J, k, static_cast<real*>(o.C), k, false));
+  }
+  {
+    PhaseScope ps(h, CURID_PHASE_CPQR_ROW);
+    CURID_TRY(cpqr_run<real>(ctx, P.Ct, k, m, m, k, 0.0, I, P.SW, m, P.rs, 1));
+  }
+  PhaseScope ps_u(h, CURID_PHASE_U);
+  if (o.TW) {
+    CURID_TRY(t_solve<real>(ctx, P.SW, m, I, k, &P.status->k_row, P.SW11, P.SW12, P.SWinv,
+                            static_cast<real*>(o.TW), o.ldtw, P));
+  } else {
+    CURID_TRY(split_s<real>(ctx, P.SW, m, I, k, m, P.SW11, P.SW12));
+    CURID_TRY(upper_tri_inverse<real>(ctx, P.SW11, k, &P.status->k_row, P.SWinv));
+  }
+  if (op == Op::Tsid) return CURID_OK;
+
+  // ---- U = V* R^+ (Eq. (3.5), Algorithm 3 line 3) ----
+  // R = A(I[:k], :) = S_W11^T Q_W^T-structured; R~ = S_W11^{-T} R has a small
+  // condition number, so its Cholesky QR R~ = L Q is accurate in the working
+  // precision; then U = (V* Q^T) L^{-1} S_W11^{-T}, whose last product is
+  // accumulated in float64.
+  {
+    PhaseScope ps(h, CURID_PHASE_GATHER);
+    CURID_TRY(gather_rows<real>(ctx, A, m, n, lda, I, k, P.R, n));
+    if (o.R) CURID_TRY(copy2d<real>(ctx, P.R, n, static_cast<real*>(o.R), n, k, n));
+  }
+  CURID_TRY(gemm<real>(ctx, true, false, k, n, k, real(1), P.SWinv, k, P.R, n, real(0), P.Rt, n,
+                       P.partial, P.partial_cap));
+  CURID_TRY(gemm<real>(ctx, false, true, k, k, n, real(1), P.Rt, n, P.Rt, n, real(0), P.Gu, k,
+                       P.partial, P.partial_cap));
+  CURID_TRY(chol_inverse<real>(ctx, P.Gu, k, 0.0, P.L1));
+  CURID_TRY(gemm<real>(ctx, false, false, k, n, k, real(1), P.L1, k, P.Rt, n, real(0), P.Q, n,
+                       P.partial, P.partial_cap));
+  CURID_TRY(gemm<real>(ctx, false, true, k, k, n, real(1), P.Q, n, P.Q, n, real(0), P.Gu, k,
+                       P.partial, P.partial_cap));
+  CURID_TRY(chol_inverse<real>(ctx, P.Gu, k, 0.0, P.L2));
+  CURID_TRY(gemm<real>(ctx, false, false, k, n, k, real(1), P.L2, k, P.Q, n, real(0), P.Rt, n,
+                       P.partial, P.partial_cap));
+  // M = V* Q^T = Q(:, J[:k])^T + T Q(:, J[k:])^T
+  CURID_TRY(split_s<real>(ctx, P.Rt, n, o.J, k, n, P.Qsk, P.Qres));
+  if (n - k > 0) {
+    CURID_TRY(gemm<real>(ctx, false, true, k, k, n - k, real(1), T, ldt, P.Qres, n - k, real(0),
+                         P.M, k, P.partial, P.partial_cap));
+  } else {
+    CURID_CUDA(cudaMemsetAsync(P.M, 0, (size_t)k * k * sizeof(real), ctx.stream));
+  }
+  CURID_TRY(add_transpose<real>(ctx, P.Qsk, k, P.M, k, k, k));
+  CURID_TRY(gemm<real>(ctx, false, false, k, k, k, real(1), P.M, k, P.L2, k, real(0), P.Uh, k,
+                       P.partial, P.partial_cap));
+  CURID_TRY(gemm<real>(ctx, false, false, k, k, k, real(1), P.Uh, k, P.L1, k, real(0), P.M, k,
+                       P.partial, P.partial_cap));
+  CURID_TRY(gemm_nt_f64acc<real>(ctx, k, k, k, P.M, k, P.SWinv, k, o.U, k));
+  return CURID_OK;
+}
+
+curid_status check_common(curid_handle* h, curid_dtype dt, const void* A, int64_t m, int64_t n,
+                          int64_t lda, int k, double tol, const curid_sketch& sk, Dims* d) {
+  if (!h) return CURID_INVALID_ARG;
+  if (dt != CURID_F32 && dt != CURID_F64) return CURID_INVALID_ARG;
+  if (!A || m <= 0 || n <= 0 || lda < n) return CURID_INVALID_ARG;
+  if (m > INT32_MAX || n > INT32_MAX) return CURID_INVALID_ARG;
+  if (k < 0 || tol < 0) return CURID_INVALID_ARG;
+  if (k == 0) return tol > 0 ? CURID_UNSUPPORTED : CURID_INVALID_ARG;
+  if (k > std::min(m, n)) return CURID_INVALID_ARG;
+  if (sk.q < 0) return CURID_INVALID_ARG;
+  if (sk.tf32 && dt != CURID_F32) return CURID_INVALID_ARG;
+  d->m = m;
+  d->n = n;
+  d->lda = lda;
+  d->k = k;
+  d->randomized = sk.p >= 0;
+  d->l = d->randomized ? k + sk.p : (int)m;
+  d->q = sk.q;
+  if (d->randomized && d->l > std::min(m, n)) return CURID_INVALID_ARG;
+  if (!d->randomized && sk.q > 0) return CURID_INVALID_ARG;
+  return CURID_OK;
+}
+
+template <typename F>
+curid_status dispatch(curid_handle* h, F&& f) {
+  DeviceGuard g(h->device);
+  if (!g.ok) return CURID_CUDA_ERROR;
+  return f();
+}
+
+}  // namespace
+
+extern "C" {
+
+curid_status curid_create(curid_handle** handle, int device) {
+  if (!handle) return CURID_INVALID_ARG;
+  *handle = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess) return CURID_CUDA_ERROR;
+  if (device < 0 || device >= count) return CURID_INVALID_ARG;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return CURID_CUDA_ERROR;
+  if (!prop.cooperativeLaunch) return CURID_UNSUPPORTED;
+  curid_handle* h = new (std::nothrow) curid_handle();
+  if (!h) return CURID_INVALID_ARG;
+  h->device = device;
+  h->num_sms = prop.multiProcessorCount;
+  h->smem_optin = prop.sharedMemPerBlockOptin;
+  *handle = h;
+  return CURID_OK;
+}
+
+curid_status curid_destroy(curid_handle* handle) {
+  if (handle) {
+    for (cudaEvent_t e : handle->pool) cudaEventDestroy(e);
+  }
+  delete handle;
+  return CURID_OK;
+}
+
+curid_status curid_profile(curid_handle* handle, int enable) {
+  if (!handle) return CURID_INVALID_ARG;
+  handle->profiling = enable ? 1 : 0;
+  handle->recs.clear();
+  handle->pool_used = 0;
+  handle->launches = 0;
+  return CURID_OK;
+}
+
+curid_status curid_profile_read(curid_handle* handle, double* ms, int* calls,
+                                long long* launches) {
+  if (!handle) return CURID_INVALID_ARG;
+  DeviceGuard g(handle->device);
+  if (!g.ok) return CURID_CUDA_ERROR;
+  if (cudaStreamSynchronize(handle->stream) != cudaSuccess) return CURID_CUDA_ERROR;
+  for (int p = 0; p < CURID_NUM_PHASES; ++p) {
+    if (ms) ms[p] = 0.0;
+    if (calls) calls[p] = 0;
+  }
+  for (const curid_phase_rec& r : handle->recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.start, r.stop) != cudaSuccess) return CURID_CUDA_ERROR;
+    if (r.phase >= 0 && r.phase < CURID_NUM_PHASES) {
+      if (ms) ms[r.phase] += t;
+      if (calls) calls[r.phase] += 1;
+    }
+  }
+  if (launches) *launches = handle->launches;
+  handle->recs.clear();
+  handle->pool_used = 0;
+  handle->launches = 0;
+  return CURID_OK;
+}
+
+curid_status curid_set_stream(curid_handle* handle, void* stream) {
+  if (!handle) return CURID_INVALID_ARG;
+  handle->stream = static_cast<cudaStream_t>(stream);
+  return CURID_OK;
+}
+
+curid_status curid_set_workspace(curid_handle* handle, void* ptr, size_t bytes) {
+  if (!handle) return CURID_INVALID_ARG;
+  if (ptr && (reinterpret_cast<uintptr_t>(ptr) & 255)) return CURID_INVALID_ARG;
+  handle->ws = static_cast<char*>(ptr);
+  handle->ws_bytes = ptr ? bytes : 0;
+  return CURID_OK;
+}
+
+curid_status curid_workspace_size(curid_handle* handle, curid_dtype dtype, int64_t m, int64_t n,
+                                  int k, curid_sketch sk, size_t* bytes) {
+  if (!handle || !bytes) return CURID_INVALID_ARG;
+  Dims d;
+  int dummy = 1;
+  CURID_TRY(check_common(handle, dtype, &dummy, m, n, n, k, 0.0, sk, &d));
+  Ctx ctx{nullptr, handle->num_sms, handle->smem_optin, nullptr};
+  const bool gen = d.randomized && sk.omega == nullptr;
+  Dims dt;
+  const bool row_ok = check_common(handle, dtype, &dummy, n, m, m, k, 0.0, sk, &dt) == CURID_OK;
+  auto size_for = [&](auto tag) -> curid_status {
+    using real = decltype(tag);
+    Plan<real> P;
+    CURID_TRY(make_plan<real>(ctx, Op::Cur, d, gen, true, nullptr, &P));
+    size_t b = P.bytes;
+    if (row_ok) {
+      Plan<real> Pt;
+      if (make_plan<real>(ctx, Op::IdCol, dt, gen, true, nullptr, &Pt) == CURID_OK)
+        b = std::max(b, (((size_t)m * n * sizeof(real) + 255) & ~size_t(255)) + Pt.bytes);
+    }
+    *bytes = b;
+    return CURID_OK;
+  };
+  if (dtype == CURID_F64) return size_for(double{});
+  return size_for(float{});
+}
+
+curid_status curid_last_status(curid_handle* handle, int* k_out) {
+  if (!handle) return CURID_INVALID_ARG;
+  if (!handle->ws) return CURID_NO_WORKSPACE;
+  DeviceGuard g(handle->device);
+  if (!g.ok) return CURID_CUDA_ERROR;
+  StatusBlock sb;
+  if (cudaStreamSynchronize(handle->stream) != cudaSuccess) return CURID_CUDA_ERROR;
+  if (cudaMemcpy(&sb, handle->ws, sizeof(sb), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return CURID_CUDA_ERROR;
+  if (k_out) *k_out = sb.k_eff;
+  if (sb.flags & FLAG_TIMEOUT) return CURID_TIMEOUT;
+  if (sb.flags & FLAG_NONFINITE) return CURID_NONFINITE;
+  if (sb.flags & FLAG_BREAKDOWN) return CURID_BREAKDOWN;
+  if (sb.flags & FLAG_RANK_DEFICIENT) return CURID_RANK_DEFICIENT;
+  return CURID_OK;
+}
+
+curid_status curid_gaussian(curid_handle* handle, curid_dtype dtype, int64_t rows, int64_t cols,
+                            uint64_t seed, void* out) {
+  if (!handle || !out || rows < 0 || cols < 0) return CURID_INVALID_ARG;
+  return dispatch(handle, [&]() -> curid_status {
+    Ctx ctx = make_ctx(handle);
+    PhaseScope ps(handle, CURID_PHASE_OMEGA);
+    if (dtype == CURID_F64) return gaussian_fill<double>(ctx, rows, cols, seed, (double*)out);
+    if (dtype == CURID_F32) return gaussian_fill<float>(ctx, rows, cols, seed, (float*)out);
+    return CURID_INVALID_ARG;
+  });
+}
+
+curid_status curid_sketch_matrix(curid_handle* handle, curid_dtype dtype, const void* A,
+                                 int64_t m, int64_t n, int64_t lda, int l, int q, int tf32,
+                                 const void* omega, void* Y) {
+  if (!handle || !A || !omega || !Y || m <= 0 || n <= 0 || lda < n || l <= 0 || q < 0)
+    return CURID_INVALID_ARG;
+  if (l > std::min(m, n)) return CURID_INVALID_ARG;
+  if (tf32 && dtype != CURID_F32) return CURID_INVALID_ARG;
+  return dispatch(handle, [&]() -> curid_status {
+    Ctx ctx = make_ctx(handle);
+    Dims d{m, n, lda, 1, l, true, q};
+    auto go = [&](auto tag) -> curid_status {
+      using real = decltype(tag);
+      Plan<real> P;
+      CURID_TRY(make_plan<real>(ctx, Op::IdCol, d, false, false, nullptr, &P));
+      if (!handle->ws || P.bytes > handle->ws_bytes) return CURID_NO_WORKSPACE;
+      CURID_TRY(make_plan<real>(ctx, Op::IdCol, d, false, false, handle->ws, &P));
+      ctx.status = P.status;
+      CURID_CUDA(cudaMemsetAsync(P.status, 0, sizeof(StatusBlock), ctx.stream));
+      real* cur;
+      CURID_TRY(sketch<real>(handle, ctx, P, static_cast<const real*>(A), m, n, lda, l, q,
+                             tf32 != 0, static_cast<const real*>(omega), &cur));
+      return copy2d<real>(ctx, cur, n, static_cast<real*>(Y), n, l, n);
+    };
+    if (dtype == CURID_F64) return go(double{});
+    if (dtype == CURID_F32) return go(float{});
+    return CURID_INVALID_ARG;
+  });
+}
+
+curid_status curid_cpqr(curid_handle* handle, curid_dtype dtype, const void* Y, int64_t l,
+                        int64_t n, int64_t ldy, int k, double tol, int32_t* J, void* S) {
+  if (!handle || !Y || !J || !S || l <= 0 || n <= 0 || ldy < n || k < 0 || tol < 0)
+    return CURID_INVALID_ARG;
+  if (k == 0 && !(tol > 0)) return CURID_INVALID_ARG;
+  if (k > std::min(l, n)) return CURID_INVALID_ARG;
+  const int k_max = k > 0 ? k : (int)std::min(l, n);
+  return dispatch(handle, [&]() -> curid_status {
+    Ctx ctx = make_ctx(handle);
+    auto go = [&](auto tag) -> curid_status {
+      using real = decltype(tag);
+      int grid;
+      size_t smem;
+      CURID_TRY(cpqr_plan<real>(ctx, l, n, &grid, &smem));
+      Carver cv(nullptr);
+      StatusBlock* st = cv.take<StatusBlock>(1);
+      CpqrScratch cs;
+      cpqr_carve<real>(cv, grid, l, &cs);
+      if (!handle->ws || cv.used > handle->ws_bytes) return CURID_NO_WORKSPACE;
+      Carver cw(handle->ws);
+      st = cw.take<StatusBlock>(1);
+      cpqr_carve<real>(cw, grid, l, &cs);
+      ctx.status = st;
+      CURID_CUDA(cudaMemsetAsync(st, 0, sizeof(StatusBlock), ctx.stream));
+      PhaseScope ps(handle, CURID_PHASE_CPQR_COL);
+      return cpqr_run<real>(ctx, static_cast<const real*>(Y), l, n, ldy, k_max, k > 0 ? 0.0 : tol,
+                            J, static_cast<real*>(S), n, cs, 0);
+    };
+    if (dtype == CURID_F64) return go(double{});
+    if (dtype == CURID_F32) return go(float{});
+    return CURID_INVALID_ARG;
+  });
+}
+
+curid_status curid_id_col(curid_handle* handle, curid_dtype dtype, const void* A, int64_t m,
+                          int64_t n, int64_t lda, int k, double tol, curid_sketch sk, int32_t* J,
+                          void* T, int64_t ldt) {
+  Dims d;
+  CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d));
+  if (!J || !T || ldt < std::max<int64_t>(1, n - k)) return CURID_INVALID_ARG;
+  Outputs o{J, T, ldt, nullptr, nullptr, 0, nullptr, nullptr, nullptr};
+  return dispatch(handle, [&]() -> curid_status {
+    if (dtype == CURID_F64)
+      return run<double>(handle, Op::IdCol, (const double*)A, d, 0.0, sk, o, handle->ws,
+                         handle->ws_bytes);
+    return run<float>(handle, Op::IdCol, (const float*)A, d, 0.0, sk, o, handle->ws,
+                      handle->ws_bytes);
+  });
+}
+
+curid_status curid_id_row(curid_handle* handle, curid_dtype dtype, const void* A, int64_t m,
+                          int64_t n, int64_t lda, int k, double tol, curid_sketch sk, int32_t* I,
+                          void* TW, int64_t ldtw) {
+  // Row ID = column ID of A^* (Remark 2.1): A^T is formed in the workspace
+  // (n x m, leading dimension m) and the column-ID pipeline runs on it.
+  Dims d0;
+  CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d0));
+  Dims d;
+  CURID_TRY(check_common(handle, dtype, A, n, m, m, k, tol, sk, &d));
+  if (!I || !TW || ldtw < std::max<int64_t>(1, m - k)) return CURID_INVALID_ARG;
+  Outputs o{I, TW, ldtw, nullptr, nullptr, 0, nullptr, nullptr, nullptr};
+  return dispatch(handle, [&]() -> curid_status {
+    Ctx ctx = make_ctx(handle);
+    auto go = [&](auto tag) -> curid_status {
+      using real = decltype(tag);
+      // the pipeline's buffers (status block first) at the start, A^T after them
+      Plan<real> P;
+      CURID_TRY(make_plan<real>(ctx, Op::IdCol, d, d.randomized && sk.omega == nullptr, true,
+                                nullptr, &P));
+      const size_t off = (P.bytes + 255) & ~size_t(255);
+      if (!handle->ws || off + (size_t)m * n * sizeof(real) > handle->ws_bytes)
+        return CURID_NO_WORKSPACE;
+      real* At = reinterpret_cast<real*>(handle->ws + off);
+      CURID_TRY(transpose2d<real>(ctx, static_cast<const real*>(A), lda, At, m, m, n));
+      return run<real>(handle, Op::IdCol, At, d, 0.0, sk, o, handle->ws, off);
+    };
+    if (dtype == CURID_F64) return go(double{});
+    return go(float{});
+  });
+}
+
+curid_status curid_tsid(curid_handle* handle, curid_dtype dtype, const void* A, int64_t m,
+                        int64_t n, int64_t lda, int k, double tol, curid_sketch sk, int32_t* J,
+                        void* T, int64_t ldt, int32_t* I, void* TW, int64_t ldtw) {
+  Dims d;
+  CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d));
+  if (!J || !T || !I || !TW || ldt < std::max<int64_t>(1, n - k) ||
+      ldtw < std::max<int64_t>(1, m - k))
+    return CURID_INVALID_ARG;
+  Outputs o{J, T, ldt, I, TW, ldtw, nullptr, nullptr, nullptr};
+  return dispatch(handle, [&]() -> curid_status {
+    if (dtype == CURID_F64)
+      return run<double>(handle, Op::Tsid, (const double*)A, d, 0.0, sk, o, handle->ws,
+                         handle->ws_bytes);
+    return run<float>(handle, Op::Tsid, (const float*)A, d, 0.0, sk, o, handle->ws,
+                      handle->ws_bytes);
+  });
+}
+
+curid_status curid_cur(curid_handle* handle, curid_dtype dtype, const void* A, int64_t m,
+                       int64_t n, int64_t lda, int k, double tol, curid_sketch sk, int32_t* J,
+                       int32_t* I, double* U, void* C, void* R, void* T, int64_t ldt, void* TW,
+                       int64_t ldtw) {
+  Dims d;
+  CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d));
+  if (!J || !I || !U) return CURID_INVALID_ARG;
+  if (T && ldt < std::max<int64_t>(1, n - k)) return CURID_INVALID_ARG;
+  if (TW && ldtw < std::max<int64_t>(1, m - k)) return CURID_INVALID_ARG;
+  Outputs o{J, T, ldt, I, TW, ldtw, U, C, R};
+  return dispatch(handle, [&]() -> curid_status {
+    if (dtype == CURID_F64)
+      return run<double>(handle, Op::Cur, (const double*)A, d, 0.0, sk, o, handle->ws,
+                         handle->ws_bytes);
+    return run<float>(handle, Op::Cur, (const float*)A, d, 0.0, sk, o, handle->ws,
+                      handle->ws_bytes);
+  });
+}
+
+}  // extern "C"

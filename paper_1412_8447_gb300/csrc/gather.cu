@@ -1,0 +1,208 @@
+// Column and row gathers (C = A(:, J[:k]), R = A(I[:k], :), Eq. (3.1)), the
+// split of S1 into S11 and S12 (Eq. (2.7)), and plain 2-D copies.
+// Memory-bound; all writes are coalesced, reads are coalesced wherever the
+// index set allows (rows of R are contiguous; a column of C is a stride-lda
+// walk, so each warp reads 32 rows of one skeleton column).
+#include "kernels.cuh"
+
+namespace curid {
+
+namespace {
+
+// out^T layout (transpose == true): out[i*ldo + r] = A[r*lda + J[i]]
+template <typename real>
+__global__ void gather_cols_t_kernel(const real* __restrict__ A, int64_t m, int64_t lda,
+                                     const int32_t* __restrict__ J, int k,
+                                     real* __restrict__ out, int64_t ldo) {
+  const int i = blockIdx.y;
+  int64_t col = J[i];
+  if (col < 0 || col >= lda) col = 0;  // indices come from the device; never read out of range
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
+       r += (int64_t)gridDim.x * blockDim.x)
+    out[(int64_t)i * ldo + r] = A[r * lda + col];
+}
+
+// out[r*ldo + i] = A[r*lda + J[i]] through a 32 x 32 shared tile
+template <typename real>
+__global__ void gather_cols_kernel(const real* __restrict__ A, int64_t m, int64_t lda,
+                                   const int32_t* __restrict__ J, int k,
+                                   real* __restrict__ out, int64_t ldo) {
+  __shared__ real tile[32][33];
+  const int i0 = blockIdx.y * 32;
+  const int64_t r0 = blockIdx.x * 32LL;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int i = i0 + yy;
+    const int64_t r = r0 + tx;
+    int64_t col = i < k ? (int64_t)J[i] : 0;
+    if (col < 0 || col >= lda) col = 0;
+    tile[yy][tx] = (i < k && r < m) ? A[r * lda + col] : real(0);
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t r = r0 + yy;
+    const int i = i0 + tx;
+    if (r < m && i < k) out[r * ldo + i] = tile[tx][yy];
+  }
+}
+
+template <typename real>
+__global__ void gather_rows_kernel(const real* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                   const int32_t* __restrict__ I, real* __restrict__ out,
+                                   int64_t ldo) {
+  const int i = blockIdx.y;
+  int64_t row = I[i];
+  if (row < 0 || row >= m) row = 0;
+  const real* src = A + row * lda;
+  real* dst = out + (int64_t)i * ldo;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x)
+    dst[c] = src[c];
+}
+
+template <typename real>
+__global__ void split_s_kernel(const real* __restrict__ S, int64_t lds,
+                               const int32_t* __restrict__ J, int k, int64_t n,
+                               real* __restrict__ S11, real* __restrict__ S12) {
+  const int i = blockIdx.y;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t col = J[t];
+    if (col < 0 || col >= n) col = 0;
+    const real v = S[(int64_t)i * lds + col];
+    if (t < k) S11[(int64_t)i * k + t] = v;
+    else S12[(int64_t)i * (n - k) + (t - k)] = v;
+  }
+}
+
+template <typename real>
+__global__ void copy2d_kernel(const real* __restrict__ src, int64_t lds, real* __restrict__ dst,
+                              int64_t ldd, int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    dst[r * ldd + c] = src[r * lds + c];
+  }
+}
+
+template <typename real>
+__global__ void add_transpose_kernel(const real* __restrict__ src, int64_t lds,
+                                     real* __restrict__ dst, int64_t ldd, int64_t rows,
+                                     int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    dst[r * ldd + c] += src[c * lds + r];
+  }
+}
+
+// dst[c*ldd + r] = src[r*lds + c] through a 32 x 32 shared tile
+template <typename real>
+__global__ void transpose2d_kernel(const real* __restrict__ src, int64_t lds,
+                                   real* __restrict__ dst, int64_t ldd, int64_t rows,
+                                   int64_t cols) {
+  __shared__ real tile[32][33];
+  const int64_t r0 = blockIdx.y * 32LL, c0 = blockIdx.x * 32LL;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t r = r0 + yy, c = c0 + tx;
+    tile[yy][tx] = (r < rows && c < cols) ? src[r * lds + c] : real(0);
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t c = c0 + yy, r = r0 + tx;
+    if (r < rows && c < cols) dst[c * ldd + r] = tile[tx][yy];
+  }
+}
+
+inline unsigned blocks_for(int64_t work, int num_sms) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 16LL * num_sms));
+}
+
+}  // namespace
+
+template <typename real>
+curid_status gather_cols(const Ctx& ctx, const real* A, int64_t m, int64_t lda, const int32_t* J,
+                         int k, real* out, int64_t ldo, bool transpose) {
+  if (k <= 0 || m <= 0) return CURID_OK;
+  if (transpose) {
+    dim3 grid((unsigned)std::min<int64_t>((m + 255) / 256, 64), (unsigned)k);
+    gather_cols_t_kernel<real><<<grid, 256, 0, ctx.stream>>>(A, m, lda, J, k, out, ldo);
+  } else {
+    dim3 grid((unsigned)((m + 31) / 32), (unsigned)((k + 31) / 32));
+    gather_cols_kernel<real><<<grid, dim3(32, 8), 0, ctx.stream>>>(A, m, lda, J, k, out, ldo);
+  }
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
+template <typename real>
+curid_status gather_rows(const Ctx& ctx, const real* A, int64_t m, int64_t n, int64_t lda,
+                         const int32_t* I, int k, real* out, int64_t ldo) {
+  if (k <= 0 || n <= 0) return CURID_OK;
+  dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)k);
+  gather_rows_kernel<real><<<grid, 256, 0, ctx.stream>>>(A, m, n, lda, I, out, ldo);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
+template <typename real>
+curid_status split_s(const Ctx& ctx, const real* S, int64_t lds, const int32_t* J, int k,
+                     int64_t n, real* S11, real* S12) {
+  if (k <= 0) return CURID_OK;
+  dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)k);
+  split_s_kernel<real><<<grid, 256, 0, ctx.stream>>>(S, lds, J, k, n, S11, S12);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
+template <typename real>
+curid_status copy2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
+                    int64_t rows, int64_t cols) {
+  if (rows <= 0 || cols <= 0) return CURID_OK;
+  copy2d_kernel<real><<<blocks_for(rows * cols, ctx.num_sms), 256, 0, ctx.stream>>>(
+      src, lds, dst, ldd, rows, cols);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
+template <typename real>
+curid_status add_transpose(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
+                           int64_t rows, int64_t cols) {
+  if (rows <= 0 || cols <= 0) return CURID_OK;
+  add_transpose_kernel<real><<<blocks_for(rows * cols, ctx.num_sms), 256, 0, ctx.stream>>>(
+      src, lds, dst, ldd, rows, cols);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
+template <typename real>
+curid_status transpose2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
+                         int64_t rows, int64_t cols) {
+  if (rows <= 0 || cols <= 0) return CURID_OK;
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  transpose2d_kernel<real><<<grid, dim3(32, 8), 0, ctx.stream>>>(src, lds, dst, ldd, rows, cols);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
+#define CURID_INST(real)                                                                       \
+  template curid_status gather_cols<real>(const Ctx&, const real*, int64_t, int64_t,           \
+                                          const int32_t*, int, real*, int64_t, bool);          \
+  template curid_status gather_rows<real>(const Ctx&, const real*, int64_t, int64_t, int64_t,  \
+                                          const int32_t*, int, real*, int64_t);                \
+  template curid_status split_s<real>(const Ctx&, const real*, int64_t, const int32_t*, int,   \
+                                      int64_t, real*, real*);                                  \
+  template curid_status copy2d<real>(const Ctx&, const real*, int64_t, real*, int64_t, int64_t, \
+                                     int64_t);                                                 \
+  template curid_status add_transpose<real>(const Ctx&, const real*, int64_t, real*, int64_t,   \
+                                            int64_t, int64_t);                                 \
+  template curid_status transpose2d<real>(const Ctx&, const real*, int64_t, real*, int64_t,     \
+                                          int64_t, int64_t);
+CURID_INST(float)
+CURID_INST(double)
+#undef CURID_INST
+
+}  // namespace curid

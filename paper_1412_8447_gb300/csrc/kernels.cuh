@@ -1,0 +1,110 @@
+// Internal interfaces between the C-ABI layer (curid_api.cu) and the
+// kernels.  Nothing here is exported from the shared library.
+#pragma once
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace curid {
+
+struct Ctx {
+  cudaStream_t stream;
+  int num_sms;
+  size_t smem_optin;
+  StatusBlock* status;          // device
+  long long* launches = nullptr;  // host counter of kernel launches (profiling)
+};
+
+// After a kernel launch: report a launch error, count the launch.
+#define CURID_LAUNCHED(ctx)                                  \
+  do {                                                       \
+    CURID_CUDA(cudaGetLastError());                          \
+    if ((ctx).launches) ++*(ctx).launches;                   \
+  } while (0)
+
+// ---- dense products (gemm_simt.cu) ----------------------------------------
+template <typename real>
+int gemm_splits(int64_t M, int64_t N, int64_t K, int num_sms);
+template <typename real>
+size_t gemm_partial_elems(int64_t M, int64_t N, int64_t K, int num_sms);
+template <typename real>
+curid_status gemm(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
+                  real alpha, const real* A, int64_t lda, const real* B, int64_t ldb,
+                  real beta, real* C, int64_t ldc, real* partial, size_t partial_cap);
+
+// ---- tensor-core products (gemm_tc.cu): TF32 inputs, FP32 accumulation ----
+// C[M x N] = op(A) op(B) with the same op convention as gemm(); returns
+// CURID_UNSUPPORTED for shapes or alignments the kernel does not take.
+curid_status gemm_tf32(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
+                       const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                       int64_t ldc, float* partial, size_t partial_cap);
+size_t gemm_tf32_partial_elems(int64_t M, int64_t N, int64_t K, int num_sms);
+
+// ---- truncated CPQR (cpqr.cu) -----------------------------------------------
+// Scratch for one CPQR launch (carved from the workspace).
+struct CpqrScratch {
+  void* slots;       // 2 * G slot records
+  void* slot_data;   // 2 * G * l reals
+  int* counts;       // G
+  int* abort_flag;   // 1
+  int grid;          // G
+};
+template <typename real>
+curid_status cpqr_plan(const Ctx& ctx, int64_t l, int64_t n, int* grid, size_t* smem);
+template <typename real>
+void cpqr_carve(Carver& cv, int grid, int64_t l, CpqrScratch* s);
+// which: 0 = column CPQR (status k_done/k_eff), 1 = row CPQR (status k_row)
+template <typename real>
+curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64_t ldy,
+                      int k_max, double tol, int32_t* J, real* S, int64_t lds,
+                      const CpqrScratch& s, int which);
+
+// ---- small dense factorizations (dense_small.cu) ---------------------------
+// Inverse of the leading triangle of S (k x k, columns gathered by J) for the
+// T solve; rows/columns at and after *k_eff are zeroed.
+template <typename real>
+curid_status upper_tri_inverse(const Ctx& ctx, const real* S11, int k, const int* k_eff,
+                               real* X);
+template <typename real>
+bool upper_tri_inverse_fits(const Ctx& ctx, int k);
+// Cholesky of G + shift*I (shift = rel_shift * trace(G)) and inverse of
+// the factor: Linv (l x l, lower triangular).  Breakdown -> FLAG_BREAKDOWN.
+template <typename real>
+curid_status chol_inverse(const Ctx& ctx, const real* G, int l, double rel_shift, real* Linv);
+template <typename real>
+bool chol_inverse_fits(const Ctx& ctx, int l);
+// C (float64) = A B^T with float64 accumulation; A M x K, B N x K.
+template <typename real>
+curid_status gemm_nt_f64acc(const Ctx& ctx, int64_t M, int64_t N, int64_t K, const real* A,
+                            int64_t lda, const real* B, int64_t ldb, double* C, int64_t ldc);
+
+// ---- gathers and copies (gather.cu) ------------------------------------------
+template <typename real>
+curid_status gather_cols(const Ctx& ctx, const real* A, int64_t m, int64_t lda,
+                         const int32_t* J, int k, real* out, int64_t ldo, bool transpose);
+template <typename real>
+curid_status gather_rows(const Ctx& ctx, const real* A, int64_t m, int64_t n, int64_t lda,
+                         const int32_t* I, int k, real* out, int64_t ldo);
+// S11[i][t] = S[i][J[t]] (t < k); S12[i][c] = S[i][J[k+c]] (c < n-k)
+template <typename real>
+curid_status split_s(const Ctx& ctx, const real* S, int64_t lds, const int32_t* J, int k,
+                     int64_t n, real* S11, real* S12);
+template <typename real>
+curid_status copy2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
+                    int64_t rows, int64_t cols);
+// dst (cols x rows, leading dimension ldd) = src^T (src rows x cols)
+template <typename real>
+curid_status transpose2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
+                         int64_t rows, int64_t cols);
+// dst[i][t] = src[t][i] (k x k transpose-add): dst += src^T
+template <typename real>
+curid_status add_transpose(const Ctx& ctx, const real* src, int64_t lds, real* dst,
+                           int64_t ldd, int64_t rows, int64_t cols);
+
+// ---- random numbers (philox.cu) --------------------------------------------
+template <typename real>
+curid_status gaussian_fill(const Ctx& ctx, int64_t rows, int64_t cols, uint64_t seed,
+                           real* out);
+
+}  // namespace curid

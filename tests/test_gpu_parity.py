@@ -1,0 +1,248 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on
+seeded synthetic inputs: sizes the oracle finishes in seconds, spanning
+several column slabs per CTA, ragged tails and the degenerate cases."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1412_8447_gb300 as curid
+import synthetic as syn
+from oracle.philox import gaussian as philox_gaussian
+from parity import (U32, U64, assert_s_rows_match, fro, gap_allows_exact, id_residual, np64,
+                    npi, s_by_column)
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def cuda(t):
+    return t.to(DEV)
+
+
+# --- Omega generator -----------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_gaussian_matches_philox_reference(dtype):
+    rows, cols, seed = 37, 1001, 0x1234567890AB
+    g = np64(curid.gaussian(rows, cols, seed, dtype=dtype, device=0))
+    ref = philox_gaussian(rows, cols, seed)
+    tol = 1e-12 if dtype == torch.float64 else 2e-5
+    np.testing.assert_allclose(g, ref, atol=tol * 10, rtol=tol)
+
+
+# --- sketch products -------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype,q", [(torch.float64, 0), (torch.float64, 1), (torch.float32, 0),
+                                     (torch.float32, 1), (torch.float64, 2)])
+def test_sketch_matrix(dtype, q):
+    m, n, l = 700, 515, 37
+    A = syn.spectrum_matrix(m, n, syn.exp_decay(min(m, n), 30.0), 501, dtype)
+    Om = syn.gaussian(l, m, 502, dtype)
+    Y = np64(curid.sketch_matrix(cuda(A), cuda(Om), q=q))
+    Yo = O.sketch(np64(A), np64(Om), q=q)
+    if q == 0:
+        tol = 1e-12 if dtype == torch.float64 else 2e-5
+        np.testing.assert_allclose(Y, Yo, atol=tol * np.abs(Yo).max(), rtol=0)
+    else:
+        # orth is unique up to the rounding of each side; compare row spaces
+        def proj(M):
+            Qm, _ = np.linalg.qr(M.T)
+            return Qm @ Qm.T
+        d = fro(proj(Y) - proj(Yo))
+        assert d <= (1e-8 if dtype == torch.float64 else 2e-3), d
+
+
+# --- CPQR ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("m,n,k,seed", [(60, 40, 12, 1), (40, 70, 20, 2), (128, 1000, 33, 3),
+                                        (33, 4099, 30, 4), (300, 157, 60, 5)])
+def test_cpqr_planted(dtype, m, n, k, seed):
+    # FP32 keeps every planted diagonal far above its rounding level
+    decay = 2.0 ** -0.5 if dtype == torch.float64 else 0.85
+    A, perm = syn.planted_pivots(m, n, k, seed, decay=decay, dtype=dtype)
+    r = curid.cpqr(cuda(A), k=k)
+    J = npi(r.J)
+    assert list(J[:k]) == list(perm[:k])
+    assert sorted(J) == list(range(n))
+    assert list(J[k:]) == sorted(J[k:])
+    o = O.cpqr(np64(A), k=k)
+    tol = 1e-11 if dtype == torch.float64 else 2e-5
+    assert_s_rows_match(r.S, s_by_column(o.S1, o.J, n), k, tol)
+
+
+@pytest.mark.parametrize("m,n,k,seed", [(400, 300, 40, 11), (64, 2000, 50, 12),
+                                        (1000, 1999, 80, 13)])
+def test_cpqr_random_f64(m, n, k, seed):
+    A = syn.spectrum_matrix(m, n, syn.exp_decay(min(m, n), 10.0), seed)
+    r = curid.cpqr(cuda(A), k=k)
+    o = O.cpqr(np64(A), k=k)
+    J = npi(r.J)
+    if gap_allows_exact(o, k, U64):
+        assert list(J[:k]) == list(o.J[:k])
+        assert_s_rows_match(r.S, s_by_column(o.S1, o.J, n), k, 1e-10)
+    else:
+        T = O.interpolation_matrix(np64(r.S)[:, J], k)
+        assert id_residual(A, J, T, k) <= 1.05 * id_residual(A, o.J, O.id_col(np64(A), k).T, k)
+
+
+def test_cpqr_adaptive_tolerance():
+    A = syn.spectrum_matrix(500, 400, syn.exp_decay(400, 8.0), 21)
+    tol = 1e-6
+    r = curid.cpqr(cuda(A), k=0, tol=tol)
+    o = O.cpqr(np64(A), tol=tol)
+    assert r.k == o.k
+    assert list(npi(r.J)[:o.k]) == list(o.J[:o.k])
+
+
+def test_cpqr_ties_smallest_index():
+    g = np.random.default_rng(7)
+    A = g.standard_normal((64, 300))
+    A[:, 250] = A[:, 17] = 10 * g.standard_normal(64)
+    r = curid.cpqr(cuda(torch.from_numpy(A)), k=3)
+    assert int(r.J[0]) == 17
+
+
+def test_cpqr_full_rank_steps_and_k1():
+    A = syn.spectrum_matrix(50, 30, syn.exp_decay(30, 5.0), 22)
+    for k in (1, 30):
+        r = curid.cpqr(cuda(A), k=k)
+        o = O.cpqr(np64(A), k=k)
+        assert list(npi(r.J)[:k]) == list(o.J[:k])
+
+
+# --- deterministic ID / tsID / CUR in FP64 (400 x 300, sigma_j = exp(-j/10), k = 40) ---
+
+def small_f64():
+    w = syn.workload_small_f64()
+    return w["A"], w["k"]
+
+
+def test_id_col_f64():
+    A, k = small_f64()
+    r = curid.id_col(cuda(A), k)
+    o = O.id_col(np64(A), k)
+    assert gap_allows_exact(o.qr, k, U64)
+    assert list(npi(r.J)) == list(o.J)
+    np.testing.assert_allclose(np64(r.T), o.T, atol=1e-11 * np.abs(o.T).max(), rtol=0)
+
+
+def test_id_row_f64():
+    A, k = small_f64()
+    r = curid.id_row(cuda(A), k)
+    o = O.id_row(np64(A), k)
+    assert list(npi(r.I)) == list(o.J)
+    np.testing.assert_allclose(np64(r.TW), o.T, atol=1e-11 * np.abs(o.T).max(), rtol=0)
+
+
+def test_tsid_f64():
+    A, k = small_f64()
+    r = curid.tsid(cuda(A), k)
+    o = O.tsid(np64(A), k)
+    assert list(npi(r.J)) == list(o.J)
+    assert list(npi(r.I)) == list(o.I)
+    np.testing.assert_allclose(np64(r.T), o.T, atol=1e-11 * np.abs(o.T).max(), rtol=0)
+    np.testing.assert_allclose(np64(r.TW), o.TW, atol=1e-11 * np.abs(o.TW).max(), rtol=0)
+
+
+def test_cur_f64():
+    A, k = small_f64()
+    r = curid.cur(cuda(A), k, want_c=True, want_r=True, want_t=True, want_tw=True)
+    o = O.cur(np64(A), k)
+    J, I = npi(r.J), npi(r.I)
+    assert list(J) == list(o.J) and list(I) == list(o.I)
+    Ah = np64(A)
+    # C and R are exact copies
+    assert np.array_equal(np64(r.C), Ah[:, J[:k]])
+    assert np.array_equal(np64(r.R), Ah[I[:k], :])
+    U = np64(r.U)
+    np.testing.assert_allclose(U, o.U, rtol=0, atol=1e-8 * np.abs(o.U).max())
+    eg = O.rel_err_fro(Ah, np64(r.C), U, np64(r.R))
+    eo = O.rel_err_fro(Ah, o.C, o.U, o.R)
+    assert abs(eg - eo) <= 1e-12, (eg, eo)
+
+
+def test_cur_exact_rank_f64():
+    A = syn.exact_rank(333, 257, 17, 23)
+    r = curid.cur(cuda(A), 17, want_c=True, want_r=True)
+    assert O.rel_err_fro(np64(A), np64(r.C), np64(r.U), np64(r.R)) <= 1e-12
+
+
+# --- randomized CUR ------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_randomized_cur_moderate(dtype):
+    m, n, k, p, q = 1500, 1100, 50, 10, 1
+    A = syn.spectrum_matrix(m, n, syn.power_decay(min(m, n)), 31, dtype)
+    Om = syn.gaussian(k + p, m, 32, dtype)
+    r = curid.cur(cuda(A), k, p=p, q=q, omega=cuda(Om), want_c=True, want_r=True, want_t=True)
+    o, _ = O.randomized_cur(np64(A), np64(Om), k, q=q)
+    Ah = np64(A)
+    J, I = npi(r.J), npi(r.I)
+    C, R, U, T = np64(r.C), np64(r.R), np64(r.U), np64(r.T)
+    assert np.array_equal(C, Ah[:, J[:k]]) and np.array_equal(R, Ah[I[:k], :])
+    eg = O.rel_err_fro(Ah, C, U, R)
+    eo = O.rel_err_fro(Ah, o.C, o.U, o.R)
+    # same skeleton: U against the FP64 least-squares U on the GPU's J, T, I
+    Uo = O.cur_middle(R, O.vstar(J, T, n))
+    e_same = O.rel_err_fro(Ah, C, Uo, R)
+    if dtype == torch.float64:
+        assert list(J) == list(o.J) and list(I) == list(o.I)
+        assert abs(eg - eo) <= 1e-12
+    else:
+        assert abs(eg - e_same) <= 1e-5, (eg, e_same)
+        assert eg <= 1.05 * eo, (eg, eo)
+
+
+def test_random_omega_generated_on_device():
+    m, n, k, p = 900, 700, 30, 10
+    A = syn.spectrum_matrix(m, n, syn.exp_decay(min(m, n), 6.0), 33)
+    r = curid.cur(cuda(A), k, p=p, q=1, seed=99, want_c=True, want_r=True)
+    Om = philox_gaussian(k + p, m, 99)
+    o, _ = O.randomized_cur(np64(A), Om, k, q=1)
+    assert list(npi(r.J)[:k]) == list(o.J[:k])
+    eg = O.rel_err_fro(np64(A), np64(r.C), np64(r.U), np64(r.R))
+    eo = O.rel_err_fro(np64(A), o.C, o.U, o.R)
+    assert abs(eg - eo) <= 1e-11
+
+
+# --- degenerate and invalid inputs -------------------------------------------------
+
+def test_rank_deficient_status():
+    A = syn.exact_rank(200, 150, 8, 41)
+    r = curid.id_col(cuda(A), 12)
+    assert r.status == 2 and r.k == 8
+    T = np64(r.T)
+    assert np.all(T[8:] == 0)
+    assert id_residual(A, npi(r.J), T, 12) <= 1e-12
+
+
+def test_nonfinite_input():
+    A = syn.spectrum_matrix(100, 80, syn.exp_decay(80), 42)
+    A[17, 33] = float("nan")
+    with pytest.raises(curid.CuridError) as e:
+        curid.id_col(cuda(A), 10)
+    assert e.value.status == 4
+
+
+def test_invalid_arguments():
+    A = cuda(syn.spectrum_matrix(50, 40, syn.exp_decay(40), 43))
+    with pytest.raises(curid.CuridError) as e:
+        curid.id_col(A, 41)
+    assert e.value.status == 1
+    with pytest.raises(curid.CuridError):
+        curid.cur(A, 10, p=40, q=0)          # k + p > min(m, n)
+    with pytest.raises(curid.CuridError):
+        curid.cur(A.double(), 5, p=5, tf32=True)  # TF32 needs float32
+
+
+def test_handworked_example_gpu():
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "handworked_2x3.json")))
+    A = torch.tensor(g["A"], dtype=torch.float64)
+    for key, k in (("k1", 1), ("k2", 2)):
+        r = curid.id_col(cuda(A), k)
+        assert list(npi(r.J)) == g[key]["J"]
+        np.testing.assert_allclose(np64(r.T), np.array(g[key]["T"]).reshape(k, -1)[:, :3 - k],
+                                   atol=1e-15)
