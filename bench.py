@@ -152,6 +152,10 @@ def phase_work(args, l):
         "cpqr_col": {"flops": 4.0 * l * n * k, "bytes": 4.0 * (l * n + k * n + n)},
         # CPQR of C^T (k x m), full k steps
         "cpqr_row": {"flops": 4.0 * k * m * k, "bytes": 4.0 * (2 * k * m + m)},
+        # one orthonormalisation pass of the l x max(m, n) sample (Gram, factor,
+        # apply): 2 l^2 c flops in the two products; the sample read twice,
+        # written once
+        "orth": {"flops": 4.0 * l * l * max(m, n), "bytes": 4.0 * 3 * l * max(m, n)},
     }
 
 
@@ -260,6 +264,16 @@ def run_ours(args, ws, rank, local):
             roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None, "kernel": "gemm_tf32 (tcgen05)",
                     "peak_source": f"{pk_kind} bf16 sustained x 1/2 (TF32 nominal ratio)"}
+        elif dominant == "orth":
+            # the phase interval covers all passes of one orthonormalisation
+            passes = 3
+            sm_mhz = pk.get("sm_max_mhz", 2070.0)
+            peak = NUM_SMS * FP32_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+            ach = passes * w["flops"] / dur_s / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None,
+                    "kernel": "orth (gemm_simt_kernel + chol_inverse_kernel), 3 passes",
+                    "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
         else:
             ach = w["bytes"] / dur_s / 1e9
             peak = pk["hbm_gbs"]

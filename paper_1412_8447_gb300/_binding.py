@@ -242,8 +242,9 @@ def cpqr(Y, k=0, tol=0.0, check=True):
     l, n = Y.shape
     k_max = k if k > 0 else min(l, n)
     dt = _dtype_code(Y.dtype)
-    h.prepare(workspace_bytes(h, dt, max(l, 1), n, min(k_max, l, n), _sketch(-1, 0, 0, None, 0))
-              if l >= 1 else 1 << 20)
+    # the workspace of a rank-1 deterministic decomposition of an l x n
+    # matrix contains the CPQR scratch for l x n
+    h.prepare(workspace_bytes(h, dt, max(l, 1), n, 1, _sketch(-1, 0, 0, None, 0)))
     J = torch.empty(n, dtype=torch.int32, device=Y.device)
     S = torch.zeros((k_max, n), dtype=Y.dtype, device=Y.device)
     _check(h.lib.curid_cpqr(h.h, dt, _ptr(Y), l, n, Y.stride(0), k, float(tol), _ptr(J), _ptr(S)),
