@@ -150,6 +150,34 @@ curid_status curid_cpqr(curid_handle* handle, curid_dtype dtype,
                         const void* Y, int64_t l, int64_t n, int64_t ldy,
                         int k, double tol, int32_t* J, void* S);
 
+/* Truncated CPQR exactly as curid_cpqr, for callers that cannot allocate
+ * device memory when they factor: a service that reserves all of its GPU
+ * memory at start-up and must not fail on an allocation later, code running
+ * inside a framework or memory pool that owns every device allocation and
+ * has no scratch buffer to lend, a plug-in with no access to the caller's
+ * allocator.  There is no counterpart in the paper; this is an interface
+ * convenience around the same kernel.
+ *   - No handle, no workspace, no cudaMalloc/cudaFree: the kernel's scratch
+ *     is a 4 MiB static device array that every GPU loading this library
+ *     keeps until the process exits.  Requests whose scratch exceeds it
+ *     (about 256 + 2 G (32 + 8 l) bytes for float64, 2 G (24 + 4 l) for
+ *     float32, G = min(number of SMs, n): on a 152-SM GPU l up to about
+ *     1700 rows in float64, 3400 in float32) return CURID_NO_WORKSPACE
+ *     before any work is enqueued.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address; make that first call before any stream
+ *     capture.
+ *   - Every call reuses the same array, so calls whose work overlaps on the
+ *     GPU (other streams, other host threads) race: serialise them.
+ *   - stream: a cudaStream_t passed as void*; Y, J, S as in curid_cpqr on
+ *     the current device; info (optional, device, 3 ints): status flags
+ *     (1 rank deficient, 2 breakdown, 4 non-finite input, 8 timed-out wait),
+ *     the number of steps taken, and the numerical rank. */
+curid_status curid_cpqr_static(void* stream, curid_dtype dtype,
+                               const void* Y, int64_t l, int64_t n,
+                               int64_t ldy, int k, double tol, int32_t* J,
+                               void* S, int* info);
+
 /* ----- the decompositions -------------------------------------------- */
 
 /* Rank selection of the decompositions below: k > 0 is a fixed rank

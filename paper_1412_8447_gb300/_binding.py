@@ -48,6 +48,7 @@ SIGNATURES = {
     "curid_gaussian": [_vp, _int, _i64, _i64, ctypes.c_uint64, _vp],
     "curid_sketch_matrix": [_vp, _int, _vp, _i64, _i64, _i64, _int, _int, _int, _vp, _vp],
     "curid_cpqr": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, _vp, _vp],
+    "curid_cpqr_static": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, _vp, _vp, _vp],
     "curid_id_col": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _i64],
     "curid_id_row": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _i64],
     "curid_tsid": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _i64, _vp,
