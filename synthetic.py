@@ -21,12 +21,12 @@ def rng(seed):
 
 
 def haar(m, r, g, device="cpu"):
-    """m x r matrix with orthonormal columns, Haar-distributed."""
-    G = torch.from_numpy(g.standard_normal((m, r))).to(device)
-    Q, R = torch.linalg.qr(G)
-    s = torch.sign(torch.diagonal(R))
+    """m x r matrix with orthonormal columns, Haar-distributed (numpy's
+    Householder QR on the host, then moved to ``device``)."""
+    Q, R = np.linalg.qr(g.standard_normal((m, r)))
+    s = np.sign(np.diag(R))
     s[s == 0] = 1.0
-    return Q * s
+    return torch.from_numpy(Q * s).to(device)
 
 
 def spectrum_matrix(m, n, sigma, seed, dtype=torch.float64, device="cpu"):
