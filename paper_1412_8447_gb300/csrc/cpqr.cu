@@ -5,18 +5,21 @@
 // are co-resident).  CTA b owns a contiguous slab of columns, held in shared
 // memory for the whole factorization, column-major with an odd stride so a
 // warp walking down a column is bank-conflict free.  A step j is:
-//   1. every CTA reads the G candidate records of step j (one per CTA: its
-//      largest residual column norm, that column's index, the sum of its
-//      squared residual norms) and picks the global pivot (largest norm,
-//      smallest index on ties) -- the records double as the grid barrier;
+//   1. warp 0 of every CTA reads the G candidate records of step j (one per
+//      CTA: its largest residual column norm, that column's index, the sum
+//      of its squared residual norms), all loads in flight together, and
+//      picks the global pivot (largest norm, smallest index on ties) -- the
+//      records double as the grid barrier;
 //   2. every CTA reads the pivot column (rows j..l-1) that its owner
 //      published and forms the same Householder reflector
 //      H = I - tau v v^T (v(j) = 1), mapping it to beta e_j;
 //   3. each warp applies H to one of the CTA's unselected columns and
 //      recomputes that column's residual norm from rows j+1..l-1 (no norm
 //      downdating, hence no cancellation to guard against);
-//   4. the CTA publishes its new local candidate for step j+1.
-// One grid-wide exchange per pivot step; no host round trip until the end.
+//   4. warp 0 publishes the CTA's new local candidate for step j+1 (one
+//      fence, one pair of 128-bit stores).
+// One grid-wide exchange and three CTA barriers per pivot step; no host
+// round trip until the end.
 // After the last step row i of S holds S1(i, c) for every original column c,
 // J lists the pivots and then the unselected columns in ascending order.
 #include "kernels.cuh"
@@ -25,13 +28,17 @@ namespace curid {
 
 namespace {
 
-template <typename real>
-struct Slot {
-  unsigned long long tag;  // (epoch << 32) | column (0xffffffff: no candidate)
-  real norm;
-  real sumsq;
-  int nonfinite;
-  int count;
+// Exchange record of one CTA for one step: four 64-bit words, each
+// (epoch << 32 | payload).  Every word carries the epoch, so a reader that
+// sees the current epoch in all four has a consistent record no matter in
+// which order the words became visible (each aligned 64-bit access is
+// single-copy atomic).  Payloads: w0 = candidate column (kNoCol: none,
+// kNonFinite: a non-finite norm was seen; the final exchange carries the
+// CTA's count of unselected columns), w1/w2 = candidate norm (float bits in
+// w1; float64 split high/low), w3 = sum of the CTA's squared residual norms
+// as float (adaptive stop only).
+struct alignas(32) Rec {
+  unsigned long long w[4];
 };
 
 template <typename real>
@@ -44,8 +51,8 @@ struct CpqrParams {
   int32_t* J;
   real* S;
   int64_t lds;
-  Slot<real>* slots;
-  real* slot_data;
+  Rec* recs;          // [2][G]
+  real* slot_data;    // [2][G][l]
   int* abort_flag;
   StatusBlock* status;
   int which;
@@ -54,6 +61,48 @@ struct CpqrParams {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned kNoCol = 0xffffffffu;
+constexpr unsigned kNonFinite = 0xfffffffeu;
+constexpr int kMaxSlotsPerLane = 8;  // G <= 256
+
+__device__ __forceinline__ unsigned long long pack(unsigned epoch, unsigned payload) {
+  return ((unsigned long long)epoch << 32) | payload;
+}
+
+template <typename real>
+__device__ __forceinline__ void norm_words(real v, unsigned* hi, unsigned* lo) {
+  if (sizeof(real) == 8) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong((double)v);
+    *hi = (unsigned)(b >> 32);
+    *lo = (unsigned)(b & 0xffffffffull);
+  } else {
+    *hi = __float_as_uint((float)v);
+    *lo = 0u;
+  }
+}
+
+template <typename real>
+__device__ __forceinline__ real words_norm(unsigned hi, unsigned lo) {
+  if (sizeof(real) == 8)
+    return (real)__longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+  return (real)__uint_as_float(hi);
+}
+
+__device__ __forceinline__ void st_rec(Rec* r, unsigned long long a, unsigned long long b,
+                                       unsigned long long c, unsigned long long d) {
+  asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(&r->w[0]), "l"(a), "l"(b)
+               : "memory");
+  asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(&r->w[2]), "l"(c), "l"(d)
+               : "memory");
+}
+
+__device__ __forceinline__ void ld_rec(const Rec* r, unsigned long long* w) {
+  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
+               : "=l"(w[0]), "=l"(w[1])
+               : "l"(&r->w[0]));
+  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
+               : "=l"(w[2]), "=l"(w[3])
+               : "l"(&r->w[2]));
+}
 
 template <typename real>
 __device__ __forceinline__ bool better(real na, unsigned ca, real nb, unsigned cb) {
@@ -65,25 +114,39 @@ __device__ __forceinline__ bool better(real na, unsigned ca, real nb, unsigned c
   return ca < cb;
 }
 
-// Poll the G records of buffer `bf` until all carry `epoch` (warp 0 only).
-// Returns false on timeout or abort.
+// Warp 0: wait until all G records of buffer `bf` carry `epoch`, keeping
+// their words.  Each lane polls up to kMaxSlotsPerLane records with all of
+// its loads in flight at once.  Returns false on timeout or abort.
 template <typename real>
-__device__ bool wait_epoch(const CpqrParams<real>& P, int bf, unsigned epoch) {
+__device__ bool gather_records(const CpqrParams<real>& P, int bf, unsigned epoch,
+                               unsigned long long (*w)[4]) {
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x;
+  const Rec* base = P.recs + (size_t)bf * G;
+  unsigned pending = 0;
+#pragma unroll
+  for (int r = 0; r < kMaxSlotsPerLane; ++r)
+    if (lane + 32 * r < G) pending |= 1u << r;
   bool ok = true;
   const long long t0 = clock64();
-  for (int s = lane; s < G && ok; s += 32) {
-    const unsigned long long* tp = &P.slots[bf * G + s].tag;
-    while (true) {
-      const unsigned long long t = ld_volatile_u64(tp);
-      if ((unsigned)(t >> 32) == epoch) break;
-      if (ld_volatile_i32(P.abort_flag)) { ok = false; break; }
-      if (clock64() - t0 > kSpinBudget) {
-        atomicExch(P.abort_flag, 1);
-        ok = false;
-        break;
-      }
+  while (pending) {
+#pragma unroll
+    for (int r = 0; r < kMaxSlotsPerLane; ++r)
+      if (pending & (1u << r)) ld_rec(base + lane + 32 * r, w[r]);
+#pragma unroll
+    for (int r = 0; r < kMaxSlotsPerLane; ++r) {
+      if (!(pending & (1u << r))) continue;
+      bool fresh = true;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) fresh &= (unsigned)(w[r][q] >> 32) == epoch;
+      if (fresh) pending &= ~(1u << r);
+    }
+    if (!pending) break;
+    if (ld_volatile_i32(P.abort_flag)) { ok = false; break; }
+    if (clock64() - t0 > kSpinBudget) {
+      atomicExch(P.abort_flag, 1);
+      ok = false;
+      break;
     }
   }
   ok = __all_sync(0xffffffffu, ok);
@@ -91,18 +154,17 @@ __device__ bool wait_epoch(const CpqrParams<real>& P, int bf, unsigned epoch) {
   return ok;
 }
 
+// Warp 0: pick the CTA's candidate (largest residual norm among its
+// unselected columns, smallest index on ties), copy its rows r0..l-1 to the
+// CTA's data slot, then publish the record of `epoch` in buffer `bf`.
 template <typename real>
 __device__ void publish(const CpqrParams<real>& P, const real* ys, const real* nrm,
-                        const int* active, int ncl, int c0, int r0, int bf, unsigned epoch,
-                        int* s_best, real* s_red, int* s_redi, int count) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+                        const int* active, int ncl, int c0, int r0, int bf, unsigned epoch) {
+  const int lane = threadIdx.x & 31;
   const int G = gridDim.x;
-  // local argmax over active columns; tie -> smallest index
-  real bn = real(-1);
-  int bi = -1;
-  real ss = real(0);
-  int nf = 0;
-  for (int lc = tid; lc < ncl; lc += kThreads) {
+  real bn = real(-1), ss = real(0);
+  int bi = -1, nf = 0;
+  for (int lc = lane; lc < ncl; lc += 32) {
     if (!active[lc]) continue;
     const real v = nrm[lc];
     if (!isfinite(v)) nf = 1;
@@ -117,45 +179,19 @@ __device__ void publish(const CpqrParams<real>& P, const real* ys, const real* n
     ss += __shfl_xor_sync(0xffffffffu, ss, o);
     nf |= __shfl_xor_sync(0xffffffffu, nf, o);
   }
-  if (lane == 0) {
-    s_red[warp] = bn;
-    s_red[kWarps + warp] = ss;
-    s_redi[warp] = bi;
-    s_redi[kWarps + warp] = nf;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    real b = real(-1), s = real(0);
-    int i = -1, f = 0;
-    for (int w = 0; w < kWarps; ++w) {
-      const int wi = s_redi[w];
-      if (wi >= 0 && (i < 0 || s_red[w] > b || (s_red[w] == b && wi < i))) { b = s_red[w]; i = wi; }
-      s += s_red[kWarps + w];
-      f |= s_redi[kWarps + w];
-    }
-    s_best[0] = i;
-    s_red[0] = b;
-    s_red[1] = s;
-    s_redi[0] = f;
-  }
-  __syncthreads();
-  const int best = s_best[0];
-  if (best >= 0) {
+  if (bi >= 0 && !nf) {
     real* dst = P.slot_data + ((int64_t)bf * G + blockIdx.x) * P.l;
-    const real* src = ys + (int64_t)best * P.ldl;
-    for (int r = r0 + tid; r < P.l; r += kThreads) dst[r] = src[r];
+    const real* src = ys + (int64_t)bi * P.ldl;
+    for (int r = r0 + lane; r < P.l; r += 32) dst[r] = src[r];
   }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    Slot<real>* sl = &P.slots[bf * G + blockIdx.x];
-    sl->norm = best >= 0 ? s_red[0] : real(0);
-    sl->sumsq = s_red[1];
-    sl->nonfinite = s_redi[0];
-    sl->count = count;
+  __syncwarp();
+  if (lane == 0) {
+    unsigned hi, lo;
+    norm_words<real>(bi >= 0 ? bn : real(0), &hi, &lo);
+    const unsigned col = nf ? kNonFinite : (bi >= 0 ? (unsigned)(c0 + bi) : kNoCol);
     __threadfence();
-    const unsigned col = best >= 0 ? (unsigned)(c0 + best) : kNoCol;
-    st_volatile_u64(&sl->tag, ((unsigned long long)epoch << 32) | col);
+    st_rec(P.recs + (size_t)bf * G + blockIdx.x, pack(epoch, col), pack(epoch, hi),
+           pack(epoch, lo), pack(epoch, __float_as_uint((float)ss)));
   }
 }
 
@@ -166,20 +202,17 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
   const int G = gridDim.x, b = blockIdx.x;
   const int nc = P.nc, ldl = P.ldl, l = P.l;
   real* ys = reinterpret_cast<real*>(smem_raw);
-  real* v = ys + (int64_t)nc * ldl;
-  real* nrm = v + ldl;
+  real* xv = ys + (int64_t)nc * ldl;
+  real* nrm = xv + ldl;
   int* active = reinterpret_cast<int*>(nrm + nc);
 
-  __shared__ int s_best[2];
-  __shared__ real s_red[2 * kWarps];
-  __shared__ int s_redi[2 * kWarps];
   __shared__ int s_stop, s_owner, s_col, s_prefix;
-  __shared__ real s_nu, s_total;
+  __shared__ real s_nu;
 
   const int c0 = b * nc;
   const int ncl = max(0, min(nc, P.n - c0));
 
-  // load the slab
+  // load the slab, column-major in shared memory
   for (int64_t e = tid; e < (int64_t)l * ncl; e += kThreads) {
     const int r = (int)(e / ncl), lc = (int)(e % ncl);
     ys[(int64_t)lc * ldl + r] = P.Y[(int64_t)r * P.ldy + c0 + lc];
@@ -194,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
     if (lane == 0) nrm[lc] = sqrt(s2);
   }
   __syncthreads();
-  publish(P, ys, nrm, active, ncl, c0, 0, 0, 1u, s_best, s_red, s_redi, 0);
+  if (warp == 0) publish(P, ys, nrm, active, ncl, c0, 0, 0, 1u);
 
   real normY = real(-1), nu_first = real(0);
   int k_eff = -1;
@@ -202,19 +235,23 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
   for (;; ++j) {
     const int bf = j & 1;
     if (warp == 0) {
-      const bool ok = wait_epoch(P, bf, (unsigned)(j + 1));
+      unsigned long long w[kMaxSlotsPerLane][4];
+      const bool ok = gather_records(P, bf, (unsigned)(j + 1), w);
       // global pivot and totals, identical in every CTA
       real bn = real(-1), tot = real(0);
       unsigned bc = kNoCol;
       int bo = -1, nf = 0;
       if (ok) {
-        for (int s = lane; s < G; s += 32) {
-          const Slot<real>* sl = &P.slots[bf * G + s];
-          const unsigned col = (unsigned)(ld_volatile_u64(&sl->tag) & 0xffffffffull);
-          const real nn = *reinterpret_cast<const volatile real*>(&sl->norm);
-          tot += *reinterpret_cast<const volatile real*>(&sl->sumsq);
-          nf |= *reinterpret_cast<const volatile int*>(&sl->nonfinite);
-          if (better(nn, col, bn, bc)) { bn = nn; bc = col; bo = s; }
+#pragma unroll
+        for (int r = 0; r < kMaxSlotsPerLane; ++r) {
+          const int s = lane + 32 * r;
+          if (s >= G) continue;
+          const unsigned col = (unsigned)(w[r][0] & 0xffffffffull);
+          const real nn = words_norm<real>((unsigned)(w[r][1] & 0xffffffffull),
+                                           (unsigned)(w[r][2] & 0xffffffffull));
+          tot += (real)__uint_as_float((unsigned)(w[r][3] & 0xffffffffull));
+          if (col == kNonFinite) nf = 1;
+          else if (better(nn, col, bn, bc)) { bn = nn; bc = col; bo = s; }
         }
       }
 #pragma unroll
@@ -244,7 +281,6 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
         s_owner = bo;
         s_col = (int)bc;
         s_nu = bn;
-        s_total = tot;
       }
     }
     __syncthreads();
@@ -256,50 +292,52 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
       k_eff = j;
       if (b == 0 && tid == 0) set_flag(&P.status->flags, FLAG_RANK_DEFICIENT);
     }
-    // pivot column rows j..l-1 from its owner
+    // pivot column rows j..l-1, as its owner published it
     const real* src = P.slot_data + ((int64_t)bf * G + owner) * l;
-    for (int r = j + tid; r < l; r += kThreads) v[r] = __ldcg(src + r);
+    for (int r = j + tid; r < l; r += kThreads) xv[r] = __ldcg(src + r);
     __syncthreads();
-    const real alpha = v[j];
+    // Householder reflector H = I - tau v v^T with v(j) = 1, v(r) = scale x(r):
+    // H x = beta e_j, beta = -sign(alpha) nu
+    const real alpha = xv[j];
     const real beta = alpha >= real(0) ? -nu : nu;
     real tau = real(0), scale = real(0);
     if (nu > real(0)) {
       tau = (beta - alpha) / beta;
       scale = real(1) / (alpha - beta);
     }
-    __syncthreads();
-    for (int r = j + 1 + tid; r < l; r += kThreads) v[r] *= scale;
-    if (tid == 0) v[j] = real(1);
-    if (b == owner) {
-      const int lc = pcol - c0;
-      real* y = ys + (int64_t)lc * ldl;
-      for (int r = j + tid; r < l; r += kThreads) y[r] = r == j ? beta : real(0);
-      if (tid == 0) {
-        active[lc] = 0;
-        P.J[j] = pcol;
-      }
-    }
-    __syncthreads();
     // apply H to every unselected local column, recompute its residual norm
+    // from rows j+1..l-1; the owner retires the pivot column
     for (int lc = warp; lc < ncl; lc += kWarps) {
       if (!active[lc]) continue;
       real* y = ys + (int64_t)lc * ldl;
+      if (c0 + lc == pcol) {
+        for (int r = j + lane; r < l; r += 32) y[r] = r == j ? beta : real(0);
+        if (lane == 0) {
+          active[lc] = 0;
+          P.J[j] = pcol;
+        }
+        continue;
+      }
       real d = real(0);
-      for (int r = j + lane; r < l; r += 32) d += v[r] * y[r];
+      for (int r = j + 1 + lane; r < l; r += 32) d += xv[r] * y[r];
       d = warp_sum(d);
-      const real w = tau * d;
+      const real wj = tau * (y[j] + scale * d);
+      const real ws = wj * scale;
       real s2 = real(0);
       for (int r = j + lane; r < l; r += 32) {
-        const real yr = y[r] - w * v[r];
-        y[r] = yr;
-        if (r > j) s2 += yr * yr;
+        if (r == j) {
+          y[r] -= wj;
+        } else {
+          const real yr = y[r] - ws * xv[r];
+          y[r] = yr;
+          s2 += yr * yr;
+        }
       }
       s2 = warp_sum(s2);
       if (lane == 0) nrm[lc] = sqrt(s2);
     }
     __syncthreads();
-    publish(P, ys, nrm, active, ncl, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2), s_best, s_red,
-            s_redi, 0);
+    if (warp == 0) publish(P, ys, nrm, active, ncl, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2));
   }
   const int k_done = j;
   if (s_stop == 2) return;  // timed out: leave without further waits
@@ -309,26 +347,29 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
     P.S[(int64_t)i * P.lds + c0 + lc] = ys[(int64_t)lc * ldl + i];
   }
   // unselected columns in ascending order after the pivots: exchange counts
-  int cnt = 0;
-  if (tid == 0)
-    for (int lc = 0; lc < ncl; ++lc) cnt += active[lc];
   const int fbf = (j + 1) & 1;
-  if (tid == 0) {
-    Slot<real>* sl = &P.slots[fbf * G + b];
-    sl->count = cnt;
-    __threadfence();
-    st_volatile_u64(&sl->tag, ((unsigned long long)(j + 2) << 32) | kNoCol);
-  }
+  const unsigned fep = (unsigned)(j + 2);
   if (warp == 0) {
-    const bool ok = wait_epoch(P, fbf, (unsigned)(j + 2));
+    int cnt = 0;
+    for (int lc = lane; lc < ncl; lc += 32) cnt += active[lc];
+    cnt = warp_sum(cnt);
+    if (lane == 0) {
+      __threadfence();
+      st_rec(P.recs + (size_t)fbf * G + b, pack(fep, (unsigned)cnt), pack(fep, 0u), pack(fep, 0u),
+             pack(fep, 0u));
+    }
+    unsigned long long w[kMaxSlotsPerLane][4];
+    const bool ok = gather_records(P, fbf, fep, w);
     int pre = 0;
-    if (ok)
-      for (int s = lane; s < b; s += 32)
-        pre += *reinterpret_cast<const volatile int*>(&P.slots[fbf * G + s].count);
+    if (ok) {
+#pragma unroll
+      for (int r = 0; r < kMaxSlotsPerLane; ++r)
+        if (lane + 32 * r < b) pre += (int)(w[r][0] & 0xffffffffull);
+    }
     pre = warp_sum(pre);
     if (lane == 0) {
       s_prefix = pre;
-      s_stop = ok ? 0 : 1;
+      s_stop = ok ? 0 : 2;
       if (!ok) set_flag(&P.status->flags, FLAG_TIMEOUT);
     }
   }
@@ -360,7 +401,7 @@ size_t cpqr_smem_bytes(int nc, int ldl) {
 template <typename real>
 curid_status cpqr_plan(const Ctx& ctx, int64_t l, int64_t n, int* grid, size_t* smem) {
   if (l <= 0 || n <= 0) return CURID_INVALID_ARG;
-  int G = (int)std::min<int64_t>(ctx.num_sms, n);
+  int G = (int)std::min<int64_t>(std::min(ctx.num_sms, 32 * kMaxSlotsPerLane), n);
   const int nc = (int)((n + G - 1) / G);
   G = (int)((n + nc - 1) / nc);
   const int ldl = (int)(l | 1);
@@ -374,7 +415,7 @@ curid_status cpqr_plan(const Ctx& ctx, int64_t l, int64_t n, int* grid, size_t* 
 template <typename real>
 void cpqr_carve(Carver& cv, int grid, int64_t l, CpqrScratch* s) {
   s->grid = grid;
-  s->slots = cv.take<Slot<real>>(2 * (size_t)grid);
+  s->slots = cv.take<Rec>(2 * (size_t)grid);
   s->slot_data = cv.take<real>(2 * (size_t)grid * l);
   s->counts = cv.take<int>(grid);
   s->abort_flag = cv.take<int>(1);
@@ -404,12 +445,12 @@ curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64
   P.J = J;
   P.S = S;
   P.lds = lds;
-  P.slots = static_cast<Slot<real>*>(s.slots);
+  P.recs = static_cast<Rec*>(s.slots);
   P.slot_data = static_cast<real*>(s.slot_data);
   P.abort_flag = s.abort_flag;
   P.status = ctx.status;
   P.which = which;
-  CURID_CUDA(cudaMemsetAsync(s.slots, 0, 2 * (size_t)G * sizeof(Slot<real>), ctx.stream));
+  CURID_CUDA(cudaMemsetAsync(s.slots, 0, 2 * (size_t)G * sizeof(Rec), ctx.stream));
   CURID_CUDA(cudaMemsetAsync(s.abort_flag, 0, sizeof(int), ctx.stream));
   auto fn = cpqr_kernel<real>;
   CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

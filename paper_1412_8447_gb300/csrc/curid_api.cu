@@ -147,7 +147,7 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
   P->Sinv = cv.take<real>((size_t)k * k);
   P->T = cv.take<real>((size_t)k * std::max<int64_t>(1, n - k));
   upd(k, n - k, k);
-  if (!upper_tri_inverse_fits<real>(ctx, k)) return CURID_UNSUPPORTED;
+  if (!tri_solve_fits<real>(ctx, k)) return CURID_UNSUPPORTED;
   if (d.randomized && d.q > 0 && !chol_inverse_fits<real>(ctx, l)) return CURID_UNSUPPORTED;
   if (op == Op::Tsid || op == Op::Cur) {
     P->Ct = cv.take<real>((size_t)k * m);
@@ -211,9 +211,8 @@ curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t 
   for (int pass = 0; pass < passes; ++pass) {
     CURID_TRY(gemm<real>(ctx, false, true, r, r, c, real(1), *X, c, *X, c, real(0), P.G, r,
                          P.partial, P.partial_cap));
-    CURID_TRY(chol_inverse<real>(ctx, P.G, (int)r, pass == 0 ? shift : 0.0, P.Linv));
-    CURID_TRY(gemm<real>(ctx, false, false, r, c, r, real(1), P.Linv, r, *X, c, real(0), *tmp, c,
-                         P.partial, P.partial_cap));
+    CURID_TRY(cholesky<real>(ctx, P.G, (int)r, pass == 0 ? shift : 0.0));
+    CURID_TRY(tri_solve<real>(ctx, (int)r, P.G, r, false, false, *X, c, *tmp, c, c, nullptr));
     std::swap(*X, *tmp);
   }
   return CURID_OK;
@@ -263,16 +262,14 @@ curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const 
   return CURID_OK;
 }
 
-// T = S11^{-1} S12 (Eq. (2.8)) from S (k x n, original column order) and J.
+// T = S11^{-1} S12 (Eq. (2.8)) from S (k x n, original column order) and J:
+// a blocked back substitution on the n - k columns of S12.
 template <typename real>
 curid_status t_solve(const Ctx& ctx, const real* S, int64_t n, const int32_t* J, int k,
-                     const int* k_eff, real* S11, real* S12, real* Sinv, real* T, int64_t ldt,
-                     const Plan<real>& P) {
+                     const int* k_eff, real* S11, real* S12, real* T, int64_t ldt) {
   CURID_TRY(split_s<real>(ctx, S, n, J, k, n, S11, S12));
-  CURID_TRY(upper_tri_inverse<real>(ctx, S11, k, k_eff, Sinv));
   if (n - k > 0)
-    CURID_TRY(gemm<real>(ctx, false, false, k, n - k, k, real(1), Sinv, k, S12, n - k, real(0),
-                         T, ldt, P.partial, P.partial_cap));
+    CURID_TRY(tri_solve<real>(ctx, k, S11, k, true, false, S12, n - k, T, ldt, n - k, k_eff));
   return CURID_OK;
 }
 
@@ -329,8 +326,7 @@ curid_status run(curid_handle* h, Op op, const real* A, const Dims& d, double to
   int64_t ldt = (T == P.T) ? std::max<int64_t>(1, n - k) : o.ldt;
   {
     PhaseScope ps(h, CURID_PHASE_T);
-    CURID_TRY(t_solve<real>(ctx, P.S, n, o.J, k, &P.status->k_eff, P.S11, P.S12, P.Sinv, T, ldt,
-                            P));
+    CURID_TRY(t_solve<real>(ctx, P.S, n, o.J, k, &P.status->k_eff, P.S11, P.S12, T, ldt));
     if (o.T && T == P.T)
       CURID_TRY(copy2d<real>(ctx, P.T, ldt, static_cast<real*>(o.T), o.ldt, k, n - k));
   }
@@ -350,12 +346,13 @@ curid_status run(curid_handle* h, Op op, const real* A, const Dims& d, double to
   }
   PhaseScope ps_u(h, CURID_PHASE_U);
   if (o.TW) {
-    CURID_TRY(t_solve<real>(ctx, P.SW, m, I, k, &P.status->k_row, P.SW11, P.SW12, P.SWinv,
-                            static_cast<real*>(o.TW), o.ldtw, P));
+    CURID_TRY(t_solve<real>(ctx, P.SW, m, I, k, &P.status->k_row, P.SW11, P.SW12,
+                            static_cast<real*>(o.TW), o.ldtw));
   } else {
     CURID_TRY(split_s<real>(ctx, P.SW, m, I, k, m, P.SW11, P.SW12));
-    CURID_TRY(upper_tri_inverse<real>(ctx, P.SW11, k, &P.status->k_row, P.SWinv));
   }
+  if (op == Op::Cur)
+    CURID_TRY(upper_tri_inverse<real>(ctx, P.SW11, k, &P.status->k_row, P.SWinv));
   if (op == Op::Tsid) return CURID_OK;
 
   // ---- U = V* R^+ (Eq. (3.5), Algorithm 3 line 3) ----

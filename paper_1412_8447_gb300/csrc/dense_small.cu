@@ -1,111 +1,126 @@
-// Small dense factorizations, one CTA with the matrix resident in shared
-// memory:
-//   * inverse of the upper-triangular S11 for T = S11^{-1} S12 (Eq. (2.8));
-//   * Cholesky factor of a (shifted) Gram matrix and the inverse of that
-//     factor, the building block of the row orthonormalisation between
-//     power steps (Section 5.3) and of the pseudo-inverse R^+ in
-//     U = V* R^+ (Eq. (3.5)).
-// Both inverses run the same right-looking, in-place scheme: step t fixes
-// row t of the inverse's diagonal and column, then folds row t of the
-// triangle into every later column; all (i, j) of a step run in parallel.
+// Small dense factorizations of order <= 256:
+//   * Cholesky factor of a (shifted) Gram matrix, the building block of the
+//     row orthonormalisation between power steps (Section 5.3) and of the
+//     pseudo-inverse R^+ in U = V* R^+ (Eq. (3.5)); one CTA, the matrix in
+//     shared memory;
+//   * explicit inverses of triangles through the blocked triangular solve
+//     (tri.cu) with an identity right-hand side;
+//   * the float64-accumulated product that ends the U chain.
 #include "kernels.cuh"
 
 namespace curid {
 
 namespace {
 
-constexpr int kSmallThreads = 1024;
-
-// In-place inverse of the upper triangle of a (k x k, row stride ld) for
-// rows/columns < kk; everything at or after kk is set to zero.
-// On entry the strictly upper part and diagonal hold U; on exit they hold
-// U^{-1} (upper triangular).  Uses `row` (k reals) as scratch.
-template <typename real>
-__device__ void inv_upper_inplace(real* a, int k, int ld, int kk, real* row) {
-  const int tid = threadIdx.x;
-  for (int t = 0; t < kk; ++t) {
-    // finalize column t: X[t][t] = 1/U[t][t]; X[i][t] = -acc[i][t] * X[t][t]
-    __syncthreads();
-    const real d = real(1) / a[t * ld + t];
-    for (int i = tid; i < t; i += kSmallThreads) a[i * ld + t] = -a[i * ld + t] * d;
-    for (int j = t + 1 + tid; j < kk; j += kSmallThreads) row[j] = a[t * ld + j];
-    __syncthreads();
-    if (tid == 0) a[t * ld + t] = d;
-    __syncthreads();
-    // acc[i][j] += X[i][t] * U[t][j] for i <= t < j  (acc[t][j] starts at 0)
-    const int rows = t + 1, cols = kk - t - 1;
-    for (int e = tid; e < rows * cols; e += kSmallThreads) {
-      const int i = e / cols, j = t + 1 + e % cols;
-      const real x = a[i * ld + t];
-      const real prev = i == t ? real(0) : a[i * ld + j];
-      a[i * ld + j] = prev + x * row[j];
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < k * k; e += kSmallThreads) {
-    const int i = e / k, j = e % k;
-    if (i >= kk || j >= kk || j < i) a[i * ld + j] = real(0);
-  }
-  __syncthreads();
-}
-
+constexpr int kSmallThreads = 512;  // 128 registers per thread for the block loops
+constexpr int kSmallWarps = kSmallThreads / 32;
+// Cholesky factor of G + shift I, blocked right-looking on 32 x 32 blocks,
+// the matrix padded to a multiple of 32 with an identity tail so no block
+// needs bounds checks.  Per block column: warp 0 factors the diagonal block
+// (lanes = rows) and inverts it (lanes = columns); every warp then finishes
+// panel rows A21 <- A21 L11^{-T} with shuffles; the trailing update
+// A22 -= A21 A21^T is spread one 32 x 32 block per warp.  The lower factor
+// overwrites G (upper part zeroed).  A non-positive or non-finite pivot
+// retries with a 100x larger shift (4 attempts), then FLAG_BREAKDOWN.
 template <typename real>
 __global__ void __launch_bounds__(kSmallThreads, 1)
-upper_tri_inverse_kernel(const real* __restrict__ S11, int k, const int* __restrict__ k_eff,
-                         real* __restrict__ X) {
+chol_kernel(real* __restrict__ G, int l, real rel_shift, StatusBlock* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int LP = (l + 31) & ~31;
+  const int ld = LP + 1;
+  const int nb = LP / 32;
   real* a = reinterpret_cast<real*>(smem_raw);
-  real* row = a + (int64_t)k * k;
-  const int kk = k_eff ? min(k, *k_eff) : k;
-  for (int e = threadIdx.x; e < k * k; e += kSmallThreads) a[e] = S11[e];
-  inv_upper_inplace(a, k, k, kk, row);
-  for (int e = threadIdx.x; e < k * k; e += kSmallThreads) X[e] = a[e];
-}
-
-// Cholesky of G + shift I, lower factor L in the lower triangle of a, then
-// Linv = L^{-1} written (lower triangular) to out.  Retries with a 100x
-// larger shift (up to 3 times) on a non-positive pivot; FLAG_BREAKDOWN if
-// every attempt fails.
-template <typename real>
-__global__ void __launch_bounds__(kSmallThreads, 1)
-chol_inverse_kernel(const real* __restrict__ G, int l, real rel_shift, real* __restrict__ out,
-                    StatusBlock* status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  real* a = reinterpret_cast<real*>(smem_raw);
-  real* row = a + (int64_t)l * l;
+  real* W = a + (size_t)LP * ld;  // 32 x 33 inverse of the current diagonal block
   __shared__ int s_fail;
-  __shared__ real s_d;
-  const int tid = threadIdx.x;
-  real tr = real(0);
-  for (int i = 0; i < l; ++i) tr += G[(int64_t)i * l + i];
+  __shared__ real s_tr;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) {
+    real tr = real(0);
+    for (int i = lane; i < l; i += 32) tr += G[(int64_t)i * l + i];
+    tr = warp_sum(tr);
+    if (lane == 0) s_tr = tr;
+  }
+  __syncthreads();
+  const real tr = s_tr;
   real shift = rel_shift * tr;
   bool done = false;
   for (int attempt = 0; attempt < 4 && !done; ++attempt) {
-    __syncthreads();
-    // a := G + shift I (the factorization reads and writes the lower triangle)
-    for (int e = tid; e < l * l; e += kSmallThreads) {
-      const int i = e / l, j = e % l;
-      a[e] = G[e] + (i == j ? shift : real(0));
+    for (int e = tid; e < LP * LP; e += kSmallThreads) {
+      const int i = e / LP, j = e % LP;
+      real v;
+      if (i < l && j < l) v = G[(int64_t)i * l + j] + (i == j ? shift : real(0));
+      else v = i == j ? real(1) : real(0);
+      a[i * ld + j] = v;
     }
     if (tid == 0) s_fail = 0;
     __syncthreads();
-    // right-looking Cholesky on the lower triangle (rows i >= column j)
-    for (int j = 0; j < l; ++j) {
-      if (tid == 0) {
-        const real d = a[j * l + j];
-        if (!(d > real(0)) || !isfinite(d)) s_fail = 1;
-        s_d = d > real(0) ? sqrt(d) : real(1);
-        a[j * l + j] = s_d;
+    for (int kb = 0; kb < LP; kb += 32) {
+      if (warp == 0) {
+        // (1) factor the diagonal block; lane i owns row kb + i
+        real* Dk = a + kb * ld + kb;
+        int fail = 0;
+        for (int j = 0; j < 32; ++j) {
+          real d = Dk[j * ld + j];
+          if (!(d > real(0)) || !isfinite(d)) fail = 1;
+          d = fail ? real(1) : sqrt(d);
+          __syncwarp();
+          if (lane == j) Dk[j * ld + j] = d;
+          real lij = real(0);
+          if (lane > j) {
+            lij = Dk[lane * ld + j] / d;
+            Dk[lane * ld + j] = lij;
+          }
+          __syncwarp();
+          if (lane > j)
+            for (int t = j + 1; t <= lane; ++t) Dk[lane * ld + t] -= lij * Dk[t * ld + j];
+          __syncwarp();
+        }
+        // (1b) W = L11^{-1}; lane c computes column c
+        real x[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          real sum = i == lane ? real(1) : real(0);
+#pragma unroll
+          for (int t = 0; t < i; ++t) sum -= Dk[i * ld + t] * x[t];
+          x[i] = i >= lane ? sum / Dk[i * ld + i] : real(0);
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) W[i * 33 + lane] = x[i];
+        if (lane == 0) s_fail = fail;
       }
       __syncthreads();
       if (s_fail) break;
-      const real inv = real(1) / s_d;
-      for (int i = j + 1 + tid; i < l; i += kSmallThreads) a[i * l + j] *= inv;
+      // (2) panel rows below: A21(i, c) <- sum_{s <= c} A21(i, s) W(c, s)
+      for (int i = kb + 32 + warp; i < LP; i += kSmallWarps) {
+        const real ais = a[i * ld + kb + lane];
+        real out = real(0);
+#pragma unroll
+        for (int s2 = 0; s2 < 32; ++s2) {
+          const real v = __shfl_sync(0xffffffffu, ais, s2);
+          out += v * W[lane * 33 + s2];
+        }
+        a[i * ld + kb + lane] = out;
+      }
       __syncthreads();
-      const int w = l - j - 1;
-      for (int e = tid; e < w * w; e += kSmallThreads) {
-        const int i = j + 1 + e / w, t = j + 1 + e % w;
-        if (t <= i) a[i * l + t] -= a[i * l + j] * a[t * l + j];
+      // (3) trailing update, one 32 x 32 block (bi >= bj > kb) per warp
+      const int b0 = kb / 32 + 1;
+      const int m = nb - b0;
+      const int nblocks = m * (m + 1) / 2;
+      for (int q = warp; q < nblocks; q += kSmallWarps) {
+        int bi = 0;
+        while ((bi + 1) * (bi + 2) / 2 <= q) ++bi;
+        const int bj = q - bi * (bi + 1) / 2;
+        const int i0 = (b0 + bi) * 32, j0 = (b0 + bj) * 32;
+        real col[32];
+#pragma unroll
+        for (int s2 = 0; s2 < 32; ++s2) col[s2] = a[(j0 + lane) * ld + kb + s2];
+        for (int r = 0; r < 32; ++r) {
+          const real* ar = a + (i0 + r) * ld + kb;
+          real sum = real(0);
+#pragma unroll
+          for (int s2 = 0; s2 < 32; ++s2) sum += ar[s2] * col[s2];
+          a[(i0 + r) * ld + j0 + lane] -= sum;
+        }
       }
       __syncthreads();
     }
@@ -113,24 +128,16 @@ chol_inverse_kernel(const real* __restrict__ G, int l, real rel_shift, real* __r
     if (!s_fail) done = true;
     shift = shift > real(0) ? shift * real(100)
                             : tr * (sizeof(real) == 8 ? real(1e-13) : real(1e-5));
+    __syncthreads();
   }
   if (!done) {
     if (tid == 0) set_flag(&status->flags, FLAG_BREAKDOWN);
-    for (int e = tid; e < l * l; e += kSmallThreads) out[e] = (e / l == e % l) ? real(1) : real(0);
+    for (int e = tid; e < l * l; e += kSmallThreads) G[e] = (e / l == e % l) ? real(1) : real(0);
     return;
   }
-  // transpose the factor into the upper triangle: U = L^T, invert, transpose back
-  __syncthreads();
   for (int e = tid; e < l * l; e += kSmallThreads) {
     const int i = e / l, j = e % l;
-    if (j > i) a[e] = a[j * l + i];
-  }
-  __syncthreads();
-  inv_upper_inplace(a, l, l, l, row);
-  // (L^{-1}) = (U^{-1})^T
-  for (int e = tid; e < l * l; e += kSmallThreads) {
-    const int i = e / l, j = e % l;
-    out[e] = a[j * l + i];
+    G[e] = j <= i ? a[i * ld + j] : real(0);
   }
 }
 
@@ -161,44 +168,44 @@ __global__ void gemm_nt_f64acc_kernel(int M, int N, int K, const real* __restric
 }
 
 template <typename real>
-size_t small_smem(int k) {
-  return (size_t)k * k * sizeof(real) + (size_t)k * sizeof(real);
+size_t chol_smem(int l) {
+  const int LP = (l + 31) & ~31;
+  return ((size_t)LP * (LP + 1) + 32 * 33) * sizeof(real);
 }
 
 }  // namespace
 
 template <typename real>
 bool upper_tri_inverse_fits(const Ctx& ctx, int k) {
-  return small_smem<real>(k) <= ctx.smem_optin;
+  return tri_solve_fits<real>(ctx, k);
 }
 template <typename real>
 bool chol_inverse_fits(const Ctx& ctx, int l) {
-  return small_smem<real>(l) <= ctx.smem_optin;
+  return l <= 256 && chol_smem<real>(l) <= ctx.smem_optin && tri_solve_fits<real>(ctx, l);
 }
 
 template <typename real>
 curid_status upper_tri_inverse(const Ctx& ctx, const real* S11, int k, const int* k_eff,
                                real* X) {
-  if (k <= 0) return CURID_OK;
-  const size_t smem = small_smem<real>(k);
-  if (smem > ctx.smem_optin) return CURID_UNSUPPORTED;
-  auto fn = upper_tri_inverse_kernel<real>;
+  return tri_solve<real>(ctx, k, S11, k, true, false, nullptr, 0, X, k, k, k_eff);
+}
+
+template <typename real>
+curid_status cholesky(const Ctx& ctx, real* G, int l, double rel_shift) {
+  if (l <= 0) return CURID_OK;
+  if (!chol_inverse_fits<real>(ctx, l)) return CURID_UNSUPPORTED;
+  const size_t smem = chol_smem<real>(l);
+  auto fn = chol_kernel<real>;
   CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  fn<<<1, kSmallThreads, smem, ctx.stream>>>(S11, k, k_eff, X);
+  fn<<<1, kSmallThreads, smem, ctx.stream>>>(G, l, (real)rel_shift, ctx.status);
   CURID_LAUNCHED(ctx);
   return CURID_OK;
 }
 
 template <typename real>
-curid_status chol_inverse(const Ctx& ctx, const real* G, int l, double rel_shift, real* Linv) {
-  if (l <= 0) return CURID_OK;
-  const size_t smem = small_smem<real>(l);
-  if (smem > ctx.smem_optin) return CURID_UNSUPPORTED;
-  auto fn = chol_inverse_kernel<real>;
-  CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  fn<<<1, kSmallThreads, smem, ctx.stream>>>(G, l, (real)rel_shift, Linv, ctx.status);
-  CURID_LAUNCHED(ctx);
-  return CURID_OK;
+curid_status chol_inverse(const Ctx& ctx, real* G, int l, double rel_shift, real* Linv) {
+  CURID_TRY(cholesky<real>(ctx, G, l, rel_shift));
+  return tri_solve<real>(ctx, l, G, l, false, false, nullptr, 0, Linv, l, l, nullptr);
 }
 
 template <typename real>
@@ -224,7 +231,9 @@ template bool chol_inverse_fits<double>(const Ctx&, int);
 template curid_status upper_tri_inverse<float>(const Ctx&, const float*, int, const int*, float*);
 template curid_status upper_tri_inverse<double>(const Ctx&, const double*, int, const int*,
                                                 double*);
-template curid_status chol_inverse<float>(const Ctx&, const float*, int, double, float*);
-template curid_status chol_inverse<double>(const Ctx&, const double*, int, double, double*);
+template curid_status cholesky<float>(const Ctx&, float*, int, double);
+template curid_status cholesky<double>(const Ctx&, double*, int, double);
+template curid_status chol_inverse<float>(const Ctx&, float*, int, double, float*);
+template curid_status chol_inverse<double>(const Ctx&, double*, int, double, double*);
 
 }  // namespace curid

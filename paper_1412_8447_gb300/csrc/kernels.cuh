@@ -68,10 +68,23 @@ curid_status upper_tri_inverse(const Ctx& ctx, const real* S11, int k, const int
                                real* X);
 template <typename real>
 bool upper_tri_inverse_fits(const Ctx& ctx, int k);
-// Cholesky of G + shift*I (shift = rel_shift * trace(G)) and inverse of
-// the factor: Linv (l x l, lower triangular).  Breakdown -> FLAG_BREAKDOWN.
+// Cholesky of G + shift*I (shift = rel_shift * trace(G)); the lower factor
+// L overwrites G.  Breakdown -> FLAG_BREAKDOWN.
 template <typename real>
-curid_status chol_inverse(const Ctx& ctx, const real* G, int l, double rel_shift, real* Linv);
+curid_status cholesky(const Ctx& ctx, real* G, int l, double rel_shift);
+// cholesky() then Linv = L^{-1} (l x l, lower triangular); G holds L after.
+template <typename real>
+curid_status chol_inverse(const Ctx& ctx, real* G, int l, double rel_shift, real* Linv);
+// Solve op(T) X = B (T k x k row-major with leading dimension ldt, upper or
+// lower, op = transpose when trans) for N columns; B == nullptr means the
+// identity (X = op(T)^{-1}).  Rows/columns at or after *kk (if given) are
+// an identity block with zero right-hand side.  X must not alias T or B.
+template <typename real>
+curid_status tri_solve(const Ctx& ctx, int k, const real* T, int64_t ldt, bool upper, bool trans,
+                       const real* B, int64_t ldb, real* X, int64_t ldx, int64_t N,
+                       const int* kk);
+template <typename real>
+bool tri_solve_fits(const Ctx& ctx, int k);
 template <typename real>
 bool chol_inverse_fits(const Ctx& ctx, int l);
 // C (float64) = A B^T with float64 accumulation; A M x K, B N x K.

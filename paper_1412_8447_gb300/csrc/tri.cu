@@ -1,0 +1,232 @@
+// Blocked triangular solve op(T) X = B for many right-hand sides.
+//
+// Used for every triangular step of the path: the T solve S11 T = S12
+// (Eq. (2.8)), the applies X <- L^{-1} X of the Cholesky-QR row
+// orthonormalisation (Section 5.3), the preconditioning S_W11^{-T} R and
+// the explicit inverses of the U = V* R^+ chain (Eq. (3.5)).
+//
+// One CTA solves for NC columns of X with the whole triangle resident in
+// shared memory, stored as 32 x 32 blocks of its lower triangle (upper or
+// transposed inputs are loaded through an index map: an upper triangle with
+// rows and columns reversed is lower).  The CTA first inverts its diagonal
+// blocks (one warp per block, one lane per column), then sweeps the block
+// rows: X_b = D_b^{-1} (B_b - sum_{t<b} L_bt X_t), each thread holding two
+// rows of NC / 32 columns.  Rows and columns at or after the numerical rank kk
+// are treated as an identity block with a zero right-hand side, so the
+// solution is zero there (the singular S11 case of Section 2.3).
+#include "kernels.cuh"
+
+namespace curid {
+
+namespace {
+
+constexpr int kTB = 32;           // block order
+constexpr int kTriThreads = 512;   // 16 warps; each owns rows w and w + 16 of a block
+constexpr int kTriLd = kTB + 1;   // padded block row
+
+template <typename real>
+struct TriCols;
+template <>
+struct TriCols<float> {
+  static constexpr int NC = 64;
+};
+template <>
+struct TriCols<double> {
+  static constexpr int NC = 32;
+};
+
+__host__ __device__ inline int packed_block(int bi, int bj) { return bi * (bi + 1) / 2 + bj; }
+
+template <typename real>
+struct TriParams {
+  int k, nb;
+  const real* T;
+  int64_t ldt;
+  bool trans, reverse;  // op: element (i, j) of the lower triangle used
+  const real* B;        // nullptr: identity right-hand side
+  int64_t ldb;
+  real* X;
+  int64_t ldx;
+  int64_t N;
+  const int* kk;        // numerical rank (device) or nullptr
+};
+
+// lower-triangle element (i, j), i >= j, in the solve's index space, read
+// from the caller's triangle
+template <typename real>
+__device__ __forceinline__ real tri_elem(const TriParams<real>& P, int i, int j, int kk) {
+  const int oi = P.reverse ? P.k - 1 - i : i;
+  const int oj = P.reverse ? P.k - 1 - j : j;
+  if (oi >= kk || oj >= kk || i >= P.k) return i == j ? real(1) : real(0);
+  return P.trans ? P.T[(int64_t)oj * P.ldt + oi] : P.T[(int64_t)oi * P.ldt + oj];
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kTriThreads, 1) tri_solve_kernel(TriParams<real> P) {
+  constexpr int NC = TriCols<real>::NC;
+  constexpr int CPT = NC / 32;  // columns per thread
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nb = P.nb;
+  const int KP = nb * kTB;
+  real* Ls = reinterpret_cast<real*>(smem_raw);                 // packed blocks, 32 x 33
+  real* Xs = Ls + (size_t)packed_block(nb, 0) * kTB * kTriLd;  // KP x NC
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int kk = P.kk ? max(0, min(P.k, *P.kk)) : P.k;
+  const int64_t c0 = (int64_t)blockIdx.x * NC;
+
+  // triangle -> packed lower blocks (identity past k and past the rank)
+  const int nblk = packed_block(nb, 0);
+  for (int e = tid; e < nblk * kTB * kTB; e += kTriThreads) {
+    const int blk = e / (kTB * kTB), w = e % (kTB * kTB);
+    int bi = 0;
+    while (packed_block(bi + 1, 0) <= blk) ++bi;
+    const int bj = blk - packed_block(bi, 0);
+    const int r = w / kTB, c = w % kTB;
+    const int i = bi * kTB + r, j = bj * kTB + c;
+    real v = real(0);
+    if (j <= i) v = tri_elem(P, i, j, kk);
+    Ls[(size_t)blk * kTB * kTriLd + r * kTriLd + c] = v;
+  }
+  // right-hand side columns c0..c0+NC (identity when B is null)
+  for (int e = tid; e < KP * NC; e += kTriThreads) {
+    const int i = e / NC, c = e % NC;
+    const int64_t col = c0 + c;
+    const int oi = P.reverse ? P.k - 1 - i : i;
+    real v = real(0);
+    if (i < P.k && oi < kk && col < P.N)
+      v = P.B ? P.B[(int64_t)oi * P.ldb + col] : (oi == col ? real(1) : real(0));
+    Xs[i * NC + c] = v;
+  }
+  __syncthreads();
+  // invert each diagonal block: warp b, lane j solves D x = e_j
+  if (warp < nb) {
+    real* D = Ls + (size_t)packed_block(warp, warp) * kTB * kTriLd;
+    real x[kTB];
+#pragma unroll
+    for (int i = 0; i < kTB; ++i) {
+      real s = i == lane ? real(1) : real(0);
+#pragma unroll
+      for (int t = 0; t < i; ++t) s -= D[i * kTriLd + t] * x[t];
+      x[i] = i >= lane ? s / D[i * kTriLd + i] : real(0);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < kTB; ++i) D[i * kTriLd + lane] = x[i];
+  }
+  __syncthreads();
+  // block-row sweep; warp w owns rows w and w + 16 of each block
+  const int rA = warp, rB = warp + 16;
+  for (int b = 0; b < nb; ++b) {
+    real acc[2][CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      acc[0][q] = Xs[(b * kTB + rA) * NC + lane + 32 * q];
+      acc[1][q] = Xs[(b * kTB + rB) * NC + lane + 32 * q];
+    }
+    for (int t = 0; t < b; ++t) {
+      const real* Lbt = Ls + (size_t)packed_block(b, t) * kTB * kTriLd;
+      const real* Xt = Xs + (t * kTB) * NC;
+#pragma unroll 8
+      for (int s = 0; s < kTB; ++s) {
+        const real la = Lbt[rA * kTriLd + s], lb = Lbt[rB * kTriLd + s];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+          const real x = Xt[s * NC + lane + 32 * q];
+          acc[0][q] -= la * x;
+          acc[1][q] -= lb * x;
+        }
+      }
+    }
+    // X_b = D_b^{-1} acc: stage acc, then multiply
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      Xs[(b * kTB + rA) * NC + lane + 32 * q] = acc[0][q];
+      Xs[(b * kTB + rB) * NC + lane + 32 * q] = acc[1][q];
+    }
+    __syncthreads();
+    const real* D = Ls + (size_t)packed_block(b, b) * kTB * kTriLd;
+    real out[2][CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) out[0][q] = out[1][q] = real(0);
+#pragma unroll 8
+    for (int s = 0; s <= rB; ++s) {
+      const real da = s <= rA ? D[rA * kTriLd + s] : real(0), db = D[rB * kTriLd + s];
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) {
+        const real x = Xs[(b * kTB + s) * NC + lane + 32 * q];
+        out[0][q] += da * x;
+        out[1][q] += db * x;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      Xs[(b * kTB + rA) * NC + lane + 32 * q] = out[0][q];
+      Xs[(b * kTB + rB) * NC + lane + 32 * q] = out[1][q];
+    }
+    __syncthreads();
+  }
+  // store (rows at and after the rank are zero already)
+  for (int e = tid; e < P.k * NC; e += kTriThreads) {
+    const int i = e / NC, c = e % NC;
+    const int64_t col = c0 + c;
+    if (col >= P.N) continue;
+    const int oi = P.reverse ? P.k - 1 - i : i;
+    P.X[(int64_t)oi * P.ldx + col] = Xs[i * NC + c];
+  }
+}
+
+template <typename real>
+size_t tri_smem(int k) {
+  const int nb = (k + kTB - 1) / kTB;
+  return ((size_t)packed_block(nb, 0) * kTB * kTriLd + (size_t)nb * kTB * TriCols<real>::NC) *
+         sizeof(real);
+}
+
+}  // namespace
+
+template <typename real>
+bool tri_solve_fits(const Ctx& ctx, int k) {
+  return k > 0 && (k + kTB - 1) / kTB <= kTriThreads / 32 && tri_smem<real>(k) <= ctx.smem_optin;
+}
+
+template <typename real>
+curid_status tri_solve(const Ctx& ctx, int k, const real* T, int64_t ldt, bool upper, bool trans,
+                       const real* B, int64_t ldb, real* X, int64_t ldx, int64_t N,
+                       const int* kk) {
+  if (k <= 0 || N <= 0) return CURID_OK;
+  if (!tri_solve_fits<real>(ctx, k)) return CURID_UNSUPPORTED;
+  TriParams<real> P;
+  P.k = k;
+  P.nb = (k + kTB - 1) / kTB;
+  P.T = T;
+  P.ldt = ldt;
+  // op(T) is lower when (lower and not transposed) or (upper and transposed);
+  // otherwise reverse the order of rows and columns to make it lower.
+  P.trans = trans;
+  P.reverse = upper != trans;
+  P.B = B;
+  P.ldb = ldb;
+  P.X = X;
+  P.ldx = ldx;
+  P.N = N;
+  P.kk = kk;
+  const size_t smem = tri_smem<real>(k);
+  auto fn = tri_solve_kernel<real>;
+  CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t grid = (N + TriCols<real>::NC - 1) / TriCols<real>::NC;
+  fn<<<(unsigned)grid, kTriThreads, smem, ctx.stream>>>(P);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
+template bool tri_solve_fits<float>(const Ctx&, int);
+template bool tri_solve_fits<double>(const Ctx&, int);
+template curid_status tri_solve<float>(const Ctx&, int, const float*, int64_t, bool, bool,
+                                       const float*, int64_t, float*, int64_t, int64_t,
+                                       const int*);
+template curid_status tri_solve<double>(const Ctx&, int, const double*, int64_t, bool, bool,
+                                        const double*, int64_t, double*, int64_t, int64_t,
+                                        const int*);
+
+}  // namespace curid
