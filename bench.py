@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--k", type=int, default=K)
     ap.add_argument("--p", type=int, default=P)
     ap.add_argument("--q", type=int, default=Q)
-    ap.add_argument("--tf32", type=int, default=0)
+    ap.add_argument("--tf32", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()

@@ -201,6 +201,14 @@ def profile_read(device=0):
             {p: calls[i] for i, p in enumerate(PHASES)}, launches.value)
 
 
+def status_block(device=0):
+    """The raw device status block of the last call (synchronises): flags,
+    k_done, k_eff, k_row, timeout site."""
+    h = handle(device)
+    torch.cuda.synchronize(device)
+    return h.ws[:20].view(torch.int32).cpu().tolist() if h.ws is not None else None
+
+
 def last_status(device=0):
     """(status, k) recorded by the last call on ``device`` (synchronises)."""
     return handle(device).status()
@@ -225,8 +233,7 @@ def sketch_matrix(A, omega, q=0, tf32=False):
     m, n = A.shape
     l = omega.shape[0]
     dt = _dtype_code(A.dtype)
-    h.prepare(workspace_bytes(h, dt, m, n, max(1, min(l, m, n)),
-                              _sketch(max(0, l - 1), q, 0, omega, tf32)))
+    h.prepare(workspace_bytes(h, dt, m, n, 1, _sketch(max(0, l - 1), q, 0, omega, tf32)))
     Y = torch.empty((l, n), dtype=A.dtype, device=A.device)
     _check(h.lib.curid_sketch_matrix(h.h, dt, _ptr(A), m, n, A.stride(0), l, q,
                                      1 if tf32 else 0, _ptr(omega.contiguous()), _ptr(Y)),

@@ -25,7 +25,8 @@ struct StatusBlock {
   int k_done;     // CPQR steps taken by the column CPQR
   int k_eff;      // numerical rank (k_out reported to the caller)
   int k_row;      // rank found by the row CPQR (row ID of C)
-  int pad[60];
+  int timeout_site;  // first wait that timed out: (role << 24) | (stage << 16) | iteration
+  int pad[59];
 };
 static_assert(sizeof(StatusBlock) == 256, "status block is 256 bytes");
 

@@ -102,11 +102,14 @@ struct Plan {
   size_t bytes = 0;
 };
 
+inline int64_t pad4(int64_t x) { return (x + 3) & ~int64_t(3); }
+
 struct Dims {
   int64_t m, n, lda;
   int k, l;
   bool randomized;
   int q;
+  bool tf32 = false;
 };
 
 template <typename real>
@@ -121,12 +124,19 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
     part = std::max(part, gemm_partial_elems<real>(M, N, K, ctx.num_sms));
   };
   if (d.randomized) {
-    if (gen_omega) P->omega = cv.take<real>((size_t)l * m);
+    // Omega is kept with a leading dimension padded to 4 elements (16 bytes,
+    // what the tensor-core loads require) when it is generated, or copied
+    // when a caller's Omega is misaligned for them.
+    if (gen_omega || (d.tf32 && (m & 3))) P->omega = cv.take<real>((size_t)l * pad4(m));
     upd(l, n, m);
+    if (d.tf32) {
+      part = std::max(part, gemm_tf32_partial_elems(l, n, m, ctx.num_sms));
+      part = std::max(part, gemm_tf32_partial_elems(l, m, n, ctx.num_sms));
+    }
     if (d.q == 0) {
-      P->B[0] = cv.take<real>((size_t)l * n);
+      P->B[0] = cv.take<real>((size_t)l * pad4(n));
     } else {
-      for (int b = 0; b < 3; ++b) P->B[b] = cv.take<real>((size_t)l * std::max(m, n));
+      for (int b = 0; b < 3; ++b) P->B[b] = cv.take<real>((size_t)l * pad4(std::max(m, n)));
       P->G = cv.take<real>((size_t)l * l);
       P->Linv = cv.take<real>((size_t)l * l);
       upd(l, l, n);
@@ -204,15 +214,15 @@ curid_status a_product(const Ctx& ctx, bool tf32, bool tb, int64_t M, int64_t N,
 // 1/eps; the later passes restore orthonormality.  Each pass writes out of
 // place; on return *X points at the result and *tmp at the other buffer.
 template <typename real>
-curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c,
+curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
                        const Plan<real>& P) {
   const int passes = 3;
   const double shift = sizeof(real) == 4 ? 1e-5 : 1e-13;
   for (int pass = 0; pass < passes; ++pass) {
-    CURID_TRY(gemm<real>(ctx, false, true, r, r, c, real(1), *X, c, *X, c, real(0), P.G, r,
+    CURID_TRY(gemm<real>(ctx, false, true, r, r, c, real(1), *X, ld, *X, ld, real(0), P.G, r,
                          P.partial, P.partial_cap));
     CURID_TRY(cholesky<real>(ctx, P.G, (int)r, pass == 0 ? shift : 0.0));
-    CURID_TRY(tri_solve<real>(ctx, (int)r, P.G, r, false, false, *X, c, *tmp, c, c, nullptr));
+    CURID_TRY(tri_solve<real>(ctx, (int)r, P.G, r, false, false, *X, ld, *tmp, ld, c, nullptr));
     std::swap(*X, *tmp);
   }
   return CURID_OK;
@@ -220,11 +230,13 @@ curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t 
 
 // Sample matrix of Algorithm 4 with the power scheme of Section 5.3:
 // (2a) Y = Omega A; for i = 1..q: (2c) Y <- orth(Y) A^*, (2d) Y <- orth(Y) A.
-// Returns the buffer holding the final Y (l x n, leading dimension n).
+// Returns the buffer holding the final Y (l x n, leading dimension
+// pad4(n)); Omega has leading dimension ldo.
 template <typename real>
 curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const real* A,
                     int64_t m, int64_t n, int64_t lda, int l, int q, bool tf32, const real* Om,
-                    real** Yout) {
+                    int64_t ldo, real** Yout) {
+  const int64_t ldy = pad4(n), ldz = pad4(m);
   auto other = [&](const real* a, const real* b) -> real* {
     for (int i = 0; i < 3; ++i)
       if (P.B[i] != a && P.B[i] != b) return P.B[i];
@@ -233,28 +245,28 @@ curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const 
   real* cur = P.B[0];
   {
     PhaseScope ps(h, CURID_PHASE_SKETCH);
-    CURID_TRY(a_product<real>(ctx, tf32, false, l, n, m, Om, m, A, lda, cur, n, P));
+    CURID_TRY(a_product<real>(ctx, tf32, false, l, n, m, Om, ldo, A, lda, cur, ldy, P));
   }
   for (int i = 0; i < q; ++i) {
     real* t = other(cur, nullptr);
     {
       PhaseScope ps(h, CURID_PHASE_ORTH);
-      CURID_TRY(orth_rows<real>(ctx, &cur, &t, l, n, P));
+      CURID_TRY(orth_rows<real>(ctx, &cur, &t, l, n, ldy, P));
     }
     real* z = other(cur, nullptr);
     {
       PhaseScope ps(h, CURID_PHASE_SKETCH);
-      CURID_TRY(a_product<real>(ctx, tf32, true, l, m, n, cur, n, A, lda, z, m, P));
+      CURID_TRY(a_product<real>(ctx, tf32, true, l, m, n, cur, ldy, A, lda, z, ldz, P));
     }
     real* zt = other(z, nullptr);
     {
       PhaseScope ps(h, CURID_PHASE_ORTH);
-      CURID_TRY(orth_rows<real>(ctx, &z, &zt, l, m, P));
+      CURID_TRY(orth_rows<real>(ctx, &z, &zt, l, m, ldz, P));
     }
     real* y = other(z, nullptr);
     {
       PhaseScope ps(h, CURID_PHASE_SKETCH);
-      CURID_TRY(a_product<real>(ctx, tf32, false, l, n, m, z, m, A, lda, y, n, P));
+      CURID_TRY(a_product<real>(ctx, tf32, false, l, n, m, z, ldz, A, lda, y, ldy, P));
     }
     cur = y;
   }
@@ -305,16 +317,22 @@ curid_status run(curid_handle* h, Op op, const real* A, const Dims& d, double to
   int64_t ly = m, ldy = lda;
   if (d.randomized) {
     const real* Om = static_cast<const real*>(sk.omega);
+    int64_t ldo = m;
     if (gen_omega) {
       PhaseScope ps(h, CURID_PHASE_OMEGA);
-      CURID_TRY(gaussian_fill<real>(ctx, l, m, sk.seed, P.omega));
+      CURID_TRY(gaussian_fill<real>(ctx, l, m, sk.seed, P.omega, pad4(m)));
       Om = P.omega;
+      ldo = pad4(m);
+    } else if (P.omega) {
+      CURID_TRY(copy2d<real>(ctx, Om, m, P.omega, pad4(m), l, m));
+      Om = P.omega;
+      ldo = pad4(m);
     }
     real* Yr;
-    CURID_TRY(sketch<real>(h, ctx, P, A, m, n, lda, l, d.q, sk.tf32 != 0, Om, &Yr));
+    CURID_TRY(sketch<real>(h, ctx, P, A, m, n, lda, l, d.q, sk.tf32 != 0, Om, ldo, &Yr));
     Y = Yr;
     ly = l;
-    ldy = n;
+    ldy = pad4(n);
   }
 
   // ---- truncated CPQR and T (Algorithm 1 / 4) ----
@@ -412,6 +430,7 @@ curid_status check_common(curid_handle* h, curid_dtype dt, const void* A, int64_
   d->randomized = sk.p >= 0;
   d->l = d->randomized ? k + sk.p : (int)m;
   d->q = sk.q;
+  d->tf32 = sk.tf32 != 0;
   if (d->randomized && d->l > std::min(m, n)) return CURID_INVALID_ARG;
   if (!d->randomized && sk.q > 0) return CURID_INVALID_ARG;
   return CURID_OK;
@@ -552,8 +571,9 @@ curid_status curid_gaussian(curid_handle* handle, curid_dtype dtype, int64_t row
   return dispatch(handle, [&]() -> curid_status {
     Ctx ctx = make_ctx(handle);
     PhaseScope ps(handle, CURID_PHASE_OMEGA);
-    if (dtype == CURID_F64) return gaussian_fill<double>(ctx, rows, cols, seed, (double*)out);
-    if (dtype == CURID_F32) return gaussian_fill<float>(ctx, rows, cols, seed, (float*)out);
+    if (dtype == CURID_F64)
+      return gaussian_fill<double>(ctx, rows, cols, seed, (double*)out, cols);
+    if (dtype == CURID_F32) return gaussian_fill<float>(ctx, rows, cols, seed, (float*)out, cols);
     return CURID_INVALID_ARG;
   });
 }
@@ -567,7 +587,7 @@ curid_status curid_sketch_matrix(curid_handle* handle, curid_dtype dtype, const 
   if (tf32 && dtype != CURID_F32) return CURID_INVALID_ARG;
   return dispatch(handle, [&]() -> curid_status {
     Ctx ctx = make_ctx(handle);
-    Dims d{m, n, lda, 1, l, true, q};
+    Dims d{m, n, lda, 1, l, true, q, tf32 != 0};
     auto go = [&](auto tag) -> curid_status {
       using real = decltype(tag);
       Plan<real> P;
@@ -576,10 +596,18 @@ curid_status curid_sketch_matrix(curid_handle* handle, curid_dtype dtype, const 
       CURID_TRY(make_plan<real>(ctx, Op::IdCol, d, false, false, handle->ws, &P));
       ctx.status = P.status;
       CURID_CUDA(cudaMemsetAsync(P.status, 0, sizeof(StatusBlock), ctx.stream));
+      const real* Om = static_cast<const real*>(omega);
+      int64_t ldo = m;
+      if (tf32 && (m & 3)) {
+        // caller's Omega rows are not 16-byte aligned: copy with a padded stride
+        CURID_TRY(copy2d<real>(ctx, Om, m, P.omega, pad4(m), l, m));
+        Om = P.omega;
+        ldo = pad4(m);
+      }
       real* cur;
       CURID_TRY(sketch<real>(handle, ctx, P, static_cast<const real*>(A), m, n, lda, l, q,
-                             tf32 != 0, static_cast<const real*>(omega), &cur));
-      return copy2d<real>(ctx, cur, n, static_cast<real*>(Y), n, l, n);
+                             tf32 != 0, Om, ldo, &cur));
+      return copy2d<real>(ctx, cur, pad4(n), static_cast<real*>(Y), n, l, n);
     };
     if (dtype == CURID_F64) return go(double{});
     if (dtype == CURID_F32) return go(float{});

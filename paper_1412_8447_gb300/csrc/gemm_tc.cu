@@ -1,15 +1,458 @@
-// Tensor-core (tcgen05, TF32 operands, FP32 accumulation) products of the
-// randomized front end.  Placeholder until the kernel lands: reports the
-// request as unsupported so callers that ask for TF32 get a clear status.
+// Products with the data matrix A on the 5th-generation tensor cores
+// (tcgen05, TMEM accumulators, TMA loads): C = X A or C = X A^T, where X is
+// the l x K sketch operand (Omega, or an orthonormal basis Q, Section 5.3)
+// and A the m x n data matrix.
+//
+// Precision: A is split in shared memory into an exactly-truncated TF32 high
+// part and the FP32 remainder, A = A_hi + A_lo, and each K-step issues two
+// TF32 MMAs, X A_hi + X A_lo, with FP32 accumulation.  X itself is read as
+// TF32.  Rounding A to TF32 alone adds a noise floor of about 2^-11 |A| to
+// every singular direction and costs the skeleton up to 8 % in residual on
+// the sigma_j = j^-2 workload; the split keeps the sample matrix at FP32
+// quality (an orthonormal or Gaussian X rounded to TF32 only perturbs
+// directions that the sample already spans).
+//
+// Tiling: the transposed product D = C^T is computed, so the MMA's M = 128
+// rows are 128 output columns and its N = l (<= 256, rounded up to 16) is
+// the whole sample: one CTA holds a 128 x l accumulator in TMEM and streams
+// its 128 columns of A exactly once over its K range.  K is split across
+// CTAs when the column tiles alone cannot fill the GPU; partial tiles are
+// summed in a fixed order.  Warp 0 issues TMA loads, warp 1 the MMAs,
+// warps 4-7 split A into hi/lo per stage and run the epilogue
+// (TMEM -> registers -> coalesced stores of C).  Both MMA operands are
+// K-major: for C = X A, where A's rows run along K, the TMA brings an
+// MN-major tile and the same warps transpose it into K-major hi/lo tiles
+// while splitting.  Every mbarrier wait is
+// bounded; a timeout raises FLAG_TIMEOUT and the CTA drains and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace curid {
 
-curid_status gemm_tf32(const Ctx&, bool, bool, int64_t, int64_t, int64_t, const float*, int64_t,
-                       const float*, int64_t, float*, int64_t, float*, size_t) {
-  return CURID_UNSUPPORTED;
+namespace {
+
+constexpr int kBM = 128;            // MMA M: output columns per CTA
+constexpr int kBK = 32;             // K per stage: 32 FP32 = one 128-byte swizzle row
+constexpr int kStages = 3;
+constexpr int kTcThreads = 256;
+constexpr int kAtileBytes = kBM * kBK * 4;  // 16 KB
+constexpr int kTmemCols = 256;
+
+struct TcParams {
+  int M;         // rows of C (= l), MMA N before rounding
+  int NP;        // M rounded up to 16
+  int N;         // columns of C
+  int K;
+  int kchunk;    // K per split, multiple of kBK
+  int mn_major;  // 1: C = X A (A read MN-major); 0: C = X A^T (K-major)
+  float* C;
+  int64_t ldc;
+  float* partial;  // [splits][M][N] when K is split
+  StatusBlock* status;
+  uint32_t idesc;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-size_t gemm_tf32_partial_elems(int64_t, int64_t, int64_t, int) { return 0; }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kSpinBudget) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading and
+// stride byte offsets (all >> 4), descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+tc_sketch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
+                 TcParams P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
+  const int xbytes = ((P.NP * 128 + 1023) / 1024) * 1024;
+  unsigned char* Ahi[kStages];
+  unsigned char* Alo[kStages];
+  unsigned char* Xs[kStages];
+  unsigned char* p = reinterpret_cast<unsigned char*>(base);
+  for (int s = 0; s < kStages; ++s) {
+    Ahi[s] = p;
+    Alo[s] = p + kAtileBytes;
+    Xs[s] = p + 2 * kAtileBytes;
+    p += 2 * kAtileBytes + xbytes;
+  }
+  uint64_t* bars = reinterpret_cast<uint64_t*>(p);  // full[S], conv[S], empty[S], acc
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto conv = [&](int s) { return smem_u32(bars + kStages + s); };
+  auto empty = [&](int s) { return smem_u32(bars + 2 * kStages + s); };
+  const uint32_t acc_bar = smem_u32(bars + 3 * kStages);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * kBM;
+  const int kbeg = blockIdx.y * P.kchunk;
+  const int kend = min(P.K, kbeg + P.kchunk);
+  const int nk = (kend - kbeg + kBK - 1) / kBK;
+  const uint32_t xtile_bytes = (uint32_t)P.NP * 128u;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(conv(s), 128);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(acc_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer: TMA loads of A and X per stage ----
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+    int issued = 0;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kStages;
+      const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+      if (i >= kStages && !mbar_wait(empty(s), ph ^ 1u)) {
+        *abort_flag = 1;
+        atomicCAS(&P.status->timeout_site, 0, (1 << 24) | (s << 16) | i);
+        break;
+      }
+      if (*abort_flag) break;
+      mbar_expect_tx(full(s), (uint32_t)kAtileBytes + xtile_bytes);
+      const int k = kbeg + i * kBK;
+      if (P.mn_major) {
+        // raw MN-major tile into the lo buffer; the converter transposes it
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          tma_load_2d(smem_u32(Alo[s] + j * 4096), &tmA, n0 + 32 * j, k, full(s));
+      } else {
+        tma_load_2d(smem_u32(Ahi[s]), &tmA, k, n0, full(s));
+      }
+      tma_load_2d(smem_u32(Xs[s]), &tmX, k, 0, full(s));
+      issued = i + 1;
+    }
+    if (*abort_flag) {
+      // let every load this thread issued land before the CTA can exit
+      for (int i = max(0, issued - kStages); i < issued; ++i)
+        mbar_wait(full(i % kStages), (uint32_t)(i / kStages) & 1u);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kStages;
+      const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+      if (!mbar_wait(conv(s), ph) || *abort_flag) {
+        *abort_flag = 1;
+        atomicCAS(&P.status->timeout_site, 0, (2 << 24) | (s << 16) | i);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ah = smem_u32(Ahi[s]), al = smem_u32(Alo[s]), xb = smem_u32(Xs[s]);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 8; ++kk) {
+        // K-major tiles: 128 rows of 128 bytes, 8 K elements = 32 bytes per MMA
+        const uint64_t dh = smem_desc(ah + kk * 32, 16, 1024);
+        const uint64_t dl = smem_desc(al + kk * 32, 16, 1024);
+        const uint64_t dx = smem_desc(xb + kk * 32, 16, 1024);
+        mma_tf32(tmem, dh, dx, P.idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, dl, dx, P.idesc, 1u);
+      }
+      mma_commit(empty(s));
+    }
+    mma_commit(acc_bar);
+  } else if (warp >= 4) {
+    // ---- split A into hi / lo, then the epilogue ----
+    const int t = threadIdx.x - 128;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kStages;
+      const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+      if (!mbar_wait(full(s), ph) || *abort_flag) {
+        *abort_flag = 1;
+        atomicCAS(&P.status->timeout_site, 0, (3 << 24) | (s << 16) | i);
+        break;
+      }
+      if (P.mn_major) {
+        // The TMA tile is MN-major: four 4 KB boxes, box j holding columns
+        // 32j..32j+31 as 32 K rows of 128 swizzled bytes.  Thread t takes
+        // output column t: it gathers its 32 K values into registers, then
+        // (after all 128 threads have read the raw tile, which is reused for
+        // the low part) writes the row t of the K-major hi and lo tiles.
+        const unsigned char* raw = Alo[s];
+        float v[kBK];
+#pragma unroll
+        for (int k = 0; k < kBK; ++k) {
+          const int off = (t >> 5) * 4096 + k * 128 + ((((t & 31) >> 2) ^ (k & 7)) << 4) + ((t & 3) << 2);
+          v[k] = *reinterpret_cast<const float*>(raw + off);
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < kBK / 4; ++c) {
+          float4 h, w;
+          h.x = __uint_as_float(__float_as_uint(v[4 * c + 0]) & 0xFFFFE000u);
+          h.y = __uint_as_float(__float_as_uint(v[4 * c + 1]) & 0xFFFFE000u);
+          h.z = __uint_as_float(__float_as_uint(v[4 * c + 2]) & 0xFFFFE000u);
+          h.w = __uint_as_float(__float_as_uint(v[4 * c + 3]) & 0xFFFFE000u);
+          w = make_float4(v[4 * c + 0] - h.x, v[4 * c + 1] - h.y, v[4 * c + 2] - h.z,
+                          v[4 * c + 3] - h.w);
+          const int off = t * 128 + ((c ^ (t & 7)) << 4);
+          *reinterpret_cast<float4*>(Ahi[s] + off) = h;
+          *reinterpret_cast<float4*>(Alo[s] + off) = w;
+        }
+      } else {
+        // K-major tile: split in place (hi over the loaded data, lo beside it)
+        float4* hi = reinterpret_cast<float4*>(Ahi[s]);
+        float4* lo = reinterpret_cast<float4*>(Alo[s]);
+#pragma unroll
+        for (int q = 0; q < kAtileBytes / 16 / 128; ++q) {
+          const int idx = t + 128 * q;
+          const float4 v = hi[idx];
+          float4 h;
+          h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+          h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+          h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+          h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+          hi[idx] = h;
+          lo[idx] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(conv(s));
+    }
+    // warp-uniform decision before the warp-collective TMEM loads
+    int ok = 0;
+    if (lane == 0) {
+      ok = mbar_wait(acc_bar, 0) ? 1 : 0;
+      if (!ok) {
+        *abort_flag = 1;
+        atomicCAS(&P.status->timeout_site, 0, 4 << 24);
+      }
+      ok = ok && !*abort_flag;
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const int q = warp - 4;             // TMEM lanes 32q .. 32q+31
+      const int col = n0 + q * 32 + lane;  // output column of this thread
+      float* dst = P.partial ? P.partial + (size_t)blockIdx.y * P.M * P.N : P.C;
+      const int64_t ld = P.partial ? P.N : P.ldc;
+      for (int c0 = 0; c0 < P.NP; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+        if (col < P.N) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < P.M) dst[(int64_t)(c0 + j) * ld + col] = __uint_as_float(r[j]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) set_flag(&P.status->flags, FLAG_TIMEOUT);
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+__global__ void tc_reduce_kernel(int M, int N, int splits, const float* __restrict__ partial,
+                                 float* __restrict__ C, int64_t ldc) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += partial[(int64_t)z * total + e];
+    C[(e / N) * ldc + e % N] = s;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool get_encoder() {
+  std::call_once(g_encode_once, []() {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  return g_encode != nullptr;
+}
+
+// 2-D FP32 tensor map, 128-byte swizzle, box {32, rows}
+bool make_map(CUtensorMap* map, const float* ptr, uint64_t inner, uint64_t outer, int64_t ld,
+              uint32_t box_rows) {
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {32, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int tc_splits(int64_t N, int64_t K, int num_sms) {
+  const int64_t tiles = (N + kBM - 1) / kBM;
+  int64_t s = std::max<int64_t>(1, num_sms / std::max<int64_t>(1, tiles));
+  s = std::min<int64_t>(s, std::max<int64_t>(1, K / (8 * kBK)));
+  return (int)s;
+}
+
+size_t tc_smem(int NP) {
+  const int xbytes = ((NP * 128 + 1023) / 1024) * 1024;
+  return 1024 + (size_t)kStages * (2 * kAtileBytes + xbytes) + (3 * kStages + 1) * 8 + 16;
+}
+
+}  // namespace
+
+size_t gemm_tf32_partial_elems(int64_t M, int64_t N, int64_t K, int num_sms) {
+  const int s = tc_splits(N, K, num_sms);
+  return s > 1 ? (size_t)s * M * N : 0;
+}
+
+curid_status gemm_tf32(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
+                       const float* X, int64_t ldx, const float* A, int64_t lda, float* C,
+                       int64_t ldc, float* partial, size_t partial_cap) {
+  if (ta || M <= 0 || M > 256 || N <= 0 || K <= 0) return CURID_UNSUPPORTED;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(A) & 15) ||
+      (ldx & 3) || (lda & 3))
+    return CURID_UNSUPPORTED;
+  if (!get_encoder()) return CURID_CUDA_ERROR;
+  const int NP = (int)((M + 15) / 16 * 16);
+  CUtensorMap mapA, mapX;
+  const bool mn = !tb;
+  // C = X A: A is K x N (rows k, columns n), box {32 columns, 32 rows};
+  // C = X A^T: A is N x K, box {32 K, 128 rows}.
+  if (!(mn ? make_map(&mapA, A, (uint64_t)N, (uint64_t)K, lda, 32)
+           : make_map(&mapA, A, (uint64_t)K, (uint64_t)N, lda, kBM)))
+    return CURID_CUDA_ERROR;
+  if (!make_map(&mapX, X, (uint64_t)K, (uint64_t)M, ldx, (uint32_t)NP)) return CURID_CUDA_ERROR;
+  int splits = tc_splits(N, K, ctx.num_sms);
+  if (splits > 1 && (!partial || (size_t)splits * M * N > partial_cap)) splits = 1;
+  const int kchunk = (int)(((K + splits - 1) / splits + kBK - 1) / kBK * kBK);
+  splits = (int)((K + kchunk - 1) / kchunk);
+  TcParams P;
+  P.M = (int)M;
+  P.NP = NP;
+  P.N = (int)N;
+  P.K = (int)K;
+  P.kchunk = kchunk;
+  P.mn_major = mn ? 1 : 0;
+  P.C = C;
+  P.ldc = ldc;
+  P.partial = splits > 1 ? partial : nullptr;
+  P.status = ctx.status;
+  // instruction descriptor: FP32 accumulator, TF32 A and B, both K-major,
+  // N >> 3, M >> 4
+  P.idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NP >> 3) << 17) |
+            ((uint32_t)(kBM >> 4) << 24);
+  const size_t smem = tc_smem(NP);
+  if (smem > ctx.smem_optin) return CURID_UNSUPPORTED;
+  CURID_CUDA(cudaFuncSetAttribute(tc_sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  dim3 grid((unsigned)((N + kBM - 1) / kBM), (unsigned)splits);
+  tc_sketch_kernel<<<grid, kTcThreads, smem, ctx.stream>>>(mapA, mapX, P);
+  CURID_LAUNCHED(ctx);
+  if (splits > 1) {
+    const int64_t total = M * N;
+    const unsigned blocks =
+        (unsigned)std::min<int64_t>((total + 255) / 256, 8LL * ctx.num_sms);
+    tc_reduce_kernel<<<blocks, 256, 0, ctx.stream>>>((int)M, (int)N, splits, partial, C, ldc);
+    CURID_LAUNCHED(ctx);
+  }
+  return CURID_OK;
+}
 
 }  // namespace curid

@@ -117,7 +117,7 @@ curid_status add_transpose(const Ctx& ctx, const real* src, int64_t lds, real* d
 
 // ---- random numbers (philox.cu) --------------------------------------------
 template <typename real>
-curid_status gaussian_fill(const Ctx& ctx, int64_t rows, int64_t cols, uint64_t seed,
-                           real* out);
+curid_status gaussian_fill(const Ctx& ctx, int64_t rows, int64_t cols, uint64_t seed, real* out,
+                           int64_t ld);
 
 }  // namespace curid

@@ -8,7 +8,8 @@
 // rounds.  Words are mapped to uniforms in (0, 1] on a 2^-24 grid and paired
 // by the Box-Muller transform.  Element e of the row-major matrix uses
 // counter (e / 4, 0, 0, 0) and word e % 4: words (0, 1) give the cosine and
-// sine branch of one pair, words (2, 3) of the next.
+// sine branch of one pair, words (2, 3) of the next.  Element e = r*cols + c
+// is stored at out[r*ld + c].
 #include "kernels.cuh"
 
 namespace curid {
@@ -32,7 +33,8 @@ __device__ __forceinline__ double u01(unsigned w) {
 }
 
 template <typename real>
-__global__ void gaussian_kernel(int64_t total, uint2 key, real* __restrict__ out) {
+__global__ void gaussian_kernel(int64_t total, int64_t cols, int64_t ld, uint2 key,
+                                real* __restrict__ out) {
   const int64_t groups = (total + 3) / 4;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -54,27 +56,32 @@ __global__ void gaussian_kernel(int64_t total, uint2 key, real* __restrict__ out
       z[3] = (real)(r1 * sinf(t1));
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (4 * g + q < total) out[4 * g + q] = z[q];
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = 4 * g + q;
+      if (e < total) out[(e / cols) * ld + e % cols] = z[q];
+    }
   }
 }
 
 }  // namespace
 
 template <typename real>
-curid_status gaussian_fill(const Ctx& ctx, int64_t rows, int64_t cols, uint64_t seed, real* out) {
+curid_status gaussian_fill(const Ctx& ctx, int64_t rows, int64_t cols, uint64_t seed, real* out,
+                           int64_t ld) {
   const int64_t total = rows * cols;
   if (total <= 0) return CURID_OK;
   const uint2 key = make_uint2((unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32));
   const int64_t groups = (total + 3) / 4;
   const unsigned blocks = (unsigned)std::max<int64_t>(
       1, std::min<int64_t>((groups + 255) / 256, 16LL * ctx.num_sms));
-  gaussian_kernel<real><<<blocks, 256, 0, ctx.stream>>>(total, key, out);
+  gaussian_kernel<real><<<blocks, 256, 0, ctx.stream>>>(total, cols, ld, key, out);
   CURID_LAUNCHED(ctx);
   return CURID_OK;
 }
 
-template curid_status gaussian_fill<float>(const Ctx&, int64_t, int64_t, uint64_t, float*);
-template curid_status gaussian_fill<double>(const Ctx&, int64_t, int64_t, uint64_t, double*);
+template curid_status gaussian_fill<float>(const Ctx&, int64_t, int64_t, uint64_t, float*,
+                                           int64_t);
+template curid_status gaussian_fill<double>(const Ctx&, int64_t, int64_t, uint64_t, double*,
+                                            int64_t);
 
 }  // namespace curid

@@ -246,3 +246,73 @@ def test_handworked_example_gpu():
         assert list(npi(r.J)) == g[key]["J"]
         np.testing.assert_allclose(np64(r.T), np.array(g[key]["T"]).reshape(k, -1)[:, :3 - k],
                                    atol=1e-15)
+
+
+# --- tensor-core (tcgen05) products: X A_hi + X A_lo with X read as TF32 ---------
+
+def tf32_exact(x):
+    """Round-free TF32 values: float32 with the 13 low mantissa bits cleared."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32) & np.uint32(0xFFFFE000)
+    return b.view(np.float32)
+
+
+@pytest.mark.parametrize("m,n,lda,l", [(700, 516, 516, 37), (1000, 1024, 1024, 128),
+                                       (333, 4000, 4000, 210), (8000, 6000, 6000, 210),
+                                       (64, 132, 132, 16), (260, 257, 260, 256),
+                                       (97, 1001, 1004, 33)])
+def test_tensor_core_sketch_product(m, n, lda, l):
+    """Y = Omega A on the tensor cores against tf32(Omega) A in float64: the
+    differences are the truncation of A's low part (2^-22 |A|) and the
+    tensor core's float32 accumulation over K (measured up to 6e-5 of |Y|
+    at K = 8000; a tile-layout error would be O(1)).  Ragged shapes: n not a multiple of the 128-column
+    tile, m (the K extent) not a multiple of 32, l not a multiple of 16, A
+    with a padded leading dimension, Omega rows not 16-byte aligned."""
+    g = np.random.default_rng(m + n + l)
+    Afull = torch.from_numpy(g.standard_normal((m, lda)).astype(np.float32))
+    A = cuda(Afull)[:, :n]
+    Om = torch.from_numpy(tf32_exact(g.standard_normal((l, m))))
+    Y = np64(curid.sketch_matrix(A, cuda(Om), q=0, tf32=True))
+    ref = np64(Om) @ np64(Afull[:, :n])
+    err = np.abs(Y - ref).max() / np.abs(ref).max()
+    assert err <= 1e-4, err
+
+
+def test_tensor_core_rejects_misaligned_rows():
+    A = cuda(torch.randn(100, 130))
+    Om = cuda(torch.randn(10, 100))
+    with pytest.raises(curid.CuridError) as e:
+        curid.sketch_matrix(A, Om, q=0, tf32=True)
+    assert e.value.status == 8
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_tensor_core_sketch_power(q):
+    """Power steps use both product kinds (Q A^T and Q A); compare row spaces."""
+    m, n, l = 1500, 1100, 60
+    A = syn.spectrum_matrix(m, n, syn.exp_decay(min(m, n), 40.0), 503, torch.float32)
+    Om = syn.gaussian(l, m, 504, torch.float32)
+    Y = np64(curid.sketch_matrix(cuda(A), cuda(Om), q=q, tf32=True))
+    Yo = O.sketch(np64(A), np64(Om), q=q)
+
+    def proj(M):
+        Qm, _ = np.linalg.qr(M.T)
+        return Qm @ Qm.T
+    assert fro(proj(Y) - proj(Yo)) <= 5e-3
+
+
+def test_tensor_core_randomized_cur():
+    m, n, k, p, q = 1500, 1100, 50, 10, 1
+    A = syn.spectrum_matrix(m, n, syn.power_decay(min(m, n)), 31, torch.float32)
+    Om = syn.gaussian(k + p, m, 32, torch.float32)
+    r = curid.cur(cuda(A), k, p=p, q=q, omega=cuda(Om), tf32=True, want_c=True, want_r=True,
+                  want_t=True)
+    o, _ = O.randomized_cur(np64(A), np64(Om), k, q=q)
+    Ah = np64(A)
+    J, I = npi(r.J), npi(r.I)
+    C, R, U, T = np64(r.C), np64(r.R), np64(r.U), np64(r.T)
+    eg = O.rel_err_fro(Ah, C, U, R)
+    eo = O.rel_err_fro(Ah, o.C, o.U, o.R)
+    assert eg <= 1.05 * eo, (eg, eo)
+    assert id_residual(Ah, J, T, k) <= 1.05 * id_residual(Ah, o.J, o.T, k)
+    Uo = O.cur_middle(R, O.vstar(J, T, n))
+    assert abs(eg - O.rel_err_fro(Ah, C, Uo, R)) <= 1e-5

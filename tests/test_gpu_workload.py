@@ -28,7 +28,7 @@ def workload():
     return A, Ah, seed, o
 
 
-@pytest.mark.parametrize("tf32", [False])
+@pytest.mark.parametrize("tf32", [False, True])
 def test_full_size_cur(workload, tf32):
     A, Ah, seed, o = workload
     r = curid.cur(A, K, p=P, q=Q, seed=seed, tf32=tf32, want_c=True, want_r=True, want_t=True)
