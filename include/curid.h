@@ -160,9 +160,9 @@ curid_status curid_cpqr(curid_handle* handle, curid_dtype dtype,
  *   - No handle, no workspace, no cudaMalloc/cudaFree: the kernel's scratch
  *     is a 4 MiB static device array that every GPU loading this library
  *     keeps until the process exits.  Requests whose scratch exceeds it
- *     (about 256 + 2 G (32 + 8 l) bytes for float64, 2 G (24 + 4 l) for
+ *     (about 256 + 2 G (32 + 16 l) bytes for float64, 2 G (32 + 8 l) for
  *     float32, G = min(number of SMs, n): on a 152-SM GPU l up to about
- *     1700 rows in float64, 3400 in float32) return CURID_NO_WORKSPACE
+ *     860 rows in float64, 1720 in float32) return CURID_NO_WORKSPACE
  *     before any work is enqueued.
  *   - The first call on a device (with that device current) looks up the
  *     array's device address; make that first call before any stream

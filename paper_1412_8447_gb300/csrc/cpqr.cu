@@ -22,6 +22,8 @@
 // round trip until the end.
 // After the last step row i of S holds S1(i, c) for every original column c,
 // J lists the pivots and then the unselected columns in ascending order.
+#include <atomic>
+
 #include "kernels.cuh"
 
 namespace curid {
@@ -37,8 +39,9 @@ namespace {
 // CTA's count of unselected columns), w1/w2 = candidate norm (float bits in
 // w1; float64 split high/low), w3 = sum of the CTA's squared residual norms
 // as float (adaptive stop only).
-struct alignas(32) Rec {
+struct alignas(128) Rec {  // one record per 128-byte line: no two writers share a line
   unsigned long long w[4];
+  unsigned long long pad[12];
 };
 
 template <typename real>
@@ -51,21 +54,72 @@ struct CpqrParams {
   int32_t* J;
   real* S;
   int64_t lds;
-  Rec* recs;          // [2][G]
-  real* slot_data;    // [2][G][l]
+  Rec* recs;                     // [2][G]
+  unsigned long long* slot_data;  // [2][G][l * words]: tagged candidate columns
   int* abort_flag;
   StatusBlock* status;
   int which;
+  unsigned gen;                  // launch generation, high bits of every tag
 };
 
-constexpr int kThreads = 256;
+// Published candidate columns are tagged word by word like the records, so a
+// reader can tell a fresh element from a stale one without any fence on the
+// writer's side: float32 -> one word (tag, bits); float64 -> two words
+// (tag, high bits), (tag, low bits).  The tag of step e in launch g is
+// (g << 20) | e.
+template <typename real>
+struct Words {
+  static constexpr int W = sizeof(real) / 4;
+};
+
+constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
+constexpr int kColsPerWarp = 4;  // columns a warp updates in one interleaved pass
 constexpr unsigned kNoCol = 0xffffffffu;
 constexpr unsigned kNonFinite = 0xfffffffeu;
 constexpr int kMaxSlotsPerLane = 8;  // G <= 256
 
 __device__ __forceinline__ unsigned long long pack(unsigned epoch, unsigned payload) {
   return ((unsigned long long)epoch << 32) | payload;
+}
+
+__device__ __forceinline__ unsigned tag_of(unsigned gen, int epoch) {
+  return (gen << 20) | (unsigned)epoch;
+}
+
+template <typename real>
+__device__ __forceinline__ void put_tagged(unsigned long long* dst, unsigned tag, real v) {
+  if (sizeof(real) == 8) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong((double)v);
+    st_volatile_u64(dst, pack(tag, (unsigned)(b >> 32)));
+    st_volatile_u64(dst + 1, pack(tag, (unsigned)(b & 0xffffffffull)));
+  } else {
+    st_volatile_u64(dst, pack(tag, __float_as_uint((float)v)));
+  }
+}
+
+// Bounded read of one tagged element; false if it never became fresh.
+template <typename real>
+__device__ __forceinline__ bool get_tagged(const unsigned long long* src, unsigned tag, real* v,
+                                           const int* abort_flag) {
+  const long long t0 = clock64();
+  while (true) {
+    if (sizeof(real) == 8) {
+      const unsigned long long a = ld_volatile_u64(src), b = ld_volatile_u64(src + 1);
+      if ((unsigned)(a >> 32) == tag && (unsigned)(b >> 32) == tag) {
+        *v = (real)__longlong_as_double((long long)(((a & 0xffffffffull) << 32) |
+                                                     (b & 0xffffffffull)));
+        return true;
+      }
+    } else {
+      const unsigned long long a = ld_volatile_u64(src);
+      if ((unsigned)(a >> 32) == tag) {
+        *v = (real)__uint_as_float((unsigned)(a & 0xffffffffull));
+        return true;
+      }
+    }
+    if (ld_volatile_i32(abort_flag) || clock64() - t0 > kSpinBudget) return false;
+  }
 }
 
 template <typename real>
@@ -123,16 +177,28 @@ __device__ bool gather_records(const CpqrParams<real>& P, int bf, unsigned epoch
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x;
   const Rec* base = P.recs + (size_t)bf * G;
+  // float32 without a tolerance needs only (column, norm): one 16-byte load
+  const bool full = sizeof(real) == 8 || P.tol > real(0);
   unsigned pending = 0;
 #pragma unroll
   for (int r = 0; r < kMaxSlotsPerLane; ++r)
     if (lane + 32 * r < G) pending |= 1u << r;
   bool ok = true;
   const long long t0 = clock64();
-  while (pending) {
+  for (int round = 0; pending; ++round) {
 #pragma unroll
-    for (int r = 0; r < kMaxSlotsPerLane; ++r)
-      if (pending & (1u << r)) ld_rec(base + lane + 32 * r, w[r]);
+    for (int r = 0; r < kMaxSlotsPerLane; ++r) {
+      if (!(pending & (1u << r))) continue;
+      const Rec* rec = base + lane + 32 * r;
+      if (full) {
+        ld_rec(rec, w[r]);
+      } else {
+        asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
+                     : "=l"(w[r][0]), "=l"(w[r][1])
+                     : "l"(&rec->w[0]));
+        w[r][2] = w[r][3] = (unsigned long long)epoch << 32;
+      }
+    }
 #pragma unroll
     for (int r = 0; r < kMaxSlotsPerLane; ++r) {
       if (!(pending & (1u << r))) continue;
@@ -142,15 +208,18 @@ __device__ bool gather_records(const CpqrParams<real>& P, int bf, unsigned epoch
       if (fresh) pending &= ~(1u << r);
     }
     if (!pending) break;
-    if (ld_volatile_i32(P.abort_flag)) { ok = false; break; }
-    if (clock64() - t0 > kSpinBudget) {
-      atomicExch(P.abort_flag, 1);
-      ok = false;
-      break;
+    // back off briefly so 150 pollers do not saturate the records' lines
+    __nanosleep(64);
+    if ((round & 15) == 15) {
+      if (ld_volatile_i32(P.abort_flag)) { ok = false; break; }
+      if (clock64() - t0 > kSpinBudget) {
+        atomicExch(P.abort_flag, 1);
+        ok = false;
+        break;
+      }
     }
   }
   ok = __all_sync(0xffffffffu, ok);
-  __threadfence();
   return ok;
 }
 
@@ -179,19 +248,19 @@ __device__ void publish(const CpqrParams<real>& P, const real* ys, const real* n
     ss += __shfl_xor_sync(0xffffffffu, ss, o);
     nf |= __shfl_xor_sync(0xffffffffu, nf, o);
   }
+  const unsigned tag = tag_of(P.gen, (int)epoch);
   if (bi >= 0 && !nf) {
-    real* dst = P.slot_data + ((int64_t)bf * G + blockIdx.x) * P.l;
+    constexpr int W = Words<real>::W;
+    unsigned long long* dst = P.slot_data + ((int64_t)bf * G + blockIdx.x) * P.l * W;
     const real* src = ys + (int64_t)bi * P.ldl;
-    for (int r = r0 + lane; r < P.l; r += 32) dst[r] = src[r];
+    for (int r = r0 + lane; r < P.l; r += 32) put_tagged<real>(dst + (int64_t)r * W, tag, src[r]);
   }
-  __syncwarp();
   if (lane == 0) {
     unsigned hi, lo;
     norm_words<real>(bi >= 0 ? bn : real(0), &hi, &lo);
     const unsigned col = nf ? kNonFinite : (bi >= 0 ? (unsigned)(c0 + bi) : kNoCol);
-    __threadfence();
-    st_rec(P.recs + (size_t)bf * G + blockIdx.x, pack(epoch, col), pack(epoch, hi),
-           pack(epoch, lo), pack(epoch, __float_as_uint((float)ss)));
+    st_rec(P.recs + (size_t)bf * G + blockIdx.x, pack(tag, col), pack(tag, hi), pack(tag, lo),
+           pack(tag, __float_as_uint((float)ss)));
   }
 }
 
@@ -228,6 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
   }
   __syncthreads();
   if (warp == 0) publish(P, ys, nrm, active, ncl, c0, 0, 0, 1u);
+  __shared__ int s_stale;
 
   real normY = real(-1), nu_first = real(0);
   int k_eff = -1;
@@ -236,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
     const int bf = j & 1;
     if (warp == 0) {
       unsigned long long w[kMaxSlotsPerLane][4];
-      const bool ok = gather_records(P, bf, (unsigned)(j + 1), w);
+      const bool ok = gather_records(P, bf, tag_of(P.gen, j + 1), w);
       // global pivot and totals, identical in every CTA
       real bn = real(-1), tot = real(0);
       unsigned bc = kNoCol;
@@ -292,10 +362,31 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
       k_eff = j;
       if (b == 0 && tid == 0) set_flag(&P.status->flags, FLAG_RANK_DEFICIENT);
     }
-    // pivot column rows j..l-1, as its owner published it
-    const real* src = P.slot_data + ((int64_t)bf * G + owner) * l;
-    for (int r = j + tid; r < l; r += kThreads) xv[r] = __ldcg(src + r);
-    __syncthreads();
+    // pivot column rows j..l-1, as its owner published it (tagged words)
+    {
+      constexpr int W = Words<real>::W;
+      const unsigned long long* src = P.slot_data + ((int64_t)bf * G + owner) * l * W;
+      const unsigned tag = tag_of(P.gen, j + 1);
+      if (tid == 0) s_stale = 0;
+      __syncthreads();
+      for (int r = j + tid; r < l; r += kThreads) {
+        real v;
+        if (!get_tagged<real>(src + (int64_t)r * W, tag, &v, P.abort_flag)) {
+          s_stale = 1;
+          v = real(0);
+        }
+        xv[r] = v;
+      }
+      __syncthreads();
+      if (s_stale) {
+        if (tid == 0) {
+          atomicExch(P.abort_flag, 1);
+          set_flag(&P.status->flags, FLAG_TIMEOUT);
+        }
+        s_stop = 2;
+        break;
+      }
+    }
     // Householder reflector H = I - tau v v^T with v(j) = 1, v(r) = scale x(r):
     // H x = beta e_j, beta = -sign(alpha) nu
     const real alpha = xv[j];
@@ -306,38 +397,78 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
       scale = real(1) / (alpha - beta);
     }
     // apply H to every unselected local column, recompute its residual norm
-    // from rows j+1..l-1; the owner retires the pivot column
-    for (int lc = warp; lc < ncl; lc += kWarps) {
-      if (!active[lc]) continue;
-      real* y = ys + (int64_t)lc * ldl;
-      if (c0 + lc == pcol) {
-        for (int r = j + lane; r < l; r += 32) y[r] = r == j ? beta : real(0);
-        if (lane == 0) {
-          active[lc] = 0;
-          P.J[j] = pcol;
-        }
-        continue;
-      }
-      real d = real(0);
-      for (int r = j + 1 + lane; r < l; r += 32) d += xv[r] * y[r];
-      d = warp_sum(d);
-      const real wj = tau * (y[j] + scale * d);
-      const real ws = wj * scale;
-      real s2 = real(0);
-      for (int r = j + lane; r < l; r += 32) {
-        if (r == j) {
-          y[r] -= wj;
-        } else {
-          const real yr = y[r] - ws * xv[r];
-          y[r] = yr;
-          s2 += yr * yr;
+    // from rows j+1..l-1; the owner retires the pivot column.  Warp w owns
+    // columns w, w + 16, w + 32, w + 48 and updates them in one interleaved
+    // pass so their reductions overlap.
+    for (int base = warp; base < ncl; base += kColsPerWarp * kWarps) {
+      bool v[kColsPerWarp];
+      real* y[kColsPerWarp];
+#pragma unroll
+      for (int c = 0; c < kColsPerWarp; ++c) {
+        const int lc = base + c * kWarps;
+        v[c] = lc < ncl && active[lc] != 0;
+        y[c] = ys + (int64_t)(lc < ncl ? lc : base) * ldl;
+        if (v[c] && c0 + lc == pcol) {
+          for (int r = j + lane; r < l; r += 32) y[c][r] = r == j ? beta : real(0);
+          if (lane == 0) {
+            active[lc] = 0;
+            P.J[j] = pcol;
+          }
+          v[c] = false;
         }
       }
-      s2 = warp_sum(s2);
-      if (lane == 0) nrm[lc] = sqrt(s2);
+      bool any = false;
+#pragma unroll
+      for (int c = 0; c < kColsPerWarp; ++c) any |= v[c];
+      if (!any) continue;
+      real d[kColsPerWarp];
+#pragma unroll
+      for (int c = 0; c < kColsPerWarp; ++c) d[c] = real(0);
+      for (int r = j + 1 + lane; r < l; r += 32) {
+        const real x = xv[r];
+#pragma unroll
+        for (int c = 0; c < kColsPerWarp; ++c)
+          if (v[c]) d[c] += x * y[c][r];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < kColsPerWarp; ++c) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
+      real wj[kColsPerWarp], ws[kColsPerWarp], q[kColsPerWarp];
+#pragma unroll
+      for (int c = 0; c < kColsPerWarp; ++c) {
+        wj[c] = v[c] ? tau * (y[c][j] + scale * d[c]) : real(0);
+        ws[c] = wj[c] * scale;
+        q[c] = real(0);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < kColsPerWarp; ++c)
+          if (v[c]) y[c][j] -= wj[c];
+      }
+      for (int r = j + 1 + lane; r < l; r += 32) {
+        const real x = xv[r];
+#pragma unroll
+        for (int c = 0; c < kColsPerWarp; ++c) {
+          if (!v[c]) continue;
+          const real nv = y[c][r] - ws[c] * x;
+          y[c][r] = nv;
+          q[c] += nv * nv;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < kColsPerWarp; ++c) q[c] += __shfl_xor_sync(0xffffffffu, q[c], o);
+      if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < kColsPerWarp; ++c)
+          if (v[c]) nrm[base + c * kWarps] = sqrt(q[c]);
+      }
     }
     __syncthreads();
     if (warp == 0) publish(P, ys, nrm, active, ncl, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2));
+
   }
   const int k_done = j;
   if (s_stop == 2) return;  // timed out: leave without further waits
@@ -348,13 +479,12 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
   }
   // unselected columns in ascending order after the pivots: exchange counts
   const int fbf = (j + 1) & 1;
-  const unsigned fep = (unsigned)(j + 2);
+  const unsigned fep = tag_of(P.gen, j + 2);
   if (warp == 0) {
     int cnt = 0;
     for (int lc = lane; lc < ncl; lc += 32) cnt += active[lc];
     cnt = warp_sum(cnt);
     if (lane == 0) {
-      __threadfence();
       st_rec(P.recs + (size_t)fbf * G + b, pack(fep, (unsigned)cnt), pack(fep, 0u), pack(fep, 0u),
              pack(fep, 0u));
     }
@@ -416,7 +546,7 @@ template <typename real>
 void cpqr_carve(Carver& cv, int grid, int64_t l, CpqrScratch* s) {
   s->grid = grid;
   s->slots = cv.take<Rec>(2 * (size_t)grid);
-  s->slot_data = cv.take<real>(2 * (size_t)grid * l);
+  s->slot_data = cv.take<unsigned long long>(2 * (size_t)grid * l * Words<real>::W);
   s->counts = cv.take<int>(grid);
   s->abort_flag = cv.take<int>(1);
 }
@@ -446,7 +576,9 @@ curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64
   P.S = S;
   P.lds = lds;
   P.recs = static_cast<Rec*>(s.slots);
-  P.slot_data = static_cast<real*>(s.slot_data);
+  P.slot_data = static_cast<unsigned long long*>(s.slot_data);
+  static std::atomic<unsigned> generation{0};
+  P.gen = (generation.fetch_add(1) + 1) & 0xfffu;
   P.abort_flag = s.abort_flag;
   P.status = ctx.status;
   P.which = which;
