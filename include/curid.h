@@ -183,7 +183,13 @@ curid_status curid_cpqr_static(void* stream, curid_dtype dtype,
 /* Rank selection of the decompositions below: k > 0 is a fixed rank
  * (1 <= k <= min(m, n); randomized: k + p <= min(m, n)).  The adaptive
  * rank (k == 0, tol > 0) is available through curid_cpqr only; the
- * decompositions return CURID_UNSUPPORTED for it. */
+ * decompositions return CURID_UNSUPPORTED for it.
+ *
+ * Order limits: the k x k triangular solves (T, the row ID, U) and the
+ * l x l Gram factorisations between power steps (q >= 1, l = k + p) hold
+ * their matrix in one SM's shared memory, so k and, when q >= 1, l are at
+ * most 256 for CURID_F32 and 192 for CURID_F64; larger requests return
+ * CURID_UNSUPPORTED before any work is queued. */
 
 /* Column ID (Algorithm 1; randomized: Algorithm 4):
  * A ~ A(:, J[:k]) [I T] P^*.  A m x n (lda).  Outputs J (n) and

@@ -6,6 +6,8 @@
 //   * explicit inverses of triangles through the blocked triangular solve
 //     (tri.cu) with an identity right-hand side;
 //   * the float64-accumulated product that ends the U chain.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace curid {
@@ -14,25 +16,219 @@ namespace {
 
 constexpr int kSmallThreads = 512;  // 128 registers per thread for the block loops
 constexpr int kSmallWarps = kSmallThreads / 32;
-// Cholesky factor of G + shift I, blocked right-looking on 32 x 32 blocks,
-// the matrix padded to a multiple of 32 with an identity tail so no block
-// needs bounds checks.  Per block column: warp 0 factors the diagonal block
-// (lanes = rows) and inverts it (lanes = columns); every warp then finishes
-// panel rows A21 <- A21 L11^{-T} with shuffles; the trailing update
-// A22 -= A21 A21^T is spread one 32 x 32 block per warp.  The lower factor
-// overwrites G (upper part zeroed).  A non-positive or non-finite pivot
-// retries with a 100x larger shift (4 attempts), then FLAG_BREAKDOWN.
+constexpr unsigned kFull = 0xffffffffu;
+
+// Row stride of a 32 x 32 block: padded so every row starts on 16 bytes
+// (vector loads) and the 32 rows a warp reads column-wise fall in distinct
+// 16-byte bank groups.
+template <typename real>
+struct CholBlk {
+  static constexpr int LD = 32 + 16 / (int)sizeof(real);
+  using V = typename std::conditional<sizeof(real) == 4, float4, double2>::type;
+  static constexpr int VN = 16 / (int)sizeof(real);  // elements per vector
+};
+
+__host__ __device__ inline int lower_block(int bi, int bj) { return bi * (bi + 1) / 2 + bj; }
+
+template <typename real>
+__device__ __forceinline__ real* chol_block(real* a, int bi, int bj) {
+  return a + (size_t)lower_block(bi, bj) * 32 * CholBlk<real>::LD;
+}
+
+// Trailing update of block (b + 1 + bi, b + 1 + bj) by one warp:
+// C -= P_i P_j^T with P_i, P_j the finished panel blocks of block column b.
+// Lane t keeps row t of P_j in registers; the rows of P_i are read as
+// broadcast vectors, four output rows at a time.
+template <typename real>
+__device__ __forceinline__ void chol_trail_block(real* a, int b, int bi, int bj, int lane) {
+  using B = CholBlk<real>;
+  using V = typename B::V;
+  constexpr int LD = B::LD;
+  const real* Pi = chol_block(a, b + 1 + bi, b);
+  const real* Pj = chol_block(a, b + 1 + bj, b);
+  real* C = chol_block(a, b + 1 + bi, b + 1 + bj);
+  real col[32];
+#pragma unroll
+  for (int s = 0; s < 32; s += B::VN) {
+    const V v = *reinterpret_cast<const V*>(Pj + lane * LD + s);
+    if constexpr (B::VN == 4) {
+      col[s] = v.x; col[s + 1] = v.y; col[s + 2] = v.z; col[s + 3] = v.w;
+    } else {
+      col[s] = v.x; col[s + 1] = v.y;
+    }
+  }
+  for (int r = 0; r < 32; r += 4) {
+    real sum[4] = {real(0), real(0), real(0), real(0)};
+#pragma unroll
+    for (int s = 0; s < 32; s += B::VN) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const V v = *reinterpret_cast<const V*>(Pi + (r + u) * LD + s);
+        if constexpr (B::VN == 4) {
+          sum[u] = fma(v.x, col[s], sum[u]);
+          sum[u] = fma(v.y, col[s + 1], sum[u]);
+          sum[u] = fma(v.z, col[s + 2], sum[u]);
+          sum[u] = fma(v.w, col[s + 3], sum[u]);
+        } else {
+          sum[u] = fma(v.x, col[s], sum[u]);
+          sum[u] = fma(v.y, col[s + 1], sum[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) C[(r + u) * LD + lane] -= sum[u];
+  }
+}
+
+// Trailing block number q = bi (bi + 1) / 2 + bj.
+template <typename real>
+__device__ __forceinline__ void chol_trail_q(real* a, int b, int q, int lane) {
+  int bi = 0;
+  while ((bi + 1) * (bi + 2) / 2 <= q) ++bi;
+  chol_trail_block(a, b, bi, q - bi * (bi + 1) / 2, lane);
+}
+
+// Diagonal block and W = L_bb^{-1} by one warp with the block in registers:
+// lane t holds column t of the Schur complement (c) and column t of the
+// running inverse (x).  At step j the pivot column comes from lane j by
+// shuffles, and lane t's own entry (j, t) is, by symmetry, L(t, j) times the
+// pivot.  Every 4 steps both arrays shift down by 4 rows, so all register
+// indices are compile-time constants while the step loop stays rolled; the
+// routine is not inlined, so one compact copy serves both call sites (long
+// straight-line code run by one warp is bound by instruction fetch).  Writes L (lower
+// part) into D and W; returns nonzero on a non-positive or non-finite pivot.
+__device__ __noinline__ int chol_diag_warp(float* D, float* W, int t) {
+  constexpr int LD = CholBlk<float>::LD;
+  float c[32], x[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    c[i] = D[i * LD + t];
+    x[i] = i == t ? 1.f : 0.f;
+  }
+  int fail = 0;
+#pragma unroll 1
+  for (int j0 = 0; j0 < 32; j0 += 4) {
+    // c[k], x[k] hold row j0 + k
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int j = j0 + jj;
+      const float d = __shfl_sync(kFull, c[jj], j);
+      if (!(d > 0.f) || !isfinite(d)) fail = 1;
+      const float inv = fail ? 1.f : rsqrtf(d);
+      const float ltj = c[jj] * inv;  // lane t > j: L(t, j)
+      if (t > j) D[t * LD + j] = ltj;
+      if (t == j) D[j * LD + j] = d * inv;
+      x[jj] *= inv;  // W(j, t)
+      W[j * 33 + t] = x[jj];
+      const float q = inv * ltj, p = inv * x[jj];
+#pragma unroll
+      for (int i = jj + 1; i < 32; ++i) {
+        const float cij = __shfl_sync(kFull, c[i], j);  // unscaled (j0 + i, j)
+        if (t > j) c[i] = fmaf(-cij, q, c[i]);
+        x[i] = fmaf(-cij, p, x[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 28; ++i) {
+      c[i] = c[i + 4];
+      x[i] = x[i + 4];
+    }
+#pragma unroll
+    for (int i = 28; i < 32; ++i) c[i] = x[i] = 0.f;
+  }
+  return fail;
+}
+
+// Diagonal block and W = L_bb^{-1} in one sweep over the 32 x 64 augmented
+// block [A_bb | I] by the whole CTA (512 threads): thread (r, c) =
+// (tid / 16, tid % 16) holds A(r, c), A(r, c + 16), W(r, c), W(r, c + 16) in
+// registers.  Step j: the owners publish column j of A, row j of W and the
+// pivot's 1 / sqrt; one barrier; every thread then applies the rank-1
+// updates of its elements.  Buffers alternate with j's parity, so one barrier
+// per step orders each publication after the previous reads.  Used for
+// float64, whose per-sub-partition rate makes one warp far too slow.
+// Returns nonzero on a non-positive or non-finite pivot (same in all threads).
+template <typename real>
+__device__ __forceinline__ int chol_diag_cta(real* D, real* W, real* pcol, real* prow, real* piv,
+                                             int tid) {
+  constexpr int LD = CholBlk<real>::LD;
+  const int r = tid >> 4, c = tid & 15;
+  real a0 = D[r * LD + c], a1 = D[r * LD + c + 16];
+  real w0 = r == c ? real(1) : real(0), w1 = r == c + 16 ? real(1) : real(0);
+  int fail = 0;
+  for (int j = 0; j < 32; ++j) {
+    real* colA = pcol + (j & 1) * 32;
+    real* rowW = prow + (j & 1) * 32;
+    const real aj = j < 16 ? a0 : a1;
+    if (c == (j & 15)) colA[r] = aj;
+    if (r == j) {
+      rowW[c] = w0;
+      rowW[c + 16] = w1;
+      if (c == (j & 15)) {
+        const bool bad = !(aj > real(0)) || !isfinite(aj);
+        const real inv = bad ? real(1) : rsqrt(aj);
+        piv[(j & 1) * 2] = inv;
+        piv[(j & 1) * 2 + 1] = bad ? real(-1) : aj * inv;
+      }
+    }
+    __syncthreads();
+    const real inv = piv[(j & 1) * 2], sj = piv[(j & 1) * 2 + 1];
+    if (sj < real(0)) fail = 1;
+    if (r > j) {
+      // A(r, c) -= L(r, j) L(c, j) and W(r, c) -= L(r, j) W(j, c) / s_j
+      // both take colA[r] / s_j^2 times an unscaled published value
+      const real m = colA[r] * (inv * inv);
+      if (c > j && c <= r) a0 = fma(-m, colA[c], a0);
+      if (c + 16 > j && c + 16 <= r) a1 = fma(-m, colA[c + 16], a1);
+      if (c == j) a0 = colA[r] * inv;
+      if (c + 16 == j) a1 = colA[r] * inv;
+      if (c <= j) w0 = fma(-m, rowW[c], w0);
+      if (c + 16 <= j) w1 = fma(-m, rowW[c + 16], w1);
+    } else if (r == j) {
+      if (c == j) a0 = fabs(sj);
+      if (c + 16 == j) a1 = fabs(sj);
+      w0 *= inv;
+      w1 *= inv;
+    }
+  }
+  D[r * LD + c] = a0;
+  D[r * LD + c + 16] = a1;
+  W[r * 33 + c] = w0;
+  W[r * 33 + c + 16] = w1;
+  return fail;
+}
+
+// Cholesky factor of G + shift I, blocked right-looking on 32 x 32 blocks of
+// the lower triangle (packed in shared memory, diagonal blocks held whole),
+// the order padded to a multiple of 32 with an identity tail.  Per block
+// column b:
+//  (1) the diagonal block is factored and W = L_bb^{-1} formed in one
+//      elimination sweep: by warp 0 with the block in registers (float32),
+//      or by the whole CTA with one barrier per column (float64);
+//  (2) every warp finishes panel rows A_ib <- A_ib L_bb^{-T} (W column in
+//      registers, row entries as broadcast vector loads);
+//  (3) the trailing update A_ij -= A_ib A_jb^T runs one 32 x 32 block per
+//      warp, the A_jb row of each lane in registers and the A_ib rows read
+//      as broadcast vectors.
+// The lower factor overwrites G (upper part zeroed).  A non-positive or
+// non-finite pivot retries with a 100x larger shift (4 attempts), then sets
+// FLAG_BREAKDOWN.
 template <typename real>
 __global__ void __launch_bounds__(kSmallThreads, 1)
 chol_kernel(real* __restrict__ G, int l, real rel_shift, StatusBlock* status) {
+  using B = CholBlk<real>;
+  using V = typename B::V;
+  constexpr int LD = B::LD;
+  constexpr bool kLookahead = sizeof(real) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int LP = (l + 31) & ~31;
-  const int ld = LP + 1;
   const int nb = LP / 32;
   real* a = reinterpret_cast<real*>(smem_raw);
-  real* W = a + (size_t)LP * ld;  // 32 x 33 inverse of the current diagonal block
+  real* W = a + (size_t)lower_block(nb, 0) * 32 * LD;  // 32 x 33, W = L_bb^{-1}
+  __shared__ real pcol[64], prow[64], piv[4];  // published pivot column / W row / 1/sqrt
   __shared__ int s_fail;
   __shared__ real s_tr;
+  int s_fail_local = 0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (warp == 0) {
     real tr = real(0);
@@ -45,82 +241,82 @@ chol_kernel(real* __restrict__ G, int l, real rel_shift, StatusBlock* status) {
   real shift = rel_shift * tr;
   bool done = false;
   for (int attempt = 0; attempt < 4 && !done; ++attempt) {
-    for (int e = tid; e < LP * LP; e += kSmallThreads) {
-      const int i = e / LP, j = e % LP;
-      real v;
-      if (i < l && j < l) v = G[(int64_t)i * l + j] + (i == j ? shift : real(0));
-      else v = i == j ? real(1) : real(0);
-      a[i * ld + j] = v;
+    // lower blocks of G + shift I (diagonal blocks whole), identity tail
+    for (int i = warp; i < LP; i += kSmallWarps) {
+      const int bi = i >> 5, r = i & 31;
+      real v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = 32 * u + lane;
+        v[u] = (u <= bi && i < l && j < l) ? G[(int64_t)i * l + j] : real(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = 32 * u + lane;
+        if (u <= bi) {
+          real x = (i < l && j < l) ? v[u] : real(0);
+          if (i == j) x += (i < l) ? shift : real(1);
+          chol_block(a, bi, u)[r * LD + lane] = x;
+        }
+      }
     }
     if (tid == 0) s_fail = 0;
     __syncthreads();
-    for (int kb = 0; kb < LP; kb += 32) {
-      if (warp == 0) {
-        // (1) factor the diagonal block; lane i owns row kb + i
-        real* Dk = a + kb * ld + kb;
-        int fail = 0;
-        for (int j = 0; j < 32; ++j) {
-          real d = Dk[j * ld + j];
-          if (!(d > real(0)) || !isfinite(d)) fail = 1;
-          d = fail ? real(1) : sqrt(d);
-          __syncwarp();
-          if (lane == j) Dk[j * ld + j] = d;
-          real lij = real(0);
-          if (lane > j) {
-            lij = Dk[lane * ld + j] / d;
-            Dk[lane * ld + j] = lij;
+    // float32 looks ahead: warp 0 factors diagonal block b + 1 while the
+    // other warps finish the trailing update of step b (step b = -1 only
+    // factors block 0)
+    for (int b = kLookahead ? -1 : 0; b < nb; ++b) {
+      if (b >= 0) {
+        if constexpr (!kLookahead) {
+          s_fail_local = chol_diag_cta(chol_block(a, b, b), W, pcol, prow, piv, tid);
+          if (tid == 0) s_fail = s_fail_local;
+          __syncthreads();
+        }
+        if (s_fail) break;
+        // (2) panel rows: A_ib(r, c) <- sum_{s <= c} A_ib(r, s) W(c, s)
+        if (b + 1 < nb) {
+          real w[32];
+#pragma unroll
+          for (int s = 0; s < 32; ++s) w[s] = W[lane * 33 + s];
+          for (int i = (b + 1) * 32 + warp; i < LP; i += kSmallWarps) {
+            real* row = chol_block(a, i >> 5, b) + (i & 31) * LD;
+            real out = real(0);
+#pragma unroll
+            for (int s = 0; s < 32; s += B::VN) {
+              const V v = *reinterpret_cast<const V*>(row + s);
+              if constexpr (B::VN == 4) {
+                out = fma(v.x, w[s], out);
+                out = fma(v.y, w[s + 1], out);
+                out = fma(v.z, w[s + 2], out);
+                out = fma(v.w, w[s + 3], out);
+              } else {
+                out = fma(v.x, w[s], out);
+                out = fma(v.y, w[s + 1], out);
+              }
+            }
+            __syncwarp();
+            row[lane] = out;
           }
-          __syncwarp();
-          if (lane > j)
-            for (int t = j + 1; t <= lane; ++t) Dk[lane * ld + t] -= lij * Dk[t * ld + j];
-          __syncwarp();
         }
-        // (1b) W = L11^{-1}; lane c computes column c
-        real x[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          real sum = i == lane ? real(1) : real(0);
-#pragma unroll
-          for (int t = 0; t < i; ++t) sum -= Dk[i * ld + t] * x[t];
-          x[i] = i >= lane ? sum / Dk[i * ld + i] : real(0);
-        }
-#pragma unroll
-        for (int i = 0; i < 32; ++i) W[i * 33 + lane] = x[i];
-        if (lane == 0) s_fail = fail;
+        __syncthreads();
       }
-      __syncthreads();
-      if (s_fail) break;
-      // (2) panel rows below: A21(i, c) <- sum_{s <= c} A21(i, s) W(c, s)
-      for (int i = kb + 32 + warp; i < LP; i += kSmallWarps) {
-        const real ais = a[i * ld + kb + lane];
-        real out = real(0);
-#pragma unroll
-        for (int s2 = 0; s2 < 32; ++s2) {
-          const real v = __shfl_sync(0xffffffffu, ais, s2);
-          out += v * W[lane * 33 + s2];
+      // (3) trailing update of blocks (bi, bj), b < bj <= bi, numbered
+      // q = bi (bi + 1) / 2 + bj from the next diagonal block q = 0
+      const int m = nb - b - 1;
+      const int nblocks = b >= 0 ? m * (m + 1) / 2 : 0;
+      if constexpr (kLookahead) {
+        if (warp == 0) {
+          if (m > 0) {
+            if (b >= 0) chol_trail_block(a, b, 0, 0, lane);
+            __syncwarp();
+            const int fail = chol_diag_warp(chol_block(a, b + 1, b + 1), W, lane);
+            if (lane == 0) s_fail = fail;
+          }
+        } else {
+          for (int q = warp; q < nblocks; q += kSmallWarps - 1) chol_trail_q(a, b, q, lane);
         }
-        a[i * ld + kb + lane] = out;
-      }
-      __syncthreads();
-      // (3) trailing update, one 32 x 32 block (bi >= bj > kb) per warp
-      const int b0 = kb / 32 + 1;
-      const int m = nb - b0;
-      const int nblocks = m * (m + 1) / 2;
-      for (int q = warp; q < nblocks; q += kSmallWarps) {
-        int bi = 0;
-        while ((bi + 1) * (bi + 2) / 2 <= q) ++bi;
-        const int bj = q - bi * (bi + 1) / 2;
-        const int i0 = (b0 + bi) * 32, j0 = (b0 + bj) * 32;
-        real col[32];
-#pragma unroll
-        for (int s2 = 0; s2 < 32; ++s2) col[s2] = a[(j0 + lane) * ld + kb + s2];
-        for (int r = 0; r < 32; ++r) {
-          const real* ar = a + (i0 + r) * ld + kb;
-          real sum = real(0);
-#pragma unroll
-          for (int s2 = 0; s2 < 32; ++s2) sum += ar[s2] * col[s2];
-          a[(i0 + r) * ld + j0 + lane] -= sum;
-        }
+      } else {
+        for (int q = warp; q < nblocks; q += kSmallWarps) chol_trail_q(a, b, q, lane);
       }
       __syncthreads();
     }
@@ -135,9 +331,10 @@ chol_kernel(real* __restrict__ G, int l, real rel_shift, StatusBlock* status) {
     for (int e = tid; e < l * l; e += kSmallThreads) G[e] = (e / l == e % l) ? real(1) : real(0);
     return;
   }
-  for (int e = tid; e < l * l; e += kSmallThreads) {
-    const int i = e / l, j = e % l;
-    G[e] = j <= i ? a[i * ld + j] : real(0);
+  for (int i = warp; i < l; i += kSmallWarps) {
+    const int bi = i >> 5, r = i & 31;
+    for (int j = lane; j < l; j += 32)
+      G[(int64_t)i * l + j] = j <= i ? chol_block(a, bi, j >> 5)[r * LD + (j & 31)] : real(0);
   }
 }
 
@@ -169,8 +366,8 @@ __global__ void gemm_nt_f64acc_kernel(int M, int N, int K, const real* __restric
 
 template <typename real>
 size_t chol_smem(int l) {
-  const int LP = (l + 31) & ~31;
-  return ((size_t)LP * (LP + 1) + 32 * 33) * sizeof(real);
+  const int nb = (l + 31) / 32;
+  return ((size_t)lower_block(nb, 0) * 32 * CholBlk<real>::LD + 32 * 33) * sizeof(real);
 }
 
 }  // namespace

@@ -195,6 +195,37 @@ def test_randomized_cur_moderate(dtype):
         assert eg <= 1.05 * eo, (eg, eo)
 
 
+@pytest.mark.parametrize("dtype,k", [(torch.float32, 246), (torch.float64, 182)])
+def test_randomized_cur_largest_order(dtype, k):
+    """l = k + p at the largest order the Gram factorisation takes in one
+    SM (256 float32, 192 float64), with a power step so it runs."""
+    m, n, p, q = 1200, 900, 10, 1
+    A = syn.spectrum_matrix(m, n, syn.exp_decay(min(m, n), 60.0), 41, dtype)
+    Om = syn.gaussian(k + p, m, 42, dtype)
+    r = curid.cur(cuda(A), k, p=p, q=q, omega=cuda(Om), want_c=True, want_r=True, want_t=True)
+    o, _ = O.randomized_cur(np64(A), np64(Om), k, q=q)
+    Ah = np64(A)
+    J, I = npi(r.J), npi(r.I)
+    C, R, U, T = np64(r.C), np64(r.R), np64(r.U), np64(r.T)
+    assert np.array_equal(C, Ah[:, J[:k]]) and np.array_equal(R, Ah[I[:k], :])
+    eg = O.rel_err_fro(Ah, C, U, R)
+    eo = O.rel_err_fro(Ah, o.C, o.U, o.R)
+    assert eg <= 1.05 * eo, (eg, eo)
+    assert id_residual(Ah, J, T, k) <= 1.05 * id_residual(Ah, o.J, o.T, k)
+    if dtype == torch.float64:
+        assert list(J) == list(o.J) and list(I) == list(o.I)
+        assert abs(eg - eo) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype,l", [(torch.float32, 257), (torch.float64, 193)])
+def test_order_beyond_limit_is_unsupported(dtype, l):
+    m, n, p = 600, 500, 10
+    A = syn.spectrum_matrix(m, n, syn.exp_decay(min(m, n), 60.0), 43, dtype)
+    with pytest.raises(curid.CuridError) as e:
+        curid.cur(cuda(A), l - p, p=p, q=1, seed=5)
+    assert e.value.status == 8
+
+
 def test_random_omega_generated_on_device():
     m, n, k, p = 900, 700, 30, 10
     A = syn.spectrum_matrix(m, n, syn.exp_decay(min(m, n), 6.0), 33)
