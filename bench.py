@@ -33,6 +33,10 @@ UNIT = "decompositions/s"
 M, N, K, P, Q = 8000, 6000, 200, 10, 1
 BASE_SEED = 1413
 FP32_FMA_PER_SM_CLK = 128          # FP32 lanes per SM
+# dram__bytes_read.sum + dram__bytes_write.sum of one cpqr_kernel launch on this
+# workload (ncu capture of the current kernel; profiles/ holds the summary):
+# CPQR of Y (210 x 6000) and of C^T (200 x 8000)
+CPQR_DRAM_BYTES = {"cpqr_col": 5.145e6 + 9.5e3, "cpqr_row": 6.504e6 + 11.5e3}
 NUM_SMS = 152
 
 
@@ -142,20 +146,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def cpqr_flops(rows, cols, steps):
+    """Algorithmic flops of a truncated CPQR with norms recomputed each step
+    (Section 4): step j applies the reflector to the cols - j - 1 trailing
+    columns of height rows - j (dot + update, 4 flops per element) and sums
+    the squares of the rows - j - 1 rows left (2 flops per element)."""
+    f = 0.0
+    for j in range(steps):
+        f += 4.0 * (rows - j) * (cols - j - 1) + 2.0 * (rows - j - 1) * (cols - j - 1)
+    return f
+
+
 def phase_work(args, l):
-    """Algorithmic flops / bytes per launch of the main phases (float32)."""
+    """Algorithmic flops / bytes per launch of the main kernels (float32)."""
     m, n, k = args.m, args.n, args.k
     return {
-        # one product with A: 2 l m n flops, A read once (m n floats)
+        # one product with A (the sketch phase times each of the 2q + 1
+        # products as one call): 2 l m n flops, A read once
         "sketch": {"flops": 2.0 * l * m * n, "bytes": 4.0 * (m * n + l * max(m, n) * 2)},
-        # CPQR of Y (l x n): Y read once, S (k x n) and J written
-        "cpqr_col": {"flops": 4.0 * l * n * k, "bytes": 4.0 * (l * n + k * n + n)},
-        # CPQR of C^T (k x m), full k steps
-        "cpqr_row": {"flops": 4.0 * k * m * k, "bytes": 4.0 * (2 * k * m + m)},
-        # one orthonormalisation pass of the l x max(m, n) sample (Gram, factor,
-        # apply): 2 l^2 c flops in the two products; the sample read twice,
-        # written once
-        "orth": {"flops": 4.0 * l * l * max(m, n), "bytes": 4.0 * 3 * l * max(m, n)},
+        # CPQR of Y (l x n, k steps) and of C^T (k x m, k steps)
+        "cpqr_col": {"flops": cpqr_flops(l, n, k), "bytes": 4.0 * (l * n + k * n + n)},
+        "cpqr_row": {"flops": cpqr_flops(k, m, k), "bytes": 4.0 * (2 * k * m + m)},
     }
 
 
@@ -245,41 +256,61 @@ def run_ours(args, ws, rank, local):
     work = phase_work(args, l)
     per_step = {p: phase_ms[p] / args.steps for p in phase_ms}
     total_phase = sum(phase_ms.values()) or 1.0
-    dominant = max(("sketch", "cpqr_col", "cpqr_row", "orth", "u_solve"),
-                   key=lambda p: phase_ms[p])
-    roof = None
-    if dominant in work and phase_calls[dominant]:
-        dur_s = phase_ms[dominant] / phase_calls[dominant] / 1e3
-        w = work[dominant]
-        if dominant == "sketch" and not tf32:
-            sm_mhz = pk.get("sm_max_mhz", 2070.0)
-            peak = NUM_SMS * FP32_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
-            ach = w["flops"] / dur_s / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None, "kernel": "gemm_simt_kernel (FP32 FMA)",
-                    "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
-        elif dominant == "sketch":
+    # kernel families: the CPQR phases are one cpqr_kernel launch each, the
+    # sketch phase the tensor-core products; orth and U are chains of small
+    # kernels (Gram products, Cholesky, triangular solves)
+    fam = {"cpqr_kernel": ("cpqr_col", "cpqr_row"), "sketch": ("sketch",),
+           "orth": ("orth",), "u_solve": ("u_solve",)}
+    fam_ms = {f: sum(phase_ms[p] for p in ps) for f, ps in fam.items()}
+    dominant = max(fam_ms, key=fam_ms.get)
+    sm_mhz_max = clk["sm_max_mhz"] or 2070.0
+    fp32_peak = NUM_SMS * FP32_FMA_PER_SM_CLK * 2 * sm_mhz_max * 1e6 / 1e12
+    fp32_src = "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"
+
+    def sketch_roof():
+        calls = phase_calls["sketch"]
+        if not calls:
+            return None
+        dur_s = phase_ms["sketch"] / calls / 1e3
+        ach = work["sketch"]["flops"] / dur_s / 1e12
+        if tf32:
             peak = pk["bf16_tflops_sustained"] / 2
-            ach = w["flops"] / dur_s / 1e12
-            roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None, "kernel": "gemm_tf32 (tcgen05)",
-                    "peak_source": f"{pk_kind} bf16 sustained x 1/2 (TF32 nominal ratio)"}
-        elif dominant == "orth":
-            # the phase interval covers all passes of one orthonormalisation
-            passes = 3
-            sm_mhz = pk.get("sm_max_mhz", 2070.0)
-            peak = NUM_SMS * FP32_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
-            ach = passes * w["flops"] / dur_s / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None,
-                    "kernel": "orth (gemm_simt_kernel + chol_inverse_kernel), 3 passes",
-                    "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
-        else:
-            ach = w["bytes"] / dur_s / 1e9
-            peak = pk["hbm_gbs"]
-            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "traffic": None, "kernel": f"cpqr_kernel ({dominant})",
-                    "peak_source": f"{pk_kind} hbm_gbs"}
+                    "kernel": "tc_sketch_kernel (tcgen05 TF32, A split hi + lo: 2 MMAs per "
+                              "K step; achieved counts each product once)",
+                    "peak_source": f"{pk_kind} bf16 sustained x 1/2 (TF32 nominal ratio)"}
+        return {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None, "kernel": "gemm_simt_kernel (FP32 FMA)",
+                "peak_source": fp32_src}
+
+    roof = None
+    if dominant == "cpqr_kernel":
+        calls = phase_calls["cpqr_col"] + phase_calls["cpqr_row"]
+        if calls:
+            flops = (work["cpqr_col"]["flops"] * phase_calls["cpqr_col"]
+                     + work["cpqr_row"]["flops"] * phase_calls["cpqr_row"])
+            ach = flops / (fam_ms["cpqr_kernel"] / 1e3) / 1e12
+            default = (args.m, args.n, args.k, args.p) == (M, N, K, P)
+            traffic = ((CPQR_DRAM_BYTES["cpqr_col"] * phase_calls["cpqr_col"]
+                        + CPQR_DRAM_BYTES["cpqr_row"] * phase_calls["cpqr_row"]) / calls
+                       if default else None)
+            roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp32_peak, "traffic": traffic,
+                    "algorithmic_bytes": (work["cpqr_col"]["bytes"] * phase_calls["cpqr_col"]
+                                          + work["cpqr_row"]["bytes"] * phase_calls["cpqr_row"])
+                                         / calls,
+                    "kernel": f"cpqr_kernel (CPQR of Y {l}x{args.n} and of C^T {args.k}x"
+                              f"{args.m}, {args.k} steps each; bound by the per-step "
+                              f"grid-wide pivot exchange, not by FP32 rate)",
+                    "peak_source": fp32_src}
+    elif dominant == "sketch":
+        roof = sketch_roof()
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": None, "traffic": None,
+                "kernel": f"{dominant} (chain of small kernels; no single-kernel figure)",
+                "peak_source": fp32_src}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, A, curid)
@@ -299,6 +330,7 @@ def run_ours(args, ws, rank, local):
                    "reasons": clk["reasons"], "samples": clk["samples"]},
         "e2e": e2e, "gpu_launches": launches,
         "roofline": roof,
+        "sketch_roofline": sketch_roof(),
         "phases_ms_per_step": {p: round(v, 4) for p, v in per_step.items()},
         "phase_share": {p: round(phase_ms[p] / total_phase, 4) for p in phase_ms},
         "cpu_baseline": cpu,
