@@ -231,6 +231,38 @@ curid_status curid_cur(curid_handle* handle, curid_dtype dtype,
                        int32_t* I, double* U, void* C, void* R, void* T,
                        int64_t ldt, void* TW, int64_t ldtw);
 
+/* ----- adjoint with frozen skeletons ----------------------------------- */
+
+/* Reverse-mode derivative of the deterministic CUR-ID (p < 0) with the index
+ * sets held fixed.  The paper does not differentiate the decomposition; the
+ * map follows from its definitions: with J and I fixed, C = A(:, J[:k]),
+ * R = A(I[:k], :), T = S11^{-1} S12, which equals the least-squares
+ * solution C^+ A(:, J[k:]) (Section 2.3, Eq. (2.8)), and U = V* R^+ with
+ * V* = [I T] P^* (Eq. (3.5)).  Given cotangents of the outputs C, U, R,
+ * the call writes Abar = the gradient with respect to A of
+ * <Cbar, C> + <Ubar, U> + <Rbar, R>.
+ *
+ * A m x n (lda); k, J (n) and I (m, only I[:k] read), T (k x (n-k), ldt;
+ * may be NULL when n == k) exactly as returned by curid_cur with p < 0 on
+ * this A.  Cotangents, each NULL for zero: Cbar m x k (leading dimension k)
+ * and Rbar k x n (leading dimension n) in the dtype of A, Ubar k x k
+ * float64 (leading dimension k, like U).  Output Abar m x n (ldab),
+ * overwritten.  All pointers are device memory owned by the caller; the
+ * scratch (curid_cur_adjoint_workspace_size bytes) is the attached
+ * workspace.  k <= 256 (CURID_F32) / 192 (CURID_F64), else
+ * CURID_UNSUPPORTED.  R or C numerically rank deficient: Cholesky breakdown,
+ * reported by curid_last_status as CURID_BREAKDOWN (Abar then undefined). */
+curid_status curid_cur_adjoint_workspace_size(curid_handle* handle,
+                                              curid_dtype dtype, int64_t m,
+                                              int64_t n, int k,
+                                              size_t* bytes);
+curid_status curid_cur_adjoint(curid_handle* handle, curid_dtype dtype,
+                               const void* A, int64_t m, int64_t n,
+                               int64_t lda, int k, const int32_t* J,
+                               const int32_t* I, const void* T, int64_t ldt,
+                               const void* Cbar, const double* Ubar,
+                               const void* Rbar, void* Abar, int64_t ldab);
+
 #ifdef __cplusplus
 }
 #endif

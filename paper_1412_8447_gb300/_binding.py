@@ -55,6 +55,10 @@ SIGNATURES = {
                    _vp, _i64],
     "curid_cur": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _vp, _vp, _vp,
                   _vp, _i64, _vp, _i64],
+    "curid_cur_adjoint_workspace_size": [_vp, _int, _i64, _i64, _int,
+                                         ctypes.POINTER(ctypes.c_size_t)],
+    "curid_cur_adjoint": [_vp, _int, _vp, _i64, _i64, _i64, _int, _vp, _vp, _vp, _i64, _vp, _vp,
+                          _vp, _vp, _i64],
 }
 
 _lib = None
@@ -328,3 +332,59 @@ def cur(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, want_c=False, want_r=Fa
                          o.TW.stride(0) if o.TW is not None else 0)
     _check(st, "curid_cur")
     return _finish(h, o, check, "curid_cur")
+
+
+def cur_adjoint(A, J, I, T, k, Cbar=None, Ubar=None, Rbar=None, out=None, check=True):
+    """Gradient with respect to A of <Cbar, C> + <Ubar, U> + <Rbar, R> for the
+    deterministic CUR-ID with the skeletons J, I frozen (T from the same
+    decomposition).  Cotangents may be None (zero); Ubar is float64 like U."""
+    A = _mat(A)
+    dev = _dev(A)
+    h = handle(dev)
+    m, n = A.shape
+    dt = _dtype_code(A.dtype)
+    b = ctypes.c_size_t(0)
+    _check(h.lib.curid_cur_adjoint_workspace_size(h.h, dt, m, n, k, ctypes.byref(b)),
+           "curid_cur_adjoint_workspace_size")
+    h.prepare(b.value)
+    Cb = Cbar.to(A.dtype).contiguous() if Cbar is not None else None
+    Ub = Ubar.to(torch.float64).contiguous() if Ubar is not None else None
+    Rb = Rbar.to(A.dtype).contiguous() if Rbar is not None else None
+    Tc = T if (T is None or T.stride(-1) == 1) else T.contiguous()
+    Ab = out if out is not None else torch.empty((m, n), dtype=A.dtype, device=A.device)
+    st = h.lib.curid_cur_adjoint(h.h, dt, _ptr(A), m, n, A.stride(0), k, _ptr(J), _ptr(I),
+                                 _ptr(Tc if n > k else None),
+                                 Tc.stride(0) if (Tc is not None and n > k) else 1,
+                                 _ptr(Cb), _ptr(Ub), _ptr(Rb), _ptr(Ab), Ab.stride(0))
+    _check(st, "curid_cur_adjoint")
+    if check:
+        st, _ = h.status()
+        if st != OK:
+            raise CuridError(st, "curid_cur_adjoint")
+    return Ab
+
+
+class CURFunction(torch.autograd.Function):
+    """(C, U, R) of the deterministic CUR-ID (Algorithm 3) as a function of A,
+    differentiable with the skeletons frozen at the forward pass's J and I;
+    the backward pass is the library's adjoint (curid_cur_adjoint)."""
+
+    @staticmethod
+    def forward(ctx, A, k):
+        r = cur(A, k, want_c=True, want_r=True, want_t=True)
+        ctx.k = k
+        ctx.save_for_backward(A, r.J, r.I, r.T)
+        ctx.mark_non_differentiable(r.J, r.I)
+        return r.C, r.U, r.R, r.J, r.I
+
+    @staticmethod
+    def backward(ctx, Cbar, Ubar, Rbar, _J, _I):
+        A, J, I, T = ctx.saved_tensors
+        k = ctx.k
+        Ab = cur_adjoint(A, J, I, T[:, :A.shape[1] - k], k, Cbar, Ubar, Rbar)
+        return Ab, None
+
+
+def cur_differentiable(A, k):
+    """C, U, R, J, I with C, U, R differentiable in A (skeletons frozen)."""
+    return CURFunction.apply(A, k)

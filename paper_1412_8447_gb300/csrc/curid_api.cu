@@ -207,25 +207,12 @@ curid_status a_product(const Ctx& ctx, bool tf32, bool tb, int64_t M, int64_t N,
                     P.partial, P.partial_cap);
 }
 
-// Row orthonormalisation without pivoting (Section 5.3): X (r x c) is
-// replaced by orth(X), computed by repeated Cholesky QR: G = X X^T,
-// G + shift I = L L^T, X <- L^{-1} X.  The first pass is shifted (FP32:
-// 1e-5 trace(G)) so the factorization exists at condition numbers near
-// 1/eps; the later passes restore orthonormality.  Each pass writes out of
-// place; on return *X points at the result and *tmp at the other buffer.
+// Row orthonormalisation without pivoting (Section 5.3): three Cholesky-QR
+// passes (chol_qr_rows), the Gram matrix in the plan's l x l buffer.
 template <typename real>
 curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
                        const Plan<real>& P) {
-  const int passes = 3;
-  const double shift = sizeof(real) == 4 ? 1e-5 : 1e-13;
-  for (int pass = 0; pass < passes; ++pass) {
-    CURID_TRY(gemm<real>(ctx, false, true, r, r, c, real(1), *X, ld, *X, ld, real(0), P.G, r,
-                         P.partial, P.partial_cap));
-    CURID_TRY(cholesky<real>(ctx, P.G, (int)r, pass == 0 ? shift : 0.0));
-    CURID_TRY(tri_solve<real>(ctx, (int)r, P.G, r, false, false, *X, ld, *tmp, ld, c, nullptr));
-    std::swap(*X, *tmp);
-  }
-  return CURID_OK;
+  return chol_qr_rows<real>(ctx, X, tmp, r, c, ld, P.G, P.partial, P.partial_cap);
 }
 
 // Sample matrix of Algorithm 4 with the power scheme of Section 5.3:

@@ -7,6 +7,7 @@
 //     (tri.cu) with an identity right-hand side;
 //   * the float64-accumulated product that ends the U chain.
 #include <type_traits>
+#include <utility>
 
 #include "kernels.cuh"
 
@@ -416,6 +417,25 @@ curid_status gemm_nt_f64acc(const Ctx& ctx, int64_t M, int64_t N, int64_t K, con
   return CURID_OK;
 }
 
+template <typename real>
+curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
+                          real* G, real* partial, size_t partial_cap) {
+  const int passes = 3;
+  const double shift = sizeof(real) == 4 ? 1e-5 : 1e-13;
+  for (int pass = 0; pass < passes; ++pass) {
+    CURID_TRY(gemm<real>(ctx, false, true, r, r, c, real(1), *X, ld, *X, ld, real(0), G, r,
+                         partial, partial_cap));
+    CURID_TRY(cholesky<real>(ctx, G, (int)r, pass == 0 ? shift : 0.0));
+    CURID_TRY(tri_solve<real>(ctx, (int)r, G, r, false, false, *X, ld, *tmp, ld, c, nullptr));
+    std::swap(*X, *tmp);
+  }
+  return CURID_OK;
+}
+
+template curid_status chol_qr_rows<float>(const Ctx&, float**, float**, int64_t, int64_t, int64_t,
+                                          float*, float*, size_t);
+template curid_status chol_qr_rows<double>(const Ctx&, double**, double**, int64_t, int64_t,
+                                           int64_t, double*, double*, size_t);
 template curid_status gemm_nt_f64acc<float>(const Ctx&, int64_t, int64_t, int64_t, const float*,
                                             int64_t, const float*, int64_t, double*, int64_t);
 template curid_status gemm_nt_f64acc<double>(const Ctx&, int64_t, int64_t, int64_t,
