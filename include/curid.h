@@ -48,7 +48,9 @@ typedef enum {
   CURID_TIMEOUT = 5,         /* an inter-block wait exceeded its bound */
   CURID_CUDA_ERROR = 6,      /* a CUDA runtime call failed */
   CURID_NO_WORKSPACE = 7,    /* attached workspace smaller than required */
-  CURID_UNSUPPORTED = 8      /* valid request outside what this build implements */
+  CURID_UNSUPPORTED = 8,     /* valid request outside what this build implements */
+  CURID_TOL_NOT_MET = 9      /* batched ID, per block: k_max steps left the
+                                residual above tol */
 } curid_status;
 
 typedef enum { CURID_F64 = 0, CURID_F32 = 1 } curid_dtype;
@@ -262,6 +264,61 @@ curid_status curid_cur_adjoint(curid_handle* handle, curid_dtype dtype,
                                const int32_t* I, const void* T, int64_t ldt,
                                const void* Cbar, const double* Ubar,
                                const void* Rbar, void* Abar, int64_t ldab);
+
+/* ----- batched adaptive-rank column ID --------------------------------- */
+
+/* Column IDs of nb independent blocks A_b (m_b x n_b) in one persistent
+ * launch: per block, the truncated column-pivoted QR of Algorithm 1 with the
+ * tolerance stop of Section 3 -- stop at the smallest j with
+ * ||A_b - A_b(:, J[:j]) V*||_F <= tol ||A_b||_F, i.e. the root of the sum
+ * of the unselected residual column norms squared (tol == 0: exactly
+ * min(m_b, n_b, k_max) steps) -- then T_b = S11^{-1} S12 (Eq. (2.8)).
+ * Pivot ties, the order of J[k:] and the rank-deficiency rule are those of
+ * curid_cpqr.
+ *
+ * Every array argument is DEVICE memory with nb entries: A (pointers to
+ * row-major blocks), lda, m, n, J (pointers to n_b int32 each), T (pointers
+ * to k_max x n_b entries each; T_b is written with leading dimension n_b,
+ * its first k_out[b] rows and n_b - k_out[b] columns meaningful), k_out
+ * (ranks); block_status (curid_status per block: OK, RANK_DEFICIENT,
+ * NONFINITE or TOL_NOT_MET) and order (a permutation of 0..nb-1 giving the
+ * processing order; largest blocks first balances the launch) may be NULL.
+ * max_m, max_n (host) bound every m_b, n_b: the workspace
+ * (curid_id_col_batched_workspace_size) holds one max_m x max_n scratch
+ * matrix per resident CTA.  Limits: k_max <= 128, max_n <= 2048, and the
+ * reflector, S11 and column flags (max_m + k_max^2 reals + max_n ints) fit
+ * one SM's shared memory; else CURID_UNSUPPORTED.  dtype is that of every
+ * block and T.  The call enqueues two memsets and one kernel on the handle's
+ * stream and performs no host synchronisation or allocation, so it can be
+ * captured into a CUDA graph once the workspace is attached. */
+curid_status curid_id_col_batched_workspace_size(curid_handle* handle,
+                                                 curid_dtype dtype, int max_m,
+                                                 int max_n, int k_max,
+                                                 size_t* bytes);
+curid_status curid_id_col_batched(curid_handle* handle, curid_dtype dtype,
+                                  int nb, const void* const* A,
+                                  const int64_t* lda, const int* m,
+                                  const int* n, const int* order, int max_m,
+                                  int max_n, double tol, int k_max,
+                                  int32_t* const* J, void* const* T,
+                                  int* k_out, int* block_status);
+
+/* Autotuner for curid_id_col_batched: runs the batch (same arguments, same
+ * outputs) once per feasible launch shape (threads per CTA x CTAs per SM),
+ * times each with CUDA events, and keeps the fastest shape for this dtype on
+ * the handle; later curid_id_col_batched calls use it.  Reports the chosen
+ * shape in threads / ctas_per_sm (may be NULL).  Synchronises the stream:
+ * call it outside graph capture. */
+curid_status curid_id_col_batched_autotune(curid_handle* handle,
+                                           curid_dtype dtype, int nb,
+                                           const void* const* A,
+                                           const int64_t* lda, const int* m,
+                                           const int* n, const int* order,
+                                           int max_m, int max_n, double tol,
+                                           int k_max, int32_t* const* J,
+                                           void* const* T, int* k_out,
+                                           int* block_status, int* threads,
+                                           int* ctas_per_sm);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ OK, INVALID_ARG, RANK_DEFICIENT, BREAKDOWN, NONFINITE, TIMEOUT, CUDA_ERROR, NO_W
     UNSUPPORTED = range(9)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "RANK_DEFICIENT", 3: "BREAKDOWN",
                 4: "NONFINITE", 5: "TIMEOUT", 6: "CUDA_ERROR", 7: "NO_WORKSPACE",
-                8: "UNSUPPORTED"}
+                8: "UNSUPPORTED", 9: "TOL_NOT_MET"}
 F64, F32 = 0, 1
 
 
@@ -57,6 +57,13 @@ SIGNATURES = {
                   _vp, _i64, _vp, _i64],
     "curid_cur_adjoint_workspace_size": [_vp, _int, _i64, _i64, _int,
                                          ctypes.POINTER(ctypes.c_size_t)],
+    "curid_id_col_batched_workspace_size": [_vp, _int, _int, _int, _int,
+                                            ctypes.POINTER(ctypes.c_size_t)],
+    "curid_id_col_batched": [_vp, _int, _int, _vp, _vp, _vp, _vp, _vp, _int, _int, _dbl, _int,
+                             _vp, _vp, _vp, _vp],
+    "curid_id_col_batched_autotune": [_vp, _int, _int, _vp, _vp, _vp, _vp, _vp, _int, _int, _dbl,
+                                      _int, _vp, _vp, _vp, _vp, ctypes.POINTER(_int),
+                                      ctypes.POINTER(_int)],
     "curid_cur_adjoint": [_vp, _int, _vp, _i64, _i64, _i64, _int, _vp, _vp, _vp, _i64, _vp, _vp,
                           _vp, _vp, _i64],
 }
@@ -388,3 +395,90 @@ class CURFunction(torch.autograd.Function):
 def cur_differentiable(A, k):
     """C, U, R, J, I with C, U, R differentiable in A (skeletons frozen)."""
     return CURFunction.apply(A, k)
+
+
+class BatchedID:
+    """Column IDs of many independent blocks in one persistent launch
+    (curid_id_col_batched).  ``flat`` holds the row-major blocks back to back
+    (block b of shape ``shapes[b]`` starting at element ``offsets[b]``);
+    outputs live in flat device buffers allocated here.  ``run()`` only
+    enqueues work (two memsets and one kernel) on the current stream, so it
+    can be captured into a CUDA graph."""
+
+    def __init__(self, flat, shapes, offsets, tol, k_max=64, largest_first=True):
+        self.flat = flat
+        dev = _dev(flat)
+        self.h = handle(dev)
+        self.dtype = flat.dtype
+        self.dt = _dtype_code(flat.dtype)
+        self.nb = len(shapes)
+        self.shapes = list(shapes)
+        self.tol = float(tol)
+        self.k_max = int(k_max)
+        d = flat.device
+        esz = flat.element_size()
+        m = [s[0] for s in shapes]
+        n = [s[1] for s in shapes]
+        self.max_m, self.max_n = max(m), max(n)
+        base = flat.data_ptr()
+        self.A_ptr = torch.tensor([base + esz * o for o in offsets], dtype=torch.int64, device=d)
+        self.lda = torch.tensor(n, dtype=torch.int64, device=d)
+        self.m = torch.tensor(m, dtype=torch.int32, device=d)
+        self.n = torch.tensor(n, dtype=torch.int32, device=d)
+        self.joff, self.toff = [], []
+        jt = tt = 0
+        for mb, nb_ in shapes:
+            self.joff.append(jt)
+            self.toff.append(tt)
+            jt += nb_
+            tt += self.k_max * nb_
+        self.Jflat = torch.zeros(max(jt, 1), dtype=torch.int32, device=d)
+        self.Tflat = torch.zeros(max(tt, 1), dtype=flat.dtype, device=d)
+        self.J_ptr = torch.tensor([self.Jflat.data_ptr() + 4 * o for o in self.joff],
+                                  dtype=torch.int64, device=d)
+        self.T_ptr = torch.tensor([self.Tflat.data_ptr() + esz * o for o in self.toff],
+                                  dtype=torch.int64, device=d)
+        self.k_out = torch.zeros(self.nb, dtype=torch.int32, device=d)
+        self.block_status = torch.zeros(self.nb, dtype=torch.int32, device=d)
+        order = sorted(range(self.nb), key=lambda b: -m[b] * n[b]) if largest_first else None
+        self.order = torch.tensor(order, dtype=torch.int32, device=d) if order else None
+        b = ctypes.c_size_t(0)
+        _check(self.h.lib.curid_id_col_batched_workspace_size(
+            self.h.h, self.dt, self.max_m, self.max_n, self.k_max, ctypes.byref(b)),
+            "curid_id_col_batched_workspace_size")
+        self.ws_bytes = b.value
+
+    def _args(self):
+        return (self.h.h, self.dt, self.nb, _ptr(self.A_ptr), _ptr(self.lda), _ptr(self.m),
+                _ptr(self.n), _ptr(self.order), self.max_m, self.max_n, self.tol, self.k_max,
+                _ptr(self.J_ptr), _ptr(self.T_ptr), _ptr(self.k_out), _ptr(self.block_status))
+
+    def prepare(self):
+        """Attach a large enough workspace and bind the current stream (call
+        before capturing ``run`` into a graph)."""
+        self.h.prepare(self.ws_bytes)
+
+    def run(self):
+        self.prepare()
+        _check(self.h.lib.curid_id_col_batched(*self._args()), "curid_id_col_batched")
+
+    def autotune(self):
+        """Time every feasible launch shape on this batch and keep the fastest
+        on the handle; returns (threads per CTA, CTAs per SM)."""
+        self.prepare()
+        t, c = ctypes.c_int(0), ctypes.c_int(0)
+        _check(self.h.lib.curid_id_col_batched_autotune(*self._args(), ctypes.byref(t),
+                                                        ctypes.byref(c)),
+               "curid_id_col_batched_autotune")
+        return t.value, c.value
+
+    def results(self):
+        """[(J_b, T_b, k_b, status_b)]: J_b int32 (n_b), T_b k_b x (n_b - k_b)."""
+        k = self.k_out.cpu().tolist()
+        st = self.block_status.cpu().tolist()
+        out = []
+        for b, (mb, nb_) in enumerate(self.shapes):
+            J = self.Jflat[self.joff[b]:self.joff[b] + nb_]
+            T = self.Tflat[self.toff[b]:self.toff[b] + self.k_max * nb_].view(self.k_max, nb_)
+            out.append((J, T[:k[b], :nb_ - k[b]], k[b], st[b]))
+        return out

@@ -91,6 +91,9 @@ struct curid_handle {
   std::vector<curid_phase_rec> recs;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
+  // batched column ID: launch shape chosen by the autotuner ([0] float64,
+  // [1] float32; -1 = not tuned)
+  int batch_shape[2] = {-1, -1};
 };
 
 #define CURID_CUDA(call)                                \

@@ -114,6 +114,32 @@ def laplace_block(m, n, seed, dtype=torch.float64, device="cpu"):
     return torch.from_numpy(1.0 / d).to(dtype).to(device).contiguous()
 
 
+def laplace_batch_shapes(nb, seed, lo=64, hi=512):
+    """Block shapes (m_b, n_b), each uniform on {lo..hi}."""
+    g = rng(seed)
+    return [(int(a), int(b)) for a, b in g.integers(lo, hi + 1, size=(nb, 2))]
+
+
+def laplace_batch(nb, seed, dtype=torch.float64, device="cpu", lo=64, hi=512):
+    """nb Laplace blocks with m_b, n_b uniform on {lo..hi}; block b uses
+    seed (seed, b) for its point clusters.  Returns (flat, shapes, offsets):
+    the blocks stored row-major back to back in one tensor, each starting
+    on a 16-byte boundary."""
+    shapes = laplace_batch_shapes(nb, seed, lo, hi)
+    esz = torch.empty((), dtype=dtype).element_size()
+    align = max(1, 16 // esz)
+    offsets, total = [], 0
+    for m, n in shapes:
+        offsets.append(total)
+        total += (m * n + align - 1) // align * align
+    flat = torch.zeros(total, dtype=dtype)
+    for b, (m, n) in enumerate(shapes):
+        blk = laplace_block(m, n, int(np.random.SeedSequence([seed, b]).generate_state(1)[0]),
+                            dtype)
+        flat[offsets[b]:offsets[b] + m * n] = blk.reshape(-1)
+    return flat.to(device), shapes, offsets
+
+
 # Named workloads -----------------------------------------------------------
 
 def workload_small_f64(seed=BASE_SEED + 0, device="cpu"):
