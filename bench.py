@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--tf32", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     return ap.parse_args()
 
 
@@ -314,6 +315,9 @@ def run_ours(args, ws, rank, local):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, A, curid)
+    forms = None
+    if rank == 0 and ws == 1 and not args.no_forms:
+        forms = {"adjoint": measure_adjoint(dev), "batched": measure_batched(dev)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -334,10 +338,118 @@ def run_ours(args, ws, rank, local):
         "phases_ms_per_step": {p: round(v, 4) for p, v in per_step.items()},
         "phase_share": {p: round(phase_ms[p] / total_phase, 4) for p in phase_ms},
         "cpu_baseline": cpu,
+        "forms": forms,
         "status": curid.STATUS_NAMES[st], "k_out": kout,
     }
     if rank == 0:
         print(json.dumps(line))
+
+
+def measure_adjoint(dev, steps=10, warmup=3):
+    """Forward + backward of the differentiable CUR-ID (skeletons frozen) on
+    A 2048 x 1024, sigma_j = exp(-j/20), k = 64, deterministic, loss
+    1/2 ||A - C U R||_F^2 in the dtype of A; float32 and the plain float64
+    GPU path, CUDA events on the current stream."""
+    import paper_1412_8447_gb300 as curid
+    import synthetic as syn
+    m, n, k = 2048, 1024, 64
+    stream = torch.cuda.current_stream(dev)
+    res = {"workload": f"differentiable CUR-ID, A {m}x{n}, sigma_j = exp(-j/20), k = {k}, "
+                       "deterministic; loss 1/2 ||A - CUR||_F^2, forward + backward through "
+                       "the library adjoint (skeletons frozen)",
+           "unit": "forward+backward/s"}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        A0 = syn.spectrum_matrix(m, n, syn.exp_decay(min(m, n), 20.0), BASE_SEED + 5, dt, dev)
+
+        def step():
+            A = A0.detach().requires_grad_(True)
+            C, U, R, _, _ = curid.cur_differentiable(A, k)
+            Res = A - C @ (U.to(dt) @ R)
+            loss = 0.5 * (Res * Res).sum()
+            loss.backward()
+            return A.grad
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        res[name] = {"value": 1e3 / ms, "ms_per_step": ms}
+    res["f32_over_f64"] = res["f32"]["value"] / res["f64"]["value"]
+    return res
+
+
+def measure_batched(dev, replays=5):
+    """Batched adaptive-rank column ID of 4096 Laplace blocks (m_b, n_b
+    uniform on 64..512): autotuned launch shape, the launch captured in a
+    CUDA graph and replayed; float64 (tol 1e-8) and float32 (tol 1e-5).  The
+    plain float64 GPU path (one adaptive curid_cpqr call per block) is timed
+    on 64 of the blocks for comparison."""
+    import paper_1412_8447_gb300 as curid
+    import synthetic as syn
+    nb = 4096
+    stream = torch.cuda.current_stream(dev)
+    res = {"workload": f"batched adaptive-rank column ID, {nb} Laplace blocks 1/|x-y| "
+                       "(unit boxes 3 apart), m_b, n_b uniform on 64..512, one persistent "
+                       "launch replayed from a CUDA graph",
+           "unit": "blocks/s"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, dt, tol, peak, src in (
+            ("f64", torch.float64, 1e-8, 1.25, "nominal FP64 1.25 TFLOP/s"),
+            ("f32", torch.float32, 1e-5, NUM_SMS * FP32_FMA_PER_SM_CLK * 2 * 2070e6 / 1e12,
+             "derived FP32 peak")):
+        flat, shapes, offs = syn.laplace_batch(nb, BASE_SEED + 4, dt, dev)
+        B = curid.BatchedID(flat, shapes, offs, tol=tol, k_max=64)
+        threads, per_sm = B.autotune()
+        B.run()
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            B.run()
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(replays):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / replays
+        k = B.k_out.cpu().tolist()
+        flops = sum(cpqr_flops(m, n, kb) + float(kb) * kb * (n - kb)
+                    for (m, n), kb in zip(shapes, k))
+        ach = flops / (ms / 1e3) / 1e12
+        entry = {"value": nb / (ms / 1e3), "ms_per_batch": ms, "tol": tol,
+                 "launch_shape": {"threads": threads, "ctas_per_sm": per_sm},
+                 "mean_rank": sum(k) / nb, "max_rank": max(k),
+                 "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                              "frac": ach / peak, "peak_source": src}}
+        if name == "f64":
+            sample = list(range(0, nb, nb // 64))[:64]
+            plain = []
+            for b in sample:
+                m, n = shapes[b]
+                plain.append(flat[offs[b]:offs[b] + m * n].view(m, n))
+            curid.cpqr(plain[0], tol=tol)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for Ab in plain:
+                curid.cpqr(Ab, tol=tol, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            pms = e0.elapsed_time(e1) / len(plain)
+            entry["plain_f64_path"] = {"value": 1e3 / pms, "unit": "blocks/s",
+                                       "how": "one adaptive curid_cpqr launch per block, "
+                                              "64 sampled blocks (T solve not included)"}
+        res[name] = entry
+        del B, g, flat
+        torch.cuda.empty_cache()
+    return res
 
 
 def cpu_baseline(args, A, curid):
