@@ -27,6 +27,7 @@ namespace {
 constexpr int kBatchKCap = 128;    // largest k_max (S11 of the T solve in shared memory)
 constexpr int kColsPerThread = 4;  // n_b <= 4 x threads per CTA
 constexpr int kMaxBlockDim = 512;
+constexpr int kRowBatch = 16;     // loads in flight per thread in a row sweep
 
 template <typename real>
 struct BatchParams {
@@ -153,10 +154,13 @@ __global__ void __launch_bounds__(kMaxBlockDim) batched_id_kernel(BatchParams<re
       nu2[u] = real(0);
       const int c = tid + u * nt;
       if (c < n) {
-#pragma unroll 4
-        for (int r = 0; r < m; ++r) {
-          const real x = X[(int64_t)r * n + c];
-          nu2[u] += x * x;
+        for (int r0 = 0; r0 < m; r0 += kRowBatch) {
+          real xv[kRowBatch];
+#pragma unroll
+          for (int q = 0; q < kRowBatch; ++q)
+            xv[q] = r0 + q < m ? X[(int64_t)(r0 + q) * n + c] : real(0);
+#pragma unroll
+          for (int q = 0; q < kRowBatch; ++q) nu2[u] += xv[q] * xv[q];
         }
       }
       local2 += nu2[u];
@@ -218,23 +222,44 @@ __global__ void __launch_bounds__(kMaxBlockDim) batched_id_kernel(BatchParams<re
         active[p] = 0;
       }
       __syncthreads();
-      // (3) w = tau v^T X[k:m, c]; X[k:m, c] -= w v; norm of rows k+1..m-1
+      // (3) w = tau v^T X[k:m, c]; X[k:m, c] -= w v; norm of rows k+1..m-1.
+      // Rows go in batches of kRowBatch loads issued before their use, so
+      // each thread keeps that many L2 requests in flight.
       real loc = real(0);
 #pragma unroll
       for (int u = 0; u < kColsPerThread; ++u) {
         const int c = tid + u * nt;
         if (c < n && active[c]) {
           real w = real(0);
-#pragma unroll 4
-          for (int r = k; r < m; ++r) w += v[r] * X[(int64_t)r * n + c];
+          for (int r0 = k; r0 < m; r0 += kRowBatch) {
+            real xv[kRowBatch];
+#pragma unroll
+            for (int q = 0; q < kRowBatch; ++q) {
+              const int r = r0 + q;
+              xv[q] = r < m ? X[(int64_t)r * n + c] : real(0);
+            }
+#pragma unroll
+            for (int q = 0; q < kRowBatch; ++q)
+              if (r0 + q < m) w += v[r0 + q] * xv[q];
+          }
           w *= tau;
-          X[(int64_t)k * n + c] -= w;
           real s2 = real(0);
-#pragma unroll 4
-          for (int r = k + 1; r < m; ++r) {
-            const real x = X[(int64_t)r * n + c] - w * v[r];
-            X[(int64_t)r * n + c] = x;
-            s2 += x * x;
+          for (int r0 = k; r0 < m; r0 += kRowBatch) {
+            real xv[kRowBatch];
+#pragma unroll
+            for (int q = 0; q < kRowBatch; ++q) {
+              const int r = r0 + q;
+              xv[q] = r < m ? X[(int64_t)r * n + c] : real(0);
+            }
+#pragma unroll
+            for (int q = 0; q < kRowBatch; ++q) {
+              const int r = r0 + q;
+              if (r < m) {
+                const real x = xv[q] - w * v[r];
+                X[(int64_t)r * n + c] = x;
+                if (r > k) s2 += x * x;
+              }
+            }
           }
           nu2[u] = s2;
           loc += s2;
