@@ -188,9 +188,9 @@ curid_status curid_cpqr_static(void* stream, curid_dtype dtype,
  * decompositions return CURID_UNSUPPORTED for it.
  *
  * Order limits: the k x k triangular solves (T, the row ID, U) and the
- * l x l Gram factorisations between power steps (q >= 1, l = k + p) hold
- * their matrix in one SM's shared memory, so k and, when q >= 1, l are at
- * most 256 for CURID_F32 and 192 for CURID_F64; larger requests return
+ * l x l Gram factorisations between power steps (q >= 1, l = k + p) run in
+ * one CTA with the matrix in shared memory up to order 256 (CURID_F32) /
+ * 192 (CURID_F64) and blockwise above that, up to 4096; larger k or l return
  * CURID_UNSUPPORTED before any work is queued. */
 
 /* Column ID (Algorithm 1; randomized: Algorithm 4):
@@ -251,9 +251,9 @@ curid_status curid_cur(curid_handle* handle, curid_dtype dtype,
  * float64 (leading dimension k, like U).  Output Abar m x n (ldab),
  * overwritten.  All pointers are device memory owned by the caller; the
  * scratch (curid_cur_adjoint_workspace_size bytes) is the attached
- * workspace.  k <= 256 (CURID_F32) / 192 (CURID_F64), else
- * CURID_UNSUPPORTED.  R or C numerically rank deficient: Cholesky breakdown,
- * reported by curid_last_status as CURID_BREAKDOWN (Abar then undefined). */
+ * workspace.  k <= 4096, else CURID_UNSUPPORTED.  R or C numerically rank
+ * deficient: Cholesky breakdown, reported by curid_last_status as
+ * CURID_BREAKDOWN (Abar then undefined). */
 curid_status curid_cur_adjoint_workspace_size(curid_handle* handle,
                                               curid_dtype dtype, int64_t m,
                                               int64_t n, int k,

@@ -49,6 +49,8 @@ struct CpqrParams {
   const real* Y;
   int64_t ldy;
   int l, n, k_max, nc, ldl;
+  int ncs;                       // columns of a slab held in shared memory (the rest: gys)
+  real* gys;                     // [G][nc - ncs][ldl] overflow columns, column-major
   real tol;
   real rank_rtol;
   int32_t* J;
@@ -223,11 +225,20 @@ __device__ bool gather_records(const CpqrParams<real>& P, int bf, unsigned epoch
   return ok;
 }
 
+// Column lc of this CTA's slab: shared memory for lc < ncs, else the CTA's
+// part of the global overflow area (same column-major layout).
+template <bool OV, typename real>
+__device__ __forceinline__ real* slab_col(const CpqrParams<real>& P, real* ys, int lc) {
+  if constexpr (!OV) return ys + (int64_t)lc * P.ldl;
+  return lc < P.ncs ? ys + (int64_t)lc * P.ldl
+                    : P.gys + ((int64_t)blockIdx.x * (P.nc - P.ncs) + (lc - P.ncs)) * P.ldl;
+}
+
 // Warp 0: pick the CTA's candidate (largest residual norm among its
 // unselected columns, smallest index on ties), copy its rows r0..l-1 to the
 // CTA's data slot, then publish the record of `epoch` in buffer `bf`.
-template <typename real>
-__device__ void publish(const CpqrParams<real>& P, const real* ys, const real* nrm,
+template <bool OV, typename real>
+__device__ void publish(const CpqrParams<real>& P, real* ys, const real* nrm,
                         const int* active, int ncl, int c0, int r0, int bf, unsigned epoch) {
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x;
@@ -252,8 +263,13 @@ __device__ void publish(const CpqrParams<real>& P, const real* ys, const real* n
   if (bi >= 0 && !nf) {
     constexpr int W = Words<real>::W;
     unsigned long long* dst = P.slot_data + ((int64_t)bf * G + blockIdx.x) * P.l * W;
-    const real* src = ys + (int64_t)bi * P.ldl;
-    for (int r = r0 + lane; r < P.l; r += 32) put_tagged<real>(dst + (int64_t)r * W, tag, src[r]);
+    if (!OV || bi < P.ncs) {
+      const real* src = ys + (int64_t)bi * P.ldl;
+      for (int r = r0 + lane; r < P.l; r += 32) put_tagged<real>(dst + (int64_t)r * W, tag, src[r]);
+    } else {
+      const real* src = slab_col<OV>(P, ys, bi);
+      for (int r = r0 + lane; r < P.l; r += 32) put_tagged<real>(dst + (int64_t)r * W, tag, src[r]);
+    }
   }
   if (lane == 0) {
     unsigned hi, lo;
@@ -264,14 +280,91 @@ __device__ void publish(const CpqrParams<real>& P, const real* ys, const real* n
   }
 }
 
-template <typename real>
+// One interleaved pass of a warp over columns base, base + kWarps, ... of
+// its slab (see the step loop).  SH: all of them are in shared memory, so
+// their pointers come straight from the shared array and the accesses
+// compile to shared-memory loads and stores.
+template <bool SH, typename real>
+__device__ __forceinline__ void update_group(const CpqrParams<real>& P, real* ys, const real* xv,
+                                             real* nrm, int* active, int ncl, int c0, int j,
+                                             int pcol, real beta, real tau, real scale, int base,
+                                             int lane) {
+  const int l = P.l;
+  bool v[kColsPerWarp];
+  real* y[kColsPerWarp];
+#pragma unroll
+  for (int c = 0; c < kColsPerWarp; ++c) {
+    const int lc = base + c * kWarps;
+    v[c] = lc < ncl && active[lc] != 0;
+    y[c] = SH ? ys + (int64_t)(lc < ncl ? lc : base) * P.ldl
+              : slab_col<true>(P, ys, lc < ncl ? lc : base);
+    if (v[c] && c0 + lc == pcol) {
+      for (int r = j + lane; r < l; r += 32) y[c][r] = r == j ? beta : real(0);
+      if (lane == 0) {
+        active[lc] = 0;
+        P.J[j] = pcol;
+      }
+      v[c] = false;
+    }
+  }
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < kColsPerWarp; ++c) any |= v[c];
+  if (!any) return;
+  real d[kColsPerWarp];
+#pragma unroll
+  for (int c = 0; c < kColsPerWarp; ++c) d[c] = real(0);
+  for (int r = j + 1 + lane; r < l; r += 32) {
+    const real x = xv[r];
+#pragma unroll
+    for (int c = 0; c < kColsPerWarp; ++c)
+      if (v[c]) d[c] += x * y[c][r];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < kColsPerWarp; ++c) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
+  real wj[kColsPerWarp], ws[kColsPerWarp], q[kColsPerWarp];
+#pragma unroll
+  for (int c = 0; c < kColsPerWarp; ++c) {
+    wj[c] = v[c] ? tau * (y[c][j] + scale * d[c]) : real(0);
+    ws[c] = wj[c] * scale;
+    q[c] = real(0);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < kColsPerWarp; ++c)
+      if (v[c]) y[c][j] -= wj[c];
+  }
+  for (int r = j + 1 + lane; r < l; r += 32) {
+    const real x = xv[r];
+#pragma unroll
+    for (int c = 0; c < kColsPerWarp; ++c) {
+      if (!v[c]) continue;
+      const real nv = y[c][r] - ws[c] * x;
+      y[c][r] = nv;
+      q[c] += nv * nv;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < kColsPerWarp; ++c) q[c] += __shfl_xor_sync(0xffffffffu, q[c], o);
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < kColsPerWarp; ++c)
+      if (v[c]) nrm[base + c * kWarps] = sqrt(q[c]);
+  }
+}
+
+template <typename real, bool OV>
 __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x, b = blockIdx.x;
   const int nc = P.nc, ldl = P.ldl, l = P.l;
   real* ys = reinterpret_cast<real*>(smem_raw);
-  real* xv = ys + (int64_t)nc * ldl;
+  real* xv = ys + (int64_t)P.ncs * ldl;
   real* nrm = xv + ldl;
   int* active = reinterpret_cast<int*>(nrm + nc);
 
@@ -284,19 +377,26 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
   // load the slab, column-major in shared memory
   for (int64_t e = tid; e < (int64_t)l * ncl; e += kThreads) {
     const int r = (int)(e / ncl), lc = (int)(e % ncl);
-    ys[(int64_t)lc * ldl + r] = P.Y[(int64_t)r * P.ldy + c0 + lc];
+    const real yv = P.Y[(int64_t)r * P.ldy + c0 + lc];
+    if (!OV || lc < P.ncs) ys[(int64_t)lc * ldl + r] = yv;
+    else slab_col<true>(P, ys, lc)[r] = yv;
   }
   for (int lc = tid; lc < nc; lc += kThreads) active[lc] = lc < ncl ? 1 : 0;
   __syncthreads();
   for (int lc = warp; lc < ncl; lc += kWarps) {
-    const real* y = ys + (int64_t)lc * ldl;
     real s2 = real(0);
-    for (int r = lane; r < l; r += 32) s2 += y[r] * y[r];
+    if (!OV || lc < P.ncs) {
+      const real* y = ys + (int64_t)lc * ldl;
+      for (int r = lane; r < l; r += 32) s2 += y[r] * y[r];
+    } else {
+      const real* y = slab_col<true>(P, ys, lc);
+      for (int r = lane; r < l; r += 32) s2 += y[r] * y[r];
+    }
     s2 = warp_sum(s2);
     if (lane == 0) nrm[lc] = sqrt(s2);
   }
   __syncthreads();
-  if (warp == 0) publish(P, ys, nrm, active, ncl, c0, 0, 0, 1u);
+  if (warp == 0) publish<OV>(P, ys, nrm, active, ncl, c0, 0, 0, 1u);
   __shared__ int s_stale;
 
   real normY = real(-1), nu_first = real(0);
@@ -401,73 +501,14 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
     // columns w, w + 16, w + 32, w + 48 and updates them in one interleaved
     // pass so their reductions overlap.
     for (int base = warp; base < ncl; base += kColsPerWarp * kWarps) {
-      bool v[kColsPerWarp];
-      real* y[kColsPerWarp];
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c) {
-        const int lc = base + c * kWarps;
-        v[c] = lc < ncl && active[lc] != 0;
-        y[c] = ys + (int64_t)(lc < ncl ? lc : base) * ldl;
-        if (v[c] && c0 + lc == pcol) {
-          for (int r = j + lane; r < l; r += 32) y[c][r] = r == j ? beta : real(0);
-          if (lane == 0) {
-            active[lc] = 0;
-            P.J[j] = pcol;
-          }
-          v[c] = false;
-        }
-      }
-      bool any = false;
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c) any |= v[c];
-      if (!any) continue;
-      real d[kColsPerWarp];
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c) d[c] = real(0);
-      for (int r = j + 1 + lane; r < l; r += 32) {
-        const real x = xv[r];
-#pragma unroll
-        for (int c = 0; c < kColsPerWarp; ++c)
-          if (v[c]) d[c] += x * y[c][r];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int c = 0; c < kColsPerWarp; ++c) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
-      real wj[kColsPerWarp], ws[kColsPerWarp], q[kColsPerWarp];
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c) {
-        wj[c] = v[c] ? tau * (y[c][j] + scale * d[c]) : real(0);
-        ws[c] = wj[c] * scale;
-        q[c] = real(0);
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int c = 0; c < kColsPerWarp; ++c)
-          if (v[c]) y[c][j] -= wj[c];
-      }
-      for (int r = j + 1 + lane; r < l; r += 32) {
-        const real x = xv[r];
-#pragma unroll
-        for (int c = 0; c < kColsPerWarp; ++c) {
-          if (!v[c]) continue;
-          const real nv = y[c][r] - ws[c] * x;
-          y[c][r] = nv;
-          q[c] += nv * nv;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int c = 0; c < kColsPerWarp; ++c) q[c] += __shfl_xor_sync(0xffffffffu, q[c], o);
-      if (lane == 0) {
-#pragma unroll
-        for (int c = 0; c < kColsPerWarp; ++c)
-          if (v[c]) nrm[base + c * kWarps] = sqrt(q[c]);
-      }
+      // columns past ncl are unused (their pointer falls back to column base)
+      if (!OV || min(ncl - 1, base + (kColsPerWarp - 1) * kWarps) < P.ncs)
+        update_group<true>(P, ys, xv, nrm, active, ncl, c0, j, pcol, beta, tau, scale, base, lane);
+      else
+        update_group<false>(P, ys, xv, nrm, active, ncl, c0, j, pcol, beta, tau, scale, base, lane);
     }
     __syncthreads();
-    if (warp == 0) publish(P, ys, nrm, active, ncl, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2));
+    if (warp == 0) publish<OV>(P, ys, nrm, active, ncl, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2));
 
   }
   const int k_done = j;
@@ -475,7 +516,8 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
   // S rows 0..k_done-1 in original column order
   for (int64_t e = tid; e < (int64_t)k_done * ncl; e += kThreads) {
     const int i = (int)(e / ncl), lc = (int)(e % ncl);
-    P.S[(int64_t)i * P.lds + c0 + lc] = ys[(int64_t)lc * ldl + i];
+    P.S[(int64_t)i * P.lds + c0 + lc] =
+        (!OV || lc < P.ncs) ? ys[(int64_t)lc * ldl + i] : slab_col<true>(P, ys, lc)[i];
   }
   // unselected columns in ascending order after the pivots: exchange counts
   const int fbf = (j + 1) & 1;
@@ -521,51 +563,70 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
 }
 
 template <typename real>
-size_t cpqr_smem_bytes(int nc, int ldl) {
-  return (size_t)nc * ldl * sizeof(real) + (size_t)ldl * sizeof(real) + (size_t)nc * sizeof(real) +
+size_t cpqr_smem_bytes(int ncs, int nc, int ldl) {
+  return (size_t)ncs * ldl * sizeof(real) + (size_t)ldl * sizeof(real) + (size_t)nc * sizeof(real) +
          (size_t)nc * sizeof(int) + 64;
+}
+
+// Grid, columns per CTA and how many of them fit in shared memory.
+template <typename real>
+curid_status cpqr_layout(const Ctx& ctx, int64_t l, int64_t n, int* G_out, int* nc_out,
+                         int* ncs_out) {
+  if (l <= 0 || n <= 0) return CURID_INVALID_ARG;
+  int G = (int)std::min<int64_t>(std::min(ctx.num_sms, 32 * kMaxSlotsPerLane), n);
+  const int nc = (int)((n + G - 1) / G);
+  G = (int)((n + nc - 1) / nc);
+  const int ldl = (int)(l | 1);
+  // the kernel's static shared variables share the per-block limit
+  const size_t fixed = cpqr_smem_bytes<real>(0, nc, ldl) + 1024;
+  if (fixed > ctx.smem_optin) return CURID_UNSUPPORTED;
+  const int ncs = (int)std::min<size_t>(nc, (ctx.smem_optin - fixed) / ((size_t)ldl * sizeof(real)));
+  *G_out = G;
+  *nc_out = nc;
+  *ncs_out = ncs;
+  return CURID_OK;
 }
 
 }  // namespace
 
 template <typename real>
 curid_status cpqr_plan(const Ctx& ctx, int64_t l, int64_t n, int* grid, size_t* smem) {
-  if (l <= 0 || n <= 0) return CURID_INVALID_ARG;
-  int G = (int)std::min<int64_t>(std::min(ctx.num_sms, 32 * kMaxSlotsPerLane), n);
-  const int nc = (int)((n + G - 1) / G);
-  G = (int)((n + nc - 1) / nc);
-  const int ldl = (int)(l | 1);
-  const size_t bytes = cpqr_smem_bytes<real>(nc, ldl);
+  int G, nc, ncs;
+  CURID_TRY(cpqr_layout<real>(ctx, l, n, &G, &nc, &ncs));
   *grid = G;
-  *smem = bytes;
-  if (bytes > ctx.smem_optin) return CURID_UNSUPPORTED;
+  *smem = cpqr_smem_bytes<real>(ncs, nc, (int)(l | 1));
   return CURID_OK;
 }
 
 template <typename real>
-void cpqr_carve(Carver& cv, int grid, int64_t l, CpqrScratch* s) {
-  s->grid = grid;
-  s->slots = cv.take<Rec>(2 * (size_t)grid);
-  s->slot_data = cv.take<unsigned long long>(2 * (size_t)grid * l * Words<real>::W);
-  s->counts = cv.take<int>(grid);
+void cpqr_carve(Carver& cv, const Ctx& ctx, int64_t l, int64_t n, CpqrScratch* s) {
+  int G = 1, nc = 1, ncs = 1;
+  if (cpqr_layout<real>(ctx, l, n, &G, &nc, &ncs) != CURID_OK) G = nc = ncs = 1;
+  s->grid = G;
+  s->slots = cv.take<Rec>(2 * (size_t)G);
+  s->slot_data = cv.take<unsigned long long>(2 * (size_t)G * l * Words<real>::W);
+  s->counts = cv.take<int>(G);
   s->abort_flag = cv.take<int>(1);
+  s->overflow = nc > ncs ? cv.take<real>((size_t)G * (nc - ncs) * (size_t)(l | 1)) : nullptr;
 }
 
 template <typename real>
 curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64_t ldy, int k_max,
                       double tol, int32_t* J, real* S, int64_t lds, const CpqrScratch& s,
                       int which) {
-  int G;
-  size_t smem;
-  CURID_TRY(cpqr_plan<real>(ctx, l, n, &G, &smem));
-  if (G != s.grid) return CURID_INVALID_ARG;
+  int G, nc, ncs;
+  CURID_TRY(cpqr_layout<real>(ctx, l, n, &G, &nc, &ncs));
+  if (G != s.grid || (nc > ncs && !s.overflow)) return CURID_INVALID_ARG;
+  const size_t smem = cpqr_smem_bytes<real>(ncs, nc, (int)(l | 1));
   CpqrParams<real> P;
   P.Y = Y;
   P.ldy = ldy;
   P.l = (int)l;
   P.n = (int)n;
   P.k_max = k_max;
-  P.nc = (int)((n + G - 1) / G);
+  P.nc = nc;
+  P.ncs = ncs;
+  P.gys = static_cast<real*>(s.overflow);
   P.ldl = (int)(l | 1);
   P.tol = (real)tol;
   // a pivot norm at or below 2 sqrt(l) eps nu_1 is rounding noise (Section 2.3's
@@ -584,7 +645,7 @@ curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64
   P.which = which;
   CURID_CUDA(cudaMemsetAsync(s.slots, 0, 2 * (size_t)G * sizeof(Rec), ctx.stream));
   CURID_CUDA(cudaMemsetAsync(s.abort_flag, 0, sizeof(int), ctx.stream));
-  auto fn = cpqr_kernel<real>;
+  auto fn = nc > ncs ? cpqr_kernel<real, true> : cpqr_kernel<real, false>;
   CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   void* args[] = {&P};
   CURID_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(G), dim3(kThreads), args, smem,
@@ -595,8 +656,8 @@ curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64
 
 template curid_status cpqr_plan<float>(const Ctx&, int64_t, int64_t, int*, size_t*);
 template curid_status cpqr_plan<double>(const Ctx&, int64_t, int64_t, int*, size_t*);
-template void cpqr_carve<float>(Carver&, int, int64_t, CpqrScratch*);
-template void cpqr_carve<double>(Carver&, int, int64_t, CpqrScratch*);
+template void cpqr_carve<float>(Carver&, const Ctx&, int64_t, int64_t, CpqrScratch*);
+template void cpqr_carve<double>(Carver&, const Ctx&, int64_t, int64_t, CpqrScratch*);
 template curid_status cpqr_run<float>(const Ctx&, const float*, int64_t, int64_t, int64_t, int,
                                       double, int32_t*, float*, int64_t, const CpqrScratch&, int);
 template curid_status cpqr_run<double>(const Ctx&, const double*, int64_t, int64_t, int64_t, int,

@@ -79,11 +79,11 @@ curid_status run_static(const StaticDevice& d, cudaStream_t stream, const real* 
   Carver count(nullptr);
   count.take<StatusBlock>(1);
   CpqrScratch cs;
-  cpqr_carve<real>(count, grid, l, &cs);
+  cpqr_carve<real>(count, ctx, l, n, &cs);
   if (count.used > kStaticScratchBytes) return CURID_NO_WORKSPACE;
   Carver cv(d.base);
   StatusBlock* st = cv.take<StatusBlock>(1);
-  cpqr_carve<real>(cv, grid, l, &cs);
+  cpqr_carve<real>(cv, ctx, l, n, &cs);
   ctx.status = st;
   CURID_CUDA(cudaMemsetAsync(st, 0, sizeof(StatusBlock), stream));
   CURID_TRY(cpqr_run<real>(ctx, Y, l, n, ldy, k_max, tol, J, S, n, cs, 0));

@@ -150,7 +150,7 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
   int grid;
   size_t smem;
   CURID_TRY(cpqr_plan<real>(ctx, ly, n, &grid, &smem));
-  cpqr_carve<real>(cv, grid, ly, &P->cs);
+  cpqr_carve<real>(cv, ctx, ly, n, &P->cs);
   P->S = cv.take<real>((size_t)k * n);
   P->S11 = cv.take<real>((size_t)k * k);
   P->S12 = cv.take<real>((size_t)k * std::max<int64_t>(1, n - k));
@@ -162,7 +162,7 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
   if (op == Op::Tsid || op == Op::Cur) {
     P->Ct = cv.take<real>((size_t)k * m);
     CURID_TRY(cpqr_plan<real>(ctx, k, m, &grid, &smem));
-    cpqr_carve<real>(cv, grid, k, &P->rs);
+    cpqr_carve<real>(cv, ctx, k, m, &P->rs);
     if (need_I) P->I = cv.take<int32_t>(m);
     P->SW = cv.take<real>((size_t)k * m);
     P->SW11 = cv.take<real>((size_t)k * k);
@@ -619,11 +619,11 @@ curid_status curid_cpqr(curid_handle* handle, curid_dtype dtype, const void* Y, 
       Carver cv(nullptr);
       StatusBlock* st = cv.take<StatusBlock>(1);
       CpqrScratch cs;
-      cpqr_carve<real>(cv, grid, l, &cs);
+      cpqr_carve<real>(cv, ctx, l, n, &cs);
       if (!handle->ws || cv.used > handle->ws_bytes) return CURID_NO_WORKSPACE;
       Carver cw(handle->ws);
       st = cw.take<StatusBlock>(1);
-      cpqr_carve<real>(cw, grid, l, &cs);
+      cpqr_carve<real>(cw, ctx, l, n, &cs);
       ctx.status = st;
       CURID_CUDA(cudaMemsetAsync(st, 0, sizeof(StatusBlock), ctx.stream));
       PhaseScope ps(handle, CURID_PHASE_CPQR_COL);

@@ -216,7 +216,7 @@ __device__ __forceinline__ int chol_diag_cta(real* D, real* W, real* pcol, real*
 // FLAG_BREAKDOWN.
 template <typename real>
 __global__ void __launch_bounds__(kSmallThreads, 1)
-chol_kernel(real* __restrict__ G, int l, real rel_shift, StatusBlock* status) {
+chol_kernel(real* __restrict__ G, int l, int64_t ldg, real rel_shift, StatusBlock* status) {
   using B = CholBlk<real>;
   using V = typename B::V;
   constexpr int LD = B::LD;
@@ -233,7 +233,7 @@ chol_kernel(real* __restrict__ G, int l, real rel_shift, StatusBlock* status) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (warp == 0) {
     real tr = real(0);
-    for (int i = lane; i < l; i += 32) tr += G[(int64_t)i * l + i];
+    for (int i = lane; i < l; i += 32) tr += G[(int64_t)i * ldg + i];
     tr = warp_sum(tr);
     if (lane == 0) s_tr = tr;
   }
@@ -249,7 +249,7 @@ chol_kernel(real* __restrict__ G, int l, real rel_shift, StatusBlock* status) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int j = 32 * u + lane;
-        v[u] = (u <= bi && i < l && j < l) ? G[(int64_t)i * l + j] : real(0);
+        v[u] = (u <= bi && i < l && j < l) ? G[(int64_t)i * ldg + j] : real(0);
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
@@ -329,13 +329,14 @@ chol_kernel(real* __restrict__ G, int l, real rel_shift, StatusBlock* status) {
   }
   if (!done) {
     if (tid == 0) set_flag(&status->flags, FLAG_BREAKDOWN);
-    for (int e = tid; e < l * l; e += kSmallThreads) G[e] = (e / l == e % l) ? real(1) : real(0);
+    for (int e = tid; e < l * l; e += kSmallThreads)
+      G[(int64_t)(e / l) * ldg + e % l] = (e / l == e % l) ? real(1) : real(0);
     return;
   }
   for (int i = warp; i < l; i += kSmallWarps) {
     const int bi = i >> 5, r = i & 31;
     for (int j = lane; j < l; j += 32)
-      G[(int64_t)i * l + j] = j <= i ? chol_block(a, bi, j >> 5)[r * LD + (j & 31)] : real(0);
+      G[(int64_t)i * ldg + j] = j <= i ? chol_block(a, bi, j >> 5)[r * LD + (j & 31)] : real(0);
   }
 }
 
@@ -378,8 +379,14 @@ bool upper_tri_inverse_fits(const Ctx& ctx, int k) {
   return tri_solve_fits<real>(ctx, k);
 }
 template <typename real>
+bool chol_one_cta(const Ctx& ctx, int l) {
+  return l <= 256 && chol_smem<real>(l) <= ctx.smem_optin;
+}
+
+template <typename real>
 bool chol_inverse_fits(const Ctx& ctx, int l) {
-  return l <= 256 && chol_smem<real>(l) <= ctx.smem_optin && tri_solve_fits<real>(ctx, l);
+  return l > 0 && l <= kMaxDenseOrder && chol_one_cta<real>(ctx, kCholBlock<real>()) &&
+         tri_solve_fits<real>(ctx, l);
 }
 
 template <typename real>
@@ -389,15 +396,83 @@ curid_status upper_tri_inverse(const Ctx& ctx, const real* S11, int k, const int
 }
 
 template <typename real>
-curid_status cholesky(const Ctx& ctx, real* G, int l, double rel_shift) {
-  if (l <= 0) return CURID_OK;
-  if (!chol_inverse_fits<real>(ctx, l)) return CURID_UNSUPPORTED;
+curid_status chol_launch(const Ctx& ctx, real* G, int l, int64_t ldg, double rel_shift) {
   const size_t smem = chol_smem<real>(l);
   auto fn = chol_kernel<real>;
   CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  fn<<<1, kSmallThreads, smem, ctx.stream>>>(G, l, (real)rel_shift, ctx.status);
+  fn<<<1, kSmallThreads, smem, ctx.stream>>>(G, l, ldg, (real)rel_shift, ctx.status);
   CURID_LAUNCHED(ctx);
   return CURID_OK;
+}
+
+// G (l x l, leading dimension l) += shift * trace(G) * I, one CTA.
+template <typename real>
+__global__ void add_trace_shift_kernel(real* G, int l, real rel_shift) {
+  __shared__ real s_red[32];
+  real tr = real(0);
+  for (int i = threadIdx.x; i < l; i += blockDim.x) tr += G[(int64_t)i * l + i];
+  tr = warp_sum(tr);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = tr;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tr = threadIdx.x < (int)(blockDim.x >> 5) ? s_red[threadIdx.x] : real(0);
+    tr = warp_sum(tr);
+    if (threadIdx.x == 0) s_red[0] = tr;
+  }
+  __syncthreads();
+  const real sh = rel_shift * s_red[0];
+  for (int i = threadIdx.x; i < l; i += blockDim.x) G[(int64_t)i * l + i] += sh;
+}
+
+// zero the strict upper triangle of G (l x l, leading dimension l)
+template <typename real>
+__global__ void zero_upper_kernel(real* G, int l) {
+  const int64_t total = (int64_t)l * l;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    if (e % l > e / l) G[e] = real(0);
+}
+
+// Cholesky of order l beyond one CTA: right-looking over diagonal blocks of
+// kCholBlock, each factored by chol_kernel; the panel L21^T = L11^{-1} G12
+// is solved in place in G's upper part (G is symmetric, so G12 = G21^T),
+// the trailing block is updated with G22 -= (L21^T)^T L21^T, and L21 is
+// written below the diagonal by a transpose.  The shift uses the trace of
+// the whole matrix, as in the one-CTA kernel.
+template <typename real>
+curid_status chol_blocked(const Ctx& ctx, real* G, int l, double rel_shift) {
+  if (rel_shift > 0) {
+    add_trace_shift_kernel<real><<<1, 512, 0, ctx.stream>>>(G, l, (real)rel_shift);
+    CURID_LAUNCHED(ctx);
+  }
+  const int bs = kCholBlock<real>();
+  for (int kb = 0; kb < l; kb += bs) {
+    const int b = std::min(bs, l - kb), rest = l - kb - b;
+    real* D = G + (int64_t)kb * l + kb;
+    CURID_TRY(chol_launch<real>(ctx, D, b, l, 0.0));
+    if (rest == 0) break;
+    real* G12 = D + b;
+    real* G21 = D + (int64_t)b * l;
+    real* G22 = G21 + b;
+    CURID_TRY(tri_solve<real>(ctx, b, D, l, false, false, G12, l, G12, l, rest, nullptr));
+    CURID_TRY(gemm<real>(ctx, true, false, rest, rest, b, real(-1), G12, l, G12, l, real(1), G22,
+                         l, nullptr, 0));
+    CURID_TRY(transpose2d<real>(ctx, G12, l, G21, l, b, rest));
+  }
+  const int64_t total = (int64_t)l * l;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256,
+                                                                      8LL * ctx.num_sms));
+  zero_upper_kernel<real><<<g, 256, 0, ctx.stream>>>(G, l);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
+template <typename real>
+curid_status cholesky(const Ctx& ctx, real* G, int l, double rel_shift) {
+  if (l <= 0) return CURID_OK;
+  if (chol_one_cta<real>(ctx, l)) return chol_launch<real>(ctx, G, l, l, rel_shift);
+  if (!chol_inverse_fits<real>(ctx, l)) return CURID_UNSUPPORTED;
+  return chol_blocked<real>(ctx, G, l, rel_shift);
 }
 
 template <typename real>

@@ -46,6 +46,7 @@ size_t gemm_tf32_partial_elems(int64_t M, int64_t N, int64_t K, int num_sms);
 struct CpqrScratch {
   void* slots;       // 2 * G slot records
   void* slot_data;   // 2 * G * l reals
+  void* overflow;    // columns beyond shared memory: G * (nc - ncs) * ldl reals
   int* counts;       // G
   int* abort_flag;   // 1
   int grid;          // G
@@ -53,7 +54,7 @@ struct CpqrScratch {
 template <typename real>
 curid_status cpqr_plan(const Ctx& ctx, int64_t l, int64_t n, int* grid, size_t* smem);
 template <typename real>
-void cpqr_carve(Carver& cv, int grid, int64_t l, CpqrScratch* s);
+void cpqr_carve(Carver& cv, const Ctx& ctx, int64_t l, int64_t n, CpqrScratch* s);
 // which: 0 = column CPQR (status k_done/k_eff), 1 = row CPQR (status k_row)
 template <typename real>
 curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64_t ldy,
@@ -61,6 +62,12 @@ curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64
                       const CpqrScratch& s, int which);
 
 // ---- small dense factorizations (dense_small.cu) ---------------------------
+// Orders up to the one-CTA limits (256 float32, 192 float64) run in one CTA
+// with the matrix in shared memory; larger orders, up to kMaxDenseOrder, are
+// blocked over diagonal blocks of that size with GEMM updates in between.
+constexpr int kMaxDenseOrder = 4096;
+template <typename real>
+constexpr int kCholBlock() { return sizeof(real) == 4 ? 256 : 192; }
 // Inverse of the leading triangle of S (k x k, columns gathered by J) for the
 // T solve; rows/columns at and after *k_eff are zeroed.
 template <typename real>
@@ -78,7 +85,9 @@ curid_status chol_inverse(const Ctx& ctx, real* G, int l, double rel_shift, real
 // Solve op(T) X = B (T k x k row-major with leading dimension ldt, upper or
 // lower, op = transpose when trans) for N columns; B == nullptr means the
 // identity (X = op(T)^{-1}).  Rows/columns at or after *kk (if given) are
-// an identity block with zero right-hand side.  X must not alias T or B.
+// an identity block with zero right-hand side.  X may be B itself (same
+// pointer and leading dimension) but must not alias T.  Orders above one
+// CTA's limit are solved blockwise (trans == false only).
 template <typename real>
 curid_status tri_solve(const Ctx& ctx, int k, const real* T, int64_t ldt, bool upper, bool trans,
                        const real* B, int64_t ldb, real* X, int64_t ldx, int64_t N,

@@ -49,6 +49,7 @@ struct TriParams {
   int64_t ldx;
   int64_t N;
   const int* kk;        // numerical rank (device) or nullptr
+  int kk_off;           // this triangle starts at row/column kk_off of the full one
 };
 
 // lower-triangle element (i, j), i >= j, in the solve's index space, read
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_solve_kernel(TriParams<rea
   real* Ls = reinterpret_cast<real*>(smem_raw);                 // packed blocks, 32 x 33
   real* Xs = Ls + (size_t)packed_block(nb, 0) * kTB * kTriLd;  // KP x NC
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int kk = P.kk ? max(0, min(P.k, *P.kk)) : P.k;
+  const int kk = P.kk ? max(0, min(P.k, *P.kk - P.kk_off)) : P.k;
   const int64_t c0 = (int64_t)blockIdx.x * NC;
 
   // triangle -> packed lower blocks (identity past k and past the rank)
@@ -186,16 +187,19 @@ size_t tri_smem(int k) {
 }  // namespace
 
 template <typename real>
-bool tri_solve_fits(const Ctx& ctx, int k) {
+bool tri_one_cta(const Ctx& ctx, int k) {
   return k > 0 && (k + kTB - 1) / kTB <= kTriThreads / 32 && tri_smem<real>(k) <= ctx.smem_optin;
 }
 
 template <typename real>
-curid_status tri_solve(const Ctx& ctx, int k, const real* T, int64_t ldt, bool upper, bool trans,
-                       const real* B, int64_t ldb, real* X, int64_t ldx, int64_t N,
-                       const int* kk) {
-  if (k <= 0 || N <= 0) return CURID_OK;
-  if (!tri_solve_fits<real>(ctx, k)) return CURID_UNSUPPORTED;
+bool tri_solve_fits(const Ctx& ctx, int k) {
+  return k > 0 && k <= kMaxDenseOrder && tri_one_cta<real>(ctx, kCholBlock<real>());
+}
+
+template <typename real>
+curid_status tri_launch(const Ctx& ctx, int k, const real* T, int64_t ldt, bool upper, bool trans,
+                        const real* B, int64_t ldb, real* X, int64_t ldx, int64_t N,
+                        const int* kk, int kk_off) {
   TriParams<real> P;
   P.k = k;
   P.nb = (k + kTB - 1) / kTB;
@@ -211,6 +215,7 @@ curid_status tri_solve(const Ctx& ctx, int k, const real* T, int64_t ldt, bool u
   P.ldx = ldx;
   P.N = N;
   P.kk = kk;
+  P.kk_off = kk_off;
   const size_t smem = tri_smem<real>(k);
   auto fn = tri_solve_kernel<real>;
   CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -218,6 +223,67 @@ curid_status tri_solve(const Ctx& ctx, int k, const real* T, int64_t ldt, bool u
   fn<<<(unsigned)grid, kTriThreads, smem, ctx.stream>>>(P);
   CURID_LAUNCHED(ctx);
   return CURID_OK;
+}
+
+// X (k x N, leading dimension ldx) = I
+template <typename real>
+__global__ void set_identity_kernel(real* X, int64_t ldx, int k, int64_t N) {
+  const int64_t total = (int64_t)k * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / N, j = e % N;
+    X[i * ldx + j] = i == j ? real(1) : real(0);
+  }
+}
+
+// Orders beyond one CTA: block substitution over diagonal blocks of
+// kCholBlock, each solved in place by tri_solve_kernel (every CTA of that
+// kernel reads all of its columns before writing them, so X may be B), the
+// blocks not yet solved updated by GEMM.  Lower: forward, top block first;
+// upper: backward.  A device rank kk is passed to every block with its
+// offset, so rows at and after kk stay zero.
+template <typename real>
+curid_status tri_blocked(const Ctx& ctx, int k, const real* T, int64_t ldt, bool upper,
+                         const real* B, int64_t ldb, real* X, int64_t ldx, int64_t N,
+                         const int* kk) {
+  if (B == nullptr) {
+    const int64_t total = (int64_t)k * N;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256,
+                                                                        16LL * ctx.num_sms));
+    set_identity_kernel<real><<<g, 256, 0, ctx.stream>>>(X, ldx, k, N);
+    CURID_LAUNCHED(ctx);
+  } else if (B != X || ldb != ldx) {
+    CURID_TRY(copy2d<real>(ctx, B, ldb, X, ldx, k, N));
+  }
+  const int bs = kCholBlock<real>();
+  const int nb = (k + bs - 1) / bs;
+  for (int t = 0; t < nb; ++t) {
+    const int i = upper ? nb - 1 - t : t;
+    const int off = i * bs, b = std::min(bs, k - off);
+    real* Xi = X + (int64_t)off * ldx;
+    CURID_TRY(tri_launch<real>(ctx, b, T + (int64_t)off * ldt + off, ldt, upper, false, Xi, ldx, Xi,
+                               ldx, N, kk, off));
+    if (!upper && off + b < k) {
+      CURID_TRY(gemm<real>(ctx, false, false, k - off - b, N, b, real(-1),
+                           T + (int64_t)(off + b) * ldt + off, ldt, Xi, ldx, real(1),
+                           X + (int64_t)(off + b) * ldx, ldx, nullptr, 0));
+    } else if (upper && off > 0) {
+      CURID_TRY(gemm<real>(ctx, false, false, off, N, b, real(-1), T + off, ldt, Xi, ldx, real(1),
+                           X, ldx, nullptr, 0));
+    }
+  }
+  return CURID_OK;
+}
+
+template <typename real>
+curid_status tri_solve(const Ctx& ctx, int k, const real* T, int64_t ldt, bool upper, bool trans,
+                       const real* B, int64_t ldb, real* X, int64_t ldx, int64_t N,
+                       const int* kk) {
+  if (k <= 0 || N <= 0) return CURID_OK;
+  if (tri_one_cta<real>(ctx, k))
+    return tri_launch<real>(ctx, k, T, ldt, upper, trans, B, ldb, X, ldx, N, kk, 0);
+  if (!tri_solve_fits<real>(ctx, k) || trans) return CURID_UNSUPPORTED;
+  return tri_blocked<real>(ctx, k, T, ldt, upper, B, ldb, X, ldx, N, kk);
 }
 
 template bool tri_solve_fits<float>(const Ctx&, int);

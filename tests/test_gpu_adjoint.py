@@ -90,10 +90,15 @@ def test_adjoint_rejects_bad_arguments():
     A = cuda(syn.spectrum_matrix(300, 280, syn.exp_decay(280, 8.0), 7, torch.float32))
     J = torch.arange(280, dtype=torch.int32, device="cuda:0")
     I = torch.arange(300, dtype=torch.int32, device="cuda:0")
-    T = torch.zeros((257, 23), dtype=torch.float32, device="cuda:0")
-    with pytest.raises(curid.CuridError) as e:
-        curid.cur_adjoint(A, J, I, T, 257)
-    assert e.value.status == 8
+    T = torch.zeros((40, 240), dtype=torch.float32, device="cuda:0")
     with pytest.raises(curid.CuridError) as e:
         curid.cur_adjoint(A, J, I, T, 0)
     assert e.value.status == 1
+    with pytest.raises(curid.CuridError) as e:
+        curid.cur_adjoint(A, J, I, T, 281)
+    assert e.value.status == 1
+    big = torch.zeros((4100, 4100), dtype=torch.float32, device="cuda:0")
+    Jb = torch.arange(4100, dtype=torch.int32, device="cuda:0")
+    with pytest.raises(curid.CuridError) as e:
+        curid.cur_adjoint(big, Jb, Jb, big[:4097, :3], 4097)
+    assert e.value.status == 8

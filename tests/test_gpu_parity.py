@@ -195,11 +195,14 @@ def test_randomized_cur_moderate(dtype):
         assert eg <= 1.05 * eo, (eg, eo)
 
 
-@pytest.mark.parametrize("dtype,k", [(torch.float32, 246), (torch.float64, 182)])
-def test_randomized_cur_largest_order(dtype, k):
-    """l = k + p at the largest order the Gram factorisation takes in one
-    SM (256 float32, 192 float64), with a power step so it runs."""
-    m, n, p, q = 1200, 900, 10, 1
+@pytest.mark.parametrize("dtype,k,p", [(torch.float32, 246, 10), (torch.float64, 182, 10),
+                                       (torch.float32, 300, 20), (torch.float64, 240, 10)])
+def test_randomized_cur_large_order(dtype, k, p):
+    """l = k + p at the largest one-CTA orders of the Gram factorisation (256
+    float32, 192 float64) and beyond them (blocked Cholesky and triangular
+    solves; the T and U solves of order k blocked as well), with a power
+    step."""
+    m, n, q = 1200, 900, 1
     A = syn.spectrum_matrix(m, n, syn.exp_decay(min(m, n), 60.0), 41, dtype)
     Om = syn.gaussian(k + p, m, 42, dtype)
     r = curid.cur(cuda(A), k, p=p, q=q, omega=cuda(Om), want_c=True, want_r=True, want_t=True)
@@ -217,13 +220,35 @@ def test_randomized_cur_largest_order(dtype, k):
         assert abs(eg - eo) <= 1e-12
 
 
-@pytest.mark.parametrize("dtype,l", [(torch.float32, 257), (torch.float64, 193)])
-def test_order_beyond_limit_is_unsupported(dtype, l):
-    m, n, p = 600, 500, 10
-    A = syn.spectrum_matrix(m, n, syn.exp_decay(min(m, n), 60.0), 43, dtype)
+def test_order_beyond_limit_is_unsupported():
+    m = n = 4200
+    A = torch.zeros((m, n), dtype=torch.float32, device="cuda:0")
     with pytest.raises(curid.CuridError) as e:
-        curid.cur(cuda(A), l - p, p=p, q=1, seed=5)
+        curid.cur(A, 4090, p=10, q=1, seed=5)
     assert e.value.status == 8
+
+
+@pytest.mark.parametrize("dtype,l,n,k", [(torch.float32, 520, 20000, 64),
+                                         (torch.float64, 300, 40000, 48)])
+def test_cpqr_overflow_columns(dtype, l, n, k):
+    """Slabs larger than one SM's shared memory (520 x 134 float32 columns,
+    300 x 264 float64): the columns that do not fit live in global memory;
+    the planted pivot order must come out exactly, and S must match the
+    oracle's rows up to sign."""
+    Y, perm = syn.planted_pivots(l, n, k, 44, decay=0.85 if dtype == torch.float32 else 2 ** -0.5,
+                                 dtype=dtype)
+    r = curid.cpqr(cuda(Y), k=k)
+    J = npi(r.J)
+    assert list(J[:k]) == list(perm[:k])
+    assert sorted(J.tolist()) == list(range(n)) and list(J[k:]) == sorted(J[k:].tolist())
+    o = O.cpqr(np64(Y), k=k)
+    S = np64(r.S)
+    So = np.zeros((k, n))
+    So[:, o.J] = o.S1
+    for i in range(k):
+        sgn = np.sign(S[i, J[i]]) * np.sign(So[i, J[i]])
+        tol = 1e-4 if dtype == torch.float32 else 1e-10
+        assert np.max(np.abs(sgn * S[i] - So[i])) <= tol * np.max(np.abs(So[i]))
 
 
 def test_random_omega_generated_on_device():
