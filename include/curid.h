@@ -53,7 +53,15 @@ typedef enum {
                                 residual above tol */
 } curid_status;
 
-typedef enum { CURID_F64 = 0, CURID_F32 = 1 } curid_dtype;
+/* Element type of A.  CURID_BF16 (bfloat16 storage; the precision form of
+ * the method): only the randomized decompositions (p >= 0) of curid_id_col,
+ * curid_tsid and curid_cur, with lda a multiple of 8 and A 16-byte aligned
+ * (else CURID_UNSUPPORTED).  The products with A run as BF16 tensor-core
+ * MMAs with float32 accumulation, the sample operand split into two BF16
+ * parts (about 16 significant bits); every other step runs in float32 and
+ * the T solve (Eq. (2.8)) in float64.  Outputs: T and TW float32, C and R
+ * bfloat16 (exact copies of A's entries), U float64. */
+typedef enum { CURID_F64 = 0, CURID_F32 = 1, CURID_BF16 = 2 } curid_dtype;
 
 /* Randomized front end (Section 5, Algorithm 4 and the power scheme of
  * Section 5.3).
@@ -136,7 +144,9 @@ curid_status curid_gaussian(curid_handle* handle, curid_dtype dtype,
 
 /* Sample matrix Y = Omega A (A^* A)^q (Eq. (5.1); Section 5.3 with orth):
  * A m x n (lda), omega l x m (leading dimension m, device, required),
- * Y l x n written with leading dimension n. */
+ * Y l x n written with leading dimension n.  With CURID_BF16, A is
+ * bfloat16 (lda a multiple of 8, 16-byte aligned) and omega and Y are
+ * float32. */
 curid_status curid_sketch_matrix(curid_handle* handle, curid_dtype dtype,
                                  const void* A, int64_t m, int64_t n,
                                  int64_t lda, int l, int q, int tf32,

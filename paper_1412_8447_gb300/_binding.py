@@ -20,7 +20,7 @@ OK, INVALID_ARG, RANK_DEFICIENT, BREAKDOWN, NONFINITE, TIMEOUT, CUDA_ERROR, NO_W
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "RANK_DEFICIENT", 3: "BREAKDOWN",
                 4: "NONFINITE", 5: "TIMEOUT", 6: "CUDA_ERROR", 7: "NO_WORKSPACE",
                 8: "UNSUPPORTED", 9: "TOL_NOT_MET"}
-F64, F32 = 0, 1
+F64, F32, BF16 = 0, 1, 2
 
 
 class CuridError(RuntimeError):
@@ -95,7 +95,14 @@ def _dtype_code(t):
         return F64
     if t == torch.float32:
         return F32
-    raise TypeError(f"unsupported dtype {t}; use float32 or float64")
+    if t == torch.bfloat16:
+        return BF16
+    raise TypeError(f"unsupported dtype {t}; use float32, float64 or bfloat16")
+
+
+def _work_dtype(t):
+    """dtype of T and TW: float32 for bfloat16 storage, else that of A."""
+    return torch.float32 if t == torch.bfloat16 else t
 
 
 def _ptr(t):
@@ -245,7 +252,7 @@ def sketch_matrix(A, omega, q=0, tf32=False):
     l = omega.shape[0]
     dt = _dtype_code(A.dtype)
     h.prepare(workspace_bytes(h, dt, m, n, 1, _sketch(max(0, l - 1), q, 0, omega, tf32)))
-    Y = torch.empty((l, n), dtype=A.dtype, device=A.device)
+    Y = torch.empty((l, n), dtype=_work_dtype(A.dtype), device=A.device)
     _check(h.lib.curid_sketch_matrix(h.h, dt, _ptr(A), m, n, A.stride(0), l, q,
                                      1 if tf32 else 0, _ptr(omega.contiguous()), _ptr(Y)),
            "curid_sketch_matrix")
@@ -286,7 +293,7 @@ def id_col(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, check=True):
     """Column ID A ~ A(:, J[:k]) [I T] P^T (Algorithm 1; p >= 0: Algorithm 4)."""
     A, h, m, n, dt, sk = _prep(A, k, p, q, seed, omega, tf32)
     J = torch.empty(n, dtype=torch.int32, device=A.device)
-    T = torch.empty((k, max(n - k, 1)), dtype=A.dtype, device=A.device)
+    T = torch.empty((k, max(n - k, 1)), dtype=_work_dtype(A.dtype), device=A.device)
     _check(h.lib.curid_id_col(h.h, dt, _ptr(A), m, n, A.stride(0), k, 0.0, sk, _ptr(J), _ptr(T),
                               T.stride(0)), "curid_id_col")
     return _finish(h, Result(J=J, T=T[:, :n - k]), check, "curid_id_col")
@@ -307,8 +314,8 @@ def tsid(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, check=True):
     A, h, m, n, dt, sk = _prep(A, k, p, q, seed, omega, tf32)
     J = torch.empty(n, dtype=torch.int32, device=A.device)
     I = torch.empty(m, dtype=torch.int32, device=A.device)
-    T = torch.empty((k, max(n - k, 1)), dtype=A.dtype, device=A.device)
-    TW = torch.empty((k, max(m - k, 1)), dtype=A.dtype, device=A.device)
+    T = torch.empty((k, max(n - k, 1)), dtype=_work_dtype(A.dtype), device=A.device)
+    TW = torch.empty((k, max(m - k, 1)), dtype=_work_dtype(A.dtype), device=A.device)
     _check(h.lib.curid_tsid(h.h, dt, _ptr(A), m, n, A.stride(0), k, 0.0, sk, _ptr(J), _ptr(T),
                             T.stride(0), _ptr(I), _ptr(TW), TW.stride(0)), "curid_tsid")
     return _finish(h, Result(J=J, T=T[:, :n - k], I=I, TW=TW[:, :m - k]), check, "curid_tsid")
@@ -324,8 +331,10 @@ def cur_outputs(A, k, want_c=False, want_r=False, want_t=False, want_tw=False):
         U=torch.empty((k, k), dtype=torch.float64, device=dev),
         C=torch.empty((m, k), dtype=A.dtype, device=dev) if want_c else None,
         R=torch.empty((k, n), dtype=A.dtype, device=dev) if want_r else None,
-        T=torch.empty((k, max(n - k, 1)), dtype=A.dtype, device=dev) if want_t else None,
-        TW=torch.empty((k, max(m - k, 1)), dtype=A.dtype, device=dev) if want_tw else None)
+        T=torch.empty((k, max(n - k, 1)), dtype=_work_dtype(A.dtype), device=dev)
+        if want_t else None,
+        TW=torch.empty((k, max(m - k, 1)), dtype=_work_dtype(A.dtype), device=dev)
+        if want_tw else None)
 
 
 def cur(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, want_c=False, want_r=False,

@@ -99,6 +99,11 @@ struct Plan {
   real* Uh = nullptr;     // k x k
   real* partial = nullptr;
   size_t partial_cap = 0;
+  // BF16 storage of A: the split sample operand, and the float64 T solve
+  void* xsplit = nullptr;
+  size_t xsplit_elems = 0;
+  double* S11d = nullptr;  // k x k
+  double* S12d = nullptr;  // k x (n - k)
   size_t bytes = 0;
 };
 
@@ -110,6 +115,7 @@ struct Dims {
   bool randomized;
   int q;
   bool tf32 = false;
+  bool bf16 = false;  // A stored as bfloat16 (float32 pipeline, BF16 tensor-core products)
 };
 
 template <typename real>
@@ -132,6 +138,10 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
     if (d.tf32) {
       part = std::max(part, gemm_tf32_partial_elems(l, n, m, ctx.num_sms));
       part = std::max(part, gemm_tf32_partial_elems(l, m, n, ctx.num_sms));
+    }
+    if (d.bf16) {
+      P->xsplit_elems = gemm_bf16_split_elems(l, std::max(m, n));
+      P->xsplit = cv.take<__nv_bfloat16>(P->xsplit_elems);
     }
     if (d.q == 0) {
       P->B[0] = cv.take<real>((size_t)l * pad4(n));
@@ -156,6 +166,10 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
   P->S12 = cv.take<real>((size_t)k * std::max<int64_t>(1, n - k));
   P->Sinv = cv.take<real>((size_t)k * k);
   P->T = cv.take<real>((size_t)k * std::max<int64_t>(1, n - k));
+  if (d.bf16) {
+    P->S11d = cv.take<double>((size_t)k * k);
+    P->S12d = cv.take<double>((size_t)k * std::max<int64_t>(1, n - k));
+  }
   upd(k, n - k, k);
   if (!tri_solve_fits<real>(ctx, k)) return CURID_UNSUPPORTED;
   if (d.randomized && d.q > 0 && !chol_inverse_fits<real>(ctx, l)) return CURID_UNSUPPORTED;
@@ -195,16 +209,18 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
 // Products that read A (Y = Omega A, Z = Q A^T, Y = Q A): FP32 FMA, FP64 FMA,
 // or TF32 tensor cores when requested.
 template <typename real>
-curid_status a_product(const Ctx& ctx, bool tf32, bool tb, int64_t M, int64_t N, int64_t K,
-                       const real* X, int64_t ldx, const real* A, int64_t lda, real* out,
-                       int64_t ldo, const Plan<real>& P) {
+curid_status a_product(const Ctx& ctx, bool tf32, bool bf16, bool tb, int64_t M, int64_t N,
+                       int64_t K, const real* X, int64_t ldx, const void* A, int64_t lda,
+                       real* out, int64_t ldo, const Plan<real>& P) {
   if constexpr (sizeof(real) == 4) {
+    if (bf16)
+      return gemm_bf16(ctx, tb, M, N, K, X, ldx, A, lda, out, ldo, P.xsplit, P.xsplit_elems);
     if (tf32)
-      return gemm_tf32(ctx, false, tb, M, N, K, X, ldx, A, lda, out, ldo, P.partial,
-                       P.partial_cap);
+      return gemm_tf32(ctx, false, tb, M, N, K, X, ldx, static_cast<const real*>(A), lda, out,
+                       ldo, P.partial, P.partial_cap);
   }
-  return gemm<real>(ctx, false, tb, M, N, K, real(1), X, ldx, A, lda, real(0), out, ldo,
-                    P.partial, P.partial_cap);
+  return gemm<real>(ctx, false, tb, M, N, K, real(1), X, ldx, static_cast<const real*>(A), lda,
+                    real(0), out, ldo, P.partial, P.partial_cap);
 }
 
 // Row orthonormalisation without pivoting (Section 5.3): three Cholesky-QR
@@ -220,9 +236,9 @@ curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t 
 // Returns the buffer holding the final Y (l x n, leading dimension
 // pad4(n)); Omega has leading dimension ldo.
 template <typename real>
-curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const real* A,
-                    int64_t m, int64_t n, int64_t lda, int l, int q, bool tf32, const real* Om,
-                    int64_t ldo, real** Yout) {
+curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const void* A,
+                    int64_t m, int64_t n, int64_t lda, int l, int q, bool tf32, bool bf16,
+                    const real* Om, int64_t ldo, real** Yout) {
   const int64_t ldy = pad4(n), ldz = pad4(m);
   auto other = [&](const real* a, const real* b) -> real* {
     for (int i = 0; i < 3; ++i)
@@ -232,7 +248,7 @@ curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const 
   real* cur = P.B[0];
   {
     PhaseScope ps(h, CURID_PHASE_SKETCH);
-    CURID_TRY(a_product<real>(ctx, tf32, false, l, n, m, Om, ldo, A, lda, cur, ldy, P));
+    CURID_TRY(a_product<real>(ctx, tf32, bf16, false, l, n, m, Om, ldo, A, lda, cur, ldy, P));
   }
   for (int i = 0; i < q; ++i) {
     real* t = other(cur, nullptr);
@@ -243,7 +259,7 @@ curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const 
     real* z = other(cur, nullptr);
     {
       PhaseScope ps(h, CURID_PHASE_SKETCH);
-      CURID_TRY(a_product<real>(ctx, tf32, true, l, m, n, cur, ldy, A, lda, z, ldz, P));
+      CURID_TRY(a_product<real>(ctx, tf32, bf16, true, l, m, n, cur, ldy, A, lda, z, ldz, P));
     }
     real* zt = other(z, nullptr);
     {
@@ -253,7 +269,7 @@ curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const 
     real* y = other(z, nullptr);
     {
       PhaseScope ps(h, CURID_PHASE_SKETCH);
-      CURID_TRY(a_product<real>(ctx, tf32, false, l, n, m, z, ldz, A, lda, y, ldy, P));
+      CURID_TRY(a_product<real>(ctx, tf32, bf16, false, l, n, m, z, ldz, A, lda, y, ldy, P));
     }
     cur = y;
   }
@@ -272,6 +288,22 @@ curid_status t_solve(const Ctx& ctx, const real* S, int64_t n, const int32_t* J,
   return CURID_OK;
 }
 
+// The same T solve in float64 (the precision form with BF16 storage keeps the
+// triangular solve in float64): S11, S12 widened, blocked float64 back
+// substitution in place, T rounded to the working precision.
+template <typename real>
+curid_status t_solve64(const Ctx& ctx, const real* S, int64_t n, const int32_t* J, int k,
+                       const int* k_eff, real* S11, real* S12, double* S11d, double* S12d,
+                       real* T, int64_t ldt) {
+  CURID_TRY(split_s<real>(ctx, S, n, J, k, n, S11, S12));
+  if (n - k <= 0) return CURID_OK;
+  CURID_TRY((convert2d<real, double>(ctx, S11, k, S11d, k, k, k)));
+  CURID_TRY((convert2d<real, double>(ctx, S12, n - k, S12d, n - k, k, n - k)));
+  CURID_TRY(tri_solve<double>(ctx, k, S11d, k, true, false, S12d, n - k, S12d, n - k, n - k,
+                              k_eff));
+  return convert2d<double, real>(ctx, S12d, n - k, T, ldt, k, n - k);
+}
+
 struct Outputs {
   int32_t* J;
   void* T;
@@ -285,8 +317,12 @@ struct Outputs {
 };
 
 template <typename real>
-curid_status run(curid_handle* h, Op op, const real* A, const Dims& d, double tol,
+curid_status run(curid_handle* h, Op op, const void* Araw, const Dims& d, double tol,
                  const curid_sketch& sk, const Outputs& o, char* ws, size_t ws_bytes) {
+  // BF16 storage: A is read only by the tensor-core products and the gathers
+  const real* A = d.bf16 ? nullptr : static_cast<const real*>(Araw);
+  const __nv_bfloat16* Ab = d.bf16 ? static_cast<const __nv_bfloat16*>(Araw) : nullptr;
+  if (d.bf16 && (reinterpret_cast<uintptr_t>(Araw) & 15)) return CURID_UNSUPPORTED;
   Ctx ctx = make_ctx(h);
   Plan<real> P;
   const bool gen_omega = d.randomized && sk.omega == nullptr;
@@ -316,7 +352,8 @@ curid_status run(curid_handle* h, Op op, const real* A, const Dims& d, double to
       ldo = pad4(m);
     }
     real* Yr;
-    CURID_TRY(sketch<real>(h, ctx, P, A, m, n, lda, l, d.q, sk.tf32 != 0, Om, ldo, &Yr));
+    CURID_TRY(sketch<real>(h, ctx, P, Araw, m, n, lda, l, d.q, sk.tf32 != 0, d.bf16, Om, ldo,
+                           &Yr));
     Y = Yr;
     ly = l;
     ldy = pad4(n);
@@ -331,7 +368,11 @@ curid_status run(curid_handle* h, Op op, const real* A, const Dims& d, double to
   int64_t ldt = (T == P.T) ? std::max<int64_t>(1, n - k) : o.ldt;
   {
     PhaseScope ps(h, CURID_PHASE_T);
-    CURID_TRY(t_solve<real>(ctx, P.S, n, o.J, k, &P.status->k_eff, P.S11, P.S12, T, ldt));
+    if (sizeof(real) == 4 && d.bf16)
+      CURID_TRY(t_solve64<real>(ctx, P.S, n, o.J, k, &P.status->k_eff, P.S11, P.S12, P.S11d,
+                                P.S12d, T, ldt));
+    else
+      CURID_TRY(t_solve<real>(ctx, P.S, n, o.J, k, &P.status->k_eff, P.S11, P.S12, T, ldt));
     if (o.T && T == P.T)
       CURID_TRY(copy2d<real>(ctx, P.T, ldt, static_cast<real*>(o.T), o.ldt, k, n - k));
   }
@@ -341,9 +382,19 @@ curid_status run(curid_handle* h, Op op, const real* A, const Dims& d, double to
   int32_t* I = o.I ? o.I : P.I;
   {
     PhaseScope ps(h, CURID_PHASE_GATHER);
-    CURID_TRY(gather_cols<real>(ctx, A, m, lda, o.J, k, P.Ct, m, true));
-    if (o.C)
-      CURID_TRY(gather_cols<real>(ctx, A, m, lda, o.J, k, static_cast<real*>(o.C), k, false));
+    if constexpr (sizeof(real) == 4) {
+      if (d.bf16) {
+        CURID_TRY((gather_cols_as<__nv_bfloat16, real>(ctx, Ab, m, lda, o.J, k, P.Ct, m, true)));
+        if (o.C)
+          CURID_TRY((gather_cols_as<__nv_bfloat16, __nv_bfloat16>(
+              ctx, Ab, m, lda, o.J, k, static_cast<__nv_bfloat16*>(o.C), k, false)));
+      }
+    }
+    if (!d.bf16) {
+      CURID_TRY(gather_cols<real>(ctx, A, m, lda, o.J, k, P.Ct, m, true));
+      if (o.C)
+        CURID_TRY(gather_cols<real>(ctx, A, m, lda, o.J, k, static_cast<real*>(o.C), k, false));
+    }
   }
   {
     PhaseScope ps(h, CURID_PHASE_CPQR_ROW);
@@ -367,8 +418,18 @@ curid_status run(curid_handle* h, Op op, const real* A, const Dims& d, double to
   // accumulated in float64.
   {
     PhaseScope ps(h, CURID_PHASE_GATHER);
-    CURID_TRY(gather_rows<real>(ctx, A, m, n, lda, I, k, P.R, n));
-    if (o.R) CURID_TRY(copy2d<real>(ctx, P.R, n, static_cast<real*>(o.R), n, k, n));
+    if constexpr (sizeof(real) == 4) {
+      if (d.bf16) {
+        CURID_TRY((gather_rows_as<__nv_bfloat16, real>(ctx, Ab, m, n, lda, I, k, P.R, n)));
+        if (o.R)
+          CURID_TRY((convert2d<real, __nv_bfloat16>(ctx, P.R, n,
+                                                     static_cast<__nv_bfloat16*>(o.R), n, k, n)));
+      }
+    }
+    if (!d.bf16) {
+      CURID_TRY(gather_rows<real>(ctx, A, m, n, lda, I, k, P.R, n));
+      if (o.R) CURID_TRY(copy2d<real>(ctx, P.R, n, static_cast<real*>(o.R), n, k, n));
+    }
   }
   CURID_TRY(gemm<real>(ctx, true, false, k, n, k, real(1), P.SWinv, k, P.R, n, real(0), P.Rt, n,
                        P.partial, P.partial_cap));
@@ -402,7 +463,7 @@ curid_status run(curid_handle* h, Op op, const real* A, const Dims& d, double to
 curid_status check_common(curid_handle* h, curid_dtype dt, const void* A, int64_t m, int64_t n,
                           int64_t lda, int k, double tol, const curid_sketch& sk, Dims* d) {
   if (!h) return CURID_INVALID_ARG;
-  if (dt != CURID_F32 && dt != CURID_F64) return CURID_INVALID_ARG;
+  if (dt != CURID_F32 && dt != CURID_F64 && dt != CURID_BF16) return CURID_INVALID_ARG;
   if (!A || m <= 0 || n <= 0 || lda < n) return CURID_INVALID_ARG;
   if (m > INT32_MAX || n > INT32_MAX) return CURID_INVALID_ARG;
   if (k < 0 || tol < 0) return CURID_INVALID_ARG;
@@ -410,6 +471,12 @@ curid_status check_common(curid_handle* h, curid_dtype dt, const void* A, int64_
   if (k > std::min(m, n)) return CURID_INVALID_ARG;
   if (sk.q < 0) return CURID_INVALID_ARG;
   if (sk.tf32 && dt != CURID_F32) return CURID_INVALID_ARG;
+  if (dt == CURID_BF16) {
+    // the randomized method only: the products run on the tensor cores from
+    // 16-byte aligned rows of A
+    if (sk.p < 0 || (lda & 7)) return CURID_UNSUPPORTED;
+  }
+  d->bf16 = dt == CURID_BF16;
   d->m = m;
   d->n = n;
   d->lda = lda;
@@ -572,9 +639,11 @@ curid_status curid_sketch_matrix(curid_handle* handle, curid_dtype dtype, const 
     return CURID_INVALID_ARG;
   if (l > std::min(m, n)) return CURID_INVALID_ARG;
   if (tf32 && dtype != CURID_F32) return CURID_INVALID_ARG;
+  const bool bf16 = dtype == CURID_BF16;
+  if (bf16 && ((lda & 7) || (reinterpret_cast<uintptr_t>(A) & 15))) return CURID_UNSUPPORTED;
   return dispatch(handle, [&]() -> curid_status {
     Ctx ctx = make_ctx(handle);
-    Dims d{m, n, lda, 1, l, true, q, tf32 != 0};
+    Dims d{m, n, lda, 1, l, true, q, tf32 != 0, bf16};
     auto go = [&](auto tag) -> curid_status {
       using real = decltype(tag);
       Plan<real> P;
@@ -592,12 +661,12 @@ curid_status curid_sketch_matrix(curid_handle* handle, curid_dtype dtype, const 
         ldo = pad4(m);
       }
       real* cur;
-      CURID_TRY(sketch<real>(handle, ctx, P, static_cast<const real*>(A), m, n, lda, l, q,
-                             tf32 != 0, Om, ldo, &cur));
+      CURID_TRY(sketch<real>(handle, ctx, P, A, m, n, lda, l, q, tf32 != 0, bf16, Om, ldo,
+                             &cur));
       return copy2d<real>(ctx, cur, pad4(n), static_cast<real*>(Y), n, l, n);
     };
     if (dtype == CURID_F64) return go(double{});
-    if (dtype == CURID_F32) return go(float{});
+    if (dtype == CURID_F32 || bf16) return go(float{});
     return CURID_INVALID_ARG;
   });
 }
@@ -659,6 +728,7 @@ curid_status curid_id_row(curid_handle* handle, curid_dtype dtype, const void* A
   // (n x m, leading dimension m) and the column-ID pipeline runs on it.
   Dims d0;
   CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d0));
+  if (dtype == CURID_BF16) return CURID_UNSUPPORTED;
   Dims d;
   CURID_TRY(check_common(handle, dtype, A, n, m, m, k, tol, sk, &d));
   if (!I || !TW || ldtw < std::max<int64_t>(1, m - k)) return CURID_INVALID_ARG;

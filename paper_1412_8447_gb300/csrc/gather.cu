@@ -9,25 +9,44 @@ namespace curid {
 
 namespace {
 
+// element conversion between storage types (bfloat16 <-> float exact or
+// round-to-nearest; float <-> double by the language rules)
+template <typename D, typename S>
+__device__ __forceinline__ D cvt(S x) {
+  return static_cast<D>(x);
+}
+template <>
+__device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, float>(float x) {
+  return __float2bfloat16_rn(x);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, __nv_bfloat16>(__nv_bfloat16 x) {
+  return x;
+}
+
 // out^T layout (transpose == true): out[i*ldo + r] = A[r*lda + J[i]]
-template <typename real>
-__global__ void gather_cols_t_kernel(const real* __restrict__ A, int64_t m, int64_t lda,
+template <typename S, typename D>
+__global__ void gather_cols_t_kernel(const S* __restrict__ A, int64_t m, int64_t lda,
                                      const int32_t* __restrict__ J, int k,
-                                     real* __restrict__ out, int64_t ldo) {
+                                     D* __restrict__ out, int64_t ldo) {
   const int i = blockIdx.y;
   int64_t col = J[i];
   if (col < 0 || col >= lda) col = 0;  // indices come from the device; never read out of range
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
        r += (int64_t)gridDim.x * blockDim.x)
-    out[(int64_t)i * ldo + r] = A[r * lda + col];
+    out[(int64_t)i * ldo + r] = cvt<D>(A[r * lda + col]);
 }
 
 // out[r*ldo + i] = A[r*lda + J[i]] through a 32 x 32 shared tile
-template <typename real>
-__global__ void gather_cols_kernel(const real* __restrict__ A, int64_t m, int64_t lda,
+template <typename S, typename D>
+__global__ void gather_cols_kernel(const S* __restrict__ A, int64_t m, int64_t lda,
                                    const int32_t* __restrict__ J, int k,
-                                   real* __restrict__ out, int64_t ldo) {
-  __shared__ real tile[32][33];
+                                   D* __restrict__ out, int64_t ldo) {
+  __shared__ D tile[32][33];
   const int i0 = blockIdx.y * 32;
   const int64_t r0 = blockIdx.x * 32LL;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
@@ -36,7 +55,7 @@ __global__ void gather_cols_kernel(const real* __restrict__ A, int64_t m, int64_
     const int64_t r = r0 + tx;
     int64_t col = i < k ? (int64_t)J[i] : 0;
     if (col < 0 || col >= lda) col = 0;
-    tile[yy][tx] = (i < k && r < m) ? A[r * lda + col] : real(0);
+    tile[yy][tx] = (i < k && r < m) ? cvt<D>(A[r * lda + col]) : cvt<D>(0.f);
   }
   __syncthreads();
   for (int yy = ty; yy < 32; yy += 8) {
@@ -46,18 +65,18 @@ __global__ void gather_cols_kernel(const real* __restrict__ A, int64_t m, int64_
   }
 }
 
-template <typename real>
-__global__ void gather_rows_kernel(const real* __restrict__ A, int64_t m, int64_t n, int64_t lda,
-                                   const int32_t* __restrict__ I, real* __restrict__ out,
+template <typename S, typename D>
+__global__ void gather_rows_kernel(const S* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                   const int32_t* __restrict__ I, D* __restrict__ out,
                                    int64_t ldo) {
   const int i = blockIdx.y;
   int64_t row = I[i];
   if (row < 0 || row >= m) row = 0;
-  const real* src = A + row * lda;
-  real* dst = out + (int64_t)i * ldo;
+  const S* src = A + row * lda;
+  D* dst = out + (int64_t)i * ldo;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x)
-    dst[c] = src[c];
+    dst[c] = cvt<D>(src[c]);
 }
 
 template <typename real>
@@ -75,14 +94,14 @@ __global__ void split_s_kernel(const real* __restrict__ S, int64_t lds,
   }
 }
 
-template <typename real>
-__global__ void copy2d_kernel(const real* __restrict__ src, int64_t lds, real* __restrict__ dst,
+template <typename S, typename D>
+__global__ void copy2d_kernel(const S* __restrict__ src, int64_t lds, D* __restrict__ dst,
                               int64_t ldd, int64_t rows, int64_t cols) {
   const int64_t total = rows * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / cols, c = e % cols;
-    dst[r * ldd + c] = src[r * lds + c];
+    dst[r * ldd + c] = cvt<D>(src[r * lds + c]);
   }
 }
 
@@ -123,29 +142,51 @@ inline unsigned blocks_for(int64_t work, int num_sms) {
 
 }  // namespace
 
-template <typename real>
-curid_status gather_cols(const Ctx& ctx, const real* A, int64_t m, int64_t lda, const int32_t* J,
-                         int k, real* out, int64_t ldo, bool transpose) {
+template <typename S, typename D>
+curid_status gather_cols_as(const Ctx& ctx, const S* A, int64_t m, int64_t lda, const int32_t* J,
+                            int k, D* out, int64_t ldo, bool transpose) {
   if (k <= 0 || m <= 0) return CURID_OK;
   if (transpose) {
     dim3 grid((unsigned)std::min<int64_t>((m + 255) / 256, 64), (unsigned)k);
-    gather_cols_t_kernel<real><<<grid, 256, 0, ctx.stream>>>(A, m, lda, J, k, out, ldo);
+    gather_cols_t_kernel<S, D><<<grid, 256, 0, ctx.stream>>>(A, m, lda, J, k, out, ldo);
   } else {
     dim3 grid((unsigned)((m + 31) / 32), (unsigned)((k + 31) / 32));
-    gather_cols_kernel<real><<<grid, dim3(32, 8), 0, ctx.stream>>>(A, m, lda, J, k, out, ldo);
+    gather_cols_kernel<S, D><<<grid, dim3(32, 8), 0, ctx.stream>>>(A, m, lda, J, k, out, ldo);
   }
   CURID_LAUNCHED(ctx);
   return CURID_OK;
 }
 
+template <typename S, typename D>
+curid_status gather_rows_as(const Ctx& ctx, const S* A, int64_t m, int64_t n, int64_t lda,
+                            const int32_t* I, int k, D* out, int64_t ldo) {
+  if (k <= 0 || n <= 0) return CURID_OK;
+  dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)k);
+  gather_rows_kernel<S, D><<<grid, 256, 0, ctx.stream>>>(A, m, n, lda, I, out, ldo);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
+template <typename S, typename D>
+curid_status convert2d(const Ctx& ctx, const S* src, int64_t lds, D* dst, int64_t ldd,
+                       int64_t rows, int64_t cols) {
+  if (rows <= 0 || cols <= 0) return CURID_OK;
+  copy2d_kernel<S, D><<<blocks_for(rows * cols, ctx.num_sms), 256, 0, ctx.stream>>>(
+      src, lds, dst, ldd, rows, cols);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
+template <typename real>
+curid_status gather_cols(const Ctx& ctx, const real* A, int64_t m, int64_t lda, const int32_t* J,
+                         int k, real* out, int64_t ldo, bool transpose) {
+  return gather_cols_as<real, real>(ctx, A, m, lda, J, k, out, ldo, transpose);
+}
+
 template <typename real>
 curid_status gather_rows(const Ctx& ctx, const real* A, int64_t m, int64_t n, int64_t lda,
                          const int32_t* I, int k, real* out, int64_t ldo) {
-  if (k <= 0 || n <= 0) return CURID_OK;
-  dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)k);
-  gather_rows_kernel<real><<<grid, 256, 0, ctx.stream>>>(A, m, n, lda, I, out, ldo);
-  CURID_LAUNCHED(ctx);
-  return CURID_OK;
+  return gather_rows_as<real, real>(ctx, A, m, n, lda, I, k, out, ldo);
 }
 
 template <typename real>
@@ -161,11 +202,7 @@ curid_status split_s(const Ctx& ctx, const real* S, int64_t lds, const int32_t* 
 template <typename real>
 curid_status copy2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
                     int64_t rows, int64_t cols) {
-  if (rows <= 0 || cols <= 0) return CURID_OK;
-  copy2d_kernel<real><<<blocks_for(rows * cols, ctx.num_sms), 256, 0, ctx.stream>>>(
-      src, lds, dst, ldd, rows, cols);
-  CURID_LAUNCHED(ctx);
-  return CURID_OK;
+  return convert2d<real, real>(ctx, src, lds, dst, ldd, rows, cols);
 }
 
 template <typename real>
@@ -204,5 +241,25 @@ curid_status transpose2d(const Ctx& ctx, const real* src, int64_t lds, real* dst
 CURID_INST(float)
 CURID_INST(double)
 #undef CURID_INST
+
+using bf16_t = __nv_bfloat16;
+template curid_status gather_cols_as<bf16_t, float>(const Ctx&, const bf16_t*, int64_t, int64_t,
+                                                    const int32_t*, int, float*, int64_t, bool);
+template curid_status gather_cols_as<bf16_t, bf16_t>(const Ctx&, const bf16_t*, int64_t,
+                                                     int64_t, const int32_t*, int, bf16_t*,
+                                                     int64_t, bool);
+template curid_status gather_rows_as<bf16_t, float>(const Ctx&, const bf16_t*, int64_t, int64_t,
+                                                    int64_t, const int32_t*, int, float*,
+                                                    int64_t);
+template curid_status convert2d<float, bf16_t>(const Ctx&, const float*, int64_t, bf16_t*,
+                                               int64_t, int64_t, int64_t);
+template curid_status convert2d<float, double>(const Ctx&, const float*, int64_t, double*,
+                                               int64_t, int64_t, int64_t);
+template curid_status convert2d<double, float>(const Ctx&, const double*, int64_t, float*,
+                                               int64_t, int64_t, int64_t);
+template curid_status convert2d<float, float>(const Ctx&, const float*, int64_t, float*,
+                                              int64_t, int64_t, int64_t);
+template curid_status convert2d<double, double>(const Ctx&, const double*, int64_t, double*,
+                                                int64_t, int64_t, int64_t);
 
 }  // namespace curid

@@ -4,6 +4,8 @@
 
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace curid {
@@ -40,6 +42,14 @@ curid_status gemm_tf32(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, i
                        const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
                        int64_t ldc, float* partial, size_t partial_cap);
 size_t gemm_tf32_partial_elems(int64_t M, int64_t N, int64_t K, int num_sms);
+// BF16 A (gemm_bf16.cu): C[M x N] = X A (tb false; A K x N) or X A^T (tb
+// true; A N x K), X float32 (M x K) split into BF16 high and low parts in
+// `split` (gemm_bf16_split_elems(M, K) bfloat16 values); A's rows 16-byte
+// aligned (lda a multiple of 8).
+size_t gemm_bf16_split_elems(int64_t M, int64_t K);
+curid_status gemm_bf16(const Ctx& ctx, bool tb, int64_t M, int64_t N, int64_t K, const float* X,
+                       int64_t ldx, const void* A, int64_t lda, float* C, int64_t ldc,
+                       void* split, size_t split_elems);
 
 // ---- truncated CPQR (cpqr.cu) -----------------------------------------------
 // Scratch for one CPQR launch (carved from the workspace).
@@ -116,6 +126,17 @@ curid_status gather_cols(const Ctx& ctx, const real* A, int64_t m, int64_t lda,
 template <typename real>
 curid_status gather_rows(const Ctx& ctx, const real* A, int64_t m, int64_t n, int64_t lda,
                          const int32_t* I, int k, real* out, int64_t ldo);
+// the same gathers and a 2-D copy with a change of element type (instantiated
+// for bfloat16 -> float / bfloat16, float -> bfloat16 / double, double -> float)
+template <typename S, typename D>
+curid_status gather_cols_as(const Ctx& ctx, const S* A, int64_t m, int64_t lda, const int32_t* J,
+                            int k, D* out, int64_t ldo, bool transpose);
+template <typename S, typename D>
+curid_status gather_rows_as(const Ctx& ctx, const S* A, int64_t m, int64_t n, int64_t lda,
+                            const int32_t* I, int k, D* out, int64_t ldo);
+template <typename S, typename D>
+curid_status convert2d(const Ctx& ctx, const S* src, int64_t lds, D* dst, int64_t ldd,
+                       int64_t rows, int64_t cols);
 // S11[i][t] = S[i][J[t]] (t < k); S12[i][c] = S[i][J[k+c]] (c < n-k)
 template <typename real>
 curid_status split_s(const Ctx& ctx, const real* S, int64_t lds, const int32_t* J, int k,

@@ -114,6 +114,27 @@ def laplace_block(m, n, seed, dtype=torch.float64, device="cpu"):
     return torch.from_numpy(1.0 / d).to(dtype).to(device).contiguous()
 
 
+def decay_with_floor(m, n, r, top_exp, floor, seed, device="cpu", dtype=torch.bfloat16):
+    """A = U_a diag(sigma) V_a^T + floor * N / sqrt(n), sigma_j = 10^(top_exp j / r)
+    for j <= r (top_exp < 0), U_a, V_a Haar (m x r, n x r), N i.i.d. N(0, 1)
+    drawn on ``device`` from a generator seeded with ``seed``; computed in
+    float32 and rounded once to ``dtype``.  The floor term stands for the
+    singular values 10^-7 beyond r (its rounding to bfloat16 is far below the
+    storage resolution of the leading part)."""
+    g = rng(seed)
+    sigma = 10.0 ** (top_exp * np.arange(1, r + 1) / r)
+    Ua = haar(m, r, g, device).to(torch.float32)
+    Va = haar(n, r, g, device).to(torch.float32)
+    s = torch.from_numpy(sigma).to(torch.float32).to(device)
+    A = (Ua * s) @ Va.T
+    if floor > 0:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(int(seed))
+        A += floor / np.sqrt(n) * torch.randn(m, n, generator=gen, device=device,
+                                              dtype=torch.float32)
+    return A.to(dtype).contiguous()
+
+
 def laplace_batch_shapes(nb, seed, lo=64, hi=512):
     """Block shapes (m_b, n_b), each uniform on {lo..hi}."""
     g = rng(seed)
@@ -146,6 +167,14 @@ def workload_small_f64(seed=BASE_SEED + 0, device="cpu"):
     """Dense FP64 400 x 300, sigma_j = exp(-j/10), deterministic, k = 40."""
     A = spectrum_matrix(400, 300, exp_decay(300), seed, torch.float64, device)
     return dict(A=A, k=40, p=-1, q=0, name="det_f64_400x300_k40")
+
+
+def workload_mixed_bf16(seed=BASE_SEED + 2, device="cpu", m=20000, n=20000, k=500, p=20,
+                        q=2):
+    """BF16 20000 x 20000, sigma_j = 10^(-6j/500) for j <= 500, floor 1e-7,
+    k = 500, p = 20, q = 2."""
+    A = decay_with_floor(m, n, k, -6.0, 1e-7, seed, device)
+    return dict(A=A, k=k, p=p, q=q, name=f"mixed_bf16_{m}x{n}_k{k}_p{p}_q{q}")
 
 
 def workload_rand_f32(seed=BASE_SEED + 1, device="cpu", m=8000, n=6000,
