@@ -317,7 +317,8 @@ def run_ours(args, ws, rank, local):
         cpu = cpu_baseline(args, A, curid)
     forms = None
     if rank == 0 and ws == 1 and not args.no_forms:
-        forms = {"adjoint": measure_adjoint(dev), "batched": measure_batched(dev)}
+        forms = {"adjoint": measure_adjoint(dev), "batched": measure_batched(dev),
+                 "mixed": measure_mixed(dev)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -449,6 +450,56 @@ def measure_batched(dev, replays=5):
         res[name] = entry
         del B, g, flat
         torch.cuda.empty_cache()
+    return res
+
+
+def measure_mixed(dev, steps=3):
+    """Precision form at A 20000 x 20000 stored in bfloat16, sigma_j =
+    10^(-6j/500) (j <= 500), floor 1e-7, k = 500, p = 20, q = 2: the BF16
+    tensor-core path against the plain float64 GPU path on the same values
+    (one timed run of the latter), both with errors ||A - CUR||_F / ||A||_F
+    computed in float64 on the GPU."""
+    import paper_1412_8447_gb300 as curid
+    import synthetic as syn
+    w = syn.workload_mixed_bf16(device=dev)
+    A, k, p, q = w["A"], w["k"], w["p"], w["q"]
+    m, n = A.shape
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def err(X, r):
+        Xd = X.double()
+        D = Xd - (r.C.double() @ r.U) @ r.R.double()
+        return float(torch.linalg.norm(D) / torch.linalg.norm(Xd))
+
+    def timed(X, nrep, seed0):
+        out = curid.cur_outputs(X, k, want_c=True, want_r=True)
+        curid.cur(X, k, p=p, q=q, seed=seed0, out=out)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for i in range(nrep):
+            curid.cur(X, k, p=p, q=q, seed=seed0 + 1 + i, out=out, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        st, _ = curid.last_status(dev.index or 0)
+        return e0.elapsed_time(e1) / nrep, out, st
+
+    res = {"workload": f"randomized CUR-ID, A {m}x{n} stored in bfloat16, sigma_j = "
+                       f"10^(-6j/500) (j <= 500), floor 1e-7, k = {k}, p = {p}, q = {q}",
+           "unit": "decompositions/s"}
+    ms, out, st = timed(A, steps, 7000)
+    flops = (2 * q + 1) * 2.0 * (k + p) * m * n
+    res["bf16"] = {"value": 1e3 / ms, "ms_per_step": ms, "status": curid.STATUS_NAMES[st],
+                   "rel_err_fro": err(A, out),
+                   "products_tflops": flops / (ms / 1e3) / 1e12}
+    A64 = A.double()
+    ms64, out64, st64 = timed(A64, 1, 7000)
+    res["f64_plain"] = {"value": 1e3 / ms64, "ms_per_step": ms64,
+                        "status": curid.STATUS_NAMES[st64], "rel_err_fro": err(A64, out64),
+                        "how": "the same pipeline in float64 (SIMT products), one timed run"}
+    res["bf16_over_f64"] = res["bf16"]["value"] / res["f64_plain"]["value"]
+    del A64, out64
+    torch.cuda.empty_cache()
     return res
 
 

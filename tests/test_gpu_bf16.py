@@ -69,3 +69,32 @@ def test_bf16_requires_randomized_and_alignment():
     with pytest.raises(curid.CuridError) as e:
         curid.cur(B, 10, p=5, seed=1)
     assert e.value.status == 8
+
+
+def rel_err_gpu(A, C, U, R):
+    """||A - C U R||_F / ||A||_F in float64 on the GPU."""
+    Ad = A.double()
+    D = Ad - (C.double() @ U) @ R.double()
+    return float(torch.linalg.norm(D) / torch.linalg.norm(Ad))
+
+
+def test_bf16_full_config():
+    """A 20000 x 20000 BF16, sigma_j = 10^(-6j/500) (j <= 500), floor 1e-7,
+    k = 500, p = 20, q = 2: C and R exact copies of A's entries, and the
+    error within 1.05x of the float32 GPU path on the same values and the
+    same Omega (the storage rounding of A bounds both near 1e-3)."""
+    w = syn.workload_mixed_bf16(device="cuda:0")
+    A, k, p, q = w["A"], w["k"], w["p"], w["q"]
+    m, n = A.shape
+    Om = curid.gaussian(k + p, m, 71, torch.float32)
+    r = curid.cur(A, k, p=p, q=q, omega=Om, want_c=True, want_r=True)
+    assert r.status == 0 and r.k == k
+    J, I = r.J.long(), r.I.long()
+    assert torch.equal(r.C, A[:, J[:k]]) and torch.equal(r.R, A[I[:k], :])
+    assert sorted(J.tolist()) == list(range(n)) and sorted(I.tolist()) == list(range(m))
+    eb = rel_err_gpu(A, r.C, r.U, r.R)
+    A32 = A.float()
+    r32 = curid.cur(A32, k, p=p, q=q, omega=Om, want_c=True, want_r=True)
+    e32 = rel_err_gpu(A32, r32.C, r32.U, r32.R)
+    assert eb < 1e-2, eb
+    assert eb <= 1.05 * e32 + 1e-6, (eb, e32)
