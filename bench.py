@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--only-form", choices=["adjoint", "batched", "mixed"], default=None,
+                    help="run only this form's measurement and print its JSON")
+    ap.add_argument("--small", action="store_true",
+                    help="with --only-form: profiling sizes (256 blocks; BF16 8192^2, q = 1)")
     return ap.parse_args()
 
 
@@ -385,7 +389,7 @@ def measure_adjoint(dev, steps=10, warmup=3):
     return res
 
 
-def measure_batched(dev, replays=5):
+def measure_batched(dev, replays=5, nb=4096):
     """Batched adaptive-rank column ID of 4096 Laplace blocks (m_b, n_b
     uniform on 64..512): autotuned launch shape, the launch captured in a
     CUDA graph and replayed; float64 (tol 1e-8) and float32 (tol 1e-5).  The
@@ -393,7 +397,6 @@ def measure_batched(dev, replays=5):
     on 64 of the blocks for comparison."""
     import paper_1412_8447_gb300 as curid
     import synthetic as syn
-    nb = 4096
     stream = torch.cuda.current_stream(dev)
     res = {"workload": f"batched adaptive-rank column ID, {nb} Laplace blocks 1/|x-y| "
                        "(unit boxes 3 apart), m_b, n_b uniform on 64..512, one persistent "
@@ -453,7 +456,7 @@ def measure_batched(dev, replays=5):
     return res
 
 
-def measure_mixed(dev, steps=3):
+def measure_mixed(dev, steps=3, size=20000, q=None, with_f64=True):
     """Precision form at A 20000 x 20000 stored in bfloat16, sigma_j =
     10^(-6j/500) (j <= 500), floor 1e-7, k = 500, p = 20, q = 2: the BF16
     tensor-core path against the plain float64 GPU path on the same values
@@ -461,8 +464,9 @@ def measure_mixed(dev, steps=3):
     computed in float64 on the GPU."""
     import paper_1412_8447_gb300 as curid
     import synthetic as syn
-    w = syn.workload_mixed_bf16(device=dev)
-    A, k, p, q = w["A"], w["k"], w["p"], w["q"]
+    w = syn.workload_mixed_bf16(device=dev, m=size, n=size)
+    A, k, p = w["A"], w["k"], w["p"]
+    q = w["q"] if q is None else q
     m, n = A.shape
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -488,10 +492,19 @@ def measure_mixed(dev, steps=3):
                        f"10^(-6j/500) (j <= 500), floor 1e-7, k = {k}, p = {p}, q = {q}",
            "unit": "decompositions/s"}
     ms, out, st = timed(A, steps, 7000)
+    curid.profile(True, dev.index or 0)
+    curid.cur(A, k, p=p, q=q, seed=6999, out=out, check=False)
+    phase_ms, _, launches = curid.profile_read(dev.index or 0)
+    curid.profile(False, dev.index or 0)
     flops = (2 * q + 1) * 2.0 * (k + p) * m * n
     res["bf16"] = {"value": 1e3 / ms, "ms_per_step": ms, "status": curid.STATUS_NAMES[st],
                    "rel_err_fro": err(A, out),
-                   "products_tflops": flops / (ms / 1e3) / 1e12}
+                   "phases_ms": {ph: round(v, 3) for ph, v in phase_ms.items()},
+                   "launches": launches,
+                   "products_tflops": flops / (sum(v for ph, v in phase_ms.items()
+                                                   if ph == "sketch") / 1e3) / 1e12}
+    if not with_f64:
+        return res
     A64 = A.double()
     ms64, out64, st64 = timed(A64, 1, 7000)
     res["f64_plain"] = {"value": 1e3 / ms64, "ms_per_step": ms64,
@@ -568,6 +581,20 @@ def run_reference(args, ws, rank, local):
 
 def main():
     args = parse()
+    if args.only_form:
+        from paper_1412_8447_gb300.build import build
+        build()
+        dev = torch.device("cuda:0")
+        torch.cuda.set_device(dev)
+        if args.only_form == "adjoint":
+            r = measure_adjoint(dev)
+        elif args.only_form == "batched":
+            r = measure_batched(dev, nb=256 if args.small else 4096)
+        else:
+            r = (measure_mixed(dev, steps=1, size=8192, q=1, with_f64=False) if args.small
+                 else measure_mixed(dev))
+        print(json.dumps({"form": args.only_form, **r}))
+        return
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank, local)
