@@ -79,7 +79,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kColsPerWarp = 4;  // columns a warp updates in one interleaved pass
 constexpr unsigned kNoCol = 0xffffffffu;
 constexpr unsigned kNonFinite = 0xfffffffeu;
-constexpr int kMaxSlotsPerLane = 8;  // G <= 256
+constexpr int kMaxSlotsPerLane = 5;  // G <= 160 (one CTA per SM; the GPU has 152)
 
 __device__ __forceinline__ unsigned long long pack(unsigned epoch, unsigned payload) {
   return ((unsigned long long)epoch << 32) | payload;
@@ -210,8 +210,6 @@ __device__ bool gather_records(const CpqrParams<real>& P, int bf, unsigned epoch
       if (fresh) pending &= ~(1u << r);
     }
     if (!pending) break;
-    // back off briefly so 150 pollers do not saturate the records' lines
-    __nanosleep(64);
     if ((round & 15) == 15) {
       if (ld_volatile_i32(P.abort_flag)) { ok = false; break; }
       if (clock64() - t0 > kSpinBudget) {
@@ -311,39 +309,84 @@ __device__ __forceinline__ void update_group(const CpqrParams<real>& P, real* ys
 #pragma unroll
   for (int c = 0; c < kColsPerWarp; ++c) any |= v[c];
   if (!any) return;
+  constexpr int RB = sizeof(real) == 4 ? 4 : 2;  // rows per lane held in registers
   real d[kColsPerWarp];
 #pragma unroll
   for (int c = 0; c < kColsPerWarp; ++c) d[c] = real(0);
-  for (int r = j + 1 + lane; r < l; r += 32) {
-    const real x = xv[r];
-#pragma unroll
-    for (int c = 0; c < kColsPerWarp; ++c)
-      if (v[c]) d[c] += x * y[c][r];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int c = 0; c < kColsPerWarp; ++c) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
   real wj[kColsPerWarp], ws[kColsPerWarp], q[kColsPerWarp];
+  if (l - j - 1 <= 32 * RB) {
+    // every row this lane touches fits in registers: one load of the
+    // column part, dot products, reflector update and new norms from the
+    // registers, one store
+    real xr[RB], yr[kColsPerWarp][RB];
 #pragma unroll
-  for (int c = 0; c < kColsPerWarp; ++c) {
-    wj[c] = v[c] ? tau * (y[c][j] + scale * d[c]) : real(0);
-    ws[c] = wj[c] * scale;
-    q[c] = real(0);
-  }
-  if (lane == 0) {
+    for (int u = 0; u < RB; ++u) {
+      const int r = j + 1 + lane + 32 * u;
+      const bool ok = r < l;
+      xr[u] = ok ? xv[r] : real(0);
 #pragma unroll
-    for (int c = 0; c < kColsPerWarp; ++c)
-      if (v[c]) y[c][j] -= wj[c];
-  }
-  for (int r = j + 1 + lane; r < l; r += 32) {
-    const real x = xv[r];
+      for (int c = 0; c < kColsPerWarp; ++c) yr[c][u] = (ok && v[c]) ? y[c][r] : real(0);
+    }
+#pragma unroll
+    for (int u = 0; u < RB; ++u)
+#pragma unroll
+      for (int c = 0; c < kColsPerWarp; ++c) d[c] += xr[u] * yr[c][u];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int c = 0; c < kColsPerWarp; ++c) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
 #pragma unroll
     for (int c = 0; c < kColsPerWarp; ++c) {
-      if (!v[c]) continue;
-      const real nv = y[c][r] - ws[c] * x;
-      y[c][r] = nv;
-      q[c] += nv * nv;
+      wj[c] = v[c] ? tau * (y[c][j] + scale * d[c]) : real(0);
+      ws[c] = wj[c] * scale;
+      q[c] = real(0);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int c = 0; c < kColsPerWarp; ++c)
+        if (v[c]) y[c][j] -= wj[c];
+    }
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int r = j + 1 + lane + 32 * u;
+#pragma unroll
+      for (int c = 0; c < kColsPerWarp; ++c) {
+        const real nv = yr[c][u] - ws[c] * xr[u];
+        q[c] += nv * nv;  // rows past l hold zeros
+        if (v[c] && r < l) y[c][r] = nv;
+      }
+    }
+  } else {
+    for (int r = j + 1 + lane; r < l; r += 32) {
+      const real x = xv[r];
+#pragma unroll
+      for (int c = 0; c < kColsPerWarp; ++c)
+        if (v[c]) d[c] += x * y[c][r];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int c = 0; c < kColsPerWarp; ++c) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
+#pragma unroll
+    for (int c = 0; c < kColsPerWarp; ++c) {
+      wj[c] = v[c] ? tau * (y[c][j] + scale * d[c]) : real(0);
+      ws[c] = wj[c] * scale;
+      q[c] = real(0);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int c = 0; c < kColsPerWarp; ++c)
+        if (v[c]) y[c][j] -= wj[c];
+    }
+    for (int r = j + 1 + lane; r < l; r += 32) {
+      const real x = xv[r];
+#pragma unroll
+      for (int c = 0; c < kColsPerWarp; ++c) {
+        if (!v[c]) continue;
+        const real nv = y[c][r] - ws[c] * x;
+        y[c][r] = nv;
+        q[c] += nv * nv;
+      }
     }
   }
 #pragma unroll
