@@ -16,8 +16,10 @@
 //   3. each warp applies H to one of the CTA's unselected columns and
 //      recomputes that column's residual norm from rows j+1..l-1 (no norm
 //      downdating, hence no cancellation to guard against);
-//   4. warp 0 publishes the CTA's new local candidate for step j+1 (one
-//      fence, one pair of 128-bit stores).
+//   4. warp 0 publishes the CTA's new local candidate for step j+1: the
+//      record first, then the candidate column; every 64-bit word of both
+//      carries the step's tag, so no fence is needed and a reader checks
+//      each word for freshness.
 // One grid-wide exchange and three CTA barriers per pivot step; no host
 // round trip until the end.
 // After the last step row i of S holds S1(i, c) for every original column c,
@@ -233,8 +235,9 @@ __device__ __forceinline__ real* slab_col(const CpqrParams<real>& P, real* ys, i
 }
 
 // Warp 0: pick the CTA's candidate (largest residual norm among its
-// unselected columns, smallest index on ties), copy its rows r0..l-1 to the
-// CTA's data slot, then publish the record of `epoch` in buffer `bf`.
+// unselected columns, smallest index on ties), publish the record of `epoch`
+// in buffer `bf`, then copy the candidate's rows r0..l-1 to the CTA's data
+// slot (tagged words; a reader waits for the fresh tag of each word).
 template <bool OV, typename real>
 __device__ void publish(const CpqrParams<real>& P, real* ys, const real* nrm,
                         const int* active, int ncl, int c0, int r0, int bf, unsigned epoch) {
@@ -258,6 +261,15 @@ __device__ void publish(const CpqrParams<real>& P, real* ys, const real* nrm,
     nf |= __shfl_xor_sync(0xffffffffu, nf, o);
   }
   const unsigned tag = tag_of(P.gen, (int)epoch);
+  // the record first: readers validate every word of the column by its tag,
+  // so the column copy below overlaps the record's way to the other CTAs
+  if (lane == 0) {
+    unsigned hi, lo;
+    norm_words<real>(bi >= 0 ? bn : real(0), &hi, &lo);
+    const unsigned col = nf ? kNonFinite : (bi >= 0 ? (unsigned)(c0 + bi) : kNoCol);
+    st_rec(P.recs + (size_t)bf * G + blockIdx.x, pack(tag, col), pack(tag, hi), pack(tag, lo),
+           pack(tag, __float_as_uint((float)ss)));
+  }
   if (bi >= 0 && !nf) {
     constexpr int W = Words<real>::W;
     unsigned long long* dst = P.slot_data + ((int64_t)bf * G + blockIdx.x) * P.l * W;
@@ -268,13 +280,6 @@ __device__ void publish(const CpqrParams<real>& P, real* ys, const real* nrm,
       const real* src = slab_col<OV>(P, ys, bi);
       for (int r = r0 + lane; r < P.l; r += 32) put_tagged<real>(dst + (int64_t)r * W, tag, src[r]);
     }
-  }
-  if (lane == 0) {
-    unsigned hi, lo;
-    norm_words<real>(bi >= 0 ? bn : real(0), &hi, &lo);
-    const unsigned col = nf ? kNonFinite : (bi >= 0 ? (unsigned)(c0 + bi) : kNoCol);
-    st_rec(P.recs + (size_t)bf * G + blockIdx.x, pack(tag, col), pack(tag, hi), pack(tag, lo),
-           pack(tag, __float_as_uint((float)ss)));
   }
 }
 
