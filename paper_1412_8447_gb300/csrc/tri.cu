@@ -21,18 +21,22 @@ namespace curid {
 namespace {
 
 constexpr int kTB = 32;           // block order
-constexpr int kTriThreads = 512;   // 16 warps; each owns rows w and w + 16 of a block
-constexpr int kTriLd = kTB + 1;   // padded block row
+constexpr int kTriThreads = 512;
 
+// NC right-hand-side columns per CTA; block rows padded to LD so that every
+// row starts on 16 bytes (vector loads of VN entries); in the sweep a thread
+// owns one column and RPT rows of a block row.
 template <typename real>
 struct TriCols;
 template <>
 struct TriCols<float> {
-  static constexpr int NC = 64;
+  static constexpr int NC = 64, LD = 36, VN = 4;
+  using V = float4;
 };
 template <>
 struct TriCols<double> {
-  static constexpr int NC = 32;
+  static constexpr int NC = 32, LD = 34, VN = 2;
+  using V = double2;
 };
 
 __host__ __device__ inline int packed_block(int bi, int bj) { return bi * (bi + 1) / 2 + bj; }
@@ -64,107 +68,142 @@ __device__ __forceinline__ real tri_elem(const TriParams<real>& P, int i, int j,
 
 template <typename real>
 __global__ void __launch_bounds__(kTriThreads, 1) tri_solve_kernel(TriParams<real> P) {
-  constexpr int NC = TriCols<real>::NC;
-  constexpr int CPT = NC / 32;  // columns per thread
+  using TC = TriCols<real>;
+  using V = typename TC::V;
+  constexpr int NC = TC::NC, LD = TC::LD, VN = TC::VN;
+  constexpr int CPT = NC / 32;                 // columns per lane when loading
+  constexpr int RPT = kTB * NC / kTriThreads;  // rows per thread in the sweep
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = P.nb;
   const int KP = nb * kTB;
   real* Ls = reinterpret_cast<real*>(smem_raw);                 // packed blocks, 32 x 33
-  real* Xs = Ls + (size_t)packed_block(nb, 0) * kTB * kTriLd;  // KP x NC
+  real* Xs = Ls + (size_t)packed_block(nb, 0) * kTB * LD;  // KP x NC
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int kk = P.kk ? max(0, min(P.k, *P.kk - P.kk_off)) : P.k;
   const int64_t c0 = (int64_t)blockIdx.x * NC;
 
-  // triangle -> packed lower blocks (identity past k and past the rank)
+  // triangle -> packed lower blocks (identity past k and past the rank): a
+  // warp per block, lane = column, rows in batches of 8 loads in flight
   const int nblk = packed_block(nb, 0);
-  for (int e = tid; e < nblk * kTB * kTB; e += kTriThreads) {
-    const int blk = e / (kTB * kTB), w = e % (kTB * kTB);
+  for (int blk = warp; blk < nblk; blk += kTriThreads / 32) {
     int bi = 0;
     while (packed_block(bi + 1, 0) <= blk) ++bi;
     const int bj = blk - packed_block(bi, 0);
-    const int r = w / kTB, c = w % kTB;
-    const int i = bi * kTB + r, j = bj * kTB + c;
-    real v = real(0);
-    if (j <= i) v = tri_elem(P, i, j, kk);
-    Ls[(size_t)blk * kTB * kTriLd + r * kTriLd + c] = v;
+    real* dst = Ls + (size_t)blk * kTB * LD;
+    const int j = bj * kTB + lane;
+    for (int r0 = 0; r0 < kTB; r0 += 8) {
+      real v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = bi * kTB + r0 + u;
+        v[u] = j <= i ? tri_elem(P, i, j, kk) : real(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) dst[(r0 + u) * LD + lane] = v[u];
+    }
   }
-  // right-hand side columns c0..c0+NC (identity when B is null)
-  for (int e = tid; e < KP * NC; e += kTriThreads) {
-    const int i = e / NC, c = e % NC;
-    const int64_t col = c0 + c;
-    const int oi = P.reverse ? P.k - 1 - i : i;
-    real v = real(0);
-    if (i < P.k && oi < kk && col < P.N)
-      v = P.B ? P.B[(int64_t)oi * P.ldb + col] : (oi == col ? real(1) : real(0));
-    Xs[i * NC + c] = v;
+  // right-hand side columns c0..c0+NC (identity when B is null), rows in
+  // batches of 4 per warp
+  for (int i0 = warp * 4; i0 < KP; i0 += 4 * (kTriThreads / 32)) {
+    real v[4][CPT];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u;
+      const int oi = P.reverse ? P.k - 1 - i : i;
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) {
+        const int64_t col = c0 + lane + 32 * q;
+        real x = real(0);
+        if (i < P.k && oi < kk && col < P.N)
+          x = P.B ? P.B[(int64_t)oi * P.ldb + col] : (oi == col ? real(1) : real(0));
+        v[u][q] = x;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int q = 0; q < CPT; ++q)
+        if (i0 + u < KP) Xs[(i0 + u) * NC + lane + 32 * q] = v[u][q];
   }
   __syncthreads();
   // invert each diagonal block: warp b, lane j solves D x = e_j
   if (warp < nb) {
-    real* D = Ls + (size_t)packed_block(warp, warp) * kTB * kTriLd;
+    real* D = Ls + (size_t)packed_block(warp, warp) * kTB * LD;
     real x[kTB];
 #pragma unroll
     for (int i = 0; i < kTB; ++i) {
       real s = i == lane ? real(1) : real(0);
 #pragma unroll
-      for (int t = 0; t < i; ++t) s -= D[i * kTriLd + t] * x[t];
-      x[i] = i >= lane ? s / D[i * kTriLd + i] : real(0);
+      for (int t = 0; t < i; ++t) s -= D[i * LD + t] * x[t];
+      x[i] = i >= lane ? s / D[i * LD + i] : real(0);
     }
     __syncwarp();
 #pragma unroll
-    for (int i = 0; i < kTB; ++i) D[i * kTriLd + lane] = x[i];
+    for (int i = 0; i < kTB; ++i) D[i * LD + lane] = x[i];
   }
   __syncthreads();
-  // block-row sweep; warp w owns rows w and w + 16 of each block
-  const int rA = warp, rB = warp + 16;
+  // block-row sweep: thread (g, col) owns rows g*RPT .. g*RPT+RPT-1 of each
+  // block row and column col; the triangle's rows are read as broadcast
+  // vectors of VN entries, the X column once per entry
+  const int col = tid % NC, r0 = (tid / NC) * RPT;
   for (int b = 0; b < nb; ++b) {
-    real acc[2][CPT];
+    real acc[RPT];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-      acc[0][q] = Xs[(b * kTB + rA) * NC + lane + 32 * q];
-      acc[1][q] = Xs[(b * kTB + rB) * NC + lane + 32 * q];
-    }
+    for (int u = 0; u < RPT; ++u) acc[u] = Xs[(b * kTB + r0 + u) * NC + col];
     for (int t = 0; t < b; ++t) {
-      const real* Lbt = Ls + (size_t)packed_block(b, t) * kTB * kTriLd;
+      const real* Lbt = Ls + (size_t)packed_block(b, t) * kTB * LD;
       const real* Xt = Xs + (t * kTB) * NC;
-#pragma unroll 8
-      for (int s = 0; s < kTB; ++s) {
-        const real la = Lbt[rA * kTriLd + s], lb = Lbt[rB * kTriLd + s];
+#pragma unroll 2
+      for (int s = 0; s < kTB; s += VN) {
+        real xv[VN];
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-          const real x = Xt[s * NC + lane + 32 * q];
-          acc[0][q] -= la * x;
-          acc[1][q] -= lb * x;
+        for (int v = 0; v < VN; ++v) xv[v] = Xt[(s + v) * NC + col];
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+          const V l = *reinterpret_cast<const V*>(Lbt + (r0 + u) * LD + s);
+          if constexpr (VN == 4) {
+            acc[u] -= l.x * xv[0];
+            acc[u] -= l.y * xv[1];
+            acc[u] -= l.z * xv[2];
+            acc[u] -= l.w * xv[3];
+          } else {
+            acc[u] -= l.x * xv[0];
+            acc[u] -= l.y * xv[1];
+          }
         }
       }
     }
-    // X_b = D_b^{-1} acc: stage acc, then multiply
+    // X_b = D_b^{-1} acc: stage acc, then multiply (D_b^{-1} is stored
+    // lower triangular with zeros above the diagonal)
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-      Xs[(b * kTB + rA) * NC + lane + 32 * q] = acc[0][q];
-      Xs[(b * kTB + rB) * NC + lane + 32 * q] = acc[1][q];
-    }
+    for (int u = 0; u < RPT; ++u) Xs[(b * kTB + r0 + u) * NC + col] = acc[u];
     __syncthreads();
-    const real* D = Ls + (size_t)packed_block(b, b) * kTB * kTriLd;
-    real out[2][CPT];
+    const real* D = Ls + (size_t)packed_block(b, b) * kTB * LD;
+    real out[RPT];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) out[0][q] = out[1][q] = real(0);
-#pragma unroll 8
-    for (int s = 0; s <= rB; ++s) {
-      const real da = s <= rA ? D[rA * kTriLd + s] : real(0), db = D[rB * kTriLd + s];
+    for (int u = 0; u < RPT; ++u) out[u] = real(0);
+    const int smax = r0 + RPT;  // entries past the thread's last row are zero
+    for (int s = 0; s < smax; s += VN) {
+      real xv[VN];
 #pragma unroll
-      for (int q = 0; q < CPT; ++q) {
-        const real x = Xs[(b * kTB + s) * NC + lane + 32 * q];
-        out[0][q] += da * x;
-        out[1][q] += db * x;
+      for (int v = 0; v < VN; ++v) xv[v] = Xs[(b * kTB + s + v) * NC + col];
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        const V d = *reinterpret_cast<const V*>(D + (r0 + u) * LD + s);
+        if constexpr (VN == 4) {
+          out[u] += d.x * xv[0];
+          out[u] += d.y * xv[1];
+          out[u] += d.z * xv[2];
+          out[u] += d.w * xv[3];
+        } else {
+          out[u] += d.x * xv[0];
+          out[u] += d.y * xv[1];
+        }
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-      Xs[(b * kTB + rA) * NC + lane + 32 * q] = out[0][q];
-      Xs[(b * kTB + rB) * NC + lane + 32 * q] = out[1][q];
-    }
+    for (int u = 0; u < RPT; ++u) Xs[(b * kTB + r0 + u) * NC + col] = out[u];
     __syncthreads();
   }
   // store (rows at and after the rank are zero already)
@@ -180,7 +219,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_solve_kernel(TriParams<rea
 template <typename real>
 size_t tri_smem(int k) {
   const int nb = (k + kTB - 1) / kTB;
-  return ((size_t)packed_block(nb, 0) * kTB * kTriLd + (size_t)nb * kTB * TriCols<real>::NC) *
+  return ((size_t)packed_block(nb, 0) * kTB * TriCols<real>::LD +
+          (size_t)nb * kTB * TriCols<real>::NC) *
          sizeof(real);
 }
 
