@@ -33,8 +33,11 @@ gemm_simt_kernel(int M, int N, int K, int kchunk, const real* __restrict__ A,
   using Tl = GemmTile<real>;
   constexpr int BM = Tl::BM, BN = Tl::BN, BK = Tl::BK, TM = Tl::TM, TN = Tl::TN;
   constexpr int RX = BN / TN, RY = BM / TM, NT = RX * RY;
-  __shared__ real As[BK][BM + 4];
-  __shared__ real Bs[BK][BN + 4];
+  constexpr int LA = BM * BK / NT, LB = BN * BK / NT;  // tile elements each thread loads
+  // two stages: the next K tile is fetched into registers while the current
+  // one is multiplied, then stored into the other buffer (one barrier per tile)
+  __shared__ real As[2][BK][BM + 4];
+  __shared__ real Bs[2][BK][BN + 4];
   const int tid = threadIdx.x;
   const int tx = tid % RX, ty = tid / RX;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -46,41 +49,66 @@ gemm_simt_kernel(int M, int N, int K, int kchunk, const real* __restrict__ A,
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = real(0);
 
-  for (int k0 = kbeg; k0 < kend; k0 += BK) {
-#pragma unroll 4
-    for (int e = tid; e < BM * BK; e += NT) {
-      int mm, kk;
-      if (TA) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+  // element e = tid + i NT of a tile; consecutive threads walk the operand's
+  // contiguous dimension
+  real ra[LA], rb[LB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+      const int e = tid + i * NT;
+      const int mm = TA ? e % BM : e / BK, kk = TA ? e / BM : e % BK;
       const int gm = m0 + mm, gk = k0 + kk;
-      real v = real(0);
-      if (gm < M && gk < kend)
-        v = TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
-      As[kk][mm] = v;
+      ra[i] = (gm < M && gk < kend) ? (TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk])
+                                    : real(0);
     }
-#pragma unroll 4
-    for (int e = tid; e < BN * BK; e += NT) {
-      int nn, kk;
-      if (TB) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+      const int e = tid + i * NT;
+      const int nn = TB ? e / BK : e % BN, kk = TB ? e % BK : e / BN;
       const int gn = n0 + nn, gk = k0 + kk;
-      real v = real(0);
-      if (gn < N && gk < kend)
-        v = TB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
-      Bs[kk][nn] = v;
+      rb[i] = (gn < N && gk < kend) ? (TB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn])
+                                    : real(0);
     }
-    __syncthreads();
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+      const int e = tid + i * NT;
+      const int mm = TA ? e % BM : e / BK, kk = TA ? e / BM : e % BK;
+      As[buf][kk][mm] = ra[i];
+    }
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+      const int e = tid + i * NT;
+      const int nn = TB ? e / BK : e % BN, kk = TB ? e % BK : e / BN;
+      Bs[buf][kk][nn] = rb[i];
+    }
+  };
+
+  int buf = 0;
+  if (kbeg < kend) {
+    fetch(kbeg);
+    stash(0);
+  }
+  __syncthreads();
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool more = k0 + BK < kend;
+    if (more) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       real a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * RY];
+      for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + i * RY];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + j * RX];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tx + j * RX];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
+    if (more) stash(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
