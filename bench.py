@@ -36,7 +36,7 @@ FP32_FMA_PER_SM_CLK = 128          # FP32 lanes per SM
 # dram__bytes_read.sum + dram__bytes_write.sum of one cpqr_kernel launch on this
 # workload (ncu capture of the current kernel; profiles/ holds the summary):
 # CPQR of Y (210 x 6000) and of C^T (200 x 8000)
-CPQR_DRAM_BYTES = {"cpqr_col": 5.145e6 + 9.5e3, "cpqr_row": 6.504e6 + 11.5e3}
+CPQR_DRAM_BYTES = {"cpqr_col": 5.142e6 + 23.0e3, "cpqr_row": 6.498e6 + 5.9e3}
 NUM_SMS = 152
 
 
