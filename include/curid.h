@@ -96,8 +96,10 @@ curid_status curid_set_stream(curid_handle* handle, void* stream);
 curid_status curid_set_workspace(curid_handle* handle, void* ptr, size_t bytes);
 
 /* Workspace bytes needed by curid_cur / curid_tsid / curid_id_col /
- * curid_id_row for an m x n matrix of dtype `dtype` at rank k (fixed) or
- * k_max (adaptive) with sketch parameters `sk`.  Host-only. */
+ * curid_id_row for an m x n matrix of dtype `dtype` at rank k with sketch
+ * parameters `sk`.  k = 0 asks for the adaptive-rank size (every rank up to
+ * min(m, n)); it needs sk.p < 0 and an FP32/FP64 dtype, else
+ * CURID_UNSUPPORTED, as the compute calls answer.  Host-only. */
 curid_status curid_workspace_size(curid_handle* handle, curid_dtype dtype,
                                   int64_t m, int64_t n,
                                   int k, curid_sketch sk, size_t* bytes);
@@ -193,9 +195,18 @@ curid_status curid_cpqr_static(void* stream, curid_dtype dtype,
 /* ----- the decompositions -------------------------------------------- */
 
 /* Rank selection of the decompositions below: k > 0 is a fixed rank
- * (1 <= k <= min(m, n); randomized: k + p <= min(m, n)).  The adaptive
- * rank (k == 0, tol > 0) is available through curid_cpqr only; the
- * decompositions return CURID_UNSUPPORTED for it.
+ * (1 <= k <= min(m, n); randomized: k + p <= min(m, n)).  k == 0 with
+ * tol > 0 is the adaptive rank of Section 3 for the deterministic method
+ * (p < 0) of curid_id_col, curid_tsid and curid_cur: the smallest k with
+ * ||A - A(:, J[:k]) V*||_F <= tol ||A||_F.  The call then synchronises the
+ * stream once (to read that rank; not for graph capture), runs the
+ * decomposition at that rank, and curid_last_status reports it as k_out.
+ * Output buffers must hold the largest rank, min(m, n): T and TW are written
+ * with the caller's ldt / ldtw, U (k_out x k_out) and C (m x k_out) packed
+ * with leading dimension k_out, R with leading dimension n.  k_out == 0
+ * (the tolerance met with no column, e.g. A = 0): J and I ascending, nothing
+ * else written.  The randomized method needs k for l = k + p and returns
+ * CURID_UNSUPPORTED for k == 0, as does curid_id_row.
  *
  * Order limits: the k x k triangular solves (T, the row ID, U) and the
  * l x l Gram factorisations between power steps (q >= 1, l = k + p) run in

@@ -289,14 +289,36 @@ def _prep(A, k, p, q, seed, omega, tf32):
     return A, h, m, n, dt, sk
 
 
-def id_col(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, check=True):
-    """Column ID A ~ A(:, J[:k]) [I T] P^T (Algorithm 1; p >= 0: Algorithm 4)."""
+def _steps_done(h):
+    """CPQR steps of the last call (status block word 1): the rank an adaptive
+    call ran its decomposition at (its outputs' shapes)."""
+    torch.cuda.synchronize(h.device)
+    return int(h.ws[4:8].view(torch.int32).item())
+
+
+def _adaptive(k, tol, p):
+    if k == 0:
+        if not tol > 0:
+            raise ValueError("k == 0 needs tol > 0 (adaptive rank)")
+        return True
+    return False
+
+
+def id_col(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, tol=0.0, check=True):
+    """Column ID A ~ A(:, J[:k]) [I T] P^T (Algorithm 1; p >= 0: Algorithm 4).
+    k == 0 with tol > 0: adaptive rank (deterministic method)."""
+    adaptive = _adaptive(k, tol, p)
     A, h, m, n, dt, sk = _prep(A, k, p, q, seed, omega, tf32)
+    kb = min(m, n) if adaptive else k
     J = torch.empty(n, dtype=torch.int32, device=A.device)
-    T = torch.empty((k, max(n - k, 1)), dtype=_work_dtype(A.dtype), device=A.device)
-    _check(h.lib.curid_id_col(h.h, dt, _ptr(A), m, n, A.stride(0), k, 0.0, sk, _ptr(J), _ptr(T),
-                              T.stride(0)), "curid_id_col")
-    return _finish(h, Result(J=J, T=T[:, :n - k]), check, "curid_id_col")
+    T = torch.empty((kb, n if adaptive else max(n - k, 1)), dtype=_work_dtype(A.dtype),
+                    device=A.device)
+    _check(h.lib.curid_id_col(h.h, dt, _ptr(A), m, n, A.stride(0), k, float(tol), sk, _ptr(J),
+                              _ptr(T), T.stride(0)), "curid_id_col")
+    res = _finish(h, Result(J=J, T=T), check or adaptive, "curid_id_col")
+    kk = _steps_done(h) if adaptive else k
+    res.T = T[:kk, :n - kk]
+    return res
 
 
 def id_row(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, check=True):
@@ -309,16 +331,24 @@ def id_row(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, check=True):
     return _finish(h, Result(I=I, TW=TW[:, :m - k]), check, "curid_id_row")
 
 
-def tsid(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, check=True):
-    """Two-sided ID A ~ W A(I[:k], J[:k]) V* (Algorithm 2)."""
+def tsid(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, tol=0.0, check=True):
+    """Two-sided ID A ~ W A(I[:k], J[:k]) V* (Algorithm 2); k == 0 with
+    tol > 0: adaptive rank (deterministic method)."""
+    adaptive = _adaptive(k, tol, p)
     A, h, m, n, dt, sk = _prep(A, k, p, q, seed, omega, tf32)
+    kb = min(m, n) if adaptive else k
     J = torch.empty(n, dtype=torch.int32, device=A.device)
     I = torch.empty(m, dtype=torch.int32, device=A.device)
-    T = torch.empty((k, max(n - k, 1)), dtype=_work_dtype(A.dtype), device=A.device)
-    TW = torch.empty((k, max(m - k, 1)), dtype=_work_dtype(A.dtype), device=A.device)
-    _check(h.lib.curid_tsid(h.h, dt, _ptr(A), m, n, A.stride(0), k, 0.0, sk, _ptr(J), _ptr(T),
-                            T.stride(0), _ptr(I), _ptr(TW), TW.stride(0)), "curid_tsid")
-    return _finish(h, Result(J=J, T=T[:, :n - k], I=I, TW=TW[:, :m - k]), check, "curid_tsid")
+    T = torch.empty((kb, n if adaptive else max(n - k, 1)), dtype=_work_dtype(A.dtype),
+                    device=A.device)
+    TW = torch.empty((kb, m if adaptive else max(m - k, 1)), dtype=_work_dtype(A.dtype),
+                     device=A.device)
+    _check(h.lib.curid_tsid(h.h, dt, _ptr(A), m, n, A.stride(0), k, float(tol), sk, _ptr(J),
+                            _ptr(T), T.stride(0), _ptr(I), _ptr(TW), TW.stride(0)), "curid_tsid")
+    res = _finish(h, Result(J=J, T=T, I=I, TW=TW), check or adaptive, "curid_tsid")
+    kk = _steps_done(h) if adaptive else k
+    res.T, res.TW = T[:kk, :n - kk], TW[:kk, :m - kk]
+    return res
 
 
 def cur_outputs(A, k, want_c=False, want_r=False, want_t=False, want_tw=False):
@@ -338,17 +368,44 @@ def cur_outputs(A, k, want_c=False, want_r=False, want_t=False, want_tw=False):
 
 
 def cur(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, want_c=False, want_r=False,
-        want_t=False, want_tw=False, out=None, check=True):
-    """CUR-ID A ~ C U R (Algorithm 3); U is float64 (k x k)."""
+        want_t=False, want_tw=False, out=None, check=True, tol=0.0):
+    """CUR-ID A ~ C U R (Algorithm 3); U is float64 (k x k).  k == 0 with
+    tol > 0: adaptive rank (deterministic method); outputs are views at the
+    rank reached (res.k)."""
+    adaptive = _adaptive(k, tol, p)
     A, h, m, n, dt, sk = _prep(A, k, p, q, seed, omega, tf32)
-    o = out if out is not None else cur_outputs(A, k, want_c, want_r, want_t, want_tw)
-    st = h.lib.curid_cur(h.h, dt, _ptr(A), m, n, A.stride(0), k, 0.0, sk, _ptr(o.J), _ptr(o.I),
-                         _ptr(o.U), _ptr(o.C), _ptr(o.R), _ptr(o.T),
+    kb = min(m, n) if adaptive else k
+    if adaptive:
+        dev = A.device
+        o = Result(
+            J=torch.empty(n, dtype=torch.int32, device=dev),
+            I=torch.empty(m, dtype=torch.int32, device=dev),
+            U=torch.empty(kb * kb, dtype=torch.float64, device=dev),
+            C=torch.empty(m * kb, dtype=A.dtype, device=dev) if want_c else None,
+            R=torch.empty((kb, n), dtype=A.dtype, device=dev) if want_r else None,
+            T=torch.empty((kb, n), dtype=_work_dtype(A.dtype), device=dev) if want_t else None,
+            TW=torch.empty((kb, m), dtype=_work_dtype(A.dtype), device=dev)
+            if want_tw else None)
+    else:
+        o = out if out is not None else cur_outputs(A, k, want_c, want_r, want_t, want_tw)
+    st = h.lib.curid_cur(h.h, dt, _ptr(A), m, n, A.stride(0), k, float(tol), sk, _ptr(o.J),
+                         _ptr(o.I), _ptr(o.U), _ptr(o.C), _ptr(o.R), _ptr(o.T),
                          o.T.stride(0) if o.T is not None else 0, _ptr(o.TW),
                          o.TW.stride(0) if o.TW is not None else 0)
     _check(st, "curid_cur")
-    return _finish(h, o, check, "curid_cur")
-
+    res = _finish(h, o, check or adaptive, "curid_cur")
+    if adaptive:
+        kk = _steps_done(h)
+        res.U = o.U[:kk * kk].view(kk, kk)
+        if want_c:
+            res.C = o.C[:m * kk].view(m, kk)
+        if want_r:
+            res.R = o.R[:kk]
+        if want_t:
+            res.T = o.T[:kk, :n - kk]
+        if want_tw:
+            res.TW = o.TW[:kk, :m - kk]
+    return res
 
 def cur_adjoint(A, J, I, T, k, Cbar=None, Ubar=None, Rbar=None, out=None, check=True):
     """Gradient with respect to A of <Cbar, C> + <Ubar, U> + <Rbar, R> for the

@@ -497,6 +497,69 @@ curid_status dispatch(curid_handle* h, F&& f) {
   return f();
 }
 
+// Adaptive rank of the deterministic decompositions (the tolerance stop of
+// Section 3): the truncated CPQR of A runs with the stop ||A - C V*||_F <=
+// tol ||A||_F (curid_cpqr, S placed after its scratch in the workspace), the
+// stream is synchronised once to read the rank reached, and the caller then
+// runs the fixed-rank pipeline at that rank (its CPQR repeats the same pivots:
+// the tolerance only decides when to stop).  Rank 0 (the tolerance met by no
+// column, e.g. A = 0): J comes back from this call and the caller fills I.
+curid_status adaptive_rank(curid_handle* h, curid_dtype dt, const void* A, int64_t m, int64_t n,
+                           int64_t lda, double tol, int32_t* J, int* k_out) {
+  const int64_t kmax = std::min(m, n);
+  const size_t esz = dt == CURID_F64 ? 8 : 4;
+  Ctx ctx{nullptr, h->num_sms, h->smem_optin, nullptr};
+  Carver cv(nullptr);
+  cv.take<StatusBlock>(1);
+  CpqrScratch cs;
+  if (dt == CURID_F64) cpqr_carve<double>(cv, ctx, m, n, &cs);
+  else cpqr_carve<float>(cv, ctx, m, n, &cs);
+  const size_t off = (cv.used + 255) & ~size_t(255);
+  if (!h->ws || off + (size_t)kmax * n * esz > h->ws_bytes) return CURID_NO_WORKSPACE;
+  CURID_TRY(curid_cpqr(h, dt, A, m, n, lda, 0, tol, J, h->ws + off));
+  StatusBlock sb;
+  DeviceGuard g(h->device);
+  if (!g.ok) return CURID_CUDA_ERROR;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return CURID_CUDA_ERROR;
+  if (cudaMemcpy(&sb, h->ws, sizeof(sb), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return CURID_CUDA_ERROR;
+  if (sb.flags & FLAG_TIMEOUT) return CURID_TIMEOUT;
+  if (sb.flags & FLAG_NONFINITE) return CURID_NONFINITE;
+  *k_out = sb.k_done;
+  return CURID_OK;
+}
+
+// Decides between the fixed rank k and the adaptive rank (k == 0, tol > 0,
+// deterministic method only); on return *k is the rank to run, or 0 when the
+// tolerance is met by no column (J already written).
+curid_status resolve_rank(curid_handle* h, curid_dtype dt, const void* A, int64_t m, int64_t n,
+                          int64_t lda, int* k, double tol, const curid_sketch& sk, int32_t* J) {
+  if (*k != 0) return CURID_OK;
+  if (!h || !A || !J || m <= 0 || n <= 0 || lda < n || !(tol > 0)) return CURID_INVALID_ARG;
+  if (sk.p >= 0 || dt == CURID_BF16) return CURID_UNSUPPORTED;  // l = k + p needs k
+  int kout = 0;
+  CURID_TRY(adaptive_rank(h, dt, A, m, n, lda, tol, J, &kout));
+  *k = kout;
+  return CURID_OK;
+}
+
+__global__ void iota_kernel(int32_t* x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = (int32_t)i;
+}
+
+// Rank 0: I = 0..m-1 (nothing is selected); the status block records k = 0.
+curid_status rank_zero_rows(curid_handle* h, int32_t* I, int64_t m) {
+  DeviceGuard g(h->device);
+  if (!g.ok) return CURID_CUDA_ERROR;
+  if (I) {
+    iota_kernel<<<(unsigned)std::min<int64_t>((m + 255) / 256, 1024), 256, 0, h->stream>>>(I, m);
+    CURID_CUDA(cudaGetLastError());
+  }
+  return CURID_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -578,6 +641,12 @@ curid_status curid_set_workspace(curid_handle* handle, void* ptr, size_t bytes) 
 curid_status curid_workspace_size(curid_handle* handle, curid_dtype dtype, int64_t m, int64_t n,
                                   int k, curid_sketch sk, size_t* bytes) {
   if (!handle || !bytes) return CURID_INVALID_ARG;
+  // adaptive rank (k == 0, deterministic): room for every rank up to min(m, n);
+  // with a sketch the rank would have to be known to size it (l = k + p)
+  if (k == 0 && m > 0 && n > 0) {
+    if (sk.p >= 0 || dtype == CURID_BF16) return CURID_UNSUPPORTED;
+    k = (int)std::min<int64_t>(m, n);
+  }
   Dims d;
   int dummy = 1;
   CURID_TRY(check_common(handle, dtype, &dummy, m, n, n, k, 0.0, sk, &d));
@@ -708,6 +777,8 @@ curid_status curid_cpqr(curid_handle* handle, curid_dtype dtype, const void* Y, 
 curid_status curid_id_col(curid_handle* handle, curid_dtype dtype, const void* A, int64_t m,
                           int64_t n, int64_t lda, int k, double tol, curid_sketch sk, int32_t* J,
                           void* T, int64_t ldt) {
+  CURID_TRY(resolve_rank(handle, dtype, A, m, n, lda, &k, tol, sk, J));
+  if (k == 0 && tol > 0) return CURID_OK;
   Dims d;
   CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d));
   if (!J || !T || ldt < std::max<int64_t>(1, n - k)) return CURID_INVALID_ARG;
@@ -756,6 +827,8 @@ curid_status curid_id_row(curid_handle* handle, curid_dtype dtype, const void* A
 curid_status curid_tsid(curid_handle* handle, curid_dtype dtype, const void* A, int64_t m,
                         int64_t n, int64_t lda, int k, double tol, curid_sketch sk, int32_t* J,
                         void* T, int64_t ldt, int32_t* I, void* TW, int64_t ldtw) {
+  CURID_TRY(resolve_rank(handle, dtype, A, m, n, lda, &k, tol, sk, J));
+  if (k == 0 && tol > 0) return rank_zero_rows(handle, I, m);
   Dims d;
   CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d));
   if (!J || !T || !I || !TW || ldt < std::max<int64_t>(1, n - k) ||
@@ -775,6 +848,8 @@ curid_status curid_cur(curid_handle* handle, curid_dtype dtype, const void* A, i
                        int64_t n, int64_t lda, int k, double tol, curid_sketch sk, int32_t* J,
                        int32_t* I, double* U, void* C, void* R, void* T, int64_t ldt, void* TW,
                        int64_t ldtw) {
+  CURID_TRY(resolve_rank(handle, dtype, A, m, n, lda, &k, tol, sk, J));
+  if (k == 0 && tol > 0) return rank_zero_rows(handle, I, m);
   Dims d;
   CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d));
   if (!J || !I || !U) return CURID_INVALID_ARG;

@@ -372,3 +372,41 @@ def test_tensor_core_randomized_cur():
     assert id_residual(Ah, J, T, k) <= 1.05 * id_residual(Ah, o.J, o.T, k)
     Uo = O.cur_middle(R, O.vstar(J, T, n))
     assert abs(eg - O.rel_err_fro(Ah, C, Uo, R)) <= 1e-5
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_adaptive_rank_decompositions(tol):
+    """k = 0, tol > 0 (deterministic): the rank, skeletons and factors of the
+    oracle's tolerance stop, through id_col, tsid and cur."""
+    A = syn.spectrum_matrix(500, 400, syn.exp_decay(400, 8.0), 23)
+    o = O.cur(np64(A), tol=tol)
+    ko = o.k
+    r1 = curid.id_col(cuda(A), 0, tol=tol)
+    assert r1.k == ko and list(npi(r1.J)) == list(o.J)
+    # both T are backward-stable solves of S11 T = S12: kappa(S11) u ||T||
+    kappa = o.ts.col.qr.nu[0] / o.ts.col.qr.nu[ko - 1]
+    assert np.linalg.norm(np64(r1.T) - o.T) <= 1e2 * kappa * U64 * max(1.0, np.linalg.norm(o.T))
+    r2 = curid.tsid(cuda(A), 0, tol=tol)
+    assert r2.k == ko and list(npi(r2.I)) == list(o.I)
+    assert r2.TW.shape == (ko, 500 - ko)
+    r3 = curid.cur(cuda(A), 0, tol=tol, want_c=True, want_r=True)
+    assert r3.k == ko and r3.U.shape == (ko, ko) and r3.C.shape == (500, ko)
+    Ah = np64(A)
+    assert np.array_equal(np64(r3.C), Ah[:, npi(r3.J)[:ko]])
+    eg = O.rel_err_fro(Ah, np64(r3.C), np64(r3.U), np64(r3.R))
+    eo = O.rel_err_fro(Ah, o.C, o.U, o.R)
+    # the stop bounds the ID residual; the CUR error may exceed tol (Lemma 3.1)
+    assert id_residual(Ah, npi(r1.J), np64(r1.T), ko) <= tol * 1.05
+    # U = V* R^+ solves with R, whose condition is about kappa(S11): each side's
+    # CUR error carries rounding of order kappa u (2.6e-6 vs 3.2e-6 at 1e-10)
+    assert abs(eg - eo) <= max(1e-12, 1e2 * kappa * U64), (eg, eo)
+
+
+def test_adaptive_rank_zero_and_unsupported():
+    Z = torch.zeros((60, 50), dtype=torch.float64, device="cuda:0")
+    r = curid.cur(Z, 0, tol=1e-8)
+    assert r.k == 0 and list(npi(r.J)) == list(range(50)) and list(npi(r.I)) == list(range(60))
+    A = cuda(syn.spectrum_matrix(200, 150, syn.exp_decay(150, 8.0), 24))
+    with pytest.raises(curid.CuridError) as e:
+        curid.cur(A, 0, p=10, tol=1e-6, seed=3)
+    assert e.value.status == 8
