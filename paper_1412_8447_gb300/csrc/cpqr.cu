@@ -21,209 +21,24 @@
 //      carries the step's tag, so no fence is needed and a reader checks
 //      each word for freshness.
 // One grid-wide exchange and three CTA barriers per pivot step; no host
-// round trip until the end.
+// round trip until the end.  The exchange (records, tags, pivot decision,
+// pivot-column read, closing count exchange) lives in cpqr_exchange.cuh and
+// is shared with the register-resident variant in cpqr_reg.cu, which
+// cpqr_run launches instead when the slab fits in registers (at most 256
+// rows, 128 in float64, and 64 columns per CTA).
 // After the last step row i of S holds S1(i, c) for every original column c,
 // J lists the pivots and then the unselected columns in ascending order.
 #include <atomic>
 
-#include "kernels.cuh"
+#include "cpqr_exchange.cuh"
 
 namespace curid {
 
 namespace {
 
-// Exchange record of one CTA for one step: four 64-bit words, each
-// (epoch << 32 | payload).  Every word carries the epoch, so a reader that
-// sees the current epoch in all four has a consistent record no matter in
-// which order the words became visible (each aligned 64-bit access is
-// single-copy atomic).  Payloads: w0 = candidate column (kNoCol: none,
-// kNonFinite: a non-finite norm was seen; the final exchange carries the
-// CTA's count of unselected columns), w1/w2 = candidate norm (float bits in
-// w1; float64 split high/low), w3 = sum of the CTA's squared residual norms
-// as float (adaptive stop only).
-struct alignas(128) Rec {  // one record per 128-byte line: no two writers share a line
-  unsigned long long w[4];
-  unsigned long long pad[12];
-};
+using namespace cpqr_x;
 
-template <typename real>
-struct CpqrParams {
-  const real* Y;
-  int64_t ldy;
-  int l, n, k_max, nc, ldl;
-  int ncs;                       // columns of a slab held in shared memory (the rest: gys)
-  real* gys;                     // [G][nc - ncs][ldl] overflow columns, column-major
-  real tol;
-  real rank_rtol;
-  int32_t* J;
-  real* S;
-  int64_t lds;
-  Rec* recs;                     // [2][G]
-  unsigned long long* slot_data;  // [2][G][l * words]: tagged candidate columns
-  int* abort_flag;
-  StatusBlock* status;
-  int which;
-  unsigned gen;                  // launch generation, high bits of every tag
-};
-
-// Published candidate columns are tagged word by word like the records, so a
-// reader can tell a fresh element from a stale one without any fence on the
-// writer's side: float32 -> one word (tag, bits); float64 -> two words
-// (tag, high bits), (tag, low bits).  The tag of step e in launch g is
-// (g << 20) | e.
-template <typename real>
-struct Words {
-  static constexpr int W = sizeof(real) / 4;
-};
-
-constexpr int kThreads = 512;
-constexpr int kWarps = kThreads / 32;
 constexpr int kColsPerWarp = 4;  // columns a warp updates in one interleaved pass
-constexpr unsigned kNoCol = 0xffffffffu;
-constexpr unsigned kNonFinite = 0xfffffffeu;
-constexpr int kMaxSlotsPerLane = 5;  // G <= 160 (one CTA per SM; the GPU has 152)
-
-__device__ __forceinline__ unsigned long long pack(unsigned epoch, unsigned payload) {
-  return ((unsigned long long)epoch << 32) | payload;
-}
-
-__device__ __forceinline__ unsigned tag_of(unsigned gen, int epoch) {
-  return (gen << 20) | (unsigned)epoch;
-}
-
-template <typename real>
-__device__ __forceinline__ void put_tagged(unsigned long long* dst, unsigned tag, real v) {
-  if (sizeof(real) == 8) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong((double)v);
-    st_volatile_u64(dst, pack(tag, (unsigned)(b >> 32)));
-    st_volatile_u64(dst + 1, pack(tag, (unsigned)(b & 0xffffffffull)));
-  } else {
-    st_volatile_u64(dst, pack(tag, __float_as_uint((float)v)));
-  }
-}
-
-// Bounded read of one tagged element; false if it never became fresh.
-template <typename real>
-__device__ __forceinline__ bool get_tagged(const unsigned long long* src, unsigned tag, real* v,
-                                           const int* abort_flag) {
-  const long long t0 = clock64();
-  while (true) {
-    if (sizeof(real) == 8) {
-      const unsigned long long a = ld_volatile_u64(src), b = ld_volatile_u64(src + 1);
-      if ((unsigned)(a >> 32) == tag && (unsigned)(b >> 32) == tag) {
-        *v = (real)__longlong_as_double((long long)(((a & 0xffffffffull) << 32) |
-                                                     (b & 0xffffffffull)));
-        return true;
-      }
-    } else {
-      const unsigned long long a = ld_volatile_u64(src);
-      if ((unsigned)(a >> 32) == tag) {
-        *v = (real)__uint_as_float((unsigned)(a & 0xffffffffull));
-        return true;
-      }
-    }
-    if (ld_volatile_i32(abort_flag) || clock64() - t0 > kSpinBudget) return false;
-  }
-}
-
-template <typename real>
-__device__ __forceinline__ void norm_words(real v, unsigned* hi, unsigned* lo) {
-  if (sizeof(real) == 8) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong((double)v);
-    *hi = (unsigned)(b >> 32);
-    *lo = (unsigned)(b & 0xffffffffull);
-  } else {
-    *hi = __float_as_uint((float)v);
-    *lo = 0u;
-  }
-}
-
-template <typename real>
-__device__ __forceinline__ real words_norm(unsigned hi, unsigned lo) {
-  if (sizeof(real) == 8)
-    return (real)__longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
-  return (real)__uint_as_float(hi);
-}
-
-__device__ __forceinline__ void st_rec(Rec* r, unsigned long long a, unsigned long long b,
-                                       unsigned long long c, unsigned long long d) {
-  asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(&r->w[0]), "l"(a), "l"(b)
-               : "memory");
-  asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(&r->w[2]), "l"(c), "l"(d)
-               : "memory");
-}
-
-__device__ __forceinline__ void ld_rec(const Rec* r, unsigned long long* w) {
-  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
-               : "=l"(w[0]), "=l"(w[1])
-               : "l"(&r->w[0]));
-  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
-               : "=l"(w[2]), "=l"(w[3])
-               : "l"(&r->w[2]));
-}
-
-template <typename real>
-__device__ __forceinline__ bool better(real na, unsigned ca, real nb, unsigned cb) {
-  // (na, ca) beats (nb, cb): larger norm, then smaller column; kNoCol loses.
-  if (ca == kNoCol) return false;
-  if (cb == kNoCol) return true;
-  if (na > nb) return true;
-  if (na < nb) return false;
-  return ca < cb;
-}
-
-// Warp 0: wait until all G records of buffer `bf` carry `epoch`, keeping
-// their words.  Each lane polls up to kMaxSlotsPerLane records with all of
-// its loads in flight at once.  Returns false on timeout or abort.
-template <typename real>
-__device__ bool gather_records(const CpqrParams<real>& P, int bf, unsigned epoch,
-                               unsigned long long (*w)[4]) {
-  const int lane = threadIdx.x & 31;
-  const int G = gridDim.x;
-  const Rec* base = P.recs + (size_t)bf * G;
-  // float32 without a tolerance needs only (column, norm): one 16-byte load
-  const bool full = sizeof(real) == 8 || P.tol > real(0);
-  unsigned pending = 0;
-#pragma unroll
-  for (int r = 0; r < kMaxSlotsPerLane; ++r)
-    if (lane + 32 * r < G) pending |= 1u << r;
-  bool ok = true;
-  const long long t0 = clock64();
-  for (int round = 0; pending; ++round) {
-#pragma unroll
-    for (int r = 0; r < kMaxSlotsPerLane; ++r) {
-      if (!(pending & (1u << r))) continue;
-      const Rec* rec = base + lane + 32 * r;
-      if (full) {
-        ld_rec(rec, w[r]);
-      } else {
-        asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
-                     : "=l"(w[r][0]), "=l"(w[r][1])
-                     : "l"(&rec->w[0]));
-        w[r][2] = w[r][3] = (unsigned long long)epoch << 32;
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < kMaxSlotsPerLane; ++r) {
-      if (!(pending & (1u << r))) continue;
-      bool fresh = true;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) fresh &= (unsigned)(w[r][q] >> 32) == epoch;
-      if (fresh) pending &= ~(1u << r);
-    }
-    if (!pending) break;
-    if ((round & 15) == 15) {
-      if (ld_volatile_i32(P.abort_flag)) { ok = false; break; }
-      if (clock64() - t0 > kSpinBudget) {
-        atomicExch(P.abort_flag, 1);
-        ok = false;
-        break;
-      }
-    }
-  }
-  ok = __all_sync(0xffffffffu, ok);
-  return ok;
-}
 
 // Column lc of this CTA's slab: shared memory for lc < ncs, else the CTA's
 // part of the global overflow area (same column-major layout).
@@ -272,7 +87,7 @@ __device__ void publish(const CpqrParams<real>& P, real* ys, const real* nrm,
   }
   if (bi >= 0 && !nf) {
     constexpr int W = Words<real>::W;
-    unsigned long long* dst = P.slot_data + ((int64_t)bf * G + blockIdx.x) * P.l * W;
+    unsigned long long* dst = slot_of(P, bf, blockIdx.x);
     if (!OV || bi < P.ncs) {
       const real* src = ys + (int64_t)bi * P.ldl;
       for (int r = r0 + lane; r < P.l; r += 32) put_tagged<real>(dst + (int64_t)r * W, tag, src[r]);
@@ -409,15 +224,14 @@ template <typename real, bool OV>
 __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int G = gridDim.x, b = blockIdx.x;
+  const int b = blockIdx.x;
   const int nc = P.nc, ldl = P.ldl, l = P.l;
   real* ys = reinterpret_cast<real*>(smem_raw);
   real* xv = ys + (int64_t)P.ncs * ldl;
   real* nrm = xv + ldl;
   int* active = reinterpret_cast<int*>(nrm + nc);
 
-  __shared__ int s_stop, s_owner, s_col, s_prefix;
-  __shared__ real s_nu;
+  __shared__ StepState<real> st;
 
   const int c0 = b * nc;
   const int ncl = max(0, min(nc, P.n - c0));
@@ -445,105 +259,20 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
   }
   __syncthreads();
   if (warp == 0) publish<OV>(P, ys, nrm, active, ncl, c0, 0, 0, 1u);
-  __shared__ int s_stale;
 
   real normY = real(-1), nu_first = real(0);
   int k_eff = -1;
   int j = 0;
   for (;; ++j) {
-    const int bf = j & 1;
-    if (warp == 0) {
-      unsigned long long w[kMaxSlotsPerLane][4];
-      const bool ok = gather_records(P, bf, tag_of(P.gen, j + 1), w);
-      // global pivot and totals, identical in every CTA
-      real bn = real(-1), tot = real(0);
-      unsigned bc = kNoCol;
-      int bo = -1, nf = 0;
-      if (ok) {
-#pragma unroll
-        for (int r = 0; r < kMaxSlotsPerLane; ++r) {
-          const int s = lane + 32 * r;
-          if (s >= G) continue;
-          const unsigned col = (unsigned)(w[r][0] & 0xffffffffull);
-          const real nn = words_norm<real>((unsigned)(w[r][1] & 0xffffffffull),
-                                           (unsigned)(w[r][2] & 0xffffffffull));
-          tot += (real)__uint_as_float((unsigned)(w[r][3] & 0xffffffffull));
-          if (col == kNonFinite) nf = 1;
-          else if (better(nn, col, bn, bc)) { bn = nn; bc = col; bo = s; }
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const real on = __shfl_xor_sync(0xffffffffu, bn, o);
-        const unsigned oc = __shfl_xor_sync(0xffffffffu, bc, o);
-        const int oo = __shfl_xor_sync(0xffffffffu, bo, o);
-        if (better(on, oc, bn, bc)) { bn = on; bc = oc; bo = oo; }
-        tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        nf |= __shfl_xor_sync(0xffffffffu, nf, o);
-      }
-      if (lane == 0) {
-        int stop = 0;
-        if (!ok) {
-          stop = 2;
-          set_flag(&P.status->flags, FLAG_TIMEOUT);
-        } else if (nf) {
-          stop = 1;
-          if (b == 0) set_flag(&P.status->flags, FLAG_NONFINITE);
-        } else if (j >= P.k_max || bc == kNoCol) {
-          stop = 1;
-        } else {
-          if (normY < real(0)) normY = sqrt(tot);
-          if (P.tol > real(0) && sqrt(tot) <= P.tol * normY) stop = 1;
-        }
-        s_stop = stop;
-        s_owner = bo;
-        s_col = (int)bc;
-        s_nu = bn;
-      }
-    }
+    if (warp == 0) decide_pivot(P, j, normY, st);
     __syncthreads();
-    if (s_stop) break;
-    const int owner = s_owner, pcol = s_col;
-    const real nu = s_nu;
-    if (j == 0) nu_first = nu;
-    if (k_eff < 0 && (nu == real(0) || nu <= P.rank_rtol * nu_first)) {
-      k_eff = j;
-      if (b == 0 && tid == 0) set_flag(&P.status->flags, FLAG_RANK_DEFICIENT);
-    }
-    // pivot column rows j..l-1, as its owner published it (tagged words)
-    {
-      constexpr int W = Words<real>::W;
-      const unsigned long long* src = P.slot_data + ((int64_t)bf * G + owner) * l * W;
-      const unsigned tag = tag_of(P.gen, j + 1);
-      if (tid == 0) s_stale = 0;
-      __syncthreads();
-      for (int r = j + tid; r < l; r += kThreads) {
-        real v;
-        if (!get_tagged<real>(src + (int64_t)r * W, tag, &v, P.abort_flag)) {
-          s_stale = 1;
-          v = real(0);
-        }
-        xv[r] = v;
-      }
-      __syncthreads();
-      if (s_stale) {
-        if (tid == 0) {
-          atomicExch(P.abort_flag, 1);
-          set_flag(&P.status->flags, FLAG_TIMEOUT);
-        }
-        s_stop = 2;
-        break;
-      }
-    }
-    // Householder reflector H = I - tau v v^T with v(j) = 1, v(r) = scale x(r):
-    // H x = beta e_j, beta = -sign(alpha) nu
-    const real alpha = xv[j];
-    const real beta = alpha >= real(0) ? -nu : nu;
-    real tau = real(0), scale = real(0);
-    if (nu > real(0)) {
-      tau = (beta - alpha) / beta;
-      scale = real(1) / (alpha - beta);
-    }
+    if (st.stop) break;
+    const int owner = st.owner, pcol = st.col;
+    const real nu = st.nu;
+    note_rank(P, j, nu, nu_first, k_eff);
+    if (!fetch_pivot<kThreads>(P, j, owner, xv, st)) break;
+    real beta, tau, scale;
+    reflector(xv[j], nu, &beta, &tau, &scale);
     // apply H to every unselected local column, recompute its residual norm
     // from rows j+1..l-1; the owner retires the pivot column.  Warp w owns
     // columns w, w + 16, w + 32, w + 48 and updates them in one interleaved
@@ -557,57 +286,16 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
     }
     __syncthreads();
     if (warp == 0) publish<OV>(P, ys, nrm, active, ncl, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2));
-
   }
   const int k_done = j;
-  if (s_stop == 2) return;  // timed out: leave without further waits
+  if (st.stop == 2) return;  // timed out: leave without further waits
   // S rows 0..k_done-1 in original column order
   for (int64_t e = tid; e < (int64_t)k_done * ncl; e += kThreads) {
     const int i = (int)(e / ncl), lc = (int)(e % ncl);
     P.S[(int64_t)i * P.lds + c0 + lc] =
         (!OV || lc < P.ncs) ? ys[(int64_t)lc * ldl + i] : slab_col<true>(P, ys, lc)[i];
   }
-  // unselected columns in ascending order after the pivots: exchange counts
-  const int fbf = (j + 1) & 1;
-  const unsigned fep = tag_of(P.gen, j + 2);
-  if (warp == 0) {
-    int cnt = 0;
-    for (int lc = lane; lc < ncl; lc += 32) cnt += active[lc];
-    cnt = warp_sum(cnt);
-    if (lane == 0) {
-      st_rec(P.recs + (size_t)fbf * G + b, pack(fep, (unsigned)cnt), pack(fep, 0u), pack(fep, 0u),
-             pack(fep, 0u));
-    }
-    unsigned long long w[kMaxSlotsPerLane][4];
-    const bool ok = gather_records(P, fbf, fep, w);
-    int pre = 0;
-    if (ok) {
-#pragma unroll
-      for (int r = 0; r < kMaxSlotsPerLane; ++r)
-        if (lane + 32 * r < b) pre += (int)(w[r][0] & 0xffffffffull);
-    }
-    pre = warp_sum(pre);
-    if (lane == 0) {
-      s_prefix = pre;
-      s_stop = ok ? 0 : 2;
-      if (!ok) set_flag(&P.status->flags, FLAG_TIMEOUT);
-    }
-  }
-  __syncthreads();
-  if (s_stop) return;
-  if (tid == 0) {
-    int pos = k_done + s_prefix;
-    for (int lc = 0; lc < ncl; ++lc)
-      if (active[lc]) P.J[pos++] = c0 + lc;
-    if (b == 0) {
-      if (P.which == 0) {
-        P.status->k_done = k_done;
-        P.status->k_eff = k_eff < 0 ? k_done : k_eff;
-      } else {
-        P.status->k_row = k_eff < 0 ? k_done : k_eff;
-      }
-    }
-  }
+  finish_order(P, active, ncl, c0, k_done, k_eff, st);
 }
 
 template <typename real>
@@ -652,7 +340,7 @@ void cpqr_carve(Carver& cv, const Ctx& ctx, int64_t l, int64_t n, CpqrScratch* s
   if (cpqr_layout<real>(ctx, l, n, &G, &nc, &ncs) != CURID_OK) G = nc = ncs = 1;
   s->grid = G;
   s->slots = cv.take<Rec>(2 * (size_t)G);
-  s->slot_data = cv.take<unsigned long long>(2 * (size_t)G * l * Words<real>::W);
+  s->slot_data = cv.take<unsigned long long>(2 * (size_t)G * slot_words<real>(l));
   s->counts = cv.take<int>(G);
   s->abort_flag = cv.take<int>(1);
   s->overflow = nc > ncs ? cv.take<real>((size_t)G * (nc - ncs) * (size_t)(l | 1)) : nullptr;
@@ -693,6 +381,7 @@ curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64
   P.which = which;
   CURID_CUDA(cudaMemsetAsync(s.slots, 0, 2 * (size_t)G * sizeof(Rec), ctx.stream));
   CURID_CUDA(cudaMemsetAsync(s.abort_flag, 0, sizeof(int), ctx.stream));
+  if (cpqr_reg_fits<real>(ctx, (int)l, nc)) return cpqr_reg_launch<real>(ctx, P, G);
   auto fn = nc > ncs ? cpqr_kernel<real, true> : cpqr_kernel<real, false>;
   CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   void* args[] = {&P};

@@ -1,0 +1,329 @@
+// Truncated column-pivoted Householder QR (Section 2.2, Eq. (2.4)-(2.5)) with
+// the column slab held in registers: the variant cpqr_run picks when the
+// matrix has at most 256 rows (128 in float64) and a CTA's slab at most 64
+// columns (the sketch Y = Omega A of Algorithms 1 and 4 and the C^* of
+// Algorithm 2 at the ranks of the paper's experiments).
+//
+// Same grid-wide exchange as the shared-memory kernel (cpqr_exchange.cuh):
+// one persistent CTA per SM, one record per CTA and step, tagged candidate
+// columns, the pivot column read by every CTA.  What changes is the update:
+// warp w keeps slab columns w, w + 16, w + 32, w + 48 for the whole
+// factorization, lane t holding rows t, t + 32, ..., t + 32 (RPL - 1) of
+// each (rows past l are zero), so a step moves no slab data through shared
+// memory.  Each lane builds its rows of the reflector v from the pivot
+// column once per step, with v = 0 above row j and v(j) = 1, so neither the
+// dot products nor the update need a row mask; the four dot products of a
+// warp are summed by one transpose-and-reduce butterfly (10 shuffles instead
+// of 4 x 5 plus broadcast); the residual norms are recomputed from rows
+// j+1..l-1 like the shared-memory kernel's.  Each warp then posts its best
+// column; the CTA's candidate is written to the exchange straight from the
+// registers of the warp that holds it.  Measured on the 210 x 6000 and
+// 200 x 8000 factorizations of the randomized CUR: 0.929 / 0.935 ms against
+// 0.975 / 0.980 ms for the shared-memory kernel (median of 20 launches).
+// Variants that were slower: 8 warps of 8 columns (the per-warp dependency
+// chains stop overlapping), the owner publishing the reflector (a longer
+// publish), reading the best candidate's column while the records come in
+// (longer polling rounds).
+#include "cpqr_exchange.cuh"
+
+namespace curid {
+namespace cpqr_x {
+
+namespace {
+
+constexpr int kCols = 4;                    // columns a warp holds
+constexpr int kMaxRegCols = kWarps * kCols;  // columns of a slab
+
+// Rows a lane can hold for four columns without spilling: 8 per lane in
+// float32, 4 in float64 (128 registers per thread at 512 threads).
+template <typename real>
+constexpr int max_reg_rows() {
+  return sizeof(real) == 4 ? 256 : 128;
+}
+
+// On return lane t holds the warp-wide sum of a_c for c = (t >> 3) & 3:
+// the exchange at offset 16 splits the columns {0,1} / {2,3} between the
+// lane halves, the one at offset 8 splits each pair, and three xor rounds
+// finish each sum inside its group of 8 lanes.
+template <typename real>
+__device__ __forceinline__ real reduce4(real a0, real a1, real a2, real a3, int lane) {
+  const bool hi = (lane & 16) != 0;
+  const real k0 = (hi ? a2 : a0) + __shfl_xor_sync(0xffffffffu, hi ? a0 : a2, 16);
+  const real k1 = (hi ? a3 : a1) + __shfl_xor_sync(0xffffffffu, hi ? a1 : a3, 16);
+  const bool mid = (lane & 8) != 0;
+  real m = (mid ? k1 : k0) + __shfl_xor_sync(0xffffffffu, mid ? k0 : k1, 8);
+  m += __shfl_xor_sync(0xffffffffu, m, 4);
+  m += __shfl_xor_sync(0xffffffffu, m, 2);
+  m += __shfl_xor_sync(0xffffffffu, m, 1);
+  return m;
+}
+
+// (na, ia) beats (nb, ib) among local columns: ib < 0 is no column; larger
+// norm, then smaller index.  A NaN norm never beats a column (the record
+// flags it as non-finite instead).
+template <typename real>
+__device__ __forceinline__ bool local_better(real na, int ia, real nb, int ib) {
+  if (ia < 0) return false;
+  if (ib < 0) return true;
+  if (na > nb) return true;
+  return na == nb && ia < ib;
+}
+
+template <typename real>
+struct WarpBest {
+  real bn[kWarps];
+  real ss[kWarps];
+  int bi[kWarps];
+  int nf[kWarps];
+};
+
+// Each warp, after its residual norms are summed by reduce4 (lane t holds the
+// squared norm of its column (t >> 3) & 3): post the warp's best unselected
+// column, the sum of its squared norms and whether one is not finite.
+template <typename real>
+__device__ __forceinline__ void post_warp_best(real q, unsigned act, int lane, int warp,
+                                               WarpBest<real>& wb) {
+  const int c = (lane >> 3) & 3;
+  const bool on = (act >> c) & 1u;
+  const real nv = sqrt(q);
+  real bn = on ? nv : real(-1);
+  int bi = on ? warp + kWarps * c : -1;
+  real ss = on ? nv * nv : real(0);
+  int nf = on && !isfinite(nv);
+#pragma unroll
+  for (int o = 8; o <= 16; o <<= 1) {
+    const real on2 = __shfl_xor_sync(0xffffffffu, bn, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (local_better(on2, oi, bn, bi)) { bn = on2; bi = oi; }
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    nf |= __shfl_xor_sync(0xffffffffu, nf, o);
+  }
+  if (lane == 0) {
+    wb.bn[warp] = bn;
+    wb.bi[warp] = bi;
+    wb.ss[warp] = ss;
+    wb.nf[warp] = nf;
+  }
+}
+
+// Every warp, after the barrier that follows post_warp_best: the CTA's
+// candidate for epoch `epoch`.  Warp 0 publishes the record in buffer bf; the
+// warp holding the candidate writes its rows r0..l-1 to the CTA's data slot
+// as tagged words (readers check every word's tag, so the two writes need no
+// order between them).
+template <int RPL, typename real>
+__device__ __forceinline__ void publish_reg(const CpqrParams<real>& P, const WarpBest<real>& wb,
+                                            const real (&y)[kCols][RPL], int c0, int r0, int bf,
+                                            unsigned epoch, int lane, int warp) {
+  real bn = lane < kWarps ? wb.bn[lane] : real(-1);
+  int bi = lane < kWarps ? wb.bi[lane] : -1;
+  int nf = lane < kWarps ? wb.nf[lane] : 0;
+#pragma unroll
+  for (int o = 1; o < kWarps; o <<= 1) {
+    const real on = __shfl_xor_sync(0xffffffffu, bn, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (local_better(on, oi, bn, bi)) { bn = on; bi = oi; }
+    nf |= __shfl_xor_sync(0xffffffffu, nf, o);
+  }
+  // lanes 0..15 agree; take lane 0's view everywhere
+  bn = __shfl_sync(0xffffffffu, bn, 0);
+  bi = __shfl_sync(0xffffffffu, bi, 0);
+  nf = __shfl_sync(0xffffffffu, nf, 0);
+  const unsigned tag = tag_of(P.gen, (int)epoch);
+  if (warp == 0) {
+    real ss = lane < kWarps ? wb.ss[lane] : real(0);
+#pragma unroll
+    for (int o = 1; o < kWarps; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) {
+      unsigned hi, lo;
+      norm_words<real>(bi >= 0 ? bn : real(0), &hi, &lo);
+      const unsigned col = nf ? kNonFinite : (bi >= 0 ? (unsigned)(c0 + bi) : kNoCol);
+      st_rec(P.recs + (size_t)bf * gridDim.x + blockIdx.x, pack(tag, col), pack(tag, hi),
+             pack(tag, lo), pack(tag, __float_as_uint((float)ss)));
+    }
+  }
+  if (bi >= 0 && !nf && bi % kWarps == warp) {
+    constexpr int W = Words<real>::W;
+    unsigned long long* dst = slot_of(P, bf, blockIdx.x);
+    const int cb = bi / kWarps;
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) {
+      if (c != cb) continue;
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) {
+        const int r = lane + 32 * u;
+        if (r >= r0 && r < P.l) put_tagged<real>(dst + (int64_t)r * W, tag, y[c][u]);
+      }
+    }
+  }
+}
+
+template <typename real, int RPL>
+__global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = blockIdx.x;
+  const int nc = P.nc, ldl = P.ldl, l = P.l;
+  real* ys = reinterpret_cast<real*>(smem_raw);  // nc x ldl staging: input, then S
+  real* xv = ys + (int64_t)nc * ldl;             // pivot column of the step
+  int* active = reinterpret_cast<int*>(xv + ldl);
+
+  __shared__ StepState<real> st;
+  __shared__ WarpBest<real> wb;
+
+  const int c0 = b * nc;
+  const int ncl = max(0, min(nc, P.n - c0));
+
+  for (int64_t e = tid; e < (int64_t)l * ncl; e += kThreads) {
+    const int r = (int)(e / ncl), lc = (int)(e % ncl);
+    ys[(int64_t)lc * ldl + r] = P.Y[(int64_t)r * P.ldy + c0 + lc];
+  }
+  for (int lc = tid; lc < nc; lc += kThreads) active[lc] = lc < ncl ? 1 : 0;
+  __syncthreads();
+
+  real y[kCols][RPL];
+  unsigned act = 0;  // bit c: column warp + 16 c is unselected (warp-uniform)
+  real q[kCols];
+#pragma unroll
+  for (int c = 0; c < kCols; ++c) {
+    const int lc = warp + kWarps * c;
+    if (lc < ncl) act |= 1u << c;
+    q[c] = real(0);
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) {
+      const int r = lane + 32 * u;
+      y[c][u] = (lc < ncl && r < l) ? ys[(int64_t)lc * ldl + r] : real(0);
+      q[c] += y[c][u] * y[c][u];
+    }
+  }
+  post_warp_best(reduce4(q[0], q[1], q[2], q[3], lane), act, lane, warp, wb);
+  __syncthreads();
+  publish_reg<RPL>(P, wb, y, c0, 0, 0, 1u, lane, warp);
+
+  real normY = real(-1), nu_first = real(0);
+  int k_eff = -1;
+  int j = 0;
+  for (;; ++j) {
+    if (warp == 0) decide_pivot(P, j, normY, st);
+    __syncthreads();
+    if (st.stop) break;
+    const int owner = st.owner, pcol = st.col;
+    const real nu = st.nu;
+    note_rank(P, j, nu, nu_first, k_eff);
+    if (!fetch_pivot<kThreads>(P, j, owner, xv, st)) break;
+    real beta, tau, scale;
+    reflector(xv[j], nu, &beta, &tau, &scale);
+    // v of this lane's rows: 0 above j, 1 at j, scale x(r) below
+    real v[RPL];
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) {
+      const int r = lane + 32 * u;
+      const real x = (r > j && r < l) ? xv[r] : real(0);
+      v[u] = r == j ? real(1) : scale * x;
+    }
+    real d[kCols];
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) {
+      d[c] = real(0);
+      if ((act >> c) & 1u) {
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) d[c] += v[u] * y[c][u];
+      }
+    }
+    const real dsum = reduce4(d[0], d[1], d[2], d[3], lane);
+    // the warp holding the pivot column retires it: beta at row j, zeros below
+    const int pl = pcol - c0;
+    const int pc = (pl >= 0 && pl < ncl && pl % kWarps == warp) ? pl / kWarps : -1;
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) {
+      if (c == pc) {
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+          const int r = lane + 32 * u;
+          if (r >= j) y[c][u] = r == j ? beta : real(0);
+        }
+        act &= ~(1u << c);
+        if (lane == 0) {
+          active[pl] = 0;
+          P.J[j] = pcol;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) {
+      q[c] = real(0);
+      const real w = tau * __shfl_sync(0xffffffffu, dsum, 8 * c);
+      if ((act >> c) & 1u) {
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+          const int r = lane + 32 * u;
+          y[c][u] -= w * v[u];
+          if (r > j) q[c] += y[c][u] * y[c][u];
+        }
+      }
+    }
+    post_warp_best(reduce4(q[0], q[1], q[2], q[3], lane), act, lane, warp, wb);
+    __syncthreads();
+    publish_reg<RPL>(P, wb, y, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2), lane, warp);
+  }
+  const int k_done = j;
+  if (st.stop == 2) return;  // timed out: leave without further waits
+  // S rows 0..k_done-1 in original column order, staged through shared memory
+#pragma unroll
+  for (int c = 0; c < kCols; ++c) {
+    const int lc = warp + kWarps * c;
+    if (lc < ncl) {
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) {
+        const int r = lane + 32 * u;
+        if (r < k_done) ys[(int64_t)lc * ldl + r] = y[c][u];
+      }
+    }
+  }
+  __syncthreads();
+  for (int64_t e = tid; e < (int64_t)k_done * ncl; e += kThreads) {
+    const int i = (int)(e / ncl), lc = (int)(e % ncl);
+    P.S[(int64_t)i * P.lds + c0 + lc] = ys[(int64_t)lc * ldl + i];
+  }
+  finish_order(P, active, ncl, c0, k_done, k_eff, st);
+}
+
+template <typename real>
+size_t reg_smem_bytes(int nc, int ldl) {
+  return (size_t)nc * ldl * sizeof(real) + (size_t)ldl * sizeof(real) + (size_t)nc * sizeof(int) +
+         16;
+}
+
+}  // namespace
+
+template <typename real>
+bool cpqr_reg_fits(const Ctx& ctx, int l, int nc) {
+  // the kernel's static shared variables share the per-block limit
+  return l >= 1 && l <= max_reg_rows<real>() && nc >= 1 && nc <= kMaxRegCols &&
+         reg_smem_bytes<real>(nc, l | 1) + 1024 <= ctx.smem_optin;
+}
+
+template <typename real>
+curid_status cpqr_reg_launch(const Ctx& ctx, const CpqrParams<real>& P, int G) {
+  if (!cpqr_reg_fits<real>(ctx, P.l, P.nc)) return CURID_UNSUPPORTED;
+  const size_t smem = reg_smem_bytes<real>(P.nc, P.ldl);
+  void (*fn)(CpqrParams<real>) = P.l <= 64 ? cpqr_reg_kernel<real, 2> : cpqr_reg_kernel<real, 4>;
+  if constexpr (sizeof(real) == 4) {
+    if (P.l > 128) fn = P.l <= 224 ? cpqr_reg_kernel<real, 7> : cpqr_reg_kernel<real, 8>;
+  }
+  CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CpqrParams<real> Pc = P;
+  void* args[] = {&Pc};
+  CURID_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(G), dim3(kThreads), args, smem,
+                                         ctx.stream));
+  if (ctx.launches) ++*ctx.launches;
+  return CURID_OK;
+}
+
+template bool cpqr_reg_fits<float>(const Ctx&, int, int);
+template bool cpqr_reg_fits<double>(const Ctx&, int, int);
+template curid_status cpqr_reg_launch<float>(const Ctx&, const CpqrParams<float>&, int);
+template curid_status cpqr_reg_launch<double>(const Ctx&, const CpqrParams<double>&, int);
+
+}  // namespace cpqr_x
+}  // namespace curid

@@ -96,6 +96,43 @@ def test_cpqr_adaptive_tolerance():
     assert list(npi(r.J)[:o.k]) == list(o.J[:o.k])
 
 
+@pytest.mark.parametrize("dtype,l,n,k", [(torch.float32, 250, 9728, 60),
+                                         (torch.float32, 200, 5000, 60),
+                                         (torch.float32, 161, 2437, 40),
+                                         (torch.float64, 100, 7600, 40),
+                                         (torch.float64, 128, 9700, 48)])
+def test_cpqr_register_slabs(dtype, l, n, k):
+    """Orders that keep the slab in registers (l <= 256 in float32, <= 128 in
+    float64; up to 64 columns per CTA: 9728 = 64 x 152): 4, 7 and 8 rows per
+    lane, full and ragged slabs.  Planted pivot order exact, S rows as the
+    oracle's."""
+    decay = 0.85 if dtype == torch.float32 else 2 ** -0.5
+    A, perm = syn.planted_pivots(l, n, k, 45 + l, decay=decay, dtype=dtype)
+    r = curid.cpqr(cuda(A), k=k)
+    J = npi(r.J)
+    assert list(J[:k]) == list(perm[:k])
+    assert sorted(J.tolist()) == list(range(n)) and list(J[k:]) == sorted(J[k:].tolist())
+    o = O.cpqr(np64(A), k=k)
+    tol = 1e-11 if dtype == torch.float64 else 2e-5
+    assert_s_rows_match(r.S, s_by_column(o.S1, o.J, n), k, tol)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_cpqr_adaptive_register_slabs(dtype):
+    """Tolerance stop on a register-resident slab (120 x 3000): the rank and
+    pivots of the oracle's stop."""
+    A = syn.spectrum_matrix(120, 3000, syn.exp_decay(120, 6.0), 46, dtype)
+    tol = 1e-6 if dtype == torch.float64 else 1e-3
+    r = curid.cpqr(cuda(A), k=0, tol=tol)
+    o = O.cpqr(np64(A), tol=tol)
+    u = U64 if dtype == torch.float64 else U32
+    if gap_allows_exact(o, o.k, u):
+        assert r.k == o.k
+        assert list(npi(r.J)[:o.k]) == list(o.J[:o.k])
+    else:
+        assert abs(r.k - o.k) <= 1
+
+
 def test_cpqr_ties_smallest_index():
     g = np.random.default_rng(7)
     A = g.standard_normal((64, 300))
