@@ -223,12 +223,21 @@ curid_status a_product(const Ctx& ctx, bool tf32, bool bf16, bool tb, int64_t M,
                     real(0), out, ldo, P.partial, P.partial_cap);
 }
 
-// Row orthonormalisation without pivoting (Section 5.3): three Cholesky-QR
+// Row orthonormalisation without pivoting (Section 5.3) by Cholesky-QR
 // passes (chol_qr_rows), the Gram matrix in the plan's l x l buffer.
+//
+// orth(X) is the Q of X = L Q with L lower triangular, positive diagonal.
+// If a product's input is N Q instead (N lower triangular, positive
+// diagonal), the product N Q B has the same Q factor as Q B, so every orth
+// whose output is multiplied by A and orthonormalised again needs only a
+// well-conditioned N: two passes (condition number 1 + O(u kappa_1^2),
+// kappa_1 <= 1 / sqrt(shift) after the shifted first pass).  The last orth,
+// whose Q forms the Y that is pivoted, takes all three.
 template <typename real>
 curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
-                       const Plan<real>& P) {
-  return chol_qr_rows<real>(ctx, X, tmp, r, c, ld, P.G, P.partial, P.partial_cap);
+                       const Plan<real>& P, bool final_orth) {
+  return chol_qr_rows<real>(ctx, X, tmp, r, c, ld, P.G, P.partial, P.partial_cap,
+                            final_orth ? 3 : 2);
 }
 
 // Sample matrix of Algorithm 4 with the power scheme of Section 5.3:
@@ -254,7 +263,7 @@ curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const 
     real* t = other(cur, nullptr);
     {
       PhaseScope ps(h, CURID_PHASE_ORTH);
-      CURID_TRY(orth_rows<real>(ctx, &cur, &t, l, n, ldy, P));
+      CURID_TRY(orth_rows<real>(ctx, &cur, &t, l, n, ldy, P, false));
     }
     real* z = other(cur, nullptr);
     {
@@ -264,7 +273,7 @@ curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const 
     real* zt = other(z, nullptr);
     {
       PhaseScope ps(h, CURID_PHASE_ORTH);
-      CURID_TRY(orth_rows<real>(ctx, &z, &zt, l, m, ldz, P));
+      CURID_TRY(orth_rows<real>(ctx, &z, &zt, l, m, ldz, P, i == q - 1));
     }
     real* y = other(z, nullptr);
     {

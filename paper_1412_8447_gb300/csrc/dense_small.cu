@@ -242,22 +242,32 @@ chol_kernel(real* __restrict__ G, int l, int64_t ldg, real rel_shift, StatusBloc
   real shift = rel_shift * tr;
   bool done = false;
   for (int attempt = 0; attempt < 4 && !done; ++attempt) {
-    // lower blocks of G + shift I (diagonal blocks whole), identity tail
-    for (int i = warp; i < LP; i += kSmallWarps) {
-      const int bi = i >> 5, r = i & 31;
-      real v[8];
+    // lower blocks of G + shift I (diagonal blocks whole), identity tail;
+    // a warp loads four rows before it stores any, so each thread keeps up
+    // to 32 loads in flight
+    for (int i0 = warp; i0 < LP; i0 += 4 * kSmallWarps) {
+      real v[4][8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int j = 32 * u + lane;
-        v[u] = (u <= bi && i < l && j < l) ? G[(int64_t)i * ldg + j] : real(0);
+      for (int h = 0; h < 4; ++h) {
+        const int i = i0 + h * kSmallWarps, bi = i >> 5;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = 32 * u + lane;
+          v[h][u] = (u <= bi && i < l && j < l) ? G[(int64_t)i * ldg + j] : real(0);
+        }
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int j = 32 * u + lane;
-        if (u <= bi) {
-          real x = (i < l && j < l) ? v[u] : real(0);
-          if (i == j) x += (i < l) ? shift : real(1);
-          chol_block(a, bi, u)[r * LD + lane] = x;
+      for (int h = 0; h < 4; ++h) {
+        const int i = i0 + h * kSmallWarps, bi = i >> 5, r = i & 31;
+        if (i >= LP) continue;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = 32 * u + lane;
+          if (u <= bi) {
+            real x = v[h][u];
+            if (i == j) x += (i < l) ? shift : real(1);
+            chol_block(a, bi, u)[r * LD + lane] = x;
+          }
         }
       }
     }
@@ -494,8 +504,7 @@ curid_status gemm_nt_f64acc(const Ctx& ctx, int64_t M, int64_t N, int64_t K, con
 
 template <typename real>
 curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
-                          real* G, real* partial, size_t partial_cap) {
-  const int passes = 3;
+                          real* G, real* partial, size_t partial_cap, int passes) {
   const double shift = sizeof(real) == 4 ? 1e-5 : 1e-13;
   for (int pass = 0; pass < passes; ++pass) {
     CURID_TRY(gemm<real>(ctx, false, true, r, r, c, real(1), *X, ld, *X, ld, real(0), G, r,
@@ -508,9 +517,9 @@ curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64
 }
 
 template curid_status chol_qr_rows<float>(const Ctx&, float**, float**, int64_t, int64_t, int64_t,
-                                          float*, float*, size_t);
+                                          float*, float*, size_t, int);
 template curid_status chol_qr_rows<double>(const Ctx&, double**, double**, int64_t, int64_t,
-                                           int64_t, double*, double*, size_t);
+                                           int64_t, double*, double*, size_t, int);
 template curid_status gemm_nt_f64acc<float>(const Ctx&, int64_t, int64_t, int64_t, const float*,
                                             int64_t, const float*, int64_t, double*, int64_t);
 template curid_status gemm_nt_f64acc<double>(const Ctx&, int64_t, int64_t, int64_t,

@@ -106,14 +106,17 @@ template <typename real>
 bool tri_solve_fits(const Ctx& ctx, int k);
 template <typename real>
 bool chol_inverse_fits(const Ctx& ctx, int l);
-// Row orthonormalisation without pivoting (Section 5.3) by three Cholesky-QR
+// Row orthonormalisation without pivoting (Section 5.3) by Cholesky-QR
 // passes: G = X X^T, G + shift I = L L^T, X <- L^{-1} X, the first pass
-// shifted (float32: 1e-5 trace(G), float64: 1e-13 trace(G)).  X is r x c
-// with leading dimension ld; each pass writes out of place, and on return *X
-// points at the result and *tmp at the other buffer.  G: r x r scratch.
+// shifted (float32: 1e-5 trace(G), float64: 1e-13 trace(G)).  Three passes
+// give rows orthonormal to working precision; two give a lower-triangular
+// multiple of them with condition number near 1, which is all a product
+// whose result is orthonormalised again needs.  X is r x c with leading
+// dimension ld; each pass writes out of place, and on return *X points at
+// the result and *tmp at the other buffer.  G: r x r scratch.
 template <typename real>
 curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
-                          real* G, real* partial, size_t partial_cap);
+                          real* G, real* partial, size_t partial_cap, int passes = 3);
 // C (float64) = A B^T with float64 accumulation; A M x K, B N x K.
 template <typename real>
 curid_status gemm_nt_f64acc(const Ctx& ctx, int64_t M, int64_t N, int64_t K, const real* A,
