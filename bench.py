@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only-form", choices=["adjoint", "batched", "mixed"], default=None,
+    ap.add_argument("--only-form", choices=["adjoint", "batched", "mixed", "srft"], default=None,
                     help="run only this form's measurement and print its JSON")
     ap.add_argument("--small", action="store_true",
                     help="with --only-form: profiling sizes (256 blocks; BF16 8192^2, q = 1)")
@@ -227,35 +227,30 @@ def run_ours(args, ws, rank, local):
     elapsed_ms = max_over_ranks(elapsed_ms, ws, dev)
     value = args.steps * ws / (elapsed_ms / 1e3)
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step copies
+    # its matrix from pinned host memory and its (J, I, U) back; HostStream
+    # overlaps the copy of matrix i + 1 with the decomposition of matrix i
     e2e = None
     if not args.no_e2e:
         A_host = A.cpu().pin_memory()
-        A2 = torch.empty_like(A)
-        Jh = torch.empty(args.n, dtype=torch.int32).pin_memory()
-        Ih = torch.empty(args.m, dtype=torch.int32).pin_memory()
-        Uh = torch.empty((args.k, args.k), dtype=torch.float64).pin_memory()
         ke = max(3, min(args.steps, 10))
-
-        def e2e_step(i):
-            A2.copy_(A_host, non_blocking=True)
-            step(i, A2)
-            Jh.copy_(out.J, non_blocking=True)
-            Ih.copy_(out.I, non_blocking=True)
-            Uh.copy_(out.U, non_blocking=True)
-
-        e2e_step(0)
+        hs = curid.HostStream(args.m, args.n, args.k, A.dtype, local, p=args.p, q=args.q,
+                              tf32=tf32)
+        res = hs.host_results(ke)
+        seeds = [BASE_SEED * 1000 + 7000 + i for i in range(ke)]
+        hs.run([A_host] * 2, res, seeds)
         torch.cuda.synchronize(dev)
         barrier(ws)
         e0.record(stream)
-        for i in range(ke):
-            e2e_step(i + 1)
+        hs.run([A_host] * ke, res, seeds)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
         e2e = {"value": ke * ws / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": A.numel() * 4,
-               "d2h_bytes_per_step": (args.n + args.m) * 4 + args.k * args.k * 8}
+               "d2h_bytes_per_step": (args.n + args.m) * 4 + args.k * args.k * 8,
+               "how": "HostStream: copy of the next matrix overlapped with the current "
+                      "decomposition (two device buffers, side copy stream)"}
 
     pk, pk_kind = peaks()
     work = phase_work(args, l)
@@ -322,7 +317,7 @@ def run_ours(args, ws, rank, local):
     forms = None
     if rank == 0 and ws == 1 and not args.no_forms:
         forms = {"adjoint": measure_adjoint(dev), "batched": measure_batched(dev),
-                 "mixed": measure_mixed(dev)}
+                 "mixed": measure_mixed(dev), "srft": measure_srft(dev)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -516,6 +511,54 @@ def measure_mixed(dev, steps=3, size=20000, q=None, with_f64=True):
     return res
 
 
+def measure_srft(dev, steps=10, m=M, n=N, k=K):
+    """Accelerated randomized scheme (Section 5.2): the structured Omega of
+    Eq. (5.2) (real form: DCT-II rows with random signs, rows and signs drawn
+    on the device each step), l = 2k, no power step, TF32 product, on the
+    benchmark matrix; against the Gaussian Omega with the same l and q = 0.
+    Errors ||A - CUR||_F / ||A||_F in float64 on the GPU."""
+    import paper_1412_8447_gb300 as curid
+    import synthetic as syn
+    l = 2 * k
+    A = syn.spectrum_matrix(m, n, syn.power_decay(min(m, n)), BASE_SEED, torch.float32, dev)
+    out = curid.cur_outputs(A, k, want_c=True, want_r=True)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def err():
+        Ad = A.double()
+        D = Ad - (out.C.double() @ out.U) @ out.R.double()
+        return float(torch.linalg.norm(D) / torch.linalg.norm(Ad))
+
+    def srft_step(i):
+        rows, signs = curid.srft_draw(m, l, 5000 + i, device=dev.index or 0)
+        Om = curid.srft_omega(rows, signs, torch.float32)
+        curid.cur(A, k, p=l - k, q=0, omega=Om, tf32=True, out=out, check=False)
+
+    def gauss_step(i):
+        curid.cur(A, k, p=l - k, q=0, seed=6000 + i, tf32=True, out=out, check=False)
+
+    res = {"workload": f"randomized CUR-ID, float32 A {m}x{n}, sigma_j = j^-2, k = {k}, "
+                       f"l = 2k = {l}, q = 0, TF32 products",
+           "unit": "decompositions/s"}
+    for name, fn in (("srft", srft_step), ("gaussian_same_l", gauss_step)):
+        for i in range(3):
+            fn(i)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for i in range(steps):
+            fn(10 + i)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        st, _ = curid.last_status(dev.index or 0)
+        res[name] = {"value": 1e3 / ms, "ms_per_step": ms, "status": curid.STATUS_NAMES[st],
+                     "rel_err_fro": err()}
+    del A, out
+    torch.cuda.empty_cache()
+    return res
+
+
 def cpu_baseline(args, A, curid):
     """The FP64 oracle on the host cores, one full decomposition of the same
     workload with the Omega the device drew for seed BASE_SEED*1000."""
@@ -590,6 +633,8 @@ def main():
             r = measure_adjoint(dev)
         elif args.only_form == "batched":
             r = measure_batched(dev, nb=256 if args.small else 4096)
+        elif args.only_form == "srft":
+            r = measure_srft(dev)
         else:
             r = (measure_mixed(dev, steps=1, size=8192, q=1, with_f64=False) if args.small
                  else measure_mixed(dev))

@@ -144,6 +144,38 @@ curid_status curid_gaussian(curid_handle* handle, curid_dtype dtype,
                             int64_t rows, int64_t cols, uint64_t seed,
                             void* out);
 
+/* Structured sampling matrix of the accelerated randomized scheme
+ * (Section 5.2, Eq. (5.2)): Omega = sqrt(m/l) R F D, l x m, written
+ * row-major to device `omega` with leading dimension ldo >= m, dtype
+ * CURID_F32 or CURID_F64 (for BF16 storage of A the sample is float32).
+ * Real form of the paper's complex construction: D = diag(signs) with
+ * signs[t] < 0 read as -1 and anything else as +1 (random signs replace
+ * the unit-circle entries), F is the orthonormal DCT-II,
+ * F(f, t) = c_f cos(pi f (2t+1) / (2m)), c_0 = sqrt(1/m), c_f = sqrt(2/m),
+ * and R keeps the rows listed in `rows` (l entries, frequencies in [0, m),
+ * drawn without replacement by the caller; other values give rows of the
+ * periodic extension of F).  rows (int32, [l]) and signs (int8, [m]) are
+ * device memory owned by the caller; nothing is allocated.  The result is
+ * passed to the decompositions as curid_sketch.omega with p = l - k
+ * (l = 2k suffices in practice, Section 5.2).  Errors: INVALID_ARG for
+ * null pointers, m < 1, l < 1 or ldo < m; UNSUPPORTED for m > about 900000
+ * (angle tables in shared memory) or another dtype. */
+curid_status curid_srft_omega(curid_handle* handle, curid_dtype dtype,
+                              int64_t m, int64_t l, const int32_t* rows,
+                              const int8_t* signs, void* omega, int64_t ldo);
+
+/* The random choices of Eq. (5.2) drawn on the device from `seed`: signs
+ * (int8, [m], each -1 or +1) for D and rows (int32, [l]) for R, l distinct
+ * values in [0, m) ("drawn randomly without replacement").  Signs come from
+ * Philox4x32-10 (top bit of word t % 4 at counter (t / 4, 0, 1, 0), key as
+ * in curid_gaussian); rows[i] = pi(i) for the permutation pi of [0, m) given
+ * by a four-round Feistel network with a Philox round function, restricted
+ * to [0, m) by cycle walking.  Device buffers owned by the caller; nothing
+ * is allocated.  INVALID_ARG for null pointers, m < 1, l < 1 or l > m;
+ * UNSUPPORTED for m > 2^30. */
+curid_status curid_srft_draw(curid_handle* handle, int64_t m, int64_t l,
+                             uint64_t seed, int32_t* rows, int8_t* signs);
+
 /* Sample matrix Y = Omega A (A^* A)^q (Eq. (5.1); Section 5.3 with orth):
  * A m x n (lda), omega l x m (leading dimension m, device, required),
  * Y l x n written with leading dimension n.  With CURID_BF16, A is

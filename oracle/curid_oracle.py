@@ -24,7 +24,7 @@ __all__ = [
     "as_f64", "CPQR", "cpqr", "interpolation_matrix", "vstar", "wmat",
     "IDResult", "id_col", "id_row", "TSIDResult", "tsid", "CURResult",
     "cur_middle", "cur", "orth_rows", "sketch", "randomized_id_col",
-    "randomized_cur", "rel_err_fro", "OK", "RANK_DEFICIENT",
+    "randomized_cur", "srft_sketch", "srft_omega_rows", "rel_err_fro", "OK", "RANK_DEFICIENT",
     "rank_threshold",
 ]
 
@@ -312,6 +312,42 @@ def randomized_cur(A, Omega, k, q=0, orth=True,
     """CUR-ID (Algorithm 3) with its column ID taken from Algorithm 4."""
     Y = sketch(A, Omega, q=q, orth=orth)
     return cur(A, k=k, Y=Y, eps=eps), Y
+
+
+def srft_sketch(A, rows, signs):
+    """Structured sample matrix of Section 5.2, Eq. (5.2), applied to A:
+    Y = sqrt(m / l) R F D A with D = diag(signs), F the m x m orthonormal
+    transform and R the l sampled rows ``rows`` (0-based, drawn without
+    replacement).  Real reading of the paper's complex construction: the
+    unit-circle entries of D become random signs +-1 and the unitary DFT
+    becomes the orthonormal DCT-II, F(f, t) = c_f cos(pi f (2t + 1) / (2m)),
+    c_0 = sqrt(1/m), c_f = sqrt(2/m) -- real, orthogonal, any m.  The
+    transform is scipy's DCT along the columns (a library primitive used as
+    one step), then row selection and scaling, in the order of Eq. (5.2)."""
+    import scipy.fft
+    A = as_f64(A)
+    m = A.shape[0]
+    rows = np.asarray(rows, dtype=np.int64)
+    d = np.asarray(signs, dtype=np.float64)
+    FDA = scipy.fft.dct(d[:, None] * A, type=2, norm="ortho", axis=0)
+    return np.sqrt(m / len(rows)) * FDA[rows, :]
+
+
+def srft_omega_rows(m, rows, signs, which=None):
+    """Rows ``which`` (default all) of the l x m matrix Omega of Eq. (5.2)
+    under the reading of ``srft_sketch``: row i is sqrt(m/l) times row
+    rows[i] of F, times the signs.  Row f of an orthogonal F equals F^T
+    applied to e_f, i.e. the inverse transform (orthonormal DCT-III) of e_f."""
+    import scipy.fft
+    rows = np.asarray(rows, dtype=np.int64)
+    d = np.asarray(signs, dtype=np.float64)
+    idx = range(len(rows)) if which is None else which
+    out = []
+    for i in idx:
+        e = np.zeros(m)
+        e[rows[i]] = 1.0
+        out.append(np.sqrt(m / len(rows)) * scipy.fft.idct(e, type=2, norm="ortho") * d)
+    return np.array(out)
 
 
 def rel_err_fro(A, C, U, R):

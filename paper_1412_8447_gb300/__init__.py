@@ -5,7 +5,7 @@ The computation lives in ``libcurid.so`` (hand-written CUDA kernels behind the
 C ABI of ``include/curid.h``); this package is its thin Python binding.
 """
 from ._binding import (  # noqa: F401
-    BatchedID, CURFunction, CuridError, LIB_PATH, PHASES, Result, STATUS_NAMES, cpqr, cur, cur_adjoint,
-    cur_differentiable, cur_outputs, gaussian, id_col, id_row, last_status, load_library, profile,
-    profile_read, sketch_matrix, tsid,
+    BatchedID, CURFunction, CuridError, HostStream, LIB_PATH, PHASES, Result, STATUS_NAMES, cpqr,
+    cur, cur_adjoint, cur_differentiable, cur_outputs, gaussian, id_col, id_row, last_status,
+    load_library, profile, profile_read, sketch_matrix, srft_draw, srft_omega, tsid,
 )

@@ -46,6 +46,8 @@ SIGNATURES = {
     "curid_profile_read": [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_int),
                            ctypes.POINTER(ctypes.c_longlong)],
     "curid_gaussian": [_vp, _int, _i64, _i64, ctypes.c_uint64, _vp],
+    "curid_srft_omega": [_vp, _int, _i64, _i64, _vp, _vp, _vp, _i64],
+    "curid_srft_draw": [_vp, _i64, _i64, ctypes.c_uint64, _vp, _vp],
     "curid_sketch_matrix": [_vp, _int, _vp, _i64, _i64, _i64, _int, _int, _int, _vp, _vp],
     "curid_cpqr": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, _vp, _vp],
     "curid_cpqr_static": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, _vp, _vp, _vp],
@@ -240,6 +242,38 @@ def gaussian(rows, cols, seed, dtype=torch.float32, device=None):
     out = torch.empty((rows, cols), dtype=dtype, device=f"cuda:{device}")
     _check(h.lib.curid_gaussian(h.h, _dtype_code(dtype), rows, cols, int(seed) & ((1 << 64) - 1),
                                 _ptr(out)), "curid_gaussian")
+    return out
+
+
+def srft_draw(m, l, seed, device=None):
+    """Random signs (int8, [m]) and l distinct rows (int32, [l]) of the
+    structured sampling matrix of Section 5.2, drawn on the device from
+    ``seed`` (curid_srft_draw)."""
+    dev = device if device is not None else torch.cuda.current_device()
+    h = handle(dev)
+    h.prepare(0)
+    rows = torch.empty(l, dtype=torch.int32, device=f"cuda:{dev}")
+    signs = torch.empty(m, dtype=torch.int8, device=f"cuda:{dev}")
+    _check(h.lib.curid_srft_draw(h.h, int(m), int(l), int(seed) & ((1 << 64) - 1), _ptr(rows),
+                                 _ptr(signs)), "curid_srft_draw")
+    return rows, signs
+
+
+def srft_omega(rows, signs, dtype=torch.float32):
+    """Omega = sqrt(m/l) R F D of Eq. (5.2) (real form: DCT-II and random
+    signs), l x m, from device ``rows`` (int32) and ``signs`` (int8)
+    (curid_srft_omega).  Pass it as ``omega`` with p = l - k and q = 0 for
+    the accelerated scheme."""
+    if rows.dtype != torch.int32 or signs.dtype != torch.int8:
+        raise ValueError("rows must be int32 and signs int8")
+    rows, signs = rows.contiguous(), signs.contiguous()
+    dev = _dev(rows)
+    h = handle(dev)
+    h.prepare(0)
+    l, m = rows.numel(), signs.numel()
+    out = torch.empty((l, m), dtype=dtype, device=rows.device)
+    _check(h.lib.curid_srft_omega(h.h, _dtype_code(out.dtype), m, l, _ptr(rows), _ptr(signs),
+                                  _ptr(out), m), "curid_srft_omega")
     return out
 
 
@@ -548,3 +582,76 @@ class BatchedID:
             T = self.Tflat[self.toff[b]:self.toff[b] + self.k_max * nb_].view(self.k_max, nb_)
             out.append((J, T[:k[b], :nb_ - k[b]], k[b], st[b]))
         return out
+
+
+class HostStream:
+    """CUR-IDs of a sequence of host matrices, each copied to the device and
+    its skeletons and U copied back, with the host-to-device copy of matrix
+    i + 1 overlapped with the decomposition of matrix i.
+
+    Two device buffers for A and two output sets alternate; the copies of A
+    run on a side stream, each waiting until the decomposition that last read
+    its buffer has finished; the decompositions and the copies of (J, I, U)
+    back to the host run on the current stream.  Host matrices should be
+    pinned (``tensor.pin_memory()``) so the copies are asynchronous.  Only
+    stream and event bookkeeping happens here: every step of each
+    decomposition is the same library call ``cur`` makes.
+    """
+
+    def __init__(self, m, n, k, dtype=torch.float32, device=None, p=-1, q=0, tf32=False):
+        dev = torch.device("cuda", device if device is not None else torch.cuda.current_device())
+        self.device, self.k, self.p, self.q, self.tf32 = dev, int(k), int(p), int(q), bool(tf32)
+        self.A = [torch.empty((m, n), dtype=dtype, device=dev) for _ in range(2)]
+        self.out = [cur_outputs(self.A[s], k) for s in range(2)]
+        self.copy_stream = torch.cuda.Stream(dev)
+        self.ready = [torch.cuda.Event() for _ in range(2)]
+        self.free = [torch.cuda.Event() for _ in range(2)]
+
+    def host_results(self, count):
+        """Pinned host buffers (J, I, U) for ``count`` decompositions."""
+        m, n = self.A[0].shape
+        k = self.k
+        return [(torch.empty(n, dtype=torch.int32).pin_memory(),
+                 torch.empty(m, dtype=torch.int32).pin_memory(),
+                 torch.empty((k, k), dtype=torch.float64).pin_memory()) for _ in range(count)]
+
+    def run(self, A_hosts, results, seeds=None):
+        """Decompose every matrix of ``A_hosts`` (host tensors of the stream's
+        shape and dtype) into ``results[i] = (J, I, U)`` host tensors.  Work is
+        queued on the current stream and returns before it finishes;
+        synchronize before reading ``results``.  Device status is not checked
+        (read it with ``last_status``)."""
+        cur_s = torch.cuda.current_stream(self.device)
+        count = len(A_hosts)
+        if len(results) < count:
+            raise ValueError("one (J, I, U) result triple per matrix is needed")
+        # no copy may start before work already queued on the current stream
+        self.copy_stream.wait_stream(cur_s)
+        first = [True, True]
+
+        def copy_in(i):
+            s = i & 1
+            with torch.cuda.stream(self.copy_stream):
+                if not first[s]:
+                    self.copy_stream.wait_event(self.free[s])
+                first[s] = False
+                self.A[s].copy_(A_hosts[i], non_blocking=True)
+                self.ready[s].record(self.copy_stream)
+
+        if count:
+            copy_in(0)
+        for i in range(count):
+            s = i & 1
+            if i + 1 < count:
+                copy_in(i + 1)
+            cur_s.wait_event(self.ready[s])
+            seed = seeds[i] if seeds is not None else i
+            cur(self.A[s], self.k, p=self.p, q=self.q, seed=seed, tf32=self.tf32,
+                out=self.out[s], check=False)
+            self.free[s].record(cur_s)
+            J, I, U = results[i]
+            J.copy_(self.out[s].J, non_blocking=True)
+            I.copy_(self.out[s].I, non_blocking=True)
+            U.copy_(self.out[s].U, non_blocking=True)
+        # the A buffers must not be reused by a later run before these copies
+        cur_s.wait_stream(self.copy_stream)

@@ -215,9 +215,17 @@ curid_status a_product(const Ctx& ctx, bool tf32, bool bf16, bool tb, int64_t M,
   if constexpr (sizeof(real) == 4) {
     if (bf16)
       return gemm_bf16(ctx, tb, M, N, K, X, ldx, A, lda, out, ldo, P.xsplit, P.xsplit_elems);
-    if (tf32)
-      return gemm_tf32(ctx, false, tb, M, N, K, X, ldx, static_cast<const real*>(A), lda, out,
-                       ldo, P.partial, P.partial_cap);
+    if (tf32) {
+      // the sample is the MMA's N (<= 256): larger samples run in row chunks
+      // of equal size (multiples of 16), each reading A once
+      const int64_t chunks = (M + 255) / 256;
+      const int64_t rows = ((M + chunks - 1) / chunks + 15) / 16 * 16;
+      for (int64_t r0 = 0; r0 < M; r0 += rows)
+        CURID_TRY(gemm_tf32(ctx, false, tb, std::min(rows, M - r0), N, K, X + r0 * ldx, ldx,
+                            static_cast<const real*>(A), lda, out + r0 * ldo, ldo, P.partial,
+                            P.partial_cap));
+      return CURID_OK;
+    }
   }
   return gemm<real>(ctx, false, tb, M, N, K, real(1), X, ldx, static_cast<const real*>(A), lda,
                     real(0), out, ldo, P.partial, P.partial_cap);
@@ -707,6 +715,32 @@ curid_status curid_gaussian(curid_handle* handle, curid_dtype dtype, int64_t row
       return gaussian_fill<double>(ctx, rows, cols, seed, (double*)out, cols);
     if (dtype == CURID_F32) return gaussian_fill<float>(ctx, rows, cols, seed, (float*)out, cols);
     return CURID_INVALID_ARG;
+  });
+}
+
+curid_status curid_srft_omega(curid_handle* handle, curid_dtype dtype, int64_t m, int64_t l,
+                              const int32_t* rows, const int8_t* signs, void* omega,
+                              int64_t ldo) {
+  if (!handle || !rows || !signs || !omega || m < 1 || l < 1 || ldo < m)
+    return CURID_INVALID_ARG;
+  return dispatch(handle, [&]() -> curid_status {
+    Ctx ctx = make_ctx(handle);
+    PhaseScope ps(handle, CURID_PHASE_OMEGA);
+    if (dtype == CURID_F64)
+      return srft_fill<double>(ctx, m, l, rows, signs, static_cast<double*>(omega), ldo);
+    if (dtype == CURID_F32)
+      return srft_fill<float>(ctx, m, l, rows, signs, static_cast<float*>(omega), ldo);
+    return CURID_UNSUPPORTED;
+  });
+}
+
+curid_status curid_srft_draw(curid_handle* handle, int64_t m, int64_t l, uint64_t seed,
+                             int32_t* rows, int8_t* signs) {
+  if (!handle || !rows || !signs || m < 1 || l < 1 || l > m) return CURID_INVALID_ARG;
+  return dispatch(handle, [&]() -> curid_status {
+    Ctx ctx = make_ctx(handle);
+    PhaseScope ps(handle, CURID_PHASE_OMEGA);
+    return srft_draw(ctx, m, l, seed, rows, signs);
   });
 }
 

@@ -161,4 +161,14 @@ template <typename real>
 curid_status gaussian_fill(const Ctx& ctx, int64_t rows, int64_t cols, uint64_t seed, real* out,
                            int64_t ld);
 
+// ---- structured sampling matrix (srft.cu) -------------------------------------
+// Omega = sqrt(m/l) R F D of Eq. (5.2), real form (DCT-II, sign flips), l x m
+// into out (leading dimension ld >= m) from the l sampled rows and m signs.
+// Its random choices from a seed (philox.cu): m signs, l distinct rows in [0, m).
+curid_status srft_draw(const Ctx& ctx, int64_t m, int64_t l, uint64_t seed, int32_t* rows,
+                       int8_t* signs);
+template <typename real>
+curid_status srft_fill(const Ctx& ctx, int64_t m, int64_t l, const int32_t* rows,
+                       const int8_t* signs, real* out, int64_t ld);
+
 }  // namespace curid

@@ -63,7 +63,68 @@ __global__ void gaussian_kernel(int64_t total, int64_t cols, int64_t ld, uint2 k
   }
 }
 
+// Random choices of the structured sampling matrix (Section 5.2, Eq. (5.2)):
+// the m signs of D and the l rows R keeps, drawn without replacement.
+// Sign t: top bit of word t % 4 of Philox4x32-10 at counter (t / 4, 0, 1, 0)
+// (third counter word 1: a stream apart from the Gaussian generator's).
+// Rows: rows[i] = pi(i) for a pseudo-random permutation pi of [0, m): a
+// four-round balanced Feistel network on 2h-bit values (2^(2h) >= m) whose
+// round function is Philox at counter (half-word, round, 2, 0), restricted to
+// [0, m) by cycle walking (Black and Rogaway, "Ciphers with arbitrary finite
+// domains", CT-RSA 2002): apply the network until the value falls below m.
+// Distinct i give distinct rows because the restriction is itself a
+// permutation.
+__device__ __forceinline__ unsigned feistel(unsigned x, int h, uint2 key) {
+  const unsigned mask = (1u << h) - 1u;
+  unsigned L = x >> h, R = x & mask;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const unsigned F = philox4x32_10(make_uint4(R, (unsigned)r, 2u, 0u), key).x & mask;
+    const unsigned nl = R;
+    R = L ^ F;
+    L = nl;
+  }
+  return (L << h) | R;
+}
+
+__global__ void srft_draw_kernel(int64_t m, int64_t l, int h, uint2 key, int32_t* __restrict__ rows,
+                                 int8_t* __restrict__ signs) {
+  const int64_t span = 1LL << (2 * h);  // the network's domain, < 4m
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m || e < l;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < m) {
+      const uint4 w = philox4x32_10(
+          make_uint4((unsigned)(e >> 2), (unsigned)(e >> 34), 1u, 0u), key);
+      const unsigned word = (e & 3) == 0 ? w.x : (e & 3) == 1 ? w.y : (e & 3) == 2 ? w.z : w.w;
+      signs[e] = (word >> 31) ? (int8_t)-1 : (int8_t)1;
+    }
+    if (e < l) {
+      unsigned y = (unsigned)e;
+      // at most span - m values >= m follow one another on a cycle
+      for (int64_t it = 0; it <= span; ++it) {
+        y = feistel(y, h, key);
+        if ((int64_t)y < m) break;
+      }
+      rows[e] = (int32_t)y;
+    }
+  }
+}
+
 }  // namespace
+
+curid_status srft_draw(const Ctx& ctx, int64_t m, int64_t l, uint64_t seed, int32_t* rows,
+                       int8_t* signs) {
+  if (m <= 0 || l <= 0) return CURID_OK;
+  if (l > m || m > (1LL << 30)) return CURID_UNSUPPORTED;
+  int h = 1;
+  while ((1LL << (2 * h)) < m) ++h;
+  const uint2 key = make_uint2((unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32));
+  const unsigned blocks = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((m + 255) / 256, 16LL * ctx.num_sms));
+  srft_draw_kernel<<<blocks, 256, 0, ctx.stream>>>(m, l, h, key, rows, signs);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
 
 template <typename real>
 curid_status gaussian_fill(const Ctx& ctx, int64_t rows, int64_t cols, uint64_t seed, real* out,

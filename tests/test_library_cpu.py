@@ -52,6 +52,8 @@ def test_null_handle_rejected_on_host(lib):
                          None, 0, None, 0) == B.INVALID_ARG
     b = ctypes.c_size_t(0)
     assert lib.curid_workspace_size(None, 0, 10, 10, 2, sk, ctypes.byref(b)) == B.INVALID_ARG
+    assert lib.curid_srft_omega(None, 1, 10, 4, vp(1), vp(1), vp(1), 10) == B.INVALID_ARG
+    assert lib.curid_srft_draw(None, 10, 4, 1, vp(1), vp(1)) == B.INVALID_ARG
 
 
 def test_philox_known_answers():

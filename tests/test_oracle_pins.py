@@ -287,3 +287,73 @@ def test_exhaustive_best_subset():
     e = fro(A - A[:, r.J[:k]] @ O.vstar(r.J, r.T, 9))
     assert best <= e * (1 + 1e-12)
     assert e <= 3 * best
+
+
+# --- structured sampling matrix (Section 5.2, Eq. (5.2)) ----------------------
+
+def _srft_draw(m, l, seed):
+    rng = np.random.default_rng(seed)
+    return rng.choice(m, l, replace=False), rng.choice([-1.0, 1.0], m)
+
+
+@pytest.mark.parametrize("m,l", [(37, 9), (64, 64), (1000, 80), (997, 250)])
+def test_srft_rows_orthogonal(m, l):
+    """R F D has orthonormal rows (F orthogonal, D a sign matrix, R a row
+    selection without replacement), so Omega Omega^T = (m / l) I."""
+    rows, signs = _srft_draw(m, l, m + l)
+    Om = O.srft_omega_rows(m, rows, signs)
+    np.testing.assert_allclose(Om @ Om.T, (m / l) * np.eye(l), atol=1e-12 * m / l, rtol=0)
+
+
+@pytest.mark.parametrize("m", [7, 12, 501])
+def test_srft_cosine_closed_form(m):
+    """Discrete orthogonality of cosines: for g_t = cos(pi f0 (2t+1) / (2m)),
+    sum_t g_t cos(pi f (2t+1) / (2m)) = (m/2) delta_{f f0} for f0 > 0 and
+    m delta_{f 0} for f0 = 0.  Fed x = D g (so D x = g), the sketch is
+    sqrt(m/l) c_{f0} (m/2 or m) at the row that samples f0 and zero
+    elsewhere: sqrt(m/l) sqrt(m/2) or sqrt(m/l) sqrt(m)."""
+    l = min(m, 5)
+    rng = np.random.default_rng(m)
+    signs = rng.choice([-1.0, 1.0], m)
+    t = np.arange(m)
+    for f0 in (0, 1, m // 2, m - 1):
+        rows = np.array([f0] + [f for f in rng.permutation(m) if f != f0][: l - 1])
+        g = np.cos(np.pi * f0 * (2 * t + 1) / (2 * m))
+        Y = O.srft_sketch((signs * g)[:, None], rows, signs)[:, 0]
+        expect = np.zeros(l)
+        expect[0] = np.sqrt(m / l) * (np.sqrt(m) if f0 == 0 else np.sqrt(m / 2))
+        np.testing.assert_allclose(Y, expect, atol=1e-12 * np.sqrt(m), rtol=0)
+
+
+def test_srft_library_convention_matches_definition():
+    """scipy's orthonormal DCT-II (the library step the oracle uses) against
+    the transform as defined, F(f, t) = c_f cos(pi f (2t+1) / (2m)), built
+    entry by entry on a small m."""
+    import scipy.fft
+    m = 11
+    f, t = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    F = np.where(f == 0, np.sqrt(1 / m), np.sqrt(2 / m)) * np.cos(np.pi * f * (2 * t + 1) / (2 * m))
+    X = np.random.default_rng(3).standard_normal((m, 4))
+    np.testing.assert_allclose(scipy.fft.dct(X, type=2, norm="ortho", axis=0), F @ X,
+                               atol=1e-13, rtol=0)
+
+
+def test_srft_sketch_equals_omega_times_a():
+    m, n, l = 300, 40, 24
+    rows, signs = _srft_draw(m, l, 11)
+    A = np.random.default_rng(12).standard_normal((m, n))
+    np.testing.assert_allclose(O.srft_sketch(A, rows, signs),
+                               O.srft_omega_rows(m, rows, signs) @ A, atol=1e-12, rtol=0)
+
+
+def test_srft_randomized_exact_rank():
+    """Algorithm 4 with the structured Omega (l = 2k) recovers an exact
+    rank-k matrix to rounding (any sketch whose rows span A's row space)."""
+    m, n, k = 400, 300, 20
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((m, k)) @ rng.standard_normal((k, n))
+    rows, signs = _srft_draw(m, 2 * k, 22)
+    Om = O.srft_omega_rows(m, rows, signs)
+    o, Y = O.randomized_cur(A, Om, k)
+    np.testing.assert_allclose(Y, O.srft_sketch(A, rows, signs), atol=1e-10, rtol=0)
+    assert O.rel_err_fro(A, o.C, o.U, o.R) <= 1e-12
