@@ -515,8 +515,9 @@ def measure_srft(dev, steps=10, m=M, n=N, k=K):
     """Accelerated randomized scheme (Section 5.2): the structured Omega of
     Eq. (5.2) (real form: DCT-II rows with random signs, rows and signs drawn
     on the device each step), l = 2k, no power step, TF32 product, on the
-    benchmark matrix; against the Gaussian Omega with the same l and q = 0.
-    Errors ||A - CUR||_F / ||A||_F in float64 on the GPU."""
+    benchmark matrix, with U = V* R^+ and with the error-corrected U of
+    Eq. (4.3); against the Gaussian Omega with the same l and q = 0.  Errors
+    ||A - CUR||_F / ||A||_F in float64 on the GPU."""
     import paper_1412_8447_gb300 as curid
     import synthetic as syn
     l = 2 * k
@@ -535,13 +536,20 @@ def measure_srft(dev, steps=10, m=M, n=N, k=K):
         Om = curid.srft_omega(rows, signs, torch.float32)
         curid.cur(A, k, p=l - k, q=0, omega=Om, tf32=True, out=out, check=False)
 
+    def srft_corrected_step(i):
+        rows, signs = curid.srft_draw(m, l, 5000 + i, device=dev.index or 0)
+        Om = curid.srft_omega(rows, signs, torch.float32)
+        curid.cur(A, k, p=l - k, q=0, omega=Om, tf32=True, out=out, check=False,
+                  corrected=True)
+
     def gauss_step(i):
         curid.cur(A, k, p=l - k, q=0, seed=6000 + i, tf32=True, out=out, check=False)
 
     res = {"workload": f"randomized CUR-ID, float32 A {m}x{n}, sigma_j = j^-2, k = {k}, "
                        f"l = 2k = {l}, q = 0, TF32 products",
            "unit": "decompositions/s"}
-    for name, fn in (("srft", srft_step), ("gaussian_same_l", gauss_step)):
+    for name, fn in (("srft", srft_step), ("srft_corrected_u", srft_corrected_step),
+                     ("gaussian_same_l", gauss_step)):
         for i in range(3):
             fn(i)
         torch.cuda.synchronize(dev)

@@ -286,6 +286,24 @@ curid_status curid_cur(curid_handle* handle, curid_dtype dtype,
                        int32_t* I, double* U, void* C, void* R, void* T,
                        int64_t ldt, void* TW, int64_t ldtw);
 
+/* CUR-ID with U from the error-corrected system of Section 4.3, Eq. (4.3):
+ * A = C V* + E gives U R = V* + C^+ E, whose least-squares solution is
+ * U = C^+ A R^+ (the U that minimises ||A - C U R||_F for the chosen C and
+ * R).  With the deterministic column ID (p < 0) C^+ E = 0 (E lies in the
+ * complement of range(C)) and U equals curid_cur's up to rounding; with a
+ * sketch (p >= 0), especially without power steps, it is more accurate.
+ * Cost over curid_cur: three Cholesky-QR passes over C^T (C^T = L Q_C), one
+ * more product with A (Q_C A, on the tensor cores when tf32 is set) and
+ * k x k work; C^+ = K^{-1} Q_C with K = Q_C C solved as upper triangular.
+ * Arguments, outputs, statuses and workspace exactly as curid_cur
+ * (curid_workspace_size covers both). */
+curid_status curid_cur_corrected(curid_handle* handle, curid_dtype dtype,
+                                 const void* A, int64_t m, int64_t n,
+                                 int64_t lda, int k, double tol,
+                                 curid_sketch sk, int32_t* J, int32_t* I,
+                                 double* U, void* C, void* R, void* T,
+                                 int64_t ldt, void* TW, int64_t ldtw);
+
 /* ----- adjoint with frozen skeletons ----------------------------------- */
 
 /* Reverse-mode derivative of the deterministic CUR-ID (p < 0) with the index

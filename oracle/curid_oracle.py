@@ -23,7 +23,8 @@ import scipy.linalg
 __all__ = [
     "as_f64", "CPQR", "cpqr", "interpolation_matrix", "vstar", "wmat",
     "IDResult", "id_col", "id_row", "TSIDResult", "tsid", "CURResult",
-    "cur_middle", "cur", "orth_rows", "sketch", "randomized_id_col",
+    "cur_middle", "cur", "cur_middle_corrected", "cur_corrected", "randomized_cur_corrected",
+    "orth_rows", "sketch", "randomized_id_col",
     "randomized_cur", "srft_sketch", "srft_omega_rows", "rel_err_fro", "OK", "RANK_DEFICIENT",
     "rank_threshold",
 ]
@@ -274,6 +275,35 @@ def cur(A, k=None, tol=None, Y=None, eps=np.finfo(np.float64).eps):
     U = cur_middle(R, vstar(ts.J, ts.T, n))
     return CURResult(J=ts.J, I=ts.I, T=ts.T, TW=ts.TW, U=U, C=C, R=R, k=kk,
                      ts=ts, status=ts.status)
+
+
+def cur_middle_corrected(A, C, R, Vs):
+    """U from the error-corrected system of Section 4.3, Eq. (4.3): with
+    E = A - C V* (the column ID's error), solve U R = V* + C^+ E in the
+    least-squares sense.  C^+ E is the least-squares solution of C X = E
+    (Householder QR of C), and the system for U is solved like Eq. (4.2)
+    (``cur_middle``)."""
+    A, C = as_f64(A), as_f64(C)
+    Vs = np.asarray(Vs, dtype=np.float64)
+    E = A - C @ Vs
+    Qc, Sc = np.linalg.qr(C)
+    CpE = scipy.linalg.solve_triangular(Sc, Qc.T @ E, lower=False)
+    return cur_middle(R, Vs + CpE)
+
+
+def cur_corrected(A, k=None, tol=None, Y=None, eps=np.finfo(np.float64).eps):
+    """Algorithm 3 with U from Eq. (4.3) instead of Eq. (4.2)."""
+    A = as_f64(A)
+    r = cur(A, k=k, tol=tol, Y=Y, eps=eps)
+    U = cur_middle_corrected(A, r.C, r.R, vstar(r.J, r.T, A.shape[1]))
+    return CURResult(J=r.J, I=r.I, T=r.T, TW=r.TW, U=U, C=r.C, R=r.R, k=r.k, ts=r.ts,
+                     status=r.status)
+
+
+def randomized_cur_corrected(A, Omega, k, q=0, orth=True, eps=np.finfo(np.float64).eps):
+    """CUR-ID with its column ID from Algorithm 4 and U from Eq. (4.3)."""
+    Y = sketch(A, Omega, q=q, orth=orth)
+    return cur_corrected(A, k=k, Y=Y, eps=eps), Y
 
 
 def orth_rows(Y):

@@ -57,6 +57,8 @@ SIGNATURES = {
                    _vp, _i64],
     "curid_cur": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _vp, _vp, _vp,
                   _vp, _i64, _vp, _i64],
+    "curid_cur_corrected": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _vp,
+                            _vp, _vp, _vp, _i64, _vp, _i64],
     "curid_cur_adjoint_workspace_size": [_vp, _int, _i64, _i64, _int,
                                          ctypes.POINTER(ctypes.c_size_t)],
     "curid_id_col_batched_workspace_size": [_vp, _int, _int, _int, _int,
@@ -402,10 +404,11 @@ def cur_outputs(A, k, want_c=False, want_r=False, want_t=False, want_tw=False):
 
 
 def cur(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, want_c=False, want_r=False,
-        want_t=False, want_tw=False, out=None, check=True, tol=0.0):
+        want_t=False, want_tw=False, out=None, check=True, tol=0.0, corrected=False):
     """CUR-ID A ~ C U R (Algorithm 3); U is float64 (k x k).  k == 0 with
     tol > 0: adaptive rank (deterministic method); outputs are views at the
-    rank reached (res.k)."""
+    rank reached (res.k).  corrected=True: U from the error-corrected system
+    of Eq. (4.3), U = C^+ A R^+ (curid_cur_corrected)."""
     adaptive = _adaptive(k, tol, p)
     A, h, m, n, dt, sk = _prep(A, k, p, q, seed, omega, tf32)
     kb = min(m, n) if adaptive else k
@@ -422,10 +425,11 @@ def cur(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, want_c=False, want_r=Fa
             if want_tw else None)
     else:
         o = out if out is not None else cur_outputs(A, k, want_c, want_r, want_t, want_tw)
-    st = h.lib.curid_cur(h.h, dt, _ptr(A), m, n, A.stride(0), k, float(tol), sk, _ptr(o.J),
-                         _ptr(o.I), _ptr(o.U), _ptr(o.C), _ptr(o.R), _ptr(o.T),
-                         o.T.stride(0) if o.T is not None else 0, _ptr(o.TW),
-                         o.TW.stride(0) if o.TW is not None else 0)
+    fn = h.lib.curid_cur_corrected if corrected else h.lib.curid_cur
+    st = fn(h.h, dt, _ptr(A), m, n, A.stride(0), k, float(tol), sk, _ptr(o.J),
+            _ptr(o.I), _ptr(o.U), _ptr(o.C), _ptr(o.R), _ptr(o.T),
+            o.T.stride(0) if o.T is not None else 0, _ptr(o.TW),
+            o.TW.stride(0) if o.TW is not None else 0)
     _check(st, "curid_cur")
     res = _finish(h, o, check or adaptive, "curid_cur")
     if adaptive:

@@ -11,7 +11,8 @@ using namespace curid;
 
 namespace {
 
-enum class Op { IdCol, Tsid, Cur };
+// CurCorrected: CUR-ID with U from the error-corrected system of Eq. (4.3)
+enum class Op { IdCol, Tsid, Cur, CurCorrected };
 
 struct DeviceGuard {
   int prev = -1;
@@ -97,6 +98,12 @@ struct Plan {
   real* Qres = nullptr;   // k x (n - k)
   real* M = nullptr;      // k x k
   real* Uh = nullptr;     // k x k
+  // error-corrected U (Eq. (4.3)): Q_C with C^T = L Q_C, K = Q_C C, Q_C A
+  real* Xc[2] = {nullptr, nullptr};  // k x pad4(m)
+  real* Bq = nullptr;     // k x pad4(n)
+  real* Bq2 = nullptr;    // k x pad4(n) (TF32: the product with the low part of Q_C)
+  real* Kc = nullptr;     // k x k
+  real* Mp = nullptr;     // k x k
   real* partial = nullptr;
   size_t partial_cap = 0;
   // BF16 storage of A: the split sample operand, and the float64 T solve
@@ -173,7 +180,8 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
   upd(k, n - k, k);
   if (!tri_solve_fits<real>(ctx, k)) return CURID_UNSUPPORTED;
   if (d.randomized && d.q > 0 && !chol_inverse_fits<real>(ctx, l)) return CURID_UNSUPPORTED;
-  if (op == Op::Tsid || op == Op::Cur) {
+  const bool cur_op = op == Op::Cur || op == Op::CurCorrected;
+  if (op == Op::Tsid || cur_op) {
     P->Ct = cv.take<real>((size_t)k * m);
     CURID_TRY(cpqr_plan<real>(ctx, k, m, &grid, &smem));
     cpqr_carve<real>(cv, ctx, k, m, &P->rs);
@@ -184,7 +192,7 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
     P->SWinv = cv.take<real>((size_t)k * k);
     upd(k, m - k, k);
   }
-  if (op == Op::Cur) {
+  if (cur_op) {
     P->R = cv.take<real>((size_t)k * n);
     P->Rt = cv.take<real>((size_t)k * n);
     P->Q = cv.take<real>((size_t)k * n);
@@ -199,6 +207,17 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
     upd(k, k, n);
     upd(k, k, n - k);
     upd(k, k, k);
+  }
+  if (op == Op::CurCorrected) {
+    for (int b = 0; b < 2; ++b) P->Xc[b] = cv.take<real>((size_t)k * pad4(m));
+    P->Bq = cv.take<real>((size_t)k * pad4(n));
+    if (d.tf32) P->Bq2 = cv.take<real>((size_t)k * pad4(n));
+    P->Kc = cv.take<real>((size_t)k * k);
+    P->Mp = cv.take<real>((size_t)k * k);
+    upd(k, k, m);
+    upd(k, m, k);
+    upd(k, n, m);
+    if (d.tf32) part = std::max(part, gemm_tf32_partial_elems(k, n, m, ctx.num_sms));
   }
   P->partial_cap = part;
   P->partial = part ? cv.take<real>(part) : nullptr;
@@ -381,7 +400,8 @@ curid_status run(curid_handle* h, Op op, const void* Araw, const Dims& d, double
     PhaseScope ps(h, CURID_PHASE_CPQR_COL);
     CURID_TRY(cpqr_run<real>(ctx, Y, ly, n, ldy, k, tol, o.J, P.S, n, P.cs, 0));
   }
-  real* T = (o.T && op != Op::Cur) ? static_cast<real*>(o.T) : P.T;
+  const bool cur_op = op == Op::Cur || op == Op::CurCorrected;
+  real* T = (o.T && !cur_op) ? static_cast<real*>(o.T) : P.T;
   int64_t ldt = (T == P.T) ? std::max<int64_t>(1, n - k) : o.ldt;
   {
     PhaseScope ps(h, CURID_PHASE_T);
@@ -424,7 +444,7 @@ curid_status run(curid_handle* h, Op op, const void* Araw, const Dims& d, double
   } else {
     CURID_TRY(split_s<real>(ctx, P.SW, m, I, k, m, P.SW11, P.SW12));
   }
-  if (op == Op::Cur)
+  if (cur_op)
     CURID_TRY(upper_tri_inverse<real>(ctx, P.SW11, k, &P.status->k_row, P.SWinv));
   if (op == Op::Tsid) return CURID_OK;
 
@@ -460,15 +480,52 @@ curid_status run(curid_handle* h, Op op, const void* Araw, const Dims& d, double
   CURID_TRY(chol_inverse<real>(ctx, P.Gu, k, 0.0, P.L2));
   CURID_TRY(gemm<real>(ctx, false, false, k, n, k, real(1), P.L2, k, P.Q, n, real(0), P.Rt, n,
                        P.partial, P.partial_cap));
-  // M = V* Q^T = Q(:, J[:k])^T + T Q(:, J[k:])^T
-  CURID_TRY(split_s<real>(ctx, P.Rt, n, o.J, k, n, P.Qsk, P.Qres));
-  if (n - k > 0) {
-    CURID_TRY(gemm<real>(ctx, false, true, k, k, n - k, real(1), T, ldt, P.Qres, n - k, real(0),
-                         P.M, k, P.partial, P.partial_cap));
+  if (op == Op::CurCorrected) {
+    // Eq. (4.3): U R = V* + C^+ E with E = A - C V*, i.e. U = C^+ A R^+.
+    // C^T = L Q_C (three Cholesky-QR passes); C^+ = K^{-1} Q_C with
+    // K = Q_C C (= L^T, upper triangular to rounding, solved as such); so
+    // M = C^+ A Q^T = K^{-1} (Q_C A) Q^T, and U = M L^{-1} S_W11^{-T} below.
+    const int64_t ldx = pad4(m);
+    CURID_TRY(copy2d<real>(ctx, P.Ct, m, P.Xc[0], ldx, k, m));
+    real* qc = P.Xc[0];
+    real* qt = P.Xc[1];
+    CURID_TRY(chol_qr_rows<real>(ctx, &qc, &qt, k, m, ldx, P.Gu, P.partial, P.partial_cap, 3));
+    CURID_TRY(gemm<real>(ctx, false, true, k, k, m, real(1), qc, ldx, P.Ct, m, real(0), P.Kc, k,
+                         P.partial, P.partial_cap));
+    // Q_C A must be accurate to the working precision (C^+ is applied to
+    // it exactly, unlike a sketch operand): with TF32 products Q_C is split
+    // into its TF32 part and the remainder, two products with A (each with
+    // A split hi + lo) summed.
+    bool split_done = false;
+    if constexpr (sizeof(real) == 4) {
+      if (sk.tf32 && !d.bf16) {
+        CURID_TRY(split_tf32(ctx, qc, ldx, qt, ldx, k, m));
+        CURID_TRY(a_product<real>(ctx, true, false, false, k, n, m, qc, ldx, Araw, lda, P.Bq,
+                                  pad4(n), P));
+        CURID_TRY(a_product<real>(ctx, true, false, false, k, n, m, qt, ldx, Araw, lda, P.Bq2,
+                                  pad4(n), P));
+        CURID_TRY(add2d<real>(ctx, P.Bq2, pad4(n), P.Bq, pad4(n), k, n));
+        split_done = true;
+      }
+    }
+    if (!split_done)
+      CURID_TRY(a_product<real>(ctx, sk.tf32 != 0, d.bf16, false, k, n, m, qc, ldx, Araw, lda,
+                                P.Bq, pad4(n), P));
+    CURID_TRY(gemm<real>(ctx, false, true, k, k, n, real(1), P.Bq, pad4(n), P.Rt, n, real(0),
+                         P.Mp, k, P.partial, P.partial_cap));
+    CURID_TRY(tri_solve<real>(ctx, k, P.Kc, k, true, false, P.Mp, k, P.M, k, k,
+                              &P.status->k_row));
   } else {
-    CURID_CUDA(cudaMemsetAsync(P.M, 0, (size_t)k * k * sizeof(real), ctx.stream));
+    // M = V* Q^T = Q(:, J[:k])^T + T Q(:, J[k:])^T
+    CURID_TRY(split_s<real>(ctx, P.Rt, n, o.J, k, n, P.Qsk, P.Qres));
+    if (n - k > 0) {
+      CURID_TRY(gemm<real>(ctx, false, true, k, k, n - k, real(1), T, ldt, P.Qres, n - k,
+                           real(0), P.M, k, P.partial, P.partial_cap));
+    } else {
+      CURID_CUDA(cudaMemsetAsync(P.M, 0, (size_t)k * k * sizeof(real), ctx.stream));
+    }
+    CURID_TRY(add_transpose<real>(ctx, P.Qsk, k, P.M, k, k, k));
   }
-  CURID_TRY(add_transpose<real>(ctx, P.Qsk, k, P.M, k, k, k));
   CURID_TRY(gemm<real>(ctx, false, false, k, k, k, real(1), P.M, k, P.L2, k, real(0), P.Uh, k,
                        P.partial, P.partial_cap));
   CURID_TRY(gemm<real>(ctx, false, false, k, k, k, real(1), P.Uh, k, P.L1, k, real(0), P.M, k,
@@ -674,7 +731,7 @@ curid_status curid_workspace_size(curid_handle* handle, curid_dtype dtype, int64
   auto size_for = [&](auto tag) -> curid_status {
     using real = decltype(tag);
     Plan<real> P;
-    CURID_TRY(make_plan<real>(ctx, Op::Cur, d, gen, true, nullptr, &P));
+    CURID_TRY(make_plan<real>(ctx, Op::CurCorrected, d, gen, true, nullptr, &P));
     size_t b = P.bytes;
     if (row_ok) {
       Plan<real> Pt;
@@ -904,6 +961,27 @@ curid_status curid_cur(curid_handle* handle, curid_dtype dtype, const void* A, i
       return run<double>(handle, Op::Cur, (const double*)A, d, 0.0, sk, o, handle->ws,
                          handle->ws_bytes);
     return run<float>(handle, Op::Cur, (const float*)A, d, 0.0, sk, o, handle->ws,
+                      handle->ws_bytes);
+  });
+}
+
+curid_status curid_cur_corrected(curid_handle* handle, curid_dtype dtype, const void* A,
+                                 int64_t m, int64_t n, int64_t lda, int k, double tol,
+                                 curid_sketch sk, int32_t* J, int32_t* I, double* U, void* C,
+                                 void* R, void* T, int64_t ldt, void* TW, int64_t ldtw) {
+  CURID_TRY(resolve_rank(handle, dtype, A, m, n, lda, &k, tol, sk, J));
+  if (k == 0 && tol > 0) return rank_zero_rows(handle, I, m);
+  Dims d;
+  CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d));
+  if (!J || !I || !U) return CURID_INVALID_ARG;
+  if (T && ldt < std::max<int64_t>(1, n - k)) return CURID_INVALID_ARG;
+  if (TW && ldtw < std::max<int64_t>(1, m - k)) return CURID_INVALID_ARG;
+  Outputs o{J, T, ldt, I, TW, ldtw, U, C, R};
+  return dispatch(handle, [&]() -> curid_status {
+    if (dtype == CURID_F64)
+      return run<double>(handle, Op::CurCorrected, (const double*)A, d, 0.0, sk, o, handle->ws,
+                         handle->ws_bytes);
+    return run<float>(handle, Op::CurCorrected, (const float*)A, d, 0.0, sk, o, handle->ws,
                       handle->ws_bytes);
   });
 }

@@ -117,6 +117,34 @@ __global__ void add_transpose_kernel(const real* __restrict__ src, int64_t lds,
   }
 }
 
+// x -> (hi, lo): hi = x with the 13 low mantissa bits cleared (exactly a
+// TF32 value, which the tensor cores use unchanged), lo = x - hi (exact in
+// float32; the tensor cores read it to about 2^-10 of itself, 2^-21 of x).
+// hi may overwrite x.
+__global__ void split_tf32_kernel(float* __restrict__ x, int64_t ldx, float* __restrict__ lo,
+                                  int64_t ldl, int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    const float v = x[r * ldx + c];
+    const float h = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
+    x[r * ldx + c] = h;
+    lo[r * ldl + c] = v - h;
+  }
+}
+
+template <typename real>
+__global__ void add2d_kernel(const real* __restrict__ src, int64_t lds, real* __restrict__ dst,
+                             int64_t ldd, int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    dst[r * ldd + c] += src[r * lds + c];
+  }
+}
+
 // dst[c*ldd + r] = src[r*lds + c] through a 32 x 32 shared tile
 template <typename real>
 __global__ void transpose2d_kernel(const real* __restrict__ src, int64_t lds,
@@ -215,6 +243,25 @@ curid_status add_transpose(const Ctx& ctx, const real* src, int64_t lds, real* d
   return CURID_OK;
 }
 
+curid_status split_tf32(const Ctx& ctx, float* x, int64_t ldx, float* lo, int64_t ldl,
+                        int64_t rows, int64_t cols) {
+  if (rows <= 0 || cols <= 0) return CURID_OK;
+  split_tf32_kernel<<<blocks_for(rows * cols, ctx.num_sms), 256, 0, ctx.stream>>>(
+      x, ldx, lo, ldl, rows, cols);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
+template <typename real>
+curid_status add2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
+                   int64_t rows, int64_t cols) {
+  if (rows <= 0 || cols <= 0) return CURID_OK;
+  add2d_kernel<real><<<blocks_for(rows * cols, ctx.num_sms), 256, 0, ctx.stream>>>(
+      src, lds, dst, ldd, rows, cols);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
 template <typename real>
 curid_status transpose2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
                          int64_t rows, int64_t cols) {
@@ -237,7 +284,9 @@ curid_status transpose2d(const Ctx& ctx, const real* src, int64_t lds, real* dst
   template curid_status add_transpose<real>(const Ctx&, const real*, int64_t, real*, int64_t,   \
                                             int64_t, int64_t);                                 \
   template curid_status transpose2d<real>(const Ctx&, const real*, int64_t, real*, int64_t,     \
-                                          int64_t, int64_t);
+                                          int64_t, int64_t);                                   \
+  template curid_status add2d<real>(const Ctx&, const real*, int64_t, real*, int64_t, int64_t,  \
+                                    int64_t);
 CURID_INST(float)
 CURID_INST(double)
 #undef CURID_INST

@@ -151,6 +151,13 @@ curid_status copy2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int
 template <typename real>
 curid_status transpose2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
                          int64_t rows, int64_t cols);
+// dst += src (rows x cols)
+template <typename real>
+curid_status add2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
+                   int64_t rows, int64_t cols);
+// x (rows x cols) -> its TF32 part in place, the float32 remainder into lo
+curid_status split_tf32(const Ctx& ctx, float* x, int64_t ldx, float* lo, int64_t ldl,
+                        int64_t rows, int64_t cols);
 // dst[i][t] = src[t][i] (k x k transpose-add): dst += src^T
 template <typename real>
 curid_status add_transpose(const Ctx& ctx, const real* src, int64_t lds, real* dst,

@@ -357,3 +357,59 @@ def test_srft_randomized_exact_rank():
     o, Y = O.randomized_cur(A, Om, k)
     np.testing.assert_allclose(Y, O.srft_sketch(A, rows, signs), atol=1e-10, rtol=0)
     assert O.rel_err_fro(A, o.C, o.U, o.R) <= 1e-12
+
+
+# --- error-corrected U (Section 4.3, Eq. (4.3)) --------------------------------
+
+def _randomized_skeleton(seed=61, q=0):
+    m, n, k = 300, 220, 25
+    A = f64(syn.spectrum_matrix(m, n, syn.power_decay(n), seed, torch.float64))
+    Om = np.random.default_rng(seed + 1).standard_normal((k + 5, m))
+    return A, Om, k, q
+
+
+def test_corrected_u_closed_form():
+    """U R = V* + C^+ E with E = A - C V* has the least-squares solution
+    C^+ (C V* + E) R^+ = C^+ A R^+; checked against library pseudo-inverses
+    on a randomized skeleton (where C^+ E is not zero)."""
+    A, Om, k, q = _randomized_skeleton()
+    o, _ = O.randomized_cur_corrected(A, Om, k, q=q)
+    U = np.linalg.pinv(o.C) @ A @ np.linalg.pinv(o.R)
+    np.testing.assert_allclose(o.U, U, atol=1e-9 * np.abs(U).max(), rtol=0)
+    base, _ = O.randomized_cur(A, Om, k, q=q)
+    assert np.abs(base.U - o.U).max() > 1e-6 * np.abs(U).max()  # the correction is not void
+
+
+def test_corrected_u_is_optimal():
+    """For fixed C and R the corrected U minimises ||A - C U R||_F: no
+    perturbation and not the uncorrected U of Eq. (4.2) does better."""
+    A, Om, k, q = _randomized_skeleton(seed=71)
+    o, _ = O.randomized_cur_corrected(A, Om, k, q=q)
+    e = O.rel_err_fro(A, o.C, o.U, o.R)
+    base, _ = O.randomized_cur(A, Om, k, q=q)
+    assert e < O.rel_err_fro(A, base.C, base.U, base.R)
+    rng = np.random.default_rng(72)
+    for _ in range(5):
+        D = rng.standard_normal(o.U.shape) * 1e-3 * np.abs(o.U).max()
+        assert e <= O.rel_err_fro(A, o.C, o.U + D, o.R) * (1 + 1e-12)
+
+
+def test_corrected_u_vanishes_for_deterministic_id():
+    """With the column ID from the CPQR of A itself, E = Q2 S22 (Eq. (2.5))
+    is orthogonal to range(C) = range(Q1), so C^+ E = 0 and Eq. (4.3)
+    reduces to Eq. (4.2)."""
+    A = f64(syn.spectrum_matrix(200, 150, syn.exp_decay(150), 81, torch.float64))
+    k = 20
+    a = O.cur(A, k)
+    b = O.cur_corrected(A, k)
+    assert list(a.J) == list(b.J) and list(a.I) == list(b.I)
+    np.testing.assert_allclose(b.U, a.U, atol=1e-8 * np.abs(a.U).max(), rtol=0)
+
+
+def test_corrected_u_exact_rank():
+    m, n, k = 250, 180, 15
+    rng = np.random.default_rng(91)
+    A = rng.standard_normal((m, k)) @ rng.standard_normal((k, n))
+    Om = rng.standard_normal((k + 5, m))
+    o, _ = O.randomized_cur_corrected(A, Om, k)
+    assert O.rel_err_fro(A, o.C, o.U, o.R) <= 1e-12
