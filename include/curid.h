@@ -196,6 +196,28 @@ curid_status curid_cpqr(curid_handle* handle, curid_dtype dtype,
                         const void* Y, int64_t l, int64_t n, int64_t ldy,
                         int k, double tol, int32_t* J, void* S);
 
+/* Regularised interpolation matrix (Section 4.1: the least-squares form
+ * Eq. (4.1) of T = S11^{-1} S12, amended by a Tikhonov term):
+ * T = argmin ||S11 T - S12||_F^2 + lam^2 ||T||_F^2, lam > 0, for an S11 too
+ * ill-conditioned for the back substitution of Eq. (2.8).  Inputs are what
+ * curid_cpqr returns: S (k x n, leading dimension lds >= n, columns in
+ * ORIGINAL order) and J (n; J[:k] the pivots).  Output T (k x (n-k),
+ * leading dimension ldt >= n-k; column c belongs to J[k + c]).  Computed
+ * without normal equations: the rows of [S11^T | lam I] are orthonormalised
+ * by three Cholesky-QR passes (Q, k x 2k), R_a = Q [S11; lam I] and
+ * T = R_a^{-1} Q(:, :k) S12.  Scratch from the handle's workspace
+ * (curid_interp_tikhonov_workspace_size); CURID_F32 or CURID_F64;
+ * k <= 4096.  Errors: INVALID_ARG (null pointers, lam <= 0 or not finite,
+ * bad sizes), NO_WORKSPACE, UNSUPPORTED; a Cholesky breakdown is recorded
+ * in the device status. */
+curid_status curid_interp_tikhonov_workspace_size(curid_handle* handle,
+                                                  curid_dtype dtype, int64_t n,
+                                                  int k, size_t* bytes);
+curid_status curid_interp_tikhonov(curid_handle* handle, curid_dtype dtype,
+                                   const void* S, int64_t lds,
+                                   const int32_t* J, int64_t n, int k,
+                                   double lam, void* T, int64_t ldt);
+
 /* Truncated CPQR exactly as curid_cpqr, for callers that cannot allocate
  * device memory when they factor: a service that reserves all of its GPU
  * memory at start-up and must not fail on an allocation later, code running

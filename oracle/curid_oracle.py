@@ -21,7 +21,8 @@ import numpy as np
 import scipy.linalg
 
 __all__ = [
-    "as_f64", "CPQR", "cpqr", "interpolation_matrix", "vstar", "wmat",
+    "as_f64", "CPQR", "cpqr", "interpolation_matrix", "interpolation_matrix_tikhonov",
+    "vstar", "wmat",
     "IDResult", "id_col", "id_row", "TSIDResult", "tsid", "CURResult",
     "cur_middle", "cur", "cur_middle_corrected", "cur_corrected", "randomized_cur_corrected",
     "orth_rows", "sketch", "randomized_id_col",
@@ -166,6 +167,20 @@ def interpolation_matrix(S1, k, k_eff=None):
         T[:k_eff] = scipy.linalg.solve_triangular(
             S1[:k_eff, :k_eff], S1[:k_eff, k:], lower=False)
     return T
+
+
+def interpolation_matrix_tikhonov(S1, k, lam):
+    """T of the regularised least-squares problem of Section 4.1 (Eq. (4.1)
+    amended by a Tikhonov term): T = argmin ||S11 T - S12||_F^2 +
+    lam^2 ||T||_F^2, as the plain least-squares solution of the augmented
+    system [S11; lam I] T = [S12; 0] (library lstsq as the single step).
+    S1 is k x n in pivot order; lam >= 0 (lam = 0 is Eq. (2.8) when S11 is
+    nonsingular)."""
+    S1 = np.asarray(S1, dtype=np.float64)
+    n = S1.shape[1]
+    W = np.vstack([S1[:k, :k], lam * np.eye(k)])
+    B = np.vstack([S1[:k, k:], np.zeros((k, n - k))])
+    return np.linalg.lstsq(W, B, rcond=None)[0]
 
 
 def vstar(J, T, n):

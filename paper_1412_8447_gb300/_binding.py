@@ -57,6 +57,9 @@ SIGNATURES = {
                    _vp, _i64],
     "curid_cur": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _vp, _vp, _vp,
                   _vp, _i64, _vp, _i64],
+    "curid_interp_tikhonov_workspace_size": [_vp, _int, _i64, _int,
+                                             ctypes.POINTER(ctypes.c_size_t)],
+    "curid_interp_tikhonov": [_vp, _int, _vp, _i64, _vp, _i64, _int, _dbl, _vp, _i64],
     "curid_cur_corrected": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _vp,
                             _vp, _vp, _vp, _i64, _vp, _i64],
     "curid_cur_adjoint_workspace_size": [_vp, _int, _i64, _i64, _int,
@@ -312,6 +315,28 @@ def cpqr(Y, k=0, tol=0.0, check=True):
     _check(h.lib.curid_cpqr(h.h, dt, _ptr(Y), l, n, Y.stride(0), k, float(tol), _ptr(J), _ptr(S)),
            "curid_cpqr")
     return _finish(h, Result(J=J, S=S), check, "curid_cpqr")
+
+
+def interp_tikhonov(S, J, k, lam):
+    """Regularised T = argmin ||S11 T - S12||^2 + lam^2 ||T||^2 (Section 4.1
+    with a Tikhonov term) from the S (k x n, original column order) and J
+    that ``cpqr`` returns; T is k x (n - k), columns following J[k:]."""
+    S = _mat(S)
+    dev = _dev(S)
+    h = handle(dev)
+    kk, n = S.shape
+    if kk < k:
+        raise ValueError("S has fewer than k rows")
+    b = ctypes.c_size_t(0)
+    _check(h.lib.curid_interp_tikhonov_workspace_size(h.h, _dtype_code(S.dtype), n, k,
+                                                      ctypes.byref(b)),
+           "curid_interp_tikhonov_workspace_size")
+    h.prepare(b.value)
+    T = torch.empty((k, max(n - k, 1)), dtype=S.dtype, device=S.device)
+    _check(h.lib.curid_interp_tikhonov(h.h, _dtype_code(S.dtype), _ptr(S), S.stride(0),
+                                       _ptr(J.contiguous()), n, k, float(lam), _ptr(T),
+                                       T.stride(0)), "curid_interp_tikhonov")
+    return T[:, :n - k]
 
 
 def _prep(A, k, p, q, seed, omega, tf32):

@@ -2,6 +2,7 @@
 // kernels for CPQR -> column ID -> row ID of C -> CUR (Algorithms 1-4).
 // Every step of the method runs in this library's kernels; the host only
 // validates, carves the caller's workspace and enqueues launches.
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -634,6 +635,71 @@ curid_status rank_zero_rows(curid_handle* h, int32_t* I, int64_t m) {
   return CURID_OK;
 }
 
+// Regularised T (Section 4.1: Eq. (4.1) with a Tikhonov term):
+// T = argmin ||S11 T - S12||^2 + lam^2 ||T||^2 is the least-squares solution
+// of [S11; lam I] T = [S12; 0].  With W = [S11; lam I] = Q_a R_a (the rows of
+// W^T = [S11^T | lam I] orthonormalised by three Cholesky-QR passes, Q = Q_a^T
+// k x 2k), T = R_a^{-1} Q(:, :k) S12 and R_a = Q W (upper triangular to
+// rounding, solved as such).  No normal equations: cond(W) <= ||S11|| / lam.
+template <typename real>
+struct TikPlan {
+  StatusBlock* status = nullptr;
+  real* S11 = nullptr;   // k x k
+  real* S12 = nullptr;   // k x (n - k)
+  real* W[3] = {nullptr, nullptr, nullptr};  // k x 2k: two passes' buffers, W^T kept
+  real* G = nullptr;     // k x k
+  real* K = nullptr;     // k x k
+  real* Z = nullptr;     // k x (n - k)
+  real* partial = nullptr;
+  size_t partial_cap = 0;
+  size_t bytes = 0;
+};
+
+template <typename real>
+void tik_plan(const Ctx& ctx, int64_t n, int k, void* base, TikPlan<real>* P) {
+  Carver cv(base);
+  const int64_t r = std::max<int64_t>(1, n - k);
+  P->status = cv.take<StatusBlock>(1);
+  P->S11 = cv.take<real>((size_t)k * k);
+  P->S12 = cv.take<real>((size_t)k * r);
+  for (int b = 0; b < 3; ++b) P->W[b] = cv.take<real>((size_t)k * 2 * k);
+  P->G = cv.take<real>((size_t)k * k);
+  P->K = cv.take<real>((size_t)k * k);
+  P->Z = cv.take<real>((size_t)k * r);
+  const size_t part = std::max(gemm_partial_elems<real>(k, k, 2 * k, ctx.num_sms),
+                               gemm_partial_elems<real>(k, r, k, ctx.num_sms));
+  P->partial_cap = part;
+  P->partial = part ? cv.take<real>(part) : nullptr;
+  P->bytes = cv.used + 256;
+}
+
+template <typename real>
+curid_status tikhonov_run(curid_handle* h, const real* S, int64_t lds, const int32_t* J,
+                          int64_t n, int k, double lam, real* T, int64_t ldt) {
+  Ctx ctx = make_ctx(h);
+  TikPlan<real> P;
+  tik_plan<real>(ctx, n, k, nullptr, &P);
+  if (!h->ws || P.bytes > h->ws_bytes) return CURID_NO_WORKSPACE;
+  tik_plan<real>(ctx, n, k, h->ws, &P);
+  if (!tri_solve_fits<real>(ctx, k) || !chol_inverse_fits<real>(ctx, k)) return CURID_UNSUPPORTED;
+  ctx.status = P.status;
+  PhaseScope ps(h, CURID_PHASE_T);
+  CURID_CUDA(cudaMemsetAsync(P.status, 0, sizeof(StatusBlock), ctx.stream));
+  CURID_TRY(split_s<real>(ctx, S, lds, J, k, n, P.S11, P.S12));
+  const int64_t lw = 2LL * k;
+  CURID_TRY(aug_transpose<real>(ctx, P.S11, k, k, (real)lam, P.W[2], lw));
+  CURID_TRY(copy2d<real>(ctx, P.W[2], lw, P.W[0], lw, k, lw));
+  real* x = P.W[0];
+  real* t = P.W[1];
+  CURID_TRY(chol_qr_rows<real>(ctx, &x, &t, k, lw, lw, P.G, P.partial, P.partial_cap, 3));
+  CURID_TRY(gemm<real>(ctx, false, true, k, k, lw, real(1), x, lw, P.W[2], lw, real(0), P.K, k,
+                       P.partial, P.partial_cap));
+  if (n - k <= 0) return CURID_OK;
+  CURID_TRY(gemm<real>(ctx, false, false, k, n - k, k, real(1), x, lw, P.S12, n - k, real(0),
+                       P.Z, n - k, P.partial, P.partial_cap));
+  return tri_solve<real>(ctx, k, P.K, k, true, false, P.Z, n - k, T, ldt, n - k, nullptr);
+}
+
 }  // namespace
 
 extern "C" {
@@ -983,6 +1049,41 @@ curid_status curid_cur_corrected(curid_handle* handle, curid_dtype dtype, const 
                          handle->ws_bytes);
     return run<float>(handle, Op::CurCorrected, (const float*)A, d, 0.0, sk, o, handle->ws,
                       handle->ws_bytes);
+  });
+}
+
+curid_status curid_interp_tikhonov_workspace_size(curid_handle* handle, curid_dtype dtype,
+                                                  int64_t n, int k, size_t* bytes) {
+  if (!handle || !bytes || n < 1 || k < 1 || k > n) return CURID_INVALID_ARG;
+  Ctx ctx{nullptr, handle->num_sms, handle->smem_optin, nullptr};
+  if (dtype == CURID_F64) {
+    TikPlan<double> P;
+    tik_plan<double>(ctx, n, k, nullptr, &P);
+    *bytes = P.bytes;
+  } else if (dtype == CURID_F32) {
+    TikPlan<float> P;
+    tik_plan<float>(ctx, n, k, nullptr, &P);
+    *bytes = P.bytes;
+  } else {
+    return CURID_UNSUPPORTED;
+  }
+  return CURID_OK;
+}
+
+curid_status curid_interp_tikhonov(curid_handle* handle, curid_dtype dtype, const void* S,
+                                   int64_t lds, const int32_t* J, int64_t n, int k, double lam,
+                                   void* T, int64_t ldt) {
+  if (!handle || !S || !J || !T || n < 1 || k < 1 || k > n || lds < n || !(lam > 0) ||
+      !std::isfinite(lam) || ldt < std::max<int64_t>(1, n - k))
+    return CURID_INVALID_ARG;
+  return dispatch(handle, [&]() -> curid_status {
+    if (dtype == CURID_F64)
+      return tikhonov_run<double>(handle, static_cast<const double*>(S), lds, J, n, k, lam,
+                                  static_cast<double*>(T), ldt);
+    if (dtype == CURID_F32)
+      return tikhonov_run<float>(handle, static_cast<const float*>(S), lds, J, n, k, lam,
+                                 static_cast<float*>(T), ldt);
+    return CURID_UNSUPPORTED;
   });
 }
 

@@ -145,6 +145,18 @@ __global__ void add2d_kernel(const real* __restrict__ src, int64_t lds, real* __
   }
 }
 
+// dst (k x 2k, leading dimension ldd) = [S11^T | lam I] from S11 (k x k)
+template <typename real>
+__global__ void aug_transpose_kernel(const real* __restrict__ S11, int64_t lds, int k, real lam,
+                                     real* __restrict__ dst, int64_t ldd) {
+  const int64_t total = 2LL * k * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / (2 * k), j = e % (2 * k);
+    dst[i * ldd + j] = j < k ? S11[j * lds + i] : (j - k == i ? lam : real(0));
+  }
+}
+
 // dst[c*ldd + r] = src[r*lds + c] through a 32 x 32 shared tile
 template <typename real>
 __global__ void transpose2d_kernel(const real* __restrict__ src, int64_t lds,
@@ -253,6 +265,16 @@ curid_status split_tf32(const Ctx& ctx, float* x, int64_t ldx, float* lo, int64_
 }
 
 template <typename real>
+curid_status aug_transpose(const Ctx& ctx, const real* S11, int64_t lds, int k, real lam,
+                           real* dst, int64_t ldd) {
+  if (k <= 0) return CURID_OK;
+  aug_transpose_kernel<real><<<blocks_for(2LL * k * k, ctx.num_sms), 256, 0, ctx.stream>>>(
+      S11, lds, k, lam, dst, ldd);
+  CURID_LAUNCHED(ctx);
+  return CURID_OK;
+}
+
+template <typename real>
 curid_status add2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
                    int64_t rows, int64_t cols) {
   if (rows <= 0 || cols <= 0) return CURID_OK;
@@ -286,7 +308,9 @@ curid_status transpose2d(const Ctx& ctx, const real* src, int64_t lds, real* dst
   template curid_status transpose2d<real>(const Ctx&, const real*, int64_t, real*, int64_t,     \
                                           int64_t, int64_t);                                   \
   template curid_status add2d<real>(const Ctx&, const real*, int64_t, real*, int64_t, int64_t,  \
-                                    int64_t);
+                                    int64_t);                                                  \
+  template curid_status aug_transpose<real>(const Ctx&, const real*, int64_t, int, real, real*, \
+                                            int64_t);
 CURID_INST(float)
 CURID_INST(double)
 #undef CURID_INST

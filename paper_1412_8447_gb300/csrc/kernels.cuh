@@ -151,6 +151,10 @@ curid_status copy2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int
 template <typename real>
 curid_status transpose2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
                          int64_t rows, int64_t cols);
+// dst (k x 2k) = [S11^T | lam I]
+template <typename real>
+curid_status aug_transpose(const Ctx& ctx, const real* S11, int64_t lds, int k, real lam,
+                           real* dst, int64_t ldd);
 // dst += src (rows x cols)
 template <typename real>
 curid_status add2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,

@@ -413,3 +413,47 @@ def test_corrected_u_exact_rank():
     Om = rng.standard_normal((k + 5, m))
     o, _ = O.randomized_cur_corrected(A, Om, k)
     assert O.rel_err_fro(A, o.C, o.U, o.R) <= 1e-12
+
+
+# --- regularised T (Section 4.1, Tikhonov term) --------------------------------
+
+def _graded_s1(k, n, cond, seed):
+    """Upper-trapezoidal S1 = [S11 S12] with S11 of condition about cond."""
+    rng = np.random.default_rng(seed)
+    d = np.logspace(0, -np.log10(cond), k)
+    S11 = np.triu(rng.standard_normal((k, k)) * 0.1 * d[None, :]) + np.diag(d)
+    S12 = rng.standard_normal((k, n - k)) * d[:, None]
+    return np.hstack([S11, S12])
+
+
+def test_tikhonov_t_zero_lambda_is_back_substitution():
+    S1 = _graded_s1(12, 40, 1e3, 1)
+    np.testing.assert_allclose(O.interpolation_matrix_tikhonov(S1, 12, 0.0),
+                               O.interpolation_matrix(S1, 12), rtol=0, atol=1e-10)
+
+
+def test_tikhonov_t_filter_factors():
+    """Closed form through the SVD S11 = U diag(s) V^T (library SVD): the
+    regularised solution is V diag(s / (s^2 + lam^2)) U^T S12."""
+    k, n = 15, 50
+    S1 = _graded_s1(k, n, 1e6, 2)
+    Us, sv, Vt = np.linalg.svd(S1[:, :k])
+    for lam in (1e-6, 1e-3, 0.1):
+        T = O.interpolation_matrix_tikhonov(S1, k, lam)
+        ref = Vt.T @ np.diag(sv / (sv ** 2 + lam ** 2)) @ Us.T @ S1[:, k:]
+        np.testing.assert_allclose(T, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+
+
+def test_tikhonov_t_normal_equations_and_shrinkage():
+    """(S11^T S11 + lam^2 I) T = S11^T S12 holds, and ||T_lam||_F decreases
+    as lam grows."""
+    k, n = 10, 30
+    S1 = _graded_s1(k, n, 1e4, 3)
+    S11, S12 = S1[:, :k], S1[:, k:]
+    norms = []
+    for lam in (1e-5, 1e-3, 1e-1, 1.0):
+        T = O.interpolation_matrix_tikhonov(S1, k, lam)
+        lhs = (S11.T @ S11 + lam ** 2 * np.eye(k)) @ T
+        np.testing.assert_allclose(lhs, S11.T @ S12, rtol=0, atol=1e-10 * np.abs(S11.T @ S12).max())
+        norms.append(np.linalg.norm(T))
+    assert all(a > b for a, b in zip(norms, norms[1:]))
