@@ -316,6 +316,10 @@ chol_kernel(real* __restrict__ G, int l, int64_t ldg, real rel_shift, StatusBloc
       const int m = nb - b - 1;
       const int nblocks = b >= 0 ? m * (m + 1) / 2 : 0;
       if constexpr (kLookahead) {
+        // Warp 0 (diagonal factorization, the critical path) shares its
+        // scheduler with warps 4, 8, 12 (warp % 4); those stay idle here so
+        // it issues at full rate, and the 12 warps on the other three
+        // schedulers take the trailing blocks.
         if (warp == 0) {
           if (m > 0) {
             if (b >= 0) chol_trail_block(a, b, 0, 0, lane);
@@ -323,8 +327,10 @@ chol_kernel(real* __restrict__ G, int l, int64_t ldg, real rel_shift, StatusBloc
             const int fail = chol_diag_warp(chol_block(a, b + 1, b + 1), W, lane);
             if (lane == 0) s_fail = fail;
           }
-        } else {
-          for (int q = warp; q < nblocks; q += kSmallWarps - 1) chol_trail_q(a, b, q, lane);
+        } else if (warp & 3) {
+          constexpr int kWorkers = kSmallWarps - kSmallWarps / 4;
+          const int idx = warp - (warp >> 2) - 1;  // 0 .. kWorkers - 1
+          for (int q = 1 + idx; q < nblocks; q += kWorkers) chol_trail_q(a, b, q, lane);
         }
       } else {
         for (int q = warp; q < nblocks; q += kSmallWarps) chol_trail_q(a, b, q, lane);
