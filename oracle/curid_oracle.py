@@ -25,7 +25,7 @@ __all__ = [
     "vstar", "wmat",
     "IDResult", "id_col", "id_row", "TSIDResult", "tsid", "CURResult",
     "cur_middle", "cur", "cur_middle_corrected", "cur_corrected", "randomized_cur_corrected",
-    "orth_rows", "sketch", "randomized_id_col",
+    "orth_rows", "sketch", "randomized_id_col", "randomized_rank_adaptive",
     "randomized_cur", "srft_sketch", "srft_omega_rows", "rel_err_fro", "OK", "RANK_DEFICIENT",
     "rank_threshold",
 ]
@@ -350,6 +350,27 @@ def randomized_id_col(A, Omega, k, q=0, orth=True,
     pivots of the full pivoted QR the algorithm states), T from S of Y."""
     Y = sketch(A, Omega, q=q, orth=orth)
     return id_col(Y, k=k, eps=eps), Y
+
+
+def randomized_rank_adaptive(A, Omega, tol, p, q=0, orth=True, l0=64, l_cap=4096,
+                             eps=np.finfo(np.float64).eps):
+    """Rank for a tolerance with a sketch (Algorithm 4 with the tolerance stop
+    of Section 3; the sample size l = k + p needs the rank, so l is searched):
+    l starts at max(l0, p + 1), capped by min(m, n, l_cap); the sample is the
+    first l rows of ``Omega`` applied as in ``sketch``; CPQR of the sample
+    runs at most l - p steps with the stop ||Y - Q_j Q_j^T Y||_F <= tol ||Y||_F.
+    A stop before l - p steps gives the rank; otherwise l doubles (at the cap
+    the rank is l - p).  Returns (k, l, Y)."""
+    A = as_f64(A)
+    m, n = A.shape
+    cap = min(m, n, l_cap)
+    l = min(cap, max(l0, p + 1))
+    while True:
+        Y = sketch(A, np.asarray(Omega)[:l], q=q, orth=orth)
+        r = cpqr(Y, k=l - p, tol=tol, eps=eps)
+        if r.k < l - p or l >= cap:
+            return r.k, l, Y
+        l = min(cap, 2 * l)
 
 
 def randomized_cur(A, Omega, k, q=0, orth=True,

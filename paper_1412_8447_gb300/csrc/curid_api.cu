@@ -604,16 +604,78 @@ curid_status adaptive_rank(curid_handle* h, curid_dtype dt, const void* A, int64
   return CURID_OK;
 }
 
-// Decides between the fixed rank k and the adaptive rank (k == 0, tol > 0,
-// deterministic method only); on return *k is the rank to run, or 0 when the
-// tolerance is met by no column (J already written).
+// First sample size of the adaptive randomized search, and its cap (the
+// largest order of the dense factorisations of the l x l Gram matrices).
+constexpr int64_t kAdaptiveL0 = 64;
+constexpr int64_t kAdaptiveLMax = kMaxDenseOrder;
+
+inline int64_t adaptive_l_cap(int64_t m, int64_t n) {
+  return std::min<int64_t>(std::min(m, n), kAdaptiveLMax);
+}
+
+// Adaptive rank with a sketch (Algorithm 4 with the tolerance stop of
+// Section 3): the rank sets the sample size l = k + p, so l is searched.
+// Starting at l = max(64, p + 1) (capped by min(m, n, 4096)), the sample
+// Y = Omega_l A (A^* A)^q is formed and its CPQR runs with at most l - p
+// steps and the stop ||Y - Q_j Q_j^T Y||_F <= tol ||Y||_F; if the stop
+// comes before l - p steps its step count is the rank, else l doubles.
+// Omega is drawn from the seed, and the rows of a smaller Omega are the
+// leading rows of a larger one, so the fixed-rank run that follows (rank k,
+// p' = l - k) samples with exactly the Y searched.  The stop is tested on the
+// sample: for q = 0 the squared residual ratio of Y estimates A's without
+// bias (E||Omega E||_F^2 = l ||E||_F^2 for Gaussian Omega); power steps
+// weight the dominant directions and make it optimistic.  At the cap the rank
+// is l - p whether or not the tolerance was met.
+curid_status adaptive_rank_randomized(curid_handle* h, curid_dtype dt, const void* A, int64_t m,
+                                      int64_t n, int64_t lda, double tol, curid_sketch* sk,
+                                      int32_t* J, int* k_out) {
+  if (sk->omega) return CURID_UNSUPPORTED;  // the sample grows: Omega comes from the seed
+  const int64_t cap = adaptive_l_cap(m, n);
+  if (sk->p < 0 || sk->p >= cap) return CURID_INVALID_ARG;
+  int64_t l = std::min<int64_t>(cap, std::max<int64_t>(kAdaptiveL0, sk->p + 1));
+  while (true) {
+    const int kmax = (int)(l - sk->p);
+    Dims d;
+    CURID_TRY(check_common(h, dt, A, m, n, lda, kmax, 0.0, *sk, &d));
+    Outputs o{J, nullptr, 0, nullptr, nullptr, 0, nullptr, nullptr, nullptr};
+    CURID_TRY(dispatch(h, [&]() -> curid_status {
+      if (dt == CURID_F64)
+        return run<double>(h, Op::IdCol, (const double*)A, d, tol, *sk, o, h->ws, h->ws_bytes);
+      return run<float>(h, Op::IdCol, A, d, tol, *sk, o, h->ws, h->ws_bytes);
+    }));
+    StatusBlock sb;
+    DeviceGuard g(h->device);
+    if (!g.ok) return CURID_CUDA_ERROR;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return CURID_CUDA_ERROR;
+    if (cudaMemcpy(&sb, h->ws, sizeof(sb), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return CURID_CUDA_ERROR;
+    if (sb.flags & FLAG_TIMEOUT) return CURID_TIMEOUT;
+    if (sb.flags & FLAG_NONFINITE) return CURID_NONFINITE;
+    if (sb.flags & FLAG_BREAKDOWN) return CURID_BREAKDOWN;
+    if (sb.k_done < kmax || l >= cap) {
+      *k_out = sb.k_done;
+      sk->p = (int)(l - sb.k_done);
+      return CURID_OK;
+    }
+    l = std::min<int64_t>(cap, 2 * l);
+  }
+}
+
+// Decides between the fixed rank k and the adaptive rank (k == 0, tol > 0);
+// on return *k is the rank to run, or 0 when the tolerance is met by no
+// column (J already written).  With a sketch, sk->p becomes the oversampling
+// of the sample size the search settled on.
 curid_status resolve_rank(curid_handle* h, curid_dtype dt, const void* A, int64_t m, int64_t n,
-                          int64_t lda, int* k, double tol, const curid_sketch& sk, int32_t* J) {
+                          int64_t lda, int* k, double tol, curid_sketch* sk, int32_t* J) {
   if (*k != 0) return CURID_OK;
   if (!h || !A || !J || m <= 0 || n <= 0 || lda < n || !(tol > 0)) return CURID_INVALID_ARG;
-  if (sk.p >= 0 || dt == CURID_BF16) return CURID_UNSUPPORTED;  // l = k + p needs k
   int kout = 0;
-  CURID_TRY(adaptive_rank(h, dt, A, m, n, lda, tol, J, &kout));
+  if (sk->p >= 0) {
+    CURID_TRY(adaptive_rank_randomized(h, dt, A, m, n, lda, tol, sk, J, &kout));
+  } else {
+    if (dt == CURID_BF16) return CURID_UNSUPPORTED;  // BF16 storage: randomized method only
+    CURID_TRY(adaptive_rank(h, dt, A, m, n, lda, tol, J, &kout));
+  }
   *k = kout;
   return CURID_OK;
 }
@@ -781,11 +843,18 @@ curid_status curid_set_workspace(curid_handle* handle, void* ptr, size_t bytes) 
 curid_status curid_workspace_size(curid_handle* handle, curid_dtype dtype, int64_t m, int64_t n,
                                   int k, curid_sketch sk, size_t* bytes) {
   if (!handle || !bytes) return CURID_INVALID_ARG;
-  // adaptive rank (k == 0, deterministic): room for every rank up to min(m, n);
-  // with a sketch the rank would have to be known to size it (l = k + p)
+  // adaptive rank (k == 0): room for every rank up to min(m, n), or with a
+  // sketch for the largest sample the search may reach (l = min(m, n, 4096))
   if (k == 0 && m > 0 && n > 0) {
-    if (sk.p >= 0 || dtype == CURID_BF16) return CURID_UNSUPPORTED;
-    k = (int)std::min<int64_t>(m, n);
+    if (sk.p >= 0) {
+      if (sk.omega) return CURID_UNSUPPORTED;
+      const int64_t cap = adaptive_l_cap(m, n);
+      if (sk.p >= cap) return CURID_INVALID_ARG;
+      k = (int)(cap - sk.p);
+    } else {
+      if (dtype == CURID_BF16) return CURID_UNSUPPORTED;
+      k = (int)std::min<int64_t>(m, n);
+    }
   }
   Dims d;
   int dummy = 1;
@@ -943,7 +1012,7 @@ curid_status curid_cpqr(curid_handle* handle, curid_dtype dtype, const void* Y, 
 curid_status curid_id_col(curid_handle* handle, curid_dtype dtype, const void* A, int64_t m,
                           int64_t n, int64_t lda, int k, double tol, curid_sketch sk, int32_t* J,
                           void* T, int64_t ldt) {
-  CURID_TRY(resolve_rank(handle, dtype, A, m, n, lda, &k, tol, sk, J));
+  CURID_TRY(resolve_rank(handle, dtype, A, m, n, lda, &k, tol, &sk, J));
   if (k == 0 && tol > 0) return CURID_OK;
   Dims d;
   CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d));
@@ -993,7 +1062,7 @@ curid_status curid_id_row(curid_handle* handle, curid_dtype dtype, const void* A
 curid_status curid_tsid(curid_handle* handle, curid_dtype dtype, const void* A, int64_t m,
                         int64_t n, int64_t lda, int k, double tol, curid_sketch sk, int32_t* J,
                         void* T, int64_t ldt, int32_t* I, void* TW, int64_t ldtw) {
-  CURID_TRY(resolve_rank(handle, dtype, A, m, n, lda, &k, tol, sk, J));
+  CURID_TRY(resolve_rank(handle, dtype, A, m, n, lda, &k, tol, &sk, J));
   if (k == 0 && tol > 0) return rank_zero_rows(handle, I, m);
   Dims d;
   CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d));
@@ -1014,7 +1083,7 @@ curid_status curid_cur(curid_handle* handle, curid_dtype dtype, const void* A, i
                        int64_t n, int64_t lda, int k, double tol, curid_sketch sk, int32_t* J,
                        int32_t* I, double* U, void* C, void* R, void* T, int64_t ldt, void* TW,
                        int64_t ldtw) {
-  CURID_TRY(resolve_rank(handle, dtype, A, m, n, lda, &k, tol, sk, J));
+  CURID_TRY(resolve_rank(handle, dtype, A, m, n, lda, &k, tol, &sk, J));
   if (k == 0 && tol > 0) return rank_zero_rows(handle, I, m);
   Dims d;
   CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d));
@@ -1035,7 +1104,7 @@ curid_status curid_cur_corrected(curid_handle* handle, curid_dtype dtype, const 
                                  int64_t m, int64_t n, int64_t lda, int k, double tol,
                                  curid_sketch sk, int32_t* J, int32_t* I, double* U, void* C,
                                  void* R, void* T, int64_t ldt, void* TW, int64_t ldtw) {
-  CURID_TRY(resolve_rank(handle, dtype, A, m, n, lda, &k, tol, sk, J));
+  CURID_TRY(resolve_rank(handle, dtype, A, m, n, lda, &k, tol, &sk, J));
   if (k == 0 && tol > 0) return rank_zero_rows(handle, I, m);
   Dims d;
   CURID_TRY(check_common(handle, dtype, A, m, n, lda, k, tol, sk, &d));

@@ -444,6 +444,8 @@ def test_adaptive_rank_zero_and_unsupported():
     r = curid.cur(Z, 0, tol=1e-8)
     assert r.k == 0 and list(npi(r.J)) == list(range(50)) and list(npi(r.I)) == list(range(60))
     A = cuda(syn.spectrum_matrix(200, 150, syn.exp_decay(150, 8.0), 24))
+    # with a sketch the rank is searched (tests/test_gpu_adaptive_sketch.py);
+    # BF16 storage has no deterministic method to adapt
     with pytest.raises(curid.CuridError) as e:
-        curid.cur(A, 0, p=10, tol=1e-6, seed=3)
+        curid.cur(A.to(torch.bfloat16), 0, tol=1e-6)
     assert e.value.status == 8

@@ -457,3 +457,38 @@ def test_tikhonov_t_normal_equations_and_shrinkage():
         np.testing.assert_allclose(lhs, S11.T @ S12, rtol=0, atol=1e-10 * np.abs(S11.T @ S12).max())
         norms.append(np.linalg.norm(T))
     assert all(a > b for a, b in zip(norms, norms[1:]))
+
+
+# --- adaptive rank with a sketch -------------------------------------------------
+
+def test_randomized_adaptive_exact_rank():
+    """An exact rank-r matrix: every sample with more than r rows has rank r,
+    its residual after r steps is rounding, so the search stops at k = r (in
+    the first sample that leaves l - p > r)."""
+    m, n, r, p = 500, 400, 70, 10
+    rng = np.random.default_rng(101)
+    A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n))
+    Om = rng.standard_normal((512, m))
+    k, l, Y = O.randomized_rank_adaptive(A, Om, 1e-10, p)
+    assert k == r and l == 128  # 64 - 10 < 70 <= 128 - 10
+
+
+def test_randomized_adaptive_stop_is_minimal():
+    """The rank returned is the smallest j whose sample residual meets the
+    tolerance: the residual of the first k - 1 pivots does not, that of k
+    does, both measured by an independent projection of the sample onto the
+    span of the chosen columns."""
+    m, n, p = 600, 450, 10
+    A = f64(syn.spectrum_matrix(m, n, syn.exp_decay(n, 6.0), 102, torch.float64))
+    Om = np.random.default_rng(103).standard_normal((600, m))
+    tol = 1e-5
+    k, l, Y = O.randomized_rank_adaptive(A, Om, tol, p)
+    assert 0 < k < l - p
+    J = O.cpqr(Y, k=k).J
+
+    def resid(j):
+        if j == 0:
+            return fro(Y)
+        Q, _ = np.linalg.qr(Y[:, J[:j]])
+        return fro(Y - Q @ (Q.T @ Y))
+    assert resid(k) <= tol * fro(Y) < resid(k - 1)
