@@ -97,9 +97,10 @@ curid_status curid_set_workspace(curid_handle* handle, void* ptr, size_t bytes);
 
 /* Workspace bytes needed by curid_cur / curid_tsid / curid_id_col /
  * curid_id_row for an m x n matrix of dtype `dtype` at rank k with sketch
- * parameters `sk`.  k = 0 asks for the adaptive-rank size (every rank up to
- * min(m, n)); it needs sk.p < 0 and an FP32/FP64 dtype, else
- * CURID_UNSUPPORTED, as the compute calls answer.  Host-only. */
+ * parameters `sk`.  k = 0 asks for the adaptive-rank size: every rank up to
+ * min(m, n) for the deterministic method (sk.p < 0, FP32/FP64), or the
+ * largest sample the randomized search may reach, l = min(m, n, 4096)
+ * (sk.p >= 0, sk.omega NULL; else CURID_UNSUPPORTED).  Host-only. */
 curid_status curid_workspace_size(curid_handle* handle, curid_dtype dtype,
                                   int64_t m, int64_t n,
                                   int k, curid_sketch sk, size_t* bytes);
@@ -259,8 +260,17 @@ curid_status curid_cpqr_static(void* stream, curid_dtype dtype,
  * with the caller's ldt / ldtw, U (k_out x k_out) and C (m x k_out) packed
  * with leading dimension k_out, R with leading dimension n.  k_out == 0
  * (the tolerance met with no column, e.g. A = 0): J and I ascending, nothing
- * else written.  The randomized method needs k for l = k + p and returns
- * CURID_UNSUPPORTED for k == 0, as does curid_id_row.
+ * else written.  With a sketch (p >= 0) the sample size l = k + p depends
+ * on the rank, so it is searched: l = max(64, p + 1), doubling up to
+ * min(m, n, 4096); each sample Y = Omega_l A (A^* A)^q (Omega from
+ * sk.seed, whose first rows do not depend on l; sk.omega must be NULL, else
+ * CURID_UNSUPPORTED) is factored by a CPQR of at most l - p steps with the
+ * stop ||Y - Q_j Q_j^T Y||_F <= tol ||Y||_F; the first stop before l - p
+ * steps gives the rank, which is then decomposed with p' = l - k on the same
+ * sample (at the cap, k = l - p).  The test is on the sample: for q = 0 its
+ * squared residual ratio estimates A's without bias; power steps make it
+ * optimistic.  One synchronisation per sample size.  curid_id_row answers
+ * CURID_UNSUPPORTED for k == 0.
  *
  * Order limits: the k x k triangular solves (T, the row ID, U) and the
  * l x l Gram factorisations between power steps (q >= 1, l = k + p) run in
