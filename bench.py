@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only-form", choices=["adjoint", "batched", "mixed", "srft"], default=None,
+    ap.add_argument("--only-form", choices=["adjoint", "batched", "mixed", "srft", "sparse"], default=None,
                     help="run only this form's measurement and print its JSON")
     ap.add_argument("--small", action="store_true",
                     help="with --only-form: profiling sizes (256 blocks; BF16 8192^2, q = 1)")
@@ -317,7 +317,8 @@ def run_ours(args, ws, rank, local):
     forms = None
     if rank == 0 and ws == 1 and not args.no_forms:
         forms = {"adjoint": measure_adjoint(dev), "batched": measure_batched(dev),
-                 "mixed": measure_mixed(dev), "srft": measure_srft(dev)}
+                 "mixed": measure_mixed(dev), "srft": measure_srft(dev),
+                 "sparse": measure_sparse(dev)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -567,6 +568,53 @@ def measure_srft(dev, steps=10, m=M, n=N, k=K):
     return res
 
 
+def measure_sparse(dev, steps=5, m=300000, n=300, k=40, p=10, q=2):
+    """Sparse input (Section 1's case for CUR): a sum of 300 sparse
+    non-negative rank-one terms shaped like A_1 of Section 6 (300000 x 300,
+    about 1.07M stored entries, float32), randomized CUR-ID with k = 40,
+    p = 10, q = 2 through the sparse path, against the dense path (TF32
+    tensor-core products) on the same values.  Errors ||A - CUR||_F / ||A||_F
+    in float64 on the GPU."""
+    import paper_1412_8447_gb300 as curid
+    import synthetic as syn
+    As = syn.sparse_rank_sum(m, n, syn.a1_coeffs(), BASE_SEED + 5)
+    A = syn.to_torch_csr(As, torch.float32, dev)
+    Ad = torch.tensor(As.toarray(), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def err(r):
+        X = Ad.double()
+        D = X - (r.C.double() @ r.U) @ r.R.double()
+        return float(torch.linalg.norm(D) / torch.linalg.norm(X))
+
+    res = {"workload": f"randomized CUR-ID of a sparse A {m}x{n} (sum of 300 sparse rank-one "
+                       f"terms, {As.nnz} stored entries), k = {k}, p = {p}, q = {q}",
+           "unit": "decompositions/s"}
+    runs = (("sparse", lambda i, out: curid.cur_sparse(A, k, p, q=q, seed=9000 + i, out=out,
+                                                       check=False)),
+            ("dense_tf32", lambda i, out: curid.cur(Ad, k, p=p, q=q, seed=9000 + i, tf32=True,
+                                                    out=out, check=False)))
+    for name, fn in runs:
+        out = curid.cur_outputs(Ad, k, want_c=True, want_r=True)
+        for i in range(2):
+            fn(i, out)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for i in range(steps):
+            fn(10 + i, out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        st, _ = curid.last_status(dev.index or 0)
+        res[name] = {"value": 1e3 / ms, "ms_per_step": ms, "status": curid.STATUS_NAMES[st],
+                     "rel_err_fro": err(out)}
+    res["sparse_over_dense"] = res["sparse"]["value"] / res["dense_tf32"]["value"]
+    del A, Ad
+    torch.cuda.empty_cache()
+    return res
+
+
 def cpu_baseline(args, A, curid):
     """The FP64 oracle on the host cores, one full decomposition of the same
     workload with the Omega the device drew for seed BASE_SEED*1000."""
@@ -643,6 +691,8 @@ def main():
             r = measure_batched(dev, nb=256 if args.small else 4096)
         elif args.only_form == "srft":
             r = measure_srft(dev)
+        elif args.only_form == "sparse":
+            r = measure_sparse(dev)
         else:
             r = (measure_mixed(dev, steps=1, size=8192, q=1, with_f64=False) if args.small
                  else measure_mixed(dev))

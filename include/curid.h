@@ -336,6 +336,44 @@ curid_status curid_cur_corrected(curid_handle* handle, curid_dtype dtype,
                                  double* U, void* C, void* R, void* T,
                                  int64_t ldt, void* TW, int64_t ldtw);
 
+/* ----- sparse A ------------------------------------------------------- */
+
+/* A sparse m x n matrix (Section 1: the case CUR is made for, as C and R
+ * keep A's sparsity), given twice, in compressed rows and in compressed
+ * columns, with the same stored values and no duplicate entries.  All
+ * arrays are device memory owned by the caller; values have the dtype of
+ * the call (float32 or float64); indices 0-based.  Entries whose index is
+ * out of range are skipped by the gathers and read row 0 in the products;
+ * the pointer arrays must be non-decreasing from 0 to nnz. */
+typedef struct {
+  int64_t nnz;
+  const int64_t* row_ptr;  /* [m + 1] */
+  const int32_t* col_idx;  /* [nnz], column of each entry in row order */
+  const void* row_val;     /* [nnz] */
+  const int64_t* col_ptr;  /* [n + 1] */
+  const int32_t* row_idx;  /* [nnz], row of each entry in column order */
+  const void* col_val;     /* [nnz] */
+} curid_sparse;
+
+/* Randomized CUR-ID of a sparse A (Algorithms 3 and 4): the products of the
+ * sketch and the power steps (Omega A, Q A^T, Q A) are sparse-times-dense
+ * products (the sample operand transposed, one warp per output row
+ * gathering l-wide rows, on the CUDA cores; sk.tf32 is not used); C and R are
+ * gathered from the compressed columns and rows; the rest is the dense
+ * pipeline of curid_cur.  Fixed rank only (k >= 1, p >= 0, k + p <=
+ * min(m, n)); corrected != 0 takes U from Eq. (4.3) as curid_cur_corrected.
+ * Outputs as curid_cur: J, I, U (float64), optional dense C (m x k) and
+ * R (k x n), T, TW.  Workspace: curid_sparse_workspace_size. */
+curid_status curid_sparse_workspace_size(curid_handle* handle, curid_dtype dtype,
+                                         int64_t m, int64_t n, int k,
+                                         curid_sketch sk, size_t* bytes);
+curid_status curid_cur_sparse(curid_handle* handle, curid_dtype dtype,
+                              int64_t m, int64_t n, const curid_sparse* A,
+                              int k, curid_sketch sk, int corrected,
+                              int32_t* J, int32_t* I, double* U, void* C,
+                              void* R, void* T, int64_t ldt, void* TW,
+                              int64_t ldtw);
+
 /* ----- adjoint with frozen skeletons ----------------------------------- */
 
 /* Reverse-mode derivative of the deterministic CUR-ID (p < 0) with the index

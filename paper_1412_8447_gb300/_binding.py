@@ -34,6 +34,13 @@ class Sketch(ctypes.Structure):
                 ("omega", ctypes.c_void_p), ("tf32", ctypes.c_int)]
 
 
+class Sparse(ctypes.Structure):
+    _fields_ = [("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("row_val", ctypes.c_void_p),
+                ("col_ptr", ctypes.c_void_p), ("row_idx", ctypes.c_void_p),
+                ("col_val", ctypes.c_void_p)]
+
+
 _vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
 SIGNATURES = {
     "curid_create": [ctypes.POINTER(_vp), _int],
@@ -60,6 +67,10 @@ SIGNATURES = {
     "curid_interp_tikhonov_workspace_size": [_vp, _int, _i64, _int,
                                              ctypes.POINTER(ctypes.c_size_t)],
     "curid_interp_tikhonov": [_vp, _int, _vp, _i64, _vp, _i64, _int, _dbl, _vp, _i64],
+    "curid_sparse_workspace_size": [_vp, _int, _i64, _i64, _int, Sketch,
+                                    ctypes.POINTER(ctypes.c_size_t)],
+    "curid_cur_sparse": [_vp, _int, _i64, _i64, ctypes.POINTER(Sparse), _int, Sketch, _int, _vp,
+                         _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64],
     "curid_cur_corrected": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _vp,
                             _vp, _vp, _vp, _i64, _vp, _i64],
     "curid_cur_adjoint_workspace_size": [_vp, _int, _i64, _i64, _int,
@@ -469,6 +480,62 @@ def cur(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, want_c=False, want_r=Fa
         if want_tw:
             res.TW = o.TW[:kk, :m - kk]
     return res
+
+def sparse_operand(A):
+    """The two compressed forms curid_cur_sparse reads, from a torch sparse
+    CSR tensor on a CUDA device: its rows, and its columns from torch's
+    CSR -> CSC conversion (indices as int32, pointers as int64).  Returns
+    (tensors to keep alive, the ctypes struct)."""
+    if A.layout != torch.sparse_csr or not A.is_cuda:
+        raise ValueError("expected a torch sparse CSR tensor on a CUDA device")
+    crow = A.crow_indices().to(torch.int64).contiguous()
+    col = A.col_indices().to(torch.int32).contiguous()
+    val = A.values().contiguous()
+    Ac = A.to_sparse_csc()
+    ccol = Ac.ccol_indices().to(torch.int64).contiguous()
+    row = Ac.row_indices().to(torch.int32).contiguous()
+    cval = Ac.values().contiguous()
+    keep = (crow, col, val, ccol, row, cval)
+    st = Sparse(int(val.numel()), _ptr(crow), _ptr(col), _ptr(val), _ptr(ccol), _ptr(row),
+                _ptr(cval))
+    return keep, st
+
+
+def cur_sparse(A, k, p, q=0, seed=0, omega=None, corrected=False, want_c=False, want_r=False,
+               want_t=False, want_tw=False, out=None, check=True):
+    """Randomized CUR-ID of a sparse A (torch sparse CSR tensor, float32 or
+    float64, on a CUDA device) through curid_cur_sparse; outputs as ``cur``
+    (C and R dense)."""
+    keep, st = sparse_operand(A)
+    m, n = A.shape
+    dev = A.device.index if A.device.index is not None else torch.cuda.current_device()
+    h = handle(dev)
+    dt = _dtype_code(A.dtype)
+    sk = _sketch(p, q, seed, omega, False)
+    b = ctypes.c_size_t(0)
+    _check(h.lib.curid_sparse_workspace_size(h.h, dt, m, n, k, sk, ctypes.byref(b)),
+           "curid_sparse_workspace_size")
+    h.prepare(b.value)
+    if out is None:
+        out = Result(
+            J=torch.empty(n, dtype=torch.int32, device=A.device),
+            I=torch.empty(m, dtype=torch.int32, device=A.device),
+            U=torch.empty((k, k), dtype=torch.float64, device=A.device),
+            C=torch.empty((m, k), dtype=A.dtype, device=A.device) if want_c else None,
+            R=torch.empty((k, n), dtype=A.dtype, device=A.device) if want_r else None,
+            T=torch.empty((k, max(n - k, 1)), dtype=A.dtype, device=A.device) if want_t else None,
+            TW=torch.empty((k, max(m - k, 1)), dtype=A.dtype, device=A.device)
+            if want_tw else None)
+    o = out
+    _check(h.lib.curid_cur_sparse(h.h, dt, m, n, ctypes.byref(st), k, sk, 1 if corrected else 0,
+                                  _ptr(o.J), _ptr(o.I), _ptr(o.U), _ptr(o.C), _ptr(o.R),
+                                  _ptr(o.T), o.T.stride(0) if o.T is not None else 0,
+                                  _ptr(o.TW), o.TW.stride(0) if o.TW is not None else 0),
+           "curid_cur_sparse")
+    res = _finish(h, o, check, "curid_cur_sparse")
+    res._keep = keep  # the compressed forms stay alive until the work is done
+    return res
+
 
 def cur_adjoint(A, J, I, T, k, Cbar=None, Ubar=None, Rbar=None, out=None, check=True):
     """Gradient with respect to A of <Cbar, C> + <Ubar, U> + <Rbar, R> for the

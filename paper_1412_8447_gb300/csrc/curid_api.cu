@@ -112,6 +112,10 @@ struct Plan {
   size_t xsplit_elems = 0;
   double* S11d = nullptr;  // k x k
   double* S12d = nullptr;  // k x (n - k)
+  // sparse A: the transposed sample operand and the transposed product
+  const SparseA* sp = nullptr;
+  real* spX = nullptr;     // max(m, n) x l
+  real* spO = nullptr;     // max(m, n) x l
   size_t bytes = 0;
 };
 
@@ -124,6 +128,7 @@ struct Dims {
   int q;
   bool tf32 = false;
   bool bf16 = false;  // A stored as bfloat16 (float32 pipeline, BF16 tensor-core products)
+  const SparseA* sp = nullptr;  // A sparse (randomized method only)
 };
 
 template <typename real>
@@ -133,6 +138,11 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
   const int64_t m = d.m, n = d.n;
   const int k = d.k, l = d.l;
   P->status = cv.take<StatusBlock>(1);
+  P->sp = d.sp;
+  if (d.sp) {
+    P->spX = cv.take<real>((size_t)std::max(m, n) * l);
+    P->spO = cv.take<real>((size_t)std::max(m, n) * l);
+  }
   size_t part = 0;
   auto upd = [&](int64_t M, int64_t N, int64_t K) {
     part = std::max(part, gemm_partial_elems<real>(M, N, K, ctx.num_sms));
@@ -232,6 +242,20 @@ template <typename real>
 curid_status a_product(const Ctx& ctx, bool tf32, bool bf16, bool tb, int64_t M, int64_t N,
                        int64_t K, const real* X, int64_t ldx, const void* A, int64_t lda,
                        real* out, int64_t ldo, const Plan<real>& P) {
+  if (P.sp) {
+    // sparse A: out = X A = ((X A)^T)^T with (X A)^T from the compressed
+    // columns; out = X A^T from the compressed rows; X^T is the gathered
+    // operand (K x M) and the product comes out transposed (N x M)
+    const SparseA& S = *P.sp;
+    CURID_TRY(transpose2d<real>(ctx, X, ldx, P.spX, M, M, K));
+    if (!tb)
+      CURID_TRY(spmm_rows<real>(ctx, N, S.col_ptr, S.row_idx, static_cast<const real*>(S.col_val),
+                                S.nnz, K, P.spX, M, M, P.spO, M));
+    else
+      CURID_TRY(spmm_rows<real>(ctx, N, S.row_ptr, S.col_idx, static_cast<const real*>(S.row_val),
+                                S.nnz, K, P.spX, M, M, P.spO, M));
+    return transpose2d<real>(ctx, P.spO, M, out, ldo, N, M);
+  }
   if constexpr (sizeof(real) == 4) {
     if (bf16)
       return gemm_bf16(ctx, tb, M, N, K, X, ldx, A, lda, out, ldo, P.xsplit, P.xsplit_elems);
@@ -428,7 +452,11 @@ curid_status run(curid_handle* h, Op op, const void* Araw, const Dims& d, double
               ctx, Ab, m, lda, o.J, k, static_cast<__nv_bfloat16*>(o.C), k, false)));
       }
     }
-    if (!d.bf16) {
+    if (d.sp) {
+      CURID_TRY(scatter_lists<real>(ctx, o.J, k, n, d.sp->col_ptr, d.sp->row_idx,
+                                    static_cast<const real*>(d.sp->col_val), m, P.Ct, m,
+                                    static_cast<real*>(o.C), k));
+    } else if (!d.bf16) {
       CURID_TRY(gather_cols<real>(ctx, A, m, lda, o.J, k, P.Ct, m, true));
       if (o.C)
         CURID_TRY(gather_cols<real>(ctx, A, m, lda, o.J, k, static_cast<real*>(o.C), k, false));
@@ -464,7 +492,12 @@ curid_status run(curid_handle* h, Op op, const void* Araw, const Dims& d, double
                                                      static_cast<__nv_bfloat16*>(o.R), n, k, n)));
       }
     }
-    if (!d.bf16) {
+    if (d.sp) {
+      CURID_TRY(scatter_lists<real>(ctx, I, k, m, d.sp->row_ptr, d.sp->col_idx,
+                                    static_cast<const real*>(d.sp->row_val), n, P.R, n, nullptr,
+                                    0));
+      if (o.R) CURID_TRY(copy2d<real>(ctx, P.R, n, static_cast<real*>(o.R), n, k, n));
+    } else if (!d.bf16) {
       CURID_TRY(gather_rows<real>(ctx, A, m, n, lda, I, k, P.R, n));
       if (o.R) CURID_TRY(copy2d<real>(ctx, P.R, n, static_cast<real*>(o.R), n, k, n));
     }
@@ -499,7 +532,7 @@ curid_status run(curid_handle* h, Op op, const void* Araw, const Dims& d, double
     // A split hi + lo) summed.
     bool split_done = false;
     if constexpr (sizeof(real) == 4) {
-      if (sk.tf32 && !d.bf16) {
+      if (sk.tf32 && !d.bf16 && !d.sp) {
         CURID_TRY(split_tf32(ctx, qc, ldx, qt, ldx, k, m));
         CURID_TRY(a_product<real>(ctx, true, false, false, k, n, m, qc, ldx, Araw, lda, P.Bq,
                                   pad4(n), P));
@@ -1118,6 +1151,74 @@ curid_status curid_cur_corrected(curid_handle* handle, curid_dtype dtype, const 
                          handle->ws_bytes);
     return run<float>(handle, Op::CurCorrected, (const float*)A, d, 0.0, sk, o, handle->ws,
                       handle->ws_bytes);
+  });
+}
+
+// Sparse A: Dims of the randomized CUR-ID (fixed rank, p >= 0; the
+// products run on the CUDA cores, so the tf32 flag is not used).
+static curid_status sparse_dims(curid_handle* h, curid_dtype dt, int64_t m, int64_t n,
+                                const curid_sparse* A, int k, const curid_sketch& sk,
+                                SparseA* sa, Dims* d) {
+  if (!h || !A || (dt != CURID_F32 && dt != CURID_F64)) return CURID_INVALID_ARG;
+  if (m <= 0 || n <= 0 || m > INT32_MAX || n > INT32_MAX || A->nnz < 0) return CURID_INVALID_ARG;
+  if (!A->row_ptr || !A->col_ptr || (A->nnz > 0 && (!A->col_idx || !A->row_val || !A->row_idx ||
+                                                    !A->col_val)))
+    return CURID_INVALID_ARG;
+  if (sk.p < 0 || sk.q < 0 || k < 1 || k + (int64_t)sk.p > std::min(m, n))
+    return CURID_INVALID_ARG;
+  *sa = SparseA{A->nnz, A->row_ptr, A->col_idx, A->row_val, A->col_ptr, A->row_idx, A->col_val};
+  d->m = m;
+  d->n = n;
+  d->lda = n;
+  d->k = k;
+  d->l = k + sk.p;
+  d->randomized = true;
+  d->q = sk.q;
+  d->tf32 = false;
+  d->bf16 = false;
+  d->sp = sa;
+  return CURID_OK;
+}
+
+curid_status curid_sparse_workspace_size(curid_handle* handle, curid_dtype dtype, int64_t m,
+                                         int64_t n, int k, curid_sketch sk, size_t* bytes) {
+  if (!bytes) return CURID_INVALID_ARG;
+  const int64_t ptr0 = 0;
+  curid_sparse dummy{0, &ptr0, nullptr, nullptr, &ptr0, nullptr, nullptr};
+  SparseA sa;
+  Dims d;
+  CURID_TRY(sparse_dims(handle, dtype, m, n, &dummy, k, sk, &sa, &d));
+  Ctx ctx{nullptr, handle->num_sms, handle->smem_optin, nullptr};
+  const bool gen = sk.omega == nullptr;
+  if (dtype == CURID_F64) {
+    Plan<double> P;
+    CURID_TRY(make_plan<double>(ctx, Op::CurCorrected, d, gen, true, nullptr, &P));
+    *bytes = P.bytes;
+  } else {
+    Plan<float> P;
+    CURID_TRY(make_plan<float>(ctx, Op::CurCorrected, d, gen, true, nullptr, &P));
+    *bytes = P.bytes;
+  }
+  return CURID_OK;
+}
+
+curid_status curid_cur_sparse(curid_handle* handle, curid_dtype dtype, int64_t m, int64_t n,
+                              const curid_sparse* A, int k, curid_sketch sk, int corrected,
+                              int32_t* J, int32_t* I, double* U, void* C, void* R, void* T,
+                              int64_t ldt, void* TW, int64_t ldtw) {
+  SparseA sa;
+  Dims d;
+  CURID_TRY(sparse_dims(handle, dtype, m, n, A, k, sk, &sa, &d));
+  if (!J || !I || !U) return CURID_INVALID_ARG;
+  if (T && ldt < std::max<int64_t>(1, n - k)) return CURID_INVALID_ARG;
+  if (TW && ldtw < std::max<int64_t>(1, m - k)) return CURID_INVALID_ARG;
+  sk.tf32 = 0;
+  Outputs o{J, T, ldt, I, TW, ldtw, U, C, R};
+  const Op op = corrected ? Op::CurCorrected : Op::Cur;
+  return dispatch(handle, [&]() -> curid_status {
+    if (dtype == CURID_F64)
+      return run<double>(handle, op, nullptr, d, 0.0, sk, o, handle->ws, handle->ws_bytes);
+    return run<float>(handle, op, nullptr, d, 0.0, sk, o, handle->ws, handle->ws_bytes);
   });
 }
 

@@ -167,6 +167,32 @@ template <typename real>
 curid_status add_transpose(const Ctx& ctx, const real* src, int64_t lds, real* dst,
                            int64_t ldd, int64_t rows, int64_t cols);
 
+// ---- sparse A (sparse.cu) ---------------------------------------------------
+// A m x n with its stored entries in compressed rows (row_ptr [m + 1],
+// col_idx, row_val) and compressed columns (col_ptr [n + 1], row_idx,
+// col_val): the same values twice, no duplicate entries.
+struct SparseA {
+  int64_t nnz;
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  const void* row_val;
+  const int64_t* col_ptr;
+  const int32_t* row_idx;
+  const void* col_val;
+};
+// out (R x L, ldo) = for each list r: sum of val[e] * in[idx[e], :] over its
+// entries (nnz in all lists); in is nrows_in x L (ldi).
+template <typename real>
+curid_status spmm_rows(const Ctx& ctx, int64_t R, const int64_t* ptr, const int32_t* idx,
+                       const real* val, int64_t nnz, int64_t nrows_in, const real* in,
+                       int64_t ldi, int64_t L, real* out, int64_t ldo);
+// dst (k x cols, ldd) row t = list sel[t] scattered densely (zeros elsewhere);
+// dst2 (cols x k, ld2), if non-null, the same as columns.
+template <typename real>
+curid_status scatter_lists(const Ctx& ctx, const int32_t* sel, int k, int64_t lists,
+                           const int64_t* ptr, const int32_t* idx, const real* val, int64_t cols,
+                           real* dst, int64_t ldd, real* dst2, int64_t ld2);
+
 // ---- random numbers (philox.cu) --------------------------------------------
 template <typename real>
 curid_status gaussian_fill(const Ctx& ctx, int64_t rows, int64_t cols, uint64_t seed, real* out,

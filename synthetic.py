@@ -186,3 +186,46 @@ def workload_rand_f32(seed=BASE_SEED + 1, device="cpu", m=8000, n=6000,
     Om = gaussian(k + p, m, seed + 1000, torch.float32, device)
     return dict(A=A, Omega=Om, k=k, p=p, q=q,
                 name=f"rand_f32_{m}x{n}_k{k}_p{p}_q{q}")
+
+
+def sparse_rank_sum(m, n, coeffs, seed, dx=0.002, dy=0.02):
+    """Sum of sparse rank-one terms, sum_j coeffs[j] x_j y_j^T, with x_j (m)
+    and y_j (n) sparse and non-negative: round(dx m) and round(dy n) entries
+    (at least one) at distinct random positions, values uniform on (0, 1].
+    The shape of the test matrices A_1, A_2 of Section 6 (m = 300000,
+    n = 300, 300 terms; the paper does not give the densities).  Returns a
+    scipy.sparse CSR matrix (float64, sorted indices, duplicates summed)."""
+    import scipy.sparse
+    g = rng(seed)
+    nx = max(1, int(round(dx * m)))
+    ny = max(1, int(round(dy * n)))
+    rows, cols, vals = [], [], []
+    for c in coeffs:
+        xi = g.choice(m, nx, replace=False)
+        xv = 1.0 - g.random(nx)
+        yi = g.choice(n, ny, replace=False)
+        yv = 1.0 - g.random(ny)
+        rows.append(np.repeat(xi, ny))
+        cols.append(np.tile(yi, nx))
+        vals.append(c * np.outer(xv, yv).ravel())
+    A = scipy.sparse.coo_matrix((np.concatenate(vals), (np.concatenate(rows),
+                                                        np.concatenate(cols))), shape=(m, n))
+    A = A.tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    return A
+
+
+def a1_coeffs(terms=300, big=2.0, lead=10):
+    """Coefficients of A_1 (big = 2) and A_2 (big = 1000) in Section 6:
+    big / j for j <= lead, 1 / j after."""
+    j = np.arange(1, terms + 1, dtype=np.float64)
+    return np.where(j <= lead, big / j, 1.0 / j)
+
+
+def to_torch_csr(A, dtype=torch.float64, device="cpu"):
+    """scipy CSR -> torch sparse CSR tensor (values cast once to dtype)."""
+    return torch.sparse_csr_tensor(torch.from_numpy(A.indptr.astype(np.int64)),
+                                   torch.from_numpy(A.indices.astype(np.int64)),
+                                   torch.from_numpy(A.data).to(dtype), size=A.shape,
+                                   device=device, check_invariants=True)
