@@ -219,6 +219,24 @@ curid_status curid_interp_tikhonov(curid_handle* handle, curid_dtype dtype,
                                    const int32_t* J, int64_t n, int k,
                                    double lam, void* T, int64_t ldt);
 
+/* Truncated-SVD interpolation matrix (Section 4.1: a stabilised
+ * pseudo-inverse of S11 from its SVD with the small singular values
+ * dropped): S11 = U diag(sigma) V^T, T = V diag(1/sigma_i : sigma_i >
+ * rtol sigma_1, else 0) U^T S12, 0 <= rtol < 1.  Inputs and output as
+ * curid_interp_tikhonov (S and J from curid_cpqr; T k x (n-k), ldt).  The
+ * SVD is a one-sided Jacobi iteration (cyclic round-robin pairs, one
+ * cooperative launch, at most 40 sweeps), k <= 256.  Scratch from the
+ * handle's workspace (curid_interp_tsvd_workspace_size); CURID_F32 or
+ * CURID_F64.  Errors: INVALID_ARG (null pointers, rtol outside [0, 1), bad
+ * sizes), NO_WORKSPACE, UNSUPPORTED (k > 256 or another dtype). */
+curid_status curid_interp_tsvd_workspace_size(curid_handle* handle,
+                                              curid_dtype dtype, int64_t n,
+                                              int k, size_t* bytes);
+curid_status curid_interp_tsvd(curid_handle* handle, curid_dtype dtype,
+                               const void* S, int64_t lds, const int32_t* J,
+                               int64_t n, int k, double rtol, void* T,
+                               int64_t ldt);
+
 /* Truncated CPQR exactly as curid_cpqr, for callers that cannot allocate
  * device memory when they factor: a service that reserves all of its GPU
  * memory at start-up and must not fail on an allocation later, code running

@@ -22,6 +22,7 @@ import scipy.linalg
 
 __all__ = [
     "as_f64", "CPQR", "cpqr", "interpolation_matrix", "interpolation_matrix_tikhonov",
+    "interpolation_matrix_tsvd",
     "vstar", "wmat",
     "IDResult", "id_col", "id_row", "TSIDResult", "tsid", "CURResult",
     "cur_middle", "cur", "cur_middle_corrected", "cur_corrected", "randomized_cur_corrected",
@@ -181,6 +182,17 @@ def interpolation_matrix_tikhonov(S1, k, lam):
     W = np.vstack([S1[:k, :k], lam * np.eye(k)])
     B = np.vstack([S1[:k, k:], np.zeros((k, n - k))])
     return np.linalg.lstsq(W, B, rcond=None)[0]
+
+
+def interpolation_matrix_tsvd(S1, k, rtol):
+    """T from the truncated SVD of S11 (Section 4.1): S11 = U diag(s) V^T
+    (library SVD as the single step), singular values s_i <= rtol * s_1
+    dropped, T = V diag(1 / s_i) U^T S12 over the kept ones.  S1 is k x n in
+    pivot order."""
+    S1 = np.asarray(S1, dtype=np.float64)
+    U, sv, Vt = np.linalg.svd(S1[:k, :k])
+    keep = sv > rtol * sv[0] if sv.size and sv[0] > 0 else np.zeros(sv.size, dtype=bool)
+    return Vt[keep].T @ np.diag(1.0 / sv[keep]) @ U[:, keep].T @ S1[:k, k:]
 
 
 def vstar(J, T, n):

@@ -67,6 +67,8 @@ SIGNATURES = {
     "curid_interp_tikhonov_workspace_size": [_vp, _int, _i64, _int,
                                              ctypes.POINTER(ctypes.c_size_t)],
     "curid_interp_tikhonov": [_vp, _int, _vp, _i64, _vp, _i64, _int, _dbl, _vp, _i64],
+    "curid_interp_tsvd_workspace_size": [_vp, _int, _i64, _int, ctypes.POINTER(ctypes.c_size_t)],
+    "curid_interp_tsvd": [_vp, _int, _vp, _i64, _vp, _i64, _int, _dbl, _vp, _i64],
     "curid_sparse_workspace_size": [_vp, _int, _i64, _i64, _int, Sketch,
                                     ctypes.POINTER(ctypes.c_size_t)],
     "curid_cur_sparse": [_vp, _int, _i64, _i64, ctypes.POINTER(Sparse), _int, Sketch, _int, _vp,
@@ -328,10 +330,7 @@ def cpqr(Y, k=0, tol=0.0, check=True):
     return _finish(h, Result(J=J, S=S), check, "curid_cpqr")
 
 
-def interp_tikhonov(S, J, k, lam):
-    """Regularised T = argmin ||S11 T - S12||^2 + lam^2 ||T||^2 (Section 4.1
-    with a Tikhonov term) from the S (k x n, original column order) and J
-    that ``cpqr`` returns; T is k x (n - k), columns following J[k:]."""
+def _interp(kind, S, J, k, param):
     S = _mat(S)
     dev = _dev(S)
     h = handle(dev)
@@ -339,15 +338,28 @@ def interp_tikhonov(S, J, k, lam):
     if kk < k:
         raise ValueError("S has fewer than k rows")
     b = ctypes.c_size_t(0)
-    _check(h.lib.curid_interp_tikhonov_workspace_size(h.h, _dtype_code(S.dtype), n, k,
-                                                      ctypes.byref(b)),
-           "curid_interp_tikhonov_workspace_size")
+    ws = getattr(h.lib, f"curid_interp_{kind}_workspace_size")
+    _check(ws(h.h, _dtype_code(S.dtype), n, k, ctypes.byref(b)),
+           f"curid_interp_{kind}_workspace_size")
     h.prepare(b.value)
     T = torch.empty((k, max(n - k, 1)), dtype=S.dtype, device=S.device)
-    _check(h.lib.curid_interp_tikhonov(h.h, _dtype_code(S.dtype), _ptr(S), S.stride(0),
-                                       _ptr(J.contiguous()), n, k, float(lam), _ptr(T),
-                                       T.stride(0)), "curid_interp_tikhonov")
+    fn = getattr(h.lib, f"curid_interp_{kind}")
+    _check(fn(h.h, _dtype_code(S.dtype), _ptr(S), S.stride(0), _ptr(J.contiguous()), n, k,
+              float(param), _ptr(T), T.stride(0)), f"curid_interp_{kind}")
     return T[:, :n - k]
+
+
+def interp_tsvd(S, J, k, rtol):
+    """Truncated-SVD T = V diag(1/sigma, sigma > rtol sigma_1) U^T S12
+    (Section 4.1) from the S and J that ``cpqr`` returns."""
+    return _interp("tsvd", S, J, k, rtol)
+
+
+def interp_tikhonov(S, J, k, lam):
+    """Regularised T = argmin ||S11 T - S12||^2 + lam^2 ||T||^2 (Section 4.1
+    with a Tikhonov term) from the S (k x n, original column order) and J
+    that ``cpqr`` returns; T is k x (n - k), columns following J[k:]."""
+    return _interp("tikhonov", S, J, k, lam)
 
 
 def _prep(A, k, p, q, seed, omega, tf32):

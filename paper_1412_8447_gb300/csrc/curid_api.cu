@@ -795,6 +795,69 @@ curid_status tikhonov_run(curid_handle* h, const real* S, int64_t lds, const int
   return tri_solve<real>(ctx, k, P.K, k, true, false, P.Z, n - k, T, ldt, n - k, nullptr);
 }
 
+// Truncated-SVD T (Section 4.1): S11 = U diag(sigma) V^T by one-sided
+// Jacobi, singular values below rtol * sigma_1 dropped, T = V D^+ U^T S12.
+// With the Jacobi output W^T = diag(sigma) U^T (rows), B = W^T S12 has rows
+// sigma_i u_i^T S12; scaling row i by 1 / sigma_i^2 (or 0) and multiplying by
+// V gives T.
+template <typename real>
+struct TsvdPlan {
+  StatusBlock* status = nullptr;
+  real* S11 = nullptr;   // k x k
+  real* S12 = nullptr;   // k x (n - k)
+  real* Wt = nullptr;    // k x k
+  real* Vt = nullptr;    // k x k
+  real* B = nullptr;     // k x (n - k)
+  real* f = nullptr;     // k
+  int* rot = nullptr;    // sweep counters
+  real* partial = nullptr;
+  size_t partial_cap = 0;
+  size_t bytes = 0;
+};
+
+template <typename real>
+void tsvd_plan(const Ctx& ctx, int64_t n, int k, void* base, TsvdPlan<real>* P) {
+  Carver cv(base);
+  const int64_t r = std::max<int64_t>(1, n - k);
+  P->status = cv.take<StatusBlock>(1);
+  P->S11 = cv.take<real>((size_t)k * k);
+  P->S12 = cv.take<real>((size_t)k * r);
+  P->Wt = cv.take<real>((size_t)k * k);
+  P->Vt = cv.take<real>((size_t)k * k);
+  P->B = cv.take<real>((size_t)k * r);
+  P->f = cv.take<real>((size_t)k);
+  P->rot = cv.take<int>(64);
+  const size_t part = gemm_partial_elems<real>(k, r, k, ctx.num_sms);
+  P->partial_cap = part;
+  P->partial = part ? cv.take<real>(part) : nullptr;
+  P->bytes = cv.used + 256;
+}
+
+template <typename real>
+curid_status tsvd_run(curid_handle* h, const real* S, int64_t lds, const int32_t* J, int64_t n,
+                      int k, double rtol, real* T, int64_t ldt) {
+  Ctx ctx = make_ctx(h);
+  if (!jacobi_svd_fits<real>(k)) return CURID_UNSUPPORTED;
+  TsvdPlan<real> P;
+  tsvd_plan<real>(ctx, n, k, nullptr, &P);
+  if (!h->ws || P.bytes > h->ws_bytes) return CURID_NO_WORKSPACE;
+  tsvd_plan<real>(ctx, n, k, h->ws, &P);
+  ctx.status = P.status;
+  PhaseScope ps(h, CURID_PHASE_T);
+  CURID_CUDA(cudaMemsetAsync(P.status, 0, sizeof(StatusBlock), ctx.stream));
+  CURID_TRY(split_s<real>(ctx, S, lds, J, k, n, P.S11, P.S12));
+  CURID_TRY(transpose2d<real>(ctx, P.S11, k, P.Wt, k, k, k));
+  CURID_TRY(identity_fill<real>(ctx, P.Vt, k));
+  CURID_TRY(jacobi_svd<real>(ctx, k, P.Wt, P.Vt, P.rot));
+  if (n - k <= 0) return CURID_OK;
+  CURID_TRY(tsvd_filter<real>(ctx, k, P.Wt, rtol, P.f));
+  CURID_TRY(gemm<real>(ctx, false, false, k, n - k, k, real(1), P.Wt, k, P.S12, n - k, real(0),
+                       P.B, n - k, P.partial, P.partial_cap));
+  CURID_TRY(scale_rows<real>(ctx, P.B, n - k, k, n - k, P.f));
+  return gemm<real>(ctx, true, false, k, n - k, k, real(1), P.Vt, k, P.B, n - k, real(0), T, ldt,
+                    P.partial, P.partial_cap);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1219,6 +1282,41 @@ curid_status curid_cur_sparse(curid_handle* handle, curid_dtype dtype, int64_t m
     if (dtype == CURID_F64)
       return run<double>(handle, op, nullptr, d, 0.0, sk, o, handle->ws, handle->ws_bytes);
     return run<float>(handle, op, nullptr, d, 0.0, sk, o, handle->ws, handle->ws_bytes);
+  });
+}
+
+curid_status curid_interp_tsvd_workspace_size(curid_handle* handle, curid_dtype dtype, int64_t n,
+                                              int k, size_t* bytes) {
+  if (!handle || !bytes || n < 1 || k < 1 || k > n) return CURID_INVALID_ARG;
+  Ctx ctx{nullptr, handle->num_sms, handle->smem_optin, nullptr};
+  if (dtype == CURID_F64) {
+    TsvdPlan<double> P;
+    tsvd_plan<double>(ctx, n, k, nullptr, &P);
+    *bytes = P.bytes;
+  } else if (dtype == CURID_F32) {
+    TsvdPlan<float> P;
+    tsvd_plan<float>(ctx, n, k, nullptr, &P);
+    *bytes = P.bytes;
+  } else {
+    return CURID_UNSUPPORTED;
+  }
+  return CURID_OK;
+}
+
+curid_status curid_interp_tsvd(curid_handle* handle, curid_dtype dtype, const void* S,
+                               int64_t lds, const int32_t* J, int64_t n, int k, double rtol,
+                               void* T, int64_t ldt) {
+  if (!handle || !S || !J || !T || n < 1 || k < 1 || k > n || lds < n || !(rtol >= 0) ||
+      !(rtol < 1) || ldt < std::max<int64_t>(1, n - k))
+    return CURID_INVALID_ARG;
+  return dispatch(handle, [&]() -> curid_status {
+    if (dtype == CURID_F64)
+      return tsvd_run<double>(handle, static_cast<const double*>(S), lds, J, n, k, rtol,
+                              static_cast<double*>(T), ldt);
+    if (dtype == CURID_F32)
+      return tsvd_run<float>(handle, static_cast<const float*>(S), lds, J, n, k, rtol,
+                             static_cast<float*>(T), ldt);
+    return CURID_UNSUPPORTED;
   });
 }
 

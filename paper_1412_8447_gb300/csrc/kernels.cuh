@@ -167,6 +167,25 @@ template <typename real>
 curid_status add_transpose(const Ctx& ctx, const real* src, int64_t lds, real* dst,
                            int64_t ldd, int64_t rows, int64_t cols);
 
+// ---- Jacobi SVD of a k x k triangle (svd.cu) ------------------------------------
+// W^T (k x k, row i = column i of the matrix) is rotated in place into
+// U diag(sigma) (as rows), V^T (k x k, identity on entry) into V^T; k <= 256;
+// rotations: device scratch of 40 ints.
+template <typename real>
+bool jacobi_svd_fits(int k);
+template <typename real>
+curid_status jacobi_svd(const Ctx& ctx, int k, real* Wt, real* Vt, int* rotations);
+// X (k x k) = I
+template <typename real>
+curid_status identity_fill(const Ctx& ctx, real* X, int k);
+// f[i] = 1 / sigma_i^2 (sigma_i = ||row i of W^T||) above rtol * max sigma, else 0
+template <typename real>
+curid_status tsvd_filter(const Ctx& ctx, int k, const real* Wt, double rtol, real* f);
+// row r of B (rows x cols, ldb) times f[r]
+template <typename real>
+curid_status scale_rows(const Ctx& ctx, real* B, int64_t ldb, int64_t rows, int64_t cols,
+                        const real* f);
+
 // ---- sparse A (sparse.cu) ---------------------------------------------------
 // A m x n with its stored entries in compressed rows (row_ptr [m + 1],
 // col_idx, row_val) and compressed columns (col_ptr [n + 1], row_idx,

@@ -492,3 +492,43 @@ def test_randomized_adaptive_stop_is_minimal():
         Q, _ = np.linalg.qr(Y[:, J[:j]])
         return fro(Y - Q @ (Q.T @ Y))
     assert resid(k) <= tol * fro(Y) < resid(k - 1)
+
+
+# --- truncated-SVD T (Section 4.1) ------------------------------------------------
+
+def test_tsvd_t_full_rank_is_back_substitution():
+    S1 = _graded_s1(14, 50, 1e4, 11)
+    np.testing.assert_allclose(O.interpolation_matrix_tsvd(S1, 14, 1e-12),
+                               O.interpolation_matrix(S1, 14), rtol=0, atol=1e-9)
+
+
+def test_tsvd_t_drops_planted_singular_values():
+    """S11 = Q1 diag(s) Q2^T with planted s (five of them below the cut):
+    the result equals the least-squares solution restricted to the kept
+    right singular directions, computed by library lstsq on S11 Q2_keep,
+    and it is orthogonal to the dropped directions."""
+    k, n = 16, 45
+    rng = np.random.default_rng(12)
+    Q1, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    s = np.concatenate([np.logspace(0, -2, k - 5), np.logspace(-7, -9, 5)])
+    S11 = Q1 @ np.diag(s) @ Q2.T
+    S12 = rng.standard_normal((k, n - k))
+    S1 = np.hstack([S11, S12])
+    T = O.interpolation_matrix_tsvd(S1, k, 1e-5)
+    Vk = Q2[:, : k - 5]
+    Y = np.linalg.lstsq(S11 @ Vk, S12, rcond=None)[0]
+    np.testing.assert_allclose(T, Vk @ Y, rtol=0, atol=1e-9 * np.abs(T).max())
+    assert np.abs(Q2[:, k - 5:].T @ T).max() <= 1e-9 * np.abs(T).max()
+
+
+def test_tsvd_t_rank_deficient_is_minimum_norm():
+    """Exactly singular S11 (rank 9 of 12): with the zero singular values
+    dropped, T is the minimum-norm least-squares solution (library pinv)."""
+    k, n = 12, 30
+    rng = np.random.default_rng(13)
+    S11 = rng.standard_normal((k, 9)) @ rng.standard_normal((9, k))
+    S1 = np.hstack([S11, rng.standard_normal((k, n - k))])
+    T = O.interpolation_matrix_tsvd(S1, k, 1e-10)
+    np.testing.assert_allclose(T, np.linalg.pinv(S11, rcond=1e-10) @ S1[:, k:], rtol=0,
+                               atol=1e-9 * np.abs(T).max())
