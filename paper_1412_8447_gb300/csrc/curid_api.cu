@@ -167,6 +167,9 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
       for (int b = 0; b < 3; ++b) P->B[b] = cv.take<real>((size_t)l * pad4(std::max(m, n)));
       P->G = cv.take<real>((size_t)l * l);
       P->Linv = cv.take<real>((size_t)l * l);
+      if (sizeof(real) == 4 && (d.tf32 || d.bf16) && !d.sp && l > 256)
+        part = std::max(part, gemm_tf32_partial_elems(std::min<int64_t>(l, 256), l,
+                                                      std::max(m, n), ctx.num_sms));
       upd(l, l, n);
       upd(l, l, m);
       upd(l, n, l);
@@ -285,11 +288,21 @@ curid_status a_product(const Ctx& ctx, bool tf32, bool bf16, bool tb, int64_t M,
 // well-conditioned N: two passes (condition number 1 + O(u kappa_1^2),
 // kappa_1 <= 1 / sqrt(shift) after the shifted first pass).  The last orth,
 // whose Q forms the Y that is pivoted, takes all three.
+//
+// With tensor-core products (TF32, or BF16 storage of A) and samples of more
+// than 256 rows the Gram matrices go to the TF32 tensor cores too, at
+// float32 accuracy (gram_tf32), with `spare` (a free sample buffer) for the
+// TF32 part and Linv as scratch: l = 520 rows of 20000, orth 13 -> 10 ms
+// per decomposition.  At l = 210 the split and the two products cost more
+// than the one FMA product they replace (orth 0.77 -> 0.80 ms), so smaller
+// samples keep it.
 template <typename real>
 curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
-                       const Plan<real>& P, bool final_orth) {
+                       const Plan<real>& P, bool final_orth, bool tc, real* spare) {
+  const bool use_tc = sizeof(real) == 4 && tc && r > 256 && spare && P.Linv && !P.sp;
   return chol_qr_rows<real>(ctx, X, tmp, r, c, ld, P.G, P.partial, P.partial_cap,
-                            final_orth ? 3 : 2);
+                            final_orth ? 3 : 2, use_tc ? spare : nullptr,
+                            use_tc ? P.Linv : nullptr);
 }
 
 // Sample matrix of Algorithm 4 with the power scheme of Section 5.3:
@@ -315,7 +328,8 @@ curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const 
     real* t = other(cur, nullptr);
     {
       PhaseScope ps(h, CURID_PHASE_ORTH);
-      CURID_TRY(orth_rows<real>(ctx, &cur, &t, l, n, ldy, P, false));
+      CURID_TRY(orth_rows<real>(ctx, &cur, &t, l, n, ldy, P, false, tf32 || bf16,
+                                other(cur, t)));
     }
     real* z = other(cur, nullptr);
     {
@@ -325,7 +339,8 @@ curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const 
     real* zt = other(z, nullptr);
     {
       PhaseScope ps(h, CURID_PHASE_ORTH);
-      CURID_TRY(orth_rows<real>(ctx, &z, &zt, l, m, ldz, P, i == q - 1));
+      CURID_TRY(orth_rows<real>(ctx, &z, &zt, l, m, ldz, P, i == q - 1, tf32 || bf16,
+                                other(z, zt)));
     }
     real* y = other(z, nullptr);
     {
@@ -533,7 +548,7 @@ curid_status run(curid_handle* h, Op op, const void* Araw, const Dims& d, double
     bool split_done = false;
     if constexpr (sizeof(real) == 4) {
       if (sk.tf32 && !d.bf16 && !d.sp) {
-        CURID_TRY(split_tf32(ctx, qc, ldx, qt, ldx, k, m));
+        CURID_TRY(split_tf32(ctx, qc, ldx, qc, ldx, qt, ldx, k, m));
         CURID_TRY(a_product<real>(ctx, true, false, false, k, n, m, qc, ldx, Araw, lda, P.Bq,
                                   pad4(n), P));
         CURID_TRY(a_product<real>(ctx, true, false, false, k, n, m, qt, ldx, Araw, lda, P.Bq2,

@@ -510,11 +510,21 @@ curid_status gemm_nt_f64acc(const Ctx& ctx, int64_t M, int64_t N, int64_t K, con
 
 template <typename real>
 curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
-                          real* G, real* partial, size_t partial_cap, int passes) {
+                          real* G, real* partial, size_t partial_cap, int passes, real* xh,
+                          real* g2) {
   const double shift = sizeof(real) == 4 ? 1e-5 : 1e-13;
   for (int pass = 0; pass < passes; ++pass) {
-    CURID_TRY(gemm<real>(ctx, false, true, r, r, c, real(1), *X, ld, *X, ld, real(0), G, r,
-                         partial, partial_cap));
+    bool tc = false;
+    if constexpr (sizeof(real) == 4) {
+      if (xh && g2) {
+        // the remainder goes to *tmp, which the triangular solve overwrites
+        CURID_TRY(gram_tf32(ctx, *X, r, c, ld, xh, *tmp, G, g2, partial, partial_cap));
+        tc = true;
+      }
+    }
+    if (!tc)
+      CURID_TRY(gemm<real>(ctx, false, true, r, r, c, real(1), *X, ld, *X, ld, real(0), G, r,
+                           partial, partial_cap));
     CURID_TRY(cholesky<real>(ctx, G, (int)r, pass == 0 ? shift : 0.0));
     CURID_TRY(tri_solve<real>(ctx, (int)r, G, r, false, false, *X, ld, *tmp, ld, c, nullptr));
     std::swap(*X, *tmp);
@@ -522,10 +532,29 @@ curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64
   return CURID_OK;
 }
 
+curid_status gram_tf32(const Ctx& ctx, const float* X, int64_t r, int64_t c, int64_t ld,
+                       float* xh, float* xl, float* G, float* g2, float* partial,
+                       size_t partial_cap) {
+  CURID_TRY(split_tf32(ctx, X, ld, xh, ld, xl, ld, r, c));
+  // the left operand is the MMA's N (<= 256 rows): equal row chunks of a
+  // multiple of 16
+  const int64_t chunks = (r + 255) / 256;
+  const int64_t rows = ((r + chunks - 1) / chunks + 15) / 16 * 16;
+  for (int64_t r0 = 0; r0 < r; r0 += rows) {
+    const int64_t mr = std::min(rows, r - r0);
+    CURID_TRY(gemm_tf32(ctx, false, true, mr, r, c, xh + r0 * ld, ld, X, ld, G + r0 * r, r,
+                        partial, partial_cap));
+    CURID_TRY(gemm_tf32(ctx, false, true, mr, r, c, xl + r0 * ld, ld, X, ld, g2 + r0 * r, r,
+                        partial, partial_cap));
+  }
+  return add2d<float>(ctx, g2, r, G, r, r, r);
+}
+
 template curid_status chol_qr_rows<float>(const Ctx&, float**, float**, int64_t, int64_t, int64_t,
-                                          float*, float*, size_t, int);
+                                          float*, float*, size_t, int, float*, float*);
 template curid_status chol_qr_rows<double>(const Ctx&, double**, double**, int64_t, int64_t,
-                                           int64_t, double*, double*, size_t, int);
+                                           int64_t, double*, double*, size_t, int, double*,
+                                           double*);
 template curid_status gemm_nt_f64acc<float>(const Ctx&, int64_t, int64_t, int64_t, const float*,
                                             int64_t, const float*, int64_t, double*, int64_t);
 template curid_status gemm_nt_f64acc<double>(const Ctx&, int64_t, int64_t, int64_t,

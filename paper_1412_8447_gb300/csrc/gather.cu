@@ -120,16 +120,17 @@ __global__ void add_transpose_kernel(const real* __restrict__ src, int64_t lds,
 // x -> (hi, lo): hi = x with the 13 low mantissa bits cleared (exactly a
 // TF32 value, which the tensor cores use unchanged), lo = x - hi (exact in
 // float32; the tensor cores read it to about 2^-10 of itself, 2^-21 of x).
-// hi may overwrite x.
-__global__ void split_tf32_kernel(float* __restrict__ x, int64_t ldx, float* __restrict__ lo,
-                                  int64_t ldl, int64_t rows, int64_t cols) {
+// hi may be x itself.
+__global__ void split_tf32_kernel(const float* x, int64_t ldx, float* hi, int64_t ldh,
+                                  float* __restrict__ lo, int64_t ldl, int64_t rows,
+                                  int64_t cols) {
   const int64_t total = rows * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / cols, c = e % cols;
     const float v = x[r * ldx + c];
     const float h = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
-    x[r * ldx + c] = h;
+    hi[r * ldh + c] = h;
     lo[r * ldl + c] = v - h;
   }
 }
@@ -255,11 +256,11 @@ curid_status add_transpose(const Ctx& ctx, const real* src, int64_t lds, real* d
   return CURID_OK;
 }
 
-curid_status split_tf32(const Ctx& ctx, float* x, int64_t ldx, float* lo, int64_t ldl,
-                        int64_t rows, int64_t cols) {
+curid_status split_tf32(const Ctx& ctx, const float* x, int64_t ldx, float* hi, int64_t ldh,
+                        float* lo, int64_t ldl, int64_t rows, int64_t cols) {
   if (rows <= 0 || cols <= 0) return CURID_OK;
   split_tf32_kernel<<<blocks_for(rows * cols, ctx.num_sms), 256, 0, ctx.stream>>>(
-      x, ldx, lo, ldl, rows, cols);
+      x, ldx, hi, ldh, lo, ldl, rows, cols);
   CURID_LAUNCHED(ctx);
   return CURID_OK;
 }

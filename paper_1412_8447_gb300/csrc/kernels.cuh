@@ -114,9 +114,18 @@ bool chol_inverse_fits(const Ctx& ctx, int l);
 // whose result is orthonormalised again needs.  X is r x c with leading
 // dimension ld; each pass writes out of place, and on return *X points at
 // the result and *tmp at the other buffer.  G: r x r scratch.
+// With xh and g2 (float32 only: r x ld and r x r scratch), each Gram matrix
+// is formed on the TF32 tensor cores at float32 accuracy (gram_tf32).
 template <typename real>
 curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
-                          real* G, real* partial, size_t partial_cap, int passes = 3);
+                          real* G, real* partial, size_t partial_cap, int passes = 3,
+                          real* xh = nullptr, real* g2 = nullptr);
+// G (r x r, leading dimension r) = X X^T on the TF32 tensor cores: X =
+// X_hi + X_lo (TF32 part and float32 remainder, into xh and xl), G = X_hi X^T
+// + X_lo X^T with X split hi + lo inside each product; g2: r x r scratch.
+curid_status gram_tf32(const Ctx& ctx, const float* X, int64_t r, int64_t c, int64_t ld,
+                       float* xh, float* xl, float* G, float* g2, float* partial,
+                       size_t partial_cap);
 // C (float64) = A B^T with float64 accumulation; A M x K, B N x K.
 template <typename real>
 curid_status gemm_nt_f64acc(const Ctx& ctx, int64_t M, int64_t N, int64_t K, const real* A,
@@ -159,9 +168,10 @@ curid_status aug_transpose(const Ctx& ctx, const real* S11, int64_t lds, int k, 
 template <typename real>
 curid_status add2d(const Ctx& ctx, const real* src, int64_t lds, real* dst, int64_t ldd,
                    int64_t rows, int64_t cols);
-// x (rows x cols) -> its TF32 part in place, the float32 remainder into lo
-curid_status split_tf32(const Ctx& ctx, float* x, int64_t ldx, float* lo, int64_t ldl,
-                        int64_t rows, int64_t cols);
+// x (rows x cols) -> its TF32 part into hi (may be x), the float32 remainder
+// into lo
+curid_status split_tf32(const Ctx& ctx, const float* x, int64_t ldx, float* hi, int64_t ldh,
+                        float* lo, int64_t ldl, int64_t rows, int64_t cols);
 // dst[i][t] = src[t][i] (k x k transpose-add): dst += src^T
 template <typename real>
 curid_status add_transpose(const Ctx& ctx, const real* src, int64_t lds, real* dst,
