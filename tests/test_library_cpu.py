@@ -54,6 +54,22 @@ def test_null_handle_rejected_on_host(lib):
     assert lib.curid_workspace_size(None, 0, 10, 10, 2, sk, ctypes.byref(b)) == B.INVALID_ARG
     assert lib.curid_srft_omega(None, 1, 10, 4, vp(1), vp(1), vp(1), 10) == B.INVALID_ARG
     assert lib.curid_srft_draw(None, 10, 4, 1, vp(1), vp(1)) == B.INVALID_ARG
+    assert lib.curid_cur_corrected(None, 0, vp(1), 10, 10, 10, 2, 0.0, sk, vp(1), vp(1), vp(1),
+                                   None, None, None, 0, None, 0) == B.INVALID_ARG
+    assert lib.curid_interp_tikhonov(None, 0, vp(1), 10, vp(1), 10, 2, 0.5, vp(1), 8) \
+        == B.INVALID_ARG
+    assert lib.curid_interp_tsvd(None, 0, vp(1), 10, vp(1), 10, 2, 1e-3, vp(1), 8) \
+        == B.INVALID_ARG
+    assert lib.curid_interp_tikhonov_workspace_size(None, 0, 10, 2, ctypes.byref(b)) \
+        == B.INVALID_ARG
+    assert lib.curid_interp_tsvd_workspace_size(None, 0, 10, 2, ctypes.byref(b)) \
+        == B.INVALID_ARG
+    sp = B.Sparse(0, vp(1), None, None, vp(1), None, None)
+    sk1 = B.Sketch(5, 0, 0, None, 0)
+    assert lib.curid_sparse_workspace_size(None, 0, 10, 10, 2, sk1, ctypes.byref(b)) \
+        == B.INVALID_ARG
+    assert lib.curid_cur_sparse(None, 0, 10, 10, ctypes.byref(sp), 2, sk1, 0, vp(1), vp(1),
+                                vp(1), None, None, None, 0, None, 0) == B.INVALID_ARG
 
 
 def test_philox_known_answers():
