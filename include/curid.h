@@ -392,6 +392,30 @@ curid_status curid_cur_sparse(curid_handle* handle, curid_dtype dtype,
                               void* R, void* T, int64_t ldt, void* TW,
                               int64_t ldtw);
 
+/* ----- complex A -------------------------------------------------------- */
+
+/* CUR-ID of a complex A (the paper works over C): A is m x n complex,
+ * interleaved (re, im) pairs of dtype CURID_F32 (complex64) or CURID_F64
+ * (complex128), leading dimension lda in complex entries.  Computed by the
+ * real pipeline on the embedding E(A) (each entry x + iy as the 2 x 2 block
+ * [[x, -y], [y, x]]; 2m x 2n, rank 2k; with a sketch, E(Omega) for a complex
+ * Gaussian Omega drawn from sk.seed, l = 2(k + p) real rows; sk.omega must
+ * be NULL): greedy pivoting on E takes each complex column as a pair of
+ * real ones, and T, U are read off the real results.  Outputs: J (n), I
+ * (m) as for curid_cur, U (k x k complex float64, interleaved), T
+ * (optional, k x (n-k) complex of A's dtype, ldt in complex entries).  A
+ * pair broken by a tie in the pivot norms within rounding sets
+ * CURID_BREAKDOWN (curid_last_status); the ranks reported there count
+ * complex pivots.  Scratch: curid_complex_workspace_size (the real pipeline
+ * for the embedding plus the embedded A, about 4 m n reals). */
+curid_status curid_complex_workspace_size(curid_handle* handle, curid_dtype dtype,
+                                          int64_t m, int64_t n, int k,
+                                          curid_sketch sk, size_t* bytes);
+curid_status curid_cur_complex(curid_handle* handle, curid_dtype dtype,
+                               const void* A, int64_t m, int64_t n, int64_t lda,
+                               int k, curid_sketch sk, int32_t* J, int32_t* I,
+                               double* U, void* T, int64_t ldt);
+
 /* ----- adjoint with frozen skeletons ----------------------------------- */
 
 /* Reverse-mode derivative of the deterministic CUR-ID (p < 0) with the index

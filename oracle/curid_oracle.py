@@ -28,7 +28,7 @@ __all__ = [
     "cur_middle", "cur", "cur_middle_corrected", "cur_corrected", "randomized_cur_corrected",
     "orth_rows", "sketch", "randomized_id_col", "randomized_rank_adaptive",
     "randomized_cur", "srft_sketch", "srft_omega_rows", "rel_err_fro", "OK", "RANK_DEFICIENT",
-    "rank_threshold",
+    "rank_threshold", "cpqr_complex", "cur_complex", "sketch_complex",
 ]
 
 OK = 0
@@ -433,3 +433,75 @@ def rel_err_fro(A, C, U, R):
     A = as_f64(A)
     E = A - as_f64(C) @ as_f64(U) @ as_f64(R)
     return float(np.sqrt(np.sum(E * E)) / np.sqrt(np.sum(A * A)))
+
+
+# --- complex A (the paper works over C throughout) ---------------------------
+
+def cpqr_complex(Y, k):
+    """k steps of column-pivoted QR of a complex Y by pivoted Gram-Schmidt,
+    the complex form of ``cpqr`` (Section 2.2 over C): norms |y|_2 recomputed
+    each step, the largest taken (smallest index on exact ties), q_j
+    re-orthogonalised once, q_j q_j^* projected out of every unselected
+    column.  Returns (J, S1) with J the full permutation (unselected columns
+    ascending) and S1 = Q1^* Y(:, J) (k x n, upper triangular in its first k
+    columns)."""
+    Y = np.asarray(Y, dtype=np.complex128)
+    l, n = Y.shape
+    R = Y.copy()
+    active = np.ones(n, dtype=bool)
+    Q = np.zeros((l, k), dtype=np.complex128)
+    J = []
+    for j in range(k):
+        nu = np.sqrt(np.sum(np.abs(R) ** 2, axis=0))
+        p = int(np.argmax(np.where(active, nu, -1.0)))
+        q = R[:, p] / nu[p]
+        q = q - Q[:, :j] @ (Q[:, :j].conj().T @ q)
+        q = q / np.linalg.norm(q)
+        Q[:, j] = q
+        J.append(p)
+        active[p] = False
+        R[:, p] = 0.0
+        R[:, active] -= np.outer(q, q.conj() @ R[:, active])
+    Jf = np.array(J + [i for i in range(n) if active[i]], dtype=np.int64)
+    S1 = Q.conj().T @ Y[:, Jf]
+    S1[:, :k] = np.triu(S1[:, :k])
+    return Jf, S1
+
+
+def cur_complex(A, k, Y=None):
+    """CUR-ID of a complex A (Algorithm 3 over C): column ID from the CPQR of
+    A (or of a sketch Y), T = S11^{-1} S12, row ID from the full k-step CPQR of
+    C^* (conjugate transpose), U = V* R^+ by least squares (Eq. (4.2)).
+    Returns a dict with J, I, T, TW, U, C, R."""
+    A = np.asarray(A, dtype=np.complex128)
+    m, n = A.shape
+    J, S1 = cpqr_complex(A if Y is None else Y, k)
+    T = scipy.linalg.solve_triangular(S1[:, :k], S1[:, k:], lower=False)
+    C = A[:, J[:k]]
+    I, SW = cpqr_complex(C.conj().T, k)
+    TW = scipy.linalg.solve_triangular(SW[:, :k], SW[:, k:], lower=False)
+    R = A[I[:k], :]
+    Vs = np.zeros((k, n), dtype=np.complex128)
+    Vs[np.arange(k), J[:k]] = 1.0
+    Vs[:, J[k:]] = T
+    U = np.linalg.lstsq(R.T, Vs.T, rcond=None)[0].T
+    return {"J": J, "I": I, "T": T, "TW": TW, "U": U, "C": C, "R": R}
+
+
+def sketch_complex(A, Omega, q=0):
+    """Sample matrix of Algorithm 4 over C with the power scheme of Section
+    5.3: Y = Omega A, then q times Y <- orth(Y) A^*, Y <- orth(Y) A, orth the
+    row orthonormalisation (Householder QR of Y^*, diagonal made positive)."""
+    A = np.asarray(A, dtype=np.complex128)
+
+    def orth(Y):
+        Qt, Rt = np.linalg.qr(Y.conj().T)
+        d = np.diag(Rt)
+        ph = np.where(d == 0, 1.0, d / np.abs(np.where(d == 0, 1.0, d)))
+        return (Qt * ph).conj().T
+
+    Y = np.asarray(Omega, dtype=np.complex128) @ A
+    for _ in range(q):
+        Y = orth(Y) @ A.conj().T
+        Y = orth(Y) @ A
+    return Y

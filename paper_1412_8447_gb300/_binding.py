@@ -73,6 +73,10 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_size_t)],
     "curid_cur_sparse": [_vp, _int, _i64, _i64, ctypes.POINTER(Sparse), _int, Sketch, _int, _vp,
                          _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64],
+    "curid_complex_workspace_size": [_vp, _int, _i64, _i64, _int, Sketch,
+                                     ctypes.POINTER(ctypes.c_size_t)],
+    "curid_cur_complex": [_vp, _int, _vp, _i64, _i64, _i64, _int, Sketch, _vp, _vp, _vp, _vp,
+                          _i64],
     "curid_cur_corrected": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, Sketch, _vp, _vp, _vp,
                             _vp, _vp, _vp, _i64, _vp, _i64],
     "curid_cur_adjoint_workspace_size": [_vp, _int, _i64, _i64, _int,
@@ -492,6 +496,37 @@ def cur(A, k, p=-1, q=0, seed=0, omega=None, tf32=False, want_c=False, want_r=Fa
         if want_tw:
             res.TW = o.TW[:kk, :m - kk]
     return res
+
+def cur_complex(A, k, p=-1, q=0, seed=0, tf32=False, want_t=False, check=True):
+    """CUR-ID of a complex A (torch complex64 / complex128, row-major, on a
+    CUDA device) through curid_cur_complex: J, I (int32), U (complex128
+    k x k), T (complex, k x (n - k), when want_t)."""
+    if A.dtype not in (torch.complex64, torch.complex128):
+        raise ValueError("expected a complex64 or complex128 tensor")
+    A = _mat(A)
+    dev = _dev(A)
+    h = handle(dev)
+    m, n = A.shape
+    dt = F32 if A.dtype == torch.complex64 else F64
+    sk = _sketch(p, q, seed, None, tf32)
+    b = ctypes.c_size_t(0)
+    _check(h.lib.curid_complex_workspace_size(h.h, dt, m, n, k, sk, ctypes.byref(b)),
+           "curid_complex_workspace_size")
+    h.prepare(b.value)
+    o = Result(J=torch.empty(n, dtype=torch.int32, device=A.device),
+               I=torch.empty(m, dtype=torch.int32, device=A.device),
+               U=torch.empty((k, k), dtype=torch.complex128, device=A.device),
+               T=torch.empty((k, max(n - k, 1)), dtype=A.dtype, device=A.device)
+               if want_t else None)
+    _check(h.lib.curid_cur_complex(h.h, dt, _ptr(A), m, n, A.stride(0), k, sk, _ptr(o.J),
+                                   _ptr(o.I), _ptr(o.U), _ptr(o.T),
+                                   o.T.stride(0) if o.T is not None else 0),
+           "curid_cur_complex")
+    res = _finish(h, o, check, "curid_cur_complex")
+    if want_t:
+        res.T = o.T[:, :n - k]
+    return res
+
 
 def sparse_operand(A):
     """The two compressed forms curid_cur_sparse reads, from a torch sparse

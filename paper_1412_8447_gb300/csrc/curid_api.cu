@@ -810,6 +810,85 @@ curid_status tikhonov_run(curid_handle* h, const real* S, int64_t lds, const int
   return tri_solve<real>(ctx, k, P.K, k, true, false, P.Z, n - k, T, ldt, n - k, nullptr);
 }
 
+// Complex A (the paper works over C): the real pipeline on the embedding
+// E(A) (2m x 2n, rank 2k, sample 2(k + p) rows from E(Omega) with a complex
+// Gaussian Omega), then the complex J, I, T, U read off the real results
+// (complex.cu).  The real plan occupies the start of the workspace (its
+// status block is the handle's), the embedding buffers follow it.
+template <typename real>
+struct ComplexPlan {
+  Dims d;
+  size_t run_bytes = 0;
+  real* E = nullptr;     // 2m x 2n
+  real* Ge = nullptr;    // l x 2m: Gaussian (re, im) pairs
+  real* Om = nullptr;    // 2l x 2m
+  int32_t* Jp = nullptr;
+  int32_t* Ip = nullptr;
+  double* Up = nullptr;  // 2k x 2k
+  real* Tp = nullptr;    // 2k x 2(n - k)
+  size_t bytes = 0;
+};
+
+template <typename real>
+curid_status complex_plan(const Ctx& ctx, int64_t m, int64_t n, int k, const curid_sketch& sk,
+                          char* base, ComplexPlan<real>* P) {
+  Dims& d = P->d;
+  d.m = 2 * m;
+  d.n = 2 * n;
+  d.lda = 2 * n;
+  d.k = 2 * k;
+  d.randomized = sk.p >= 0;
+  d.l = d.randomized ? 2 * (k + sk.p) : (int)(2 * m);
+  d.q = sk.q;
+  d.tf32 = sk.tf32 != 0;
+  d.bf16 = false;
+  Plan<real> rp;
+  CURID_TRY(make_plan<real>(ctx, Op::Cur, d, false, false, nullptr, &rp));
+  P->run_bytes = (rp.bytes + 255) & ~size_t(255);
+  Carver cv(base ? base + P->run_bytes : nullptr);
+  P->E = cv.take<real>((size_t)4 * m * n);
+  if (d.randomized) {
+    const int64_t l = k + sk.p;
+    P->Ge = cv.take<real>((size_t)l * 2 * m);
+    P->Om = cv.take<real>((size_t)4 * l * m);
+  }
+  P->Jp = cv.take<int32_t>((size_t)2 * n);
+  P->Ip = cv.take<int32_t>((size_t)2 * m);
+  P->Up = cv.take<double>((size_t)4 * k * k);
+  P->Tp = cv.take<real>((size_t)2 * k * std::max<int64_t>(1, 2 * (n - k)));
+  P->bytes = P->run_bytes + cv.used + 256;
+  return CURID_OK;
+}
+
+template <typename real>
+curid_status cur_complex_run(curid_handle* h, const real* A, int64_t m, int64_t n, int64_t lda,
+                             int k, const curid_sketch& sk, int32_t* J, int32_t* I, double* U,
+                             real* T, int64_t ldt) {
+  Ctx ctx = make_ctx(h);
+  ComplexPlan<real> P;
+  CURID_TRY(complex_plan<real>(ctx, m, n, k, sk, nullptr, &P));
+  if (!h->ws || P.bytes > h->ws_bytes) return CURID_NO_WORKSPACE;
+  CURID_TRY(complex_plan<real>(ctx, m, n, k, sk, h->ws, &P));
+  CURID_TRY(embed_complex<real>(ctx, A, m, n, lda, P.E, 2 * n));
+  curid_sketch sk2 = sk;
+  if (P.d.randomized) {
+    const int64_t l = k + sk.p;
+    CURID_TRY(gaussian_fill<real>(ctx, l, 2 * m, sk.seed, P.Ge, 2 * m));
+    CURID_TRY(embed_complex<real>(ctx, P.Ge, l, m, m, P.Om, 2 * m));
+    sk2.p = 2 * sk.p;
+    sk2.omega = P.Om;
+  }
+  const int64_t ldtp = std::max<int64_t>(1, 2 * (n - k));
+  Outputs o{P.Jp, P.Tp, ldtp, P.Ip, nullptr, 0, P.Up, nullptr, nullptr};
+  CURID_TRY(run<real>(h, Op::Cur, P.E, P.d, 0.0, sk2, o, h->ws, P.run_bytes));
+  ctx.status = reinterpret_cast<StatusBlock*>(h->ws);
+  CURID_TRY(extract_pivots(ctx, P.Jp, k, n, J, true));
+  CURID_TRY(extract_pivots(ctx, P.Ip, k, m, I, false));
+  CURID_TRY(extract_u(ctx, P.Up, P.Jp, P.Ip, k, U));
+  if (T && n - k > 0) CURID_TRY(extract_t<real>(ctx, P.Tp, ldtp, P.Jp, k, n - k, T, ldt));
+  return CURID_OK;
+}
+
 // Truncated-SVD T (Section 4.1): S11 = U diag(sigma) V^T by one-sided
 // Jacobi, singular values below rtol * sigma_1 dropped, T = V D^+ U^T S12.
 // With the Jacobi output W^T = diag(sigma) U^T (rows), B = W^T S12 has rows
@@ -1297,6 +1376,50 @@ curid_status curid_cur_sparse(curid_handle* handle, curid_dtype dtype, int64_t m
     if (dtype == CURID_F64)
       return run<double>(handle, op, nullptr, d, 0.0, sk, o, handle->ws, handle->ws_bytes);
     return run<float>(handle, op, nullptr, d, 0.0, sk, o, handle->ws, handle->ws_bytes);
+  });
+}
+
+static curid_status complex_check(curid_handle* h, curid_dtype dt, int64_t m, int64_t n,
+                                  int k, const curid_sketch& sk) {
+  if (!h || (dt != CURID_F32 && dt != CURID_F64)) return CURID_INVALID_ARG;
+  if (m <= 0 || n <= 0 || 2 * m > INT32_MAX || 2 * n > INT32_MAX) return CURID_INVALID_ARG;
+  if (k < 1 || k > std::min(m, n) || sk.q < 0) return CURID_INVALID_ARG;
+  if (sk.p >= 0 && k + (int64_t)sk.p > std::min(m, n)) return CURID_INVALID_ARG;
+  if (sk.p < 0 && sk.q > 0) return CURID_INVALID_ARG;
+  if (sk.tf32 && dt != CURID_F32) return CURID_INVALID_ARG;
+  if (sk.omega) return CURID_UNSUPPORTED;  // the sample is drawn from the seed
+  return CURID_OK;
+}
+
+curid_status curid_complex_workspace_size(curid_handle* handle, curid_dtype dtype, int64_t m,
+                                          int64_t n, int k, curid_sketch sk, size_t* bytes) {
+  if (!bytes) return CURID_INVALID_ARG;
+  CURID_TRY(complex_check(handle, dtype, m, n, k, sk));
+  Ctx ctx{nullptr, handle->num_sms, handle->smem_optin, nullptr};
+  if (dtype == CURID_F64) {
+    ComplexPlan<double> P;
+    CURID_TRY(complex_plan<double>(ctx, m, n, k, sk, nullptr, &P));
+    *bytes = P.bytes;
+  } else {
+    ComplexPlan<float> P;
+    CURID_TRY(complex_plan<float>(ctx, m, n, k, sk, nullptr, &P));
+    *bytes = P.bytes;
+  }
+  return CURID_OK;
+}
+
+curid_status curid_cur_complex(curid_handle* handle, curid_dtype dtype, const void* A, int64_t m,
+                               int64_t n, int64_t lda, int k, curid_sketch sk, int32_t* J,
+                               int32_t* I, double* U, void* T, int64_t ldt) {
+  CURID_TRY(complex_check(handle, dtype, m, n, k, sk));
+  if (!A || !J || !I || !U || lda < n) return CURID_INVALID_ARG;
+  if (T && ldt < std::max<int64_t>(1, n - k)) return CURID_INVALID_ARG;
+  return dispatch(handle, [&]() -> curid_status {
+    if (dtype == CURID_F64)
+      return cur_complex_run<double>(handle, static_cast<const double*>(A), m, n, lda, k, sk, J,
+                                     I, U, static_cast<double*>(T), ldt);
+    return cur_complex_run<float>(handle, static_cast<const float*>(A), m, n, lda, k, sk, J, I, U,
+                                  static_cast<float*>(T), ldt);
   });
 }
 

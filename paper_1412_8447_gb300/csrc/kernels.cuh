@@ -196,6 +196,24 @@ template <typename real>
 curid_status scale_rows(const Ctx& ctx, real* B, int64_t ldb, int64_t rows, int64_t cols,
                         const real* f);
 
+// ---- complex A through its real embedding (complex.cu) -------------------------
+// E (2m x 2n, lde) = the real 2 x 2 blocks [[x, -y], [y, x]] of A (m x n
+// complex, interleaved, lda in complex entries)
+template <typename real>
+curid_status embed_complex(const Ctx& ctx, const real* A, int64_t m, int64_t n, int64_t lda,
+                           real* E, int64_t lde);
+// J (n) from the real pivots Jp (2n): pairs -> complex indices; a broken
+// pair sets FLAG_BREAKDOWN; halve_ranks halves the status block's ranks
+curid_status extract_pivots(const Ctx& ctx, const int32_t* Jp, int k, int64_t n, int32_t* J,
+                            bool halve_ranks);
+// T (k x cols complex, ldt complex entries) from the real Tp (2k x 2 cols)
+template <typename real>
+curid_status extract_t(const Ctx& ctx, const real* Tp, int64_t ldtp, const int32_t* Jp, int k,
+                       int64_t cols, real* T, int64_t ldt);
+// U (k x k complex float64) from the real Up (2k x 2k float64)
+curid_status extract_u(const Ctx& ctx, const double* Up, const int32_t* Jp, const int32_t* Ip,
+                       int k, double* U);
+
 // ---- sparse A (sparse.cu) ---------------------------------------------------
 // A m x n with its stored entries in compressed rows (row_ptr [m + 1],
 // col_idx, row_val) and compressed columns (col_ptr [n + 1], row_idx,

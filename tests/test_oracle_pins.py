@@ -532,3 +532,54 @@ def test_tsvd_t_rank_deficient_is_minimum_norm():
     T = O.interpolation_matrix_tsvd(S1, k, 1e-10)
     np.testing.assert_allclose(T, np.linalg.pinv(S11, rcond=1e-10) @ S1[:, k:], rtol=0,
                                atol=1e-9 * np.abs(T).max())
+
+
+# --- complex A ----------------------------------------------------------------
+
+def _complex_spectrum(m, n, decay, seed):
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    return U @ np.diag(np.exp(-np.arange(n) / decay)) @ V.conj().T
+
+
+def test_complex_oracle_on_real_input_is_the_real_oracle():
+    A = f64(syn.spectrum_matrix(120, 90, syn.exp_decay(90), 301, torch.float64))
+    r = O.cur(A, 15)
+    c = O.cur_complex(A.astype(np.complex128), 15)
+    assert list(c["J"]) == list(r.J) and list(c["I"]) == list(r.I)
+    np.testing.assert_allclose(c["T"].real, r.T, atol=1e-10, rtol=0)
+    np.testing.assert_allclose(c["U"].real, r.U, atol=1e-8 * np.abs(r.U).max(), rtol=0)
+    assert np.abs(c["U"].imag).max() <= 1e-10 * np.abs(r.U).max()
+
+
+def test_complex_pivots_invariant_under_unitary_rows():
+    """Norms and projections of columns are unchanged by a unitary factor on
+    the left, so the pivots are too (against LAPACK-free brute force: the
+    same routine on W Y)."""
+    A = _complex_spectrum(80, 60, 6.0, 302)
+    W, _ = np.linalg.qr(np.random.default_rng(303).standard_normal((80, 80))
+                        + 1j * np.random.default_rng(304).standard_normal((80, 80)))
+    J1, _ = O.cpqr_complex(A, 12)
+    J2, _ = O.cpqr_complex(W @ A, 12)
+    assert list(J1[:12]) == list(J2[:12])
+
+
+def test_complex_closed_forms_and_exact_rank():
+    A = _complex_spectrum(100, 70, 5.0, 305)
+    k = 14
+    c = O.cur_complex(A, k)
+    # T = C^+ A(:, J[k:]) and U = V* R^+ (library complex lstsq / pinv)
+    Tls = np.linalg.lstsq(c["C"], A[:, c["J"][k:]], rcond=None)[0]
+    np.testing.assert_allclose(c["T"], Tls, atol=1e-9 * np.abs(Tls).max(), rtol=0)
+    Vs = np.zeros((k, 70), dtype=complex)
+    Vs[np.arange(k), c["J"][:k]] = 1.0
+    Vs[:, c["J"][k:]] = c["T"]
+    np.testing.assert_allclose(c["U"], Vs @ np.linalg.pinv(c["R"]), atol=1e-8 * np.abs(c["U"]).max(),
+                               rtol=0)
+    rng = np.random.default_rng(306)
+    B = (rng.standard_normal((90, 9)) + 1j * rng.standard_normal((90, 9))) @ \
+        (rng.standard_normal((9, 60)) + 1j * rng.standard_normal((9, 60)))
+    e = O.cur_complex(B, 9)
+    E = B - e["C"] @ e["U"] @ e["R"]
+    assert np.linalg.norm(E) <= 1e-12 * np.linalg.norm(B)
