@@ -70,6 +70,10 @@ def test_null_handle_rejected_on_host(lib):
         == B.INVALID_ARG
     assert lib.curid_cur_sparse(None, 0, 10, 10, ctypes.byref(sp), 2, sk1, 0, vp(1), vp(1),
                                 vp(1), None, None, None, 0, None, 0) == B.INVALID_ARG
+    assert lib.curid_complex_workspace_size(None, 0, 10, 10, 2, sk, ctypes.byref(b)) \
+        == B.INVALID_ARG
+    assert lib.curid_cur_complex(None, 0, vp(1), 10, 10, 10, 2, sk, vp(1), vp(1), vp(1), None,
+                                 0) == B.INVALID_ARG
 
 
 def test_philox_known_answers():
