@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only-form", choices=["adjoint", "batched", "mixed", "srft", "sparse"], default=None,
+    ap.add_argument("--only-form", choices=["adjoint", "batched", "mixed", "srft", "sparse", "extras"], default=None,
                     help="run only this form's measurement and print its JSON")
     ap.add_argument("--small", action="store_true",
                     help="with --only-form: profiling sizes (256 blocks; BF16 8192^2, q = 1)")
@@ -615,6 +615,67 @@ def measure_sparse(dev, steps=5, m=300000, n=300, k=40, p=10, q=2):
     return res
 
 
+def measure_extras(dev, steps=5):
+    """Rows measured on request (``--only-form extras``): the adaptive rank
+    with a sketch (benchmark matrix, tol 1e-3, p = 10, q = 1, TF32: time per
+    call including its sample-size search), complex A (2000 x 1500
+    complex64 with sigma_j = j^-2, k = 100, p = 10, q = 1, through the real
+    embedding) against the real path on the real part, and the two
+    stabilised T solves (k = 200, n = 6000)."""
+    import paper_1412_8447_gb300 as curid
+    import synthetic as syn
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, n=steps):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / n
+
+    res = {}
+    A = syn.spectrum_matrix(M, N, syn.power_decay(N), BASE_SEED, torch.float32, dev)
+    r = curid.cur(A, 0, p=10, q=1, seed=3, tf32=True, tol=1e-3, want_c=True, want_r=True)
+    ms = timed(lambda: curid.cur(A, 0, p=10, q=1, seed=3, tf32=True, tol=1e-3))
+    Ad = A.double()
+    e = float(torch.linalg.norm(Ad - (r.C.double() @ r.U) @ r.R.double()) / torch.linalg.norm(Ad))
+    res["adaptive_sketch"] = {"workload": f"float32 A {M}x{N}, sigma_j = j^-2, tol 1e-3, p = 10, "
+                                          f"q = 1, TF32", "ms_per_call": ms, "k": r.k,
+                              "rel_err_fro": e}
+    del Ad, r
+    m, n, k = 2000, 1500, 100
+    Ar = syn.spectrum_matrix(m, n, syn.power_decay(n), BASE_SEED + 7, torch.float32, dev)
+    Ai = syn.spectrum_matrix(m, n, syn.power_decay(n), BASE_SEED + 8, torch.float32, dev)
+    Ac = torch.complex(Ar, Ai)
+    rc = curid.cur_complex(Ac, k, p=10, q=1, seed=5)
+    ms_c = timed(lambda: curid.cur_complex(Ac, k, p=10, q=1, seed=5, check=False))
+    Acd = Ac.to(torch.complex128)
+    Cc, Rc = Acd[:, rc.J[:k].long()], Acd[rc.I[:k].long(), :]
+    ec = float(torch.linalg.norm(Acd - Cc @ rc.U @ Rc) / torch.linalg.norm(Acd))
+    ms_r = timed(lambda: curid.cur(Ar, k, p=10, q=1, seed=5, check=False))
+    res["complex"] = {"workload": f"complex64 A {m}x{n} (real and imaginary parts sigma_j = "
+                                  f"j^-2), k = {k}, p = 10, q = 1", "unit": "decompositions/s",
+                      "value": 1e3 / ms_c, "ms_per_step": ms_c, "rel_err_fro": ec,
+                      "real_path_same_size": {"value": 1e3 / ms_r, "ms_per_step": ms_r}}
+    del Ar, Ai, Ac, Acd
+    kk, nn = 200, 6000
+    g = np.random.default_rng(1)
+    S = torch.tensor(np.triu(g.standard_normal((kk, nn))) + np.eye(kk, nn), device=dev)
+    J = torch.arange(nn, dtype=torch.int32, device=dev)
+    ts = {}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        Sd = S.to(dt)
+        ts[name] = {"tikhonov_ms": timed(lambda: curid.interp_tikhonov(Sd, J, kk, 1e-6), 3),
+                    "tsvd_ms": timed(lambda: curid.interp_tsvd(Sd, J, kk, 1e-6), 3)}
+    res["t_solves"] = {"workload": f"k = {kk}, n = {nn}", **ts}
+    torch.cuda.empty_cache()
+    return res
+
+
 def cpu_baseline(args, A, curid):
     """The FP64 oracle on the host cores, one full decomposition of the same
     workload with the Omega the device drew for seed BASE_SEED*1000."""
@@ -693,6 +754,8 @@ def main():
             r = measure_srft(dev)
         elif args.only_form == "sparse":
             r = measure_sparse(dev)
+        elif args.only_form == "extras":
+            r = measure_extras(dev)
         else:
             r = (measure_mixed(dev, steps=1, size=8192, q=1, with_f64=False) if args.small
                  else measure_mixed(dev))
