@@ -583,3 +583,19 @@ def test_complex_closed_forms_and_exact_rank():
     e = O.cur_complex(B, 9)
     E = B - e["C"] @ e["U"] @ e["R"]
     assert np.linalg.norm(E) <= 1e-12 * np.linalg.norm(B)
+
+
+def test_complex_power_scheme_spans_closed_form():
+    """With q = 1 the sample's row space is that of Omega (A A^*) A (the
+    orthonormalisations change only a left factor): compare the orthogonal
+    projectors onto the two row spaces."""
+    rng = np.random.default_rng(307)
+    A = _complex_spectrum(90, 70, 4.0, 308)
+    Om = rng.standard_normal((12, 90)) + 1j * rng.standard_normal((12, 90))
+    Y = O.sketch_complex(A, Om, q=1)
+    Z = Om @ (A @ A.conj().T) @ A
+
+    def proj(X):
+        Q, _ = np.linalg.qr(X.conj().T)
+        return Q @ Q.conj().T
+    assert np.abs(proj(Y) - proj(Z)).max() <= 1e-9
