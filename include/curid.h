@@ -7,7 +7,9 @@
  * ----------------------------------------
  *  - Matrices are dense, row-major, real (float64 or float32), with an
  *    explicit leading dimension (elements between consecutive rows).  The
- *    paper's A^* is the transpose.
+ *    paper's A^* is the transpose.  Sparse A (curid_cur_sparse) comes in
+ *    compressed rows and columns; complex A (curid_cur_complex) as
+ *    interleaved (re, im) pairs, its A^* the conjugate transpose.
  *  - Every matrix / index pointer passed to a compute entry point is DEVICE
  *    memory on the handle's device, owned by the caller; the library never
  *    frees or keeps it after the call's work has finished on the stream.
@@ -25,7 +27,8 @@
  *    handle's device status word and read with curid_last_status().
  *  - The library allocates no device memory: scratch comes from the
  *    workspace the caller attaches with curid_set_workspace(), sized by
- *    curid_workspace_size().
+ *    curid_workspace_size() (or the *_workspace_size call beside an entry
+ *    point that has its own).
  *  - Errors are returned, never trapped; no kernel of this library faults
  *    or spins without a bound.
  */
@@ -43,7 +46,8 @@ typedef enum {
   CURID_OK = 0,
   CURID_INVALID_ARG = 1,     /* a size, pointer or leading dimension is invalid */
   CURID_RANK_DEFICIENT = 2,  /* S11 numerically singular: k_out < k (Section 2.3) */
-  CURID_BREAKDOWN = 3,       /* row orthonormalisation failed (non-positive Gram pivot) */
+  CURID_BREAKDOWN = 3,       /* row orthonormalisation failed (non-positive Gram pivot),
+                                or a complex pivot pair was split (curid_cur_complex) */
   CURID_NONFINITE = 4,       /* NaN or Inf found in the input */
   CURID_TIMEOUT = 5,         /* an inter-block wait exceeded its bound */
   CURID_CUDA_ERROR = 6,      /* a CUDA runtime call failed */
