@@ -599,3 +599,14 @@ def test_complex_power_scheme_spans_closed_form():
         Q, _ = np.linalg.qr(X.conj().T)
         return Q @ Q.conj().T
     assert np.abs(proj(Y) - proj(Z)).max() <= 1e-9
+
+
+def test_complex_row_id_reconstructs_c():
+    """The row ID of C (CPQR of the conjugate transpose, Eq. (2.11) over C)
+    is exact: C(I[k:], :) = T_W^* C(I[:k], :)."""
+    A = _complex_spectrum(90, 60, 5.0, 309)
+    k = 12
+    c = O.cur_complex(A, k)
+    C, I, TW = c["C"], c["I"], c["TW"]
+    np.testing.assert_allclose(C[I[k:], :], TW.conj().T @ C[I[:k], :],
+                               atol=1e-10 * np.abs(C).max(), rtol=0)
