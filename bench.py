@@ -34,9 +34,10 @@ M, N, K, P, Q = 8000, 6000, 200, 10, 1
 BASE_SEED = 1413
 FP32_FMA_PER_SM_CLK = 128          # FP32 lanes per SM
 # dram__bytes_read.sum + dram__bytes_write.sum of one cpqr_reg_kernel launch on
-# this workload (ncu capture of the current kernel; profiles/ holds the summary):
-# CPQR of Y (210 x 6000) and of C^T (200 x 8000)
-CPQR_DRAM_BYTES = {"cpqr_col": 5.144e6 + 17.4e3, "cpqr_row": 6.550e6}
+# this workload from the ncu capture named below (empty: no capture of the
+# current kernel yet)
+CPQR_DRAM_BYTES = {}
+CPQR_DRAM_SOURCE = None
 NUM_SMS = 152
 
 
@@ -61,10 +62,13 @@ def parse():
     ap.add_argument("--p", type=int, default=P)
     ap.add_argument("--q", type=int, default=Q)
     ap.add_argument("--tf32", type=int, default=1)
+    ap.add_argument("--inflight", type=int, default=4,
+                    help="decompositions in flight (one stream and workspace each)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only-form", choices=["adjoint", "batched", "mixed", "srft", "sparse", "extras"], default=None,
+    ap.add_argument("--only-form", choices=["adjoint", "batched", "mixed", "srft", "sparse", "extras",
+                                                "c1"], default=None,
                     help="run only this form's measurement and print its JSON")
     ap.add_argument("--small", action="store_true",
                     help="with --only-form: profiling sizes (256 blocks; BF16 8192^2, q = 1)")
@@ -151,15 +155,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpqr_flops(rows, cols, steps):
-    """Algorithmic flops of a truncated CPQR with norms recomputed each step
-    (Section 4): step j applies the reflector to the cols - j - 1 trailing
-    columns of height rows - j (dot + update, 4 flops per element) and sums
-    the squares of the rows - j - 1 rows left (2 flops per element)."""
-    f = 0.0
-    for j in range(steps):
-        f += 4.0 * (rows - j) * (cols - j - 1) + 2.0 * (rows - j - 1) * (cols - j - 1)
-    return f
+def cpqr_flops(m, n, k):
+    """Algorithmic flops of a rank-k Householder CPQR of an m x n matrix
+    (the cost model of Section 4): 4 [m n k - (m + n) k^2 / 2 + k^3 / 3]."""
+    return 4.0 * (m * n * k - (m + n) * k * k / 2.0 + k ** 3 / 3.0)
 
 
 def phase_work(args, l):
@@ -173,6 +172,15 @@ def phase_work(args, l):
         "cpqr_col": {"flops": cpqr_flops(l, n, k), "bytes": 4.0 * (l * n + k * n + n)},
         "cpqr_row": {"flops": cpqr_flops(k, m, k), "bytes": 4.0 * (2 * k * m + m)},
     }
+
+
+def rel_err_gpu(A, J, I, U, k):
+    """||A - C U R||_F / ||A||_F in float64 on the GPU, C = A(:, J[:k]),
+    R = A(I[:k], :)."""
+    Ad = A.double()
+    C = Ad[:, J[:k].long()]
+    R = Ad[I[:k].long(), :]
+    return float(torch.linalg.norm(Ad - (C @ U.double()) @ R) / torch.linalg.norm(Ad))
 
 
 def run_ours(args, ws, rank, local):
@@ -190,75 +198,121 @@ def run_ours(args, ws, rank, local):
     l = args.k + args.p
     A = syn.spectrum_matrix(args.m, args.n, syn.power_decay(min(args.m, args.n)),
                             BASE_SEED + rank, torch.float32, dev)
-    out = curid.cur_outputs(A, args.k)
     tf32 = bool(args.tf32)
+    kin = max(1, args.inflight)
+    main = torch.cuda.current_stream(dev)
+    # one stream and one library handle (slot) per decomposition in flight
+    streams = [main] + [torch.cuda.Stream(dev) for _ in range(kin - 1)]
+    outs = []
+    for s in range(kin):
+        with torch.cuda.stream(streams[s]), curid.inflight(s):
+            outs.append(curid.cur_outputs(A, args.k))
 
-    def step(i, Adev=A):
-        return curid.cur(Adev, args.k, p=args.p, q=args.q, seed=BASE_SEED * 1000 + i, tf32=tf32,
-                         out=out, check=False)
+    def step(i, slot=None):
+        s = i % kin if slot is None else slot
+        with torch.cuda.stream(streams[s]), curid.inflight(s):
+            curid.cur(A, args.k, p=args.p, q=args.q, seed=BASE_SEED * 1000 + i, tf32=tf32,
+                      out=outs[s], check=False)
 
+    def slot_status(s):
+        with torch.cuda.stream(streams[s]), curid.inflight(s):
+            return curid.last_status(local)
+
+    def check_status(where, slots):
+        for s in range(slots):
+            st, _ = slot_status(s)
+            if st not in (0, 2):
+                raise RuntimeError(f"device status {curid.STATUS_NAMES[st]} in {where}")
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # ---- 1. one decomposition at a time: latency, per-phase times and the
+    # launch durations the roofline uses (kernels timed in isolation) --------
     for i in range(args.warmup):
-        step(i)
-    st, kout = curid.last_status(local)
-    if st not in (0, 2):
-        raise RuntimeError(f"device status {curid.STATUS_NAMES[st]} in warm-up")
+        step(i, 0)
+    check_status("warm-up", 1)
+    curid.profile(True, local)
+    lat_steps = max(5, min(args.steps, 10))
+    torch.cuda.synchronize(dev)
+    e0.record(main)
+    for i in range(lat_steps):
+        step(args.warmup + i, 0)
+    e1.record(main)
+    torch.cuda.synchronize(dev)
+    lat_ms = e0.elapsed_time(e1) / lat_steps
+    phase_ms, phase_calls, lat_launches = curid.profile_read(local)
+    curid.profile(False, local)
+    # accuracy of the decomposition whose Omega the oracle uses below
+    step(0, 0)
+    torch.cuda.synchronize(dev)
+    err_gpu = rel_err_gpu(A, outs[0].J, outs[0].I, outs[0].U, args.k)
 
+    # ---- 2. throughput: kin decompositions in flight, K timed steps ---------
+    for i in range(max(args.warmup, 2 * kin)):
+        step(1000 + i)
+    torch.cuda.synchronize(dev)
+    check_status("warm-up", kin)
+    for s in range(kin):
+        with torch.cuda.stream(streams[s]), curid.inflight(s):
+            curid.profile(True, local)
+            curid.profile_read(local)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.4)
-    curid.profile(True, local)
-    stream = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(ws)
     torch.cuda.synchronize(dev)
-    e0.record(stream)
+    e0.record(main)
+    for st in streams[1:]:
+        st.wait_event(e0)
     for i in range(args.steps):
-        step(args.warmup + i)
-    e1.record(stream)
+        step(2000 + i)
+    for st in streams[1:]:
+        main.wait_stream(st)
+    e1.record(main)
     torch.cuda.synchronize(dev)
     barrier(ws)
     elapsed_ms = e0.elapsed_time(e1)
-    phase_ms, phase_calls, launches = curid.profile_read(local)
-    curid.profile(False, local)
+    launches = 0
+    for s in range(kin):
+        with torch.cuda.stream(streams[s]), curid.inflight(s):
+            launches += curid.profile_read(local)[2]
+            curid.profile(False, local)
     clk = clocks.stop()
-    st, kout = curid.last_status(local)
-    if st not in (0, 2):
-        raise RuntimeError(f"device status {curid.STATUS_NAMES[st]} in timed region")
+    check_status("timed region", kin)
     elapsed_ms = max_over_ranks(elapsed_ms, ws, dev)
     value = args.steps * ws / (elapsed_ms / 1e3)
 
     # end to end through the public API with host buffers: every step copies
     # its matrix from pinned host memory and its (J, I, U) back; HostStream
-    # overlaps the copy of matrix i + 1 with the decomposition of matrix i
+    # keeps kin decompositions in flight and overlaps the copies with them
     e2e = None
     if not args.no_e2e:
         A_host = A.cpu().pin_memory()
-        ke = max(3, min(args.steps, 10))
+        ke = max(2 * kin, min(args.steps, 12))
         hs = curid.HostStream(args.m, args.n, args.k, A.dtype, local, p=args.p, q=args.q,
-                              tf32=tf32)
+                              tf32=tf32, inflight=kin)
         res = hs.host_results(ke)
         seeds = [BASE_SEED * 1000 + 7000 + i for i in range(ke)]
-        hs.run([A_host] * 2, res, seeds)
+        hs.run([A_host] * ke, res, seeds)
         torch.cuda.synchronize(dev)
         barrier(ws)
-        e0.record(stream)
+        e0.record(main)
         hs.run([A_host] * ke, res, seeds)
-        e1.record(stream)
+        e1.record(main)
         torch.cuda.synchronize(dev)
         e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
         e2e = {"value": ke * ws / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": A.numel() * 4,
                "d2h_bytes_per_step": (args.n + args.m) * 4 + args.k * args.k * 8,
-               "how": "HostStream: copy of the next matrix overlapped with the current "
-                      "decomposition (two device buffers, side copy stream)"}
+               "steps": ke,
+               "how": f"HostStream: {kin} decompositions in flight on {kin} streams, the copy "
+                      "of the next matrix on a side stream"}
+        del hs
 
     pk, pk_kind = peaks()
     work = phase_work(args, l)
-    per_step = {p: phase_ms[p] / args.steps for p in phase_ms}
+    per_step = {p: phase_ms[p] / lat_steps for p in phase_ms}
     total_phase = sum(phase_ms.values()) or 1.0
-    # kernel families: the CPQR phases are one cpqr_reg_kernel launch each, the
-    # sketch phase the tensor-core products; orth and U are chains of small
-    # kernels (Gram products, Cholesky, triangular solves)
     fam = {"cpqr": ("cpqr_col", "cpqr_row"), "sketch": ("sketch",),
            "orth": ("orth",), "u_solve": ("u_solve",)}
     fam_ms = {f: sum(phase_ms[p] for p in ps) for f, ps in fam.items()}
@@ -277,6 +331,7 @@ def run_ours(args, ws, rank, local):
             peak = pk["bf16_tflops_sustained"] / 2
             return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None,
+                    "hbm_frac": work["sketch"]["bytes"] / dur_s / 1e9 / pk["hbm_gbs"],
                     "kernel": "tc_sketch_kernel (tcgen05 TF32, A split hi + lo: 2 MMAs per "
                               "K step; achieved counts each product once)",
                     "peak_source": f"{pk_kind} bf16 sustained x 1/2 (TF32 nominal ratio)"}
@@ -294,14 +349,18 @@ def run_ours(args, ws, rank, local):
             default = (args.m, args.n, args.k, args.p) == (M, N, K, P)
             traffic = ((CPQR_DRAM_BYTES["cpqr_col"] * phase_calls["cpqr_col"]
                         + CPQR_DRAM_BYTES["cpqr_row"] * phase_calls["cpqr_row"]) / calls
-                       if default else None)
+                       if default and CPQR_DRAM_BYTES else None)
             roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": ach / fp32_peak, "traffic": traffic,
+                    "traffic_source": CPQR_DRAM_SOURCE if traffic else None,
+                    "algorithmic_flops_per_launch": flops / calls,
                     "algorithmic_bytes": (work["cpqr_col"]["bytes"] * phase_calls["cpqr_col"]
                                           + work["cpqr_row"]["bytes"] * phase_calls["cpqr_row"])
                                          / calls,
+                    "launch_ms": fam_ms["cpqr"] / calls,
                     "kernel": f"cpqr_reg_kernel (CPQR of Y {l}x{args.n} and of C^T {args.k}x"
-                              f"{args.m}, {args.k} steps each; bound by the per-step "
+                              f"{args.m}, {args.k} steps each, flops 4[mnk - (m+n)k^2/2 + k^3/3]; "
+                              f"timed one decomposition at a time; bound by the per-step "
                               f"grid-wide pivot exchange, not by FP32 rate)",
                     "peak_source": fp32_src}
     elif dominant == "sketch":
@@ -312,13 +371,14 @@ def run_ours(args, ws, rank, local):
                 "kernel": f"{dominant} (chain of small kernels; no single-kernel figure)",
                 "peak_source": fp32_src}
     cpu = None
+    err_oracle = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args, A, curid)
+        cpu, err_oracle = cpu_baseline(args, A, curid)
     forms = None
     if rank == 0 and ws == 1 and not args.no_forms:
         forms = {"adjoint": measure_adjoint(dev), "batched": measure_batched(dev),
                  "mixed": measure_mixed(dev), "srft": measure_srft(dev),
-                 "sparse": measure_sparse(dev)}
+                 "sparse": measure_sparse(dev), "c1": measure_c1(dev)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -329,8 +389,15 @@ def run_ours(args, ws, rank, local):
         "config": {"workload": f"randomized CUR-ID, float32 A {args.m}x{args.n}, k={args.k}, "
                                f"p={args.p}, q={args.q}, Omega {l}x{args.m}",
                    "m": args.m, "n": args.n, "k": args.k, "p": args.p, "q": args.q,
+                   "inflight": kin,
                    "l2": "inputs larger than L2 (A is %.0f MB), no flush" % (A.numel() * 4 / 1e6),
-                   "parallelism": f"replicas x{ws}"},
+                   "parallelism": f"replicas x{ws}; {kin} decompositions in flight per GPU "
+                                  f"(one stream and workspace each)"},
+        "latency_ms": lat_ms,
+        "accuracy": {"rel_err_fro": err_gpu, "oracle_rel_err_fro": err_oracle,
+                     "abs_diff": (abs(err_gpu - err_oracle) if err_oracle is not None else None),
+                     "how": f"||A - CUR||_F / ||A||_F in float64 for the decomposition with "
+                            f"seed {BASE_SEED * 1000}; the oracle runs the same Omega"},
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
         "e2e": e2e, "gpu_launches": launches,
@@ -338,9 +405,9 @@ def run_ours(args, ws, rank, local):
         "sketch_roofline": sketch_roof(),
         "phases_ms_per_step": {p: round(v, 4) for p, v in per_step.items()},
         "phase_share": {p: round(phase_ms[p] / total_phase, 4) for p in phase_ms},
+        "launches_per_decomposition": lat_launches / lat_steps,
         "cpu_baseline": cpu,
         "forms": forms,
-        "status": curid.STATUS_NAMES[st], "k_out": kout,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -382,7 +449,80 @@ def measure_adjoint(dev, steps=10, warmup=3):
         ms = e0.elapsed_time(e1) / steps
         res[name] = {"value": 1e3 / ms, "ms_per_step": ms}
     res["f32_over_f64"] = res["f32"]["value"] / res["f64"]["value"]
+    # algorithmic work of one forward + backward: the cost model of Section 4
+    # for the two CPQRs, T and U, and six m x n x k products for the adjoint
+    fwd = (cpqr_flops(m, n, k) + cpqr_flops(k, m, k) + float(k) * k * (n - k)
+           + 6.0 * k * k * n)
+    bwd = 6 * 2.0 * m * n * k
+    peak = NUM_SMS * FP32_FMA_PER_SM_CLK * 2 * 2070e6 / 1e12
+    ach = (fwd + bwd) / (res["f32"]["ms_per_step"] / 1e3) / 1e12
+    res["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                       "frac": ach / peak, "flops_per_step": fwd + bwd,
+                       "peak_source": "derived FP32: 152 SMs x 128 FMA/clk x 2 x 2070 MHz",
+                       "note": "latency-bound: about 40 dependent launches per step"}
     return res
+
+
+def measure_c1(dev, reps=20, inflight=8, steps=64):
+    """The small deterministic workload: CUR-ID of a float64 400 x 300
+    matrix (sigma_j = exp(-j/10), Haar factors), k = 40, no sketch: latency
+    of one call (median of single calls, CUDA events), throughput with
+    `inflight` decompositions in flight (one stream and workspace each), the
+    FP64 rate achieved on the cost model of Section 4, and the error against
+    the FP64 oracle."""
+    import oracle as O
+    import paper_1412_8447_gb300 as curid
+    import synthetic as syn
+    m, n, k = 400, 300, 40
+    A = syn.spectrum_matrix(m, n, syn.exp_decay(min(m, n), 10.0), BASE_SEED, torch.float64, dev)
+    main = torch.cuda.current_stream(dev)
+    streams = [main] + [torch.cuda.Stream(dev) for _ in range(inflight - 1)]
+    outs = []
+    for s in range(inflight):
+        with torch.cuda.stream(streams[s]), curid.inflight(s):
+            outs.append(curid.cur_outputs(A, k))
+
+    def call(s):
+        with torch.cuda.stream(streams[s]), curid.inflight(s):
+            curid.cur(A, k, out=outs[s], check=False)
+
+    for s in range(inflight):
+        call(s)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat = []
+    for _ in range(reps):
+        e0.record(main)
+        call(0)
+        e1.record(main)
+        torch.cuda.synchronize(dev)
+        lat.append(e0.elapsed_time(e1))
+    e0.record(main)
+    for st in streams[1:]:
+        st.wait_event(e0)
+    for i in range(steps):
+        call(i % inflight)
+    for st in streams[1:]:
+        main.wait_stream(st)
+    e1.record(main)
+    torch.cuda.synchronize(dev)
+    thr = steps / (e0.elapsed_time(e1) / 1e3)
+    flops = (cpqr_flops(m, n, k) + cpqr_flops(k, m, k) + float(k) * k * (n - k)
+             + 2.0 * k * k * n + 4.0 * k * k * n)
+    Ah = A.cpu().numpy()
+    o = O.cur(Ah, k)
+    eg = rel_err_gpu(A, outs[0].J, outs[0].I, outs[0].U, k)
+    eo = O.rel_err_fro(Ah, o.C, o.U, o.R)
+    return {"workload": f"deterministic CUR-ID, float64 A {m}x{n}, sigma_j = exp(-j/10), "
+                        f"k = {k}", "unit": "decompositions/s",
+            "latency_ms": statistics.median(lat), "value": thr, "inflight": inflight,
+            "flops_per_decomposition": flops,
+            "fp64_tflops": flops * thr / 1e12, "fp64_peak_tflops": 1.25,
+            "fp64_frac": flops * thr / 1e12 / 1.25,
+            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s",
+            "rel_err_fro": eg, "oracle_rel_err_fro": eo, "same_skeleton":
+                bool(list(outs[0].J[:k].cpu().tolist()) == list(o.J[:k])
+                     and list(outs[0].I[:k].cpu().tolist()) == list(o.I[:k]))}
 
 
 def measure_batched(dev, replays=5, nb=4096):
@@ -678,19 +818,21 @@ def measure_extras(dev, steps=5):
 
 def cpu_baseline(args, A, curid):
     """The FP64 oracle on the host cores, one full decomposition of the same
-    workload with the Omega the device drew for seed BASE_SEED*1000."""
+    workload with the Omega the device drew for seed BASE_SEED*1000; returns
+    the baseline entry and the oracle's ||A - CUR||_F / ||A||_F."""
     import oracle as O
     l = args.k + args.p
     Om = curid.gaussian(l, args.m, BASE_SEED * 1000, dtype=torch.float32,
                         device=A.device.index).cpu().numpy()
     Ah = A.cpu().numpy()
     t = time.perf_counter()
-    O.randomized_cur(Ah, Om, args.k, q=args.q)
+    o, _ = O.randomized_cur(Ah, Om, args.k, q=args.q)
     dt = time.perf_counter() - t
-    return {"value": 1.0 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"one full randomized CUR-ID of the same {args.m}x{args.n} float32 A "
-                      f"(numpy float64, OpenBLAS threads = all {os.cpu_count()} cores), "
-                      f"{dt:.1f} s"}
+    err = O.rel_err_fro(Ah.astype(np.float64), o.C, o.U, o.R)
+    return ({"value": 1.0 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+             "sample": f"one full randomized CUR-ID of the same {args.m}x{args.n} float32 A "
+                       f"(numpy float64, OpenBLAS threads = all {os.cpu_count()} cores), "
+                       f"{dt:.1f} s"}, err)
 
 
 def run_reference(args, ws, rank, local):
@@ -732,7 +874,10 @@ def run_reference(args, ws, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded)",
         "config": {"workload": f"randomized CUR-ID, float32 A {args.m}x{args.n}, k={args.k}, "
-                               f"p={args.p}, q={args.q}, Omega {l}x{args.m}"},
+                               f"p={args.p}, q={args.q}, Omega {l}x{args.m}",
+                   "m": args.m, "n": args.n, "k": args.k, "p": args.p, "q": args.q,
+                   "inflight": 1,
+                   "l2": "host run", "parallelism": f"{os.cpu_count()} host cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -756,6 +901,8 @@ def main():
             r = measure_sparse(dev)
         elif args.only_form == "extras":
             r = measure_extras(dev)
+        elif args.only_form == "c1":
+            r = measure_c1(dev)
         else:
             r = (measure_mixed(dev, steps=1, size=8192, q=1, with_f64=False) if args.small
                  else measure_mixed(dev))

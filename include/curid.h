@@ -98,6 +98,13 @@ curid_status curid_set_stream(curid_handle* handle, void* stream);
 /* ptr: device memory of `bytes` bytes, 256-byte aligned, owned by the
  * caller and kept alive while work that uses it is in flight. */
 curid_status curid_set_workspace(curid_handle* handle, void* ptr, size_t bytes);
+/* Bound of every wait between the blocks of a persistent kernel (the CPQR
+ * pivot exchange), in SM clock cycles; 0 restores the default (4e9, about
+ * 2 s).  A wait that runs out ends the kernel without fault: the call's
+ * status becomes CURID_TIMEOUT (curid_last_status) and the handle stays
+ * usable.  Not part of the paper's method (failure handling for the
+ * persistent kernels).  Errors: INVALID_ARG (null handle, cycles < 0). */
+curid_status curid_set_timeout(curid_handle* handle, long long cycles);
 
 /* Workspace bytes needed by curid_cur / curid_tsid / curid_id_col /
  * curid_id_row for an m x n matrix of dtype `dtype` at rank k with sketch
@@ -256,7 +263,9 @@ curid_status curid_interp_tsvd(curid_handle* handle, curid_dtype dtype,
  *     860 rows in float64, 1720 in float32) return CURID_NO_WORKSPACE
  *     before any work is enqueued.
  *   - The first call on a device (with that device current) looks up the
- *     array's device address; make that first call before any stream
+ *     array's device address; with lazy module loading that call is also
+ *     where the array is reserved (and can fail for lack of memory), so make
+ *     it before reserving the rest of device memory, and before any stream
  *     capture.
  *   - Every call reuses the same array, so calls whose work overlaps on the
  *     GPU (other streams, other host threads) race: serialise them.

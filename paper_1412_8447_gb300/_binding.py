@@ -47,6 +47,7 @@ SIGNATURES = {
     "curid_destroy": [_vp],
     "curid_set_stream": [_vp, _vp],
     "curid_set_workspace": [_vp, _vp, ctypes.c_size_t],
+    "curid_set_timeout": [_vp, ctypes.c_longlong],
     "curid_workspace_size": [_vp, _int, _i64, _i64, _int, Sketch, ctypes.POINTER(ctypes.c_size_t)],
     "curid_last_status": [_vp, ctypes.POINTER(_int)],
     "curid_profile": [_vp, _int],
@@ -139,7 +140,8 @@ def _check(st, where):
 
 
 class _Handle:
-    """One library handle per CUDA device, with a growable workspace."""
+    """A library handle on one CUDA device, with a growable workspace; each
+    call binds torch's current stream."""
 
     def __init__(self, device):
         self.lib = load_library()
@@ -165,12 +167,33 @@ class _Handle:
 
 
 _handles = {}
+_slot = threading.local()
+
+
+class inflight:
+    """Context in which library calls use handle ``slot`` of their device
+    (its own workspace and status): decompositions queued on different
+    streams under different slots can run on the GPU at the same time.
+    Outside any context, slot 0."""
+
+    def __init__(self, slot):
+        self.slot = int(slot)
+
+    def __enter__(self):
+        self.prev = getattr(_slot, "v", 0)
+        _slot.v = self.slot
+        return self
+
+    def __exit__(self, *exc):
+        _slot.v = self.prev
+        return False
 
 
 def handle(device):
-    if device not in _handles:
-        _handles[device] = _Handle(device)
-    return _handles[device]
+    key = (device, getattr(_slot, "v", 0))
+    if key not in _handles:
+        _handles[key] = _Handle(device)
+    return _handles[key]
 
 
 def _dev(t):
@@ -249,6 +272,13 @@ def status_block(device=0):
     h = handle(device)
     torch.cuda.synchronize(device)
     return h.ws[:20].view(torch.int32).cpu().tolist() if h.ws is not None else None
+
+
+def set_timeout(cycles, device=0):
+    """Bound of the waits between blocks of the persistent kernels, in SM
+    clock cycles (0: the default, about 2 s)."""
+    h = handle(device)
+    _check(h.lib.curid_set_timeout(h.h, int(cycles)), "curid_set_timeout")
 
 
 def last_status(device=0):
@@ -729,26 +759,33 @@ class BatchedID:
 
 class HostStream:
     """CUR-IDs of a sequence of host matrices, each copied to the device and
-    its skeletons and U copied back, with the host-to-device copy of matrix
-    i + 1 overlapped with the decomposition of matrix i.
+    its skeletons and U copied back, with the host-to-device copies
+    overlapped with the decompositions.
 
-    Two device buffers for A and two output sets alternate; the copies of A
-    run on a side stream, each waiting until the decomposition that last read
-    its buffer has finished; the decompositions and the copies of (J, I, U)
-    back to the host run on the current stream.  Host matrices should be
-    pinned (``tensor.pin_memory()``) so the copies are asynchronous.  Only
-    stream and event bookkeeping happens here: every step of each
-    decomposition is the same library call ``cur`` makes.
+    ``inflight`` decompositions run at once, each on its own stream and
+    library handle (``inflight`` slots); inflight + 1 device buffers for A
+    rotate, so the copy of the next matrix runs while ``inflight``
+    decompositions use the others.  The copies of A run on a side stream,
+    each waiting until the decomposition that last read its buffer has
+    finished; the copies of (J, I, U) back to the host run on the stream of
+    their decomposition.  Host matrices should be pinned
+    (``tensor.pin_memory()``) so the copies are asynchronous.  Only stream
+    and event bookkeeping happens here: every step of each decomposition is
+    the same library call ``cur`` makes.
     """
 
-    def __init__(self, m, n, k, dtype=torch.float32, device=None, p=-1, q=0, tf32=False):
+    def __init__(self, m, n, k, dtype=torch.float32, device=None, p=-1, q=0, tf32=False,
+                 inflight=1):
         dev = torch.device("cuda", device if device is not None else torch.cuda.current_device())
         self.device, self.k, self.p, self.q, self.tf32 = dev, int(k), int(p), int(q), bool(tf32)
-        self.A = [torch.empty((m, n), dtype=dtype, device=dev) for _ in range(2)]
-        self.out = [cur_outputs(self.A[s], k) for s in range(2)]
+        self.inflight = max(1, int(inflight))
+        nbuf = self.inflight + 1
+        self.A = [torch.empty((m, n), dtype=dtype, device=dev) for _ in range(nbuf)]
+        self.out = [cur_outputs(self.A[0], k) for _ in range(self.inflight)]
         self.copy_stream = torch.cuda.Stream(dev)
-        self.ready = [torch.cuda.Event() for _ in range(2)]
-        self.free = [torch.cuda.Event() for _ in range(2)]
+        self.streams = [None] + [torch.cuda.Stream(dev) for _ in range(self.inflight - 1)]
+        self.ready = [torch.cuda.Event() for _ in range(nbuf)]
+        self.free = [torch.cuda.Event() for _ in range(nbuf)]
 
     def host_results(self, count):
         """Pinned host buffers (J, I, U) for ``count`` decompositions."""
@@ -761,40 +798,50 @@ class HostStream:
     def run(self, A_hosts, results, seeds=None):
         """Decompose every matrix of ``A_hosts`` (host tensors of the stream's
         shape and dtype) into ``results[i] = (J, I, U)`` host tensors.  Work is
-        queued on the current stream and returns before it finishes;
+        queued behind the current stream and returns before it finishes;
         synchronize before reading ``results``.  Device status is not checked
-        (read it with ``last_status``)."""
+        (read it with ``last_status`` inside ``inflight(slot)``)."""
         cur_s = torch.cuda.current_stream(self.device)
+        streams = [cur_s] + self.streams[1:]
         count = len(A_hosts)
+        nbuf = len(self.A)
         if len(results) < count:
             raise ValueError("one (J, I, U) result triple per matrix is needed")
-        # no copy may start before work already queued on the current stream
+        # no copy or decomposition may start before work already queued on
+        # the current stream
         self.copy_stream.wait_stream(cur_s)
-        first = [True, True]
+        for st in streams[1:]:
+            st.wait_stream(cur_s)
+        first = [True] * nbuf
 
         def copy_in(i):
-            s = i & 1
+            b = i % nbuf
             with torch.cuda.stream(self.copy_stream):
-                if not first[s]:
-                    self.copy_stream.wait_event(self.free[s])
-                first[s] = False
-                self.A[s].copy_(A_hosts[i], non_blocking=True)
-                self.ready[s].record(self.copy_stream)
+                if not first[b]:
+                    self.copy_stream.wait_event(self.free[b])
+                first[b] = False
+                self.A[b].copy_(A_hosts[i], non_blocking=True)
+                self.ready[b].record(self.copy_stream)
 
-        if count:
-            copy_in(0)
+        for i in range(min(count, self.inflight)):
+            copy_in(i)
         for i in range(count):
-            s = i & 1
-            if i + 1 < count:
-                copy_in(i + 1)
-            cur_s.wait_event(self.ready[s])
+            b, slot = i % nbuf, i % self.inflight
+            if i + self.inflight < count:
+                copy_in(i + self.inflight)
+            st = streams[slot]
+            st.wait_event(self.ready[b])
             seed = seeds[i] if seeds is not None else i
-            cur(self.A[s], self.k, p=self.p, q=self.q, seed=seed, tf32=self.tf32,
-                out=self.out[s], check=False)
-            self.free[s].record(cur_s)
-            J, I, U = results[i]
-            J.copy_(self.out[s].J, non_blocking=True)
-            I.copy_(self.out[s].I, non_blocking=True)
-            U.copy_(self.out[s].U, non_blocking=True)
-        # the A buffers must not be reused by a later run before these copies
+            with torch.cuda.stream(st), inflight(slot):
+                cur(self.A[b], self.k, p=self.p, q=self.q, seed=seed, tf32=self.tf32,
+                    out=self.out[slot], check=False)
+                self.free[b].record(st)
+                J, I, U = results[i]
+                J.copy_(self.out[slot].J, non_blocking=True)
+                I.copy_(self.out[slot].I, non_blocking=True)
+                U.copy_(self.out[slot].U, non_blocking=True)
+        # the A buffers must not be reused by a later run before these copies,
+        # and the current stream ends after every decomposition
         cur_s.wait_stream(self.copy_stream)
+        for st in streams[1:]:
+            cur_s.wait_stream(st)

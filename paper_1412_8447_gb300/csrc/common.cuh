@@ -94,6 +94,8 @@ struct curid_handle {
   // batched column ID: launch shape chosen by the autotuner ([0] float64,
   // [1] float32; -1 = not tuned)
   int batch_shape[2] = {-1, -1};
+  // bound of every inter-block wait in SM clock cycles (curid_set_timeout)
+  long long spin = curid::kSpinBudget;
 };
 
 #define CURID_CUDA(call)                                \

@@ -29,6 +29,8 @@
 // After the last step row i of S holds S1(i, c) for every original column c,
 // J lists the pivots and then the unselected columns in ascending order.
 #include <atomic>
+#include <cstdlib>
+#include <cstring>
 
 #include "cpqr_exchange.cuh"
 
@@ -309,7 +311,17 @@ template <typename real>
 curid_status cpqr_layout(const Ctx& ctx, int64_t l, int64_t n, int* G_out, int* nc_out,
                          int* ncs_out) {
   if (l <= 0 || n <= 0) return CURID_INVALID_ARG;
-  int G = (int)std::min<int64_t>(std::min(ctx.num_sms, 32 * kMaxSlotsPerLane), n);
+  const int gmax = std::min(ctx.num_sms, 32 * kMaxSlotsPerLane);
+  int G = (int)std::min<int64_t>(gmax, n);
+  // register-resident slabs: the fewest CTAs whose registers hold the matrix.
+  // The pivot exchange gets cheaper with fewer CTAs (records of 38-64 CTAs
+  // meet in about 2.4K cycles on GB300, of 152 in about twice that) while
+  // the update has work to spare, and the SMs left free serve other streams.
+  // CURID_CPQR_CTAS=all keeps one CTA per SM (for comparisons).
+  const int64_t rc = cpqr_reg_cols<real>((int)std::min<int64_t>(l, INT32_MAX));
+  const char* env = std::getenv("CURID_CPQR_CTAS");
+  const bool all = env && std::strcmp(env, "all") == 0;
+  if (rc > 0 && !all && (n + rc - 1) / rc <= gmax) G = (int)((n + rc - 1) / rc);
   const int nc = (int)((n + G - 1) / G);
   G = (int)((n + nc - 1) / nc);
   const int ldl = (int)(l | 1);
@@ -379,6 +391,7 @@ curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64
   P.abort_flag = s.abort_flag;
   P.status = ctx.status;
   P.which = which;
+  P.spin = ctx.spin;
   CURID_CUDA(cudaMemsetAsync(s.slots, 0, 2 * (size_t)G * sizeof(Rec), ctx.stream));
   CURID_CUDA(cudaMemsetAsync(s.abort_flag, 0, sizeof(int), ctx.stream));
   if (cpqr_reg_fits<real>(ctx, (int)l, nc)) return cpqr_reg_launch<real>(ctx, P, G);

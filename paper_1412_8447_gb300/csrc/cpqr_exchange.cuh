@@ -42,6 +42,7 @@ struct CpqrParams {
   StatusBlock* status;
   int which;
   unsigned gen;                  // launch generation, high bits of every tag
+  long long spin;                // bound of every inter-block wait, SM clock cycles
 };
 
 // Published candidate columns are tagged word by word like the records, so a
@@ -94,7 +95,7 @@ __device__ __forceinline__ void put_tagged(unsigned long long* dst, unsigned tag
 // Bounded read of one tagged element; false if it never became fresh.
 template <typename real>
 __device__ __forceinline__ bool get_tagged(const unsigned long long* src, unsigned tag, real* v,
-                                           const int* abort_flag) {
+                                           const int* abort_flag, long long spin) {
   const long long t0 = clock64();
   while (true) {
     if (sizeof(real) == 8) {
@@ -111,7 +112,7 @@ __device__ __forceinline__ bool get_tagged(const unsigned long long* src, unsign
         return true;
       }
     }
-    if (ld_volatile_i32(abort_flag) || clock64() - t0 > kSpinBudget) return false;
+    if (ld_volatile_i32(abort_flag) || clock64() - t0 > spin) return false;
   }
 }
 
@@ -178,7 +179,7 @@ __device__ bool gather_records(const CpqrParams<real>& P, int bf, unsigned epoch
     if (lane + 32 * r < G) pending |= 1u << r;
   bool ok = true;
   const long long t0 = clock64();
-  for (int round = 0; pending; ++round) {
+  while (pending) {
 #pragma unroll
     for (int r = 0; r < kMaxSlotsPerLane; ++r) {
       if (!(pending & (1u << r))) continue;
@@ -201,13 +202,11 @@ __device__ bool gather_records(const CpqrParams<real>& P, int bf, unsigned epoch
       if (fresh) pending &= ~(1u << r);
     }
     if (!pending) break;
-    if ((round & 15) == 15) {
-      if (ld_volatile_i32(P.abort_flag)) { ok = false; break; }
-      if (clock64() - t0 > kSpinBudget) {
-        atomicExch(P.abort_flag, 1);
-        ok = false;
-        break;
-      }
+    if (ld_volatile_i32(P.abort_flag)) { ok = false; break; }
+    if (clock64() - t0 > P.spin) {
+      atomicExch(P.abort_flag, 1);
+      ok = false;
+      break;
     }
   }
   ok = __all_sync(0xffffffffu, ok);
@@ -302,7 +301,7 @@ __device__ __forceinline__ bool fetch_pivot(const CpqrParams<real>& P, int j, in
   // st.stale was cleared by decide_pivot before the barrier that precedes this
   for (int r = j + tid; r < l; r += kThreadsPerCta) {
     real v;
-    if (!get_tagged<real>(src + (int64_t)r * W, tag, &v, P.abort_flag)) {
+    if (!get_tagged<real>(src + (int64_t)r * W, tag, &v, P.abort_flag, P.spin)) {
       st.stale = 1;
       v = real(0);
     }
@@ -401,9 +400,12 @@ __device__ __forceinline__ void reflector(real alpha, real nu, real* beta, real*
 // factorization with nc columns per CTA, and its launch (scratch already
 // reset by the caller).
 template <typename real>
+int cpqr_reg_cols(int l);  // most columns of a register-resident slab (0: l too large)
+template <typename real>
 bool cpqr_reg_fits(const Ctx& ctx, int l, int nc);
 template <typename real>
 curid_status cpqr_reg_launch(const Ctx& ctx, const CpqrParams<real>& P, int G);
 
 }  // namespace cpqr_x
+
 }  // namespace curid

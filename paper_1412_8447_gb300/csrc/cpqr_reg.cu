@@ -31,8 +31,8 @@ namespace cpqr_x {
 
 namespace {
 
-constexpr int kCols = 4;                    // columns a warp holds
-constexpr int kMaxRegCols = kWarps * kCols;  // columns of a slab
+constexpr int kMaxCols = 8;                    // columns a warp holds (at most)
+constexpr int kMaxRegCols = kWarps * kMaxCols;  // columns of a slab
 
 // Rows a lane can hold for four columns without spilling: 8 per lane in
 // float32, 4 in float64 (128 registers per thread at 512 threads).
@@ -77,19 +77,25 @@ struct WarpBest {
   int nf[kWarps];
 };
 
-// Each warp, after its residual norms are summed by reduce4 (lane t holds the
-// squared norm of its column (t >> 3) & 3): post the warp's best unselected
-// column, the sum of its squared norms and whether one is not finite.
-template <typename real>
-__device__ __forceinline__ void post_warp_best(real q, unsigned act, int lane, int warp,
-                                               WarpBest<real>& wb) {
-  const int c = (lane >> 3) & 3;
-  const bool on = (act >> c) & 1u;
-  const real nv = sqrt(q);
-  real bn = on ? nv : real(-1);
-  int bi = on ? warp + kWarps * c : -1;
-  real ss = on ? nv * nv : real(0);
-  int nf = on && !isfinite(nv);
+// Each warp, after its residual norms are summed by reduce4 per group of four
+// columns (lane t holds the squared norm of column 4 g + ((t >> 3) & 3) in
+// qg[g]): post the warp's best unselected column, the sum of its squared
+// norms and whether one is not finite.
+template <int KC, typename real>
+__device__ __forceinline__ void post_warp_best(const real (&qg)[KC / 4], unsigned act, int lane,
+                                               int warp, WarpBest<real>& wb) {
+  const int cs = (lane >> 3) & 3;
+  real bn = real(-1), ss = real(0);
+  int bi = -1, nf = 0;
+#pragma unroll
+  for (int g = 0; g < KC / 4; ++g) {
+    const int c = 4 * g + cs;
+    if (!((act >> c) & 1u)) continue;
+    const real nv = sqrt(qg[g]);
+    ss += nv * nv;
+    if (!isfinite(nv)) nf = 1;
+    else if (local_better(nv, warp + kWarps * c, bn, bi)) { bn = nv; bi = warp + kWarps * c; }
+  }
 #pragma unroll
   for (int o = 8; o <= 16; o <<= 1) {
     const real on2 = __shfl_xor_sync(0xffffffffu, bn, o);
@@ -111,9 +117,9 @@ __device__ __forceinline__ void post_warp_best(real q, unsigned act, int lane, i
 // warp holding the candidate writes its rows r0..l-1 to the CTA's data slot
 // as tagged words (readers check every word's tag, so the two writes need no
 // order between them).
-template <int RPL, typename real>
+template <int RPL, int KC, typename real>
 __device__ __forceinline__ void publish_reg(const CpqrParams<real>& P, const WarpBest<real>& wb,
-                                            const real (&y)[kCols][RPL], int c0, int r0, int bf,
+                                            const real (&y)[KC][RPL], int c0, int r0, int bf,
                                             unsigned epoch, int lane, int warp) {
   real bn = lane < kWarps ? wb.bn[lane] : real(-1);
   int bi = lane < kWarps ? wb.bi[lane] : -1;
@@ -147,7 +153,7 @@ __device__ __forceinline__ void publish_reg(const CpqrParams<real>& P, const War
     unsigned long long* dst = slot_of(P, bf, blockIdx.x);
     const int cb = bi / kWarps;
 #pragma unroll
-    for (int c = 0; c < kCols; ++c) {
+    for (int c = 0; c < KC; ++c) {
       if (c != cb) continue;
 #pragma unroll
       for (int u = 0; u < RPL; ++u) {
@@ -158,8 +164,9 @@ __device__ __forceinline__ void publish_reg(const CpqrParams<real>& P, const War
   }
 }
 
-template <typename real, int RPL>
+template <typename real, int RPL, int KC>
 __global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> P) {
+  constexpr int NG = KC / 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b = blockIdx.x;
@@ -181,24 +188,30 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> 
   for (int lc = tid; lc < nc; lc += kThreads) active[lc] = lc < ncl ? 1 : 0;
   __syncthreads();
 
-  real y[kCols][RPL];
+  real y[KC][RPL];
   unsigned act = 0;  // bit c: column warp + 16 c is unselected (warp-uniform)
-  real q[kCols];
+  {
+    real q[KC];
 #pragma unroll
-  for (int c = 0; c < kCols; ++c) {
-    const int lc = warp + kWarps * c;
-    if (lc < ncl) act |= 1u << c;
-    q[c] = real(0);
+    for (int c = 0; c < KC; ++c) {
+      const int lc = warp + kWarps * c;
+      if (lc < ncl) act |= 1u << c;
+      q[c] = real(0);
 #pragma unroll
-    for (int u = 0; u < RPL; ++u) {
-      const int r = lane + 32 * u;
-      y[c][u] = (lc < ncl && r < l) ? ys[(int64_t)lc * ldl + r] : real(0);
-      q[c] += y[c][u] * y[c][u];
+      for (int u = 0; u < RPL; ++u) {
+        const int r = lane + 32 * u;
+        y[c][u] = (lc < ncl && r < l) ? ys[(int64_t)lc * ldl + r] : real(0);
+        q[c] += y[c][u] * y[c][u];
+      }
     }
+    real qg[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+      qg[g] = reduce4(q[4 * g], q[4 * g + 1], q[4 * g + 2], q[4 * g + 3], lane);
+    post_warp_best<KC>(qg, act, lane, warp, wb);
   }
-  post_warp_best(reduce4(q[0], q[1], q[2], q[3], lane), act, lane, warp, wb);
   __syncthreads();
-  publish_reg<RPL>(P, wb, y, c0, 0, 0, 1u, lane, warp);
+  publish_reg<RPL, KC>(P, wb, y, c0, 0, 0, 1u, lane, warp);
 
   real normY = real(-1), nu_first = real(0);
   int k_eff = -1;
@@ -221,21 +234,27 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> 
       const real x = (r > j && r < l) ? xv[r] : real(0);
       v[u] = r == j ? real(1) : scale * x;
     }
-    real d[kCols];
+    // dot products (a selected column is zero from row j on, so it needs no
+    // mask); with eight columns a warp skips the row blocks of 32 above the
+    // pivot row (v is zero there), a warp-uniform branch per block
+    real d[KC];
 #pragma unroll
-    for (int c = 0; c < kCols; ++c) {
-      d[c] = real(0);
-      if ((act >> c) & 1u) {
+    for (int c = 0; c < KC; ++c) d[c] = real(0);
 #pragma unroll
-        for (int u = 0; u < RPL; ++u) d[c] += v[u] * y[c][u];
-      }
+    for (int u = 0; u < RPL; ++u) {
+      if (KC > 4 && 32 * u + 31 < j) continue;
+#pragma unroll
+      for (int c = 0; c < KC; ++c) d[c] += v[u] * y[c][u];
     }
-    const real dsum = reduce4(d[0], d[1], d[2], d[3], lane);
+    real dg[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+      dg[g] = reduce4(d[4 * g], d[4 * g + 1], d[4 * g + 2], d[4 * g + 3], lane);
     // the warp holding the pivot column retires it: beta at row j, zeros below
     const int pl = pcol - c0;
     const int pc = (pl >= 0 && pl < ncl && pl % kWarps == warp) ? pl / kWarps : -1;
 #pragma unroll
-    for (int c = 0; c < kCols; ++c) {
+    for (int c = 0; c < KC; ++c) {
       if (c == pc) {
 #pragma unroll
         for (int u = 0; u < RPL; ++u) {
@@ -249,28 +268,34 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> 
         }
       }
     }
+    real q[KC];
 #pragma unroll
-    for (int c = 0; c < kCols; ++c) {
+    for (int c = 0; c < KC; ++c) {
       q[c] = real(0);
-      const real w = tau * __shfl_sync(0xffffffffu, dsum, 8 * c);
+      const real w = tau * __shfl_sync(0xffffffffu, dg[c / 4], 8 * (c % 4));
       if ((act >> c) & 1u) {
 #pragma unroll
         for (int u = 0; u < RPL; ++u) {
+          if (KC > 4 && 32 * u + 31 < j) continue;
           const int r = lane + 32 * u;
           y[c][u] -= w * v[u];
           if (r > j) q[c] += y[c][u] * y[c][u];
         }
       }
     }
-    post_warp_best(reduce4(q[0], q[1], q[2], q[3], lane), act, lane, warp, wb);
+    real qg[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+      qg[g] = reduce4(q[4 * g], q[4 * g + 1], q[4 * g + 2], q[4 * g + 3], lane);
+    post_warp_best<KC>(qg, act, lane, warp, wb);
     __syncthreads();
-    publish_reg<RPL>(P, wb, y, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2), lane, warp);
+    publish_reg<RPL, KC>(P, wb, y, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2), lane, warp);
   }
   const int k_done = j;
   if (st.stop == 2) return;  // timed out: leave without further waits
   // S rows 0..k_done-1 in original column order, staged through shared memory
 #pragma unroll
-  for (int c = 0; c < kCols; ++c) {
+  for (int c = 0; c < KC; ++c) {
     const int lc = warp + kWarps * c;
     if (lc < ncl) {
 #pragma unroll
@@ -296,10 +321,19 @@ size_t reg_smem_bytes(int nc, int ldl) {
 
 }  // namespace
 
+// Eight columns per warp fit the registers without spilling up to 224 rows
+// in float32 and 64 in float64; four up to 256 / 128 rows.
+template <typename real>
+int cpqr_reg_cols(int l) {
+  if (l < 1 || l > max_reg_rows<real>()) return 0;
+  const int wide_rows = sizeof(real) == 4 ? 224 : 64;
+  return kWarps * (l <= wide_rows ? 8 : 4);
+}
+
 template <typename real>
 bool cpqr_reg_fits(const Ctx& ctx, int l, int nc) {
   // the kernel's static shared variables share the per-block limit
-  return l >= 1 && l <= max_reg_rows<real>() && nc >= 1 && nc <= kMaxRegCols &&
+  return nc >= 1 && nc <= cpqr_reg_cols<real>(l) &&
          reg_smem_bytes<real>(nc, l | 1) + 1024 <= ctx.smem_optin;
 }
 
@@ -307,10 +341,20 @@ template <typename real>
 curid_status cpqr_reg_launch(const Ctx& ctx, const CpqrParams<real>& P, int G) {
   if (!cpqr_reg_fits<real>(ctx, P.l, P.nc)) return CURID_UNSUPPORTED;
   const size_t smem = reg_smem_bytes<real>(P.nc, P.ldl);
-  void (*fn)(CpqrParams<real>) = P.l <= 64 ? cpqr_reg_kernel<real, 2> : cpqr_reg_kernel<real, 4>;
-  if constexpr (sizeof(real) == 4) {
-    if (P.l > 128) fn = P.l <= 224 ? cpqr_reg_kernel<real, 7> : cpqr_reg_kernel<real, 8>;
+  // rows per lane from l; four columns per warp when the slab has at most
+  // 64 columns, else eight
+  const bool wide = P.nc > kWarps * 4;
+  void (*fn)(CpqrParams<real>) = nullptr;
+  if (P.l <= 64) fn = wide ? cpqr_reg_kernel<real, 2, 8> : cpqr_reg_kernel<real, 2, 4>;
+  else if (P.l <= 128) {
+    if constexpr (sizeof(real) == 4) fn = wide ? cpqr_reg_kernel<real, 4, 8> : cpqr_reg_kernel<real, 4, 4>;
+    else fn = cpqr_reg_kernel<real, 4, 4>;
   }
+  if constexpr (sizeof(real) == 4) {
+    if (P.l > 128 && P.l <= 224) fn = wide ? cpqr_reg_kernel<real, 7, 8> : cpqr_reg_kernel<real, 7, 4>;
+    else if (P.l > 224) fn = cpqr_reg_kernel<real, 8, 4>;
+  }
+  if (!fn) return CURID_UNSUPPORTED;
   CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CpqrParams<real> Pc = P;
   void* args[] = {&Pc};
@@ -320,6 +364,8 @@ curid_status cpqr_reg_launch(const Ctx& ctx, const CpqrParams<real>& P, int G) {
   return CURID_OK;
 }
 
+template int cpqr_reg_cols<float>(int);
+template int cpqr_reg_cols<double>(int);
 template bool cpqr_reg_fits<float>(const Ctx&, int, int);
 template bool cpqr_reg_fits<double>(const Ctx&, int, int);
 template curid_status cpqr_reg_launch<float>(const Ctx&, const CpqrParams<float>&, int);

@@ -13,14 +13,19 @@
 //
 // The scratch is a file-scope __device__ array of kStaticScratchBytes
 // (4 MiB); every GPU that loads this library keeps it until the process
-// exits.  Host code may not use the array's name as a device address (on
-// the host it is only a stand-in object), so the first call on each device,
-// with that device current, looks the address up with cudaGetSymbolAddress
-// and caches it; make that first call before any stream capture.  All calls
-// share the one array and it keeps the previous call's contents, so each
-// call clears the parts that must start at zero; two calls whose work
-// overlaps on the GPU (different streams, or different host threads) race
-// on the array and must be serialised by the caller.
+// exits.  With CUDA's lazy module loading the array is reserved when this
+// module is first used on a device, which is this entry point's first call
+// there: that call is the one point where the reservation can fail, so make
+// it before reserving the rest of device memory.  Host code may not use the
+// array's name as a device address (on the host it is only a stand-in
+// object), so the first call on each device, with that device current,
+// looks the address up with cudaGetSymbolAddress and caches it; make that
+// first call before any stream capture too.  All calls share the one array and it
+// keeps the previous call's contents, so each call clears the parts that
+// must start at zero; two calls whose work overlaps on the GPU (different
+// streams, or different host threads) race on the array and must be
+// serialised by the caller.
+#include <cstddef>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -87,6 +92,10 @@ curid_status run_static(const StaticDevice& d, cudaStream_t stream, const real* 
   ctx.status = st;
   CURID_CUDA(cudaMemsetAsync(st, 0, sizeof(StatusBlock), stream));
   CURID_TRY(cpqr_run<real>(ctx, Y, l, n, ldy, k_max, tol, J, S, n, cs, 0));
+  // info = the status block's first three words (flags, steps, rank)
+  static_assert(offsetof(StatusBlock, flags) == 0 && offsetof(StatusBlock, k_done) == 4 &&
+                    offsetof(StatusBlock, k_eff) == 8,
+                "info copies flags, k_done and k_eff in this order");
   if (info) CURID_CUDA(cudaMemcpyAsync(info, st, 3 * sizeof(int), cudaMemcpyDeviceToDevice, stream));
   return CURID_OK;
 }

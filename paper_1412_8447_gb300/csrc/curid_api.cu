@@ -60,6 +60,7 @@ struct PhaseScope {
 Ctx make_ctx(curid_handle* h) {
   Ctx c{h->stream, h->num_sms, h->smem_optin, nullptr};
   c.launches = h->profiling ? &h->launches : nullptr;
+  c.spin = h->spin;
   return c;
 }
 
@@ -1019,6 +1020,12 @@ curid_status curid_profile_read(curid_handle* handle, double* ms, int* calls,
 curid_status curid_set_stream(curid_handle* handle, void* stream) {
   if (!handle) return CURID_INVALID_ARG;
   handle->stream = static_cast<cudaStream_t>(stream);
+  return CURID_OK;
+}
+
+curid_status curid_set_timeout(curid_handle* handle, long long cycles) {
+  if (!handle || cycles < 0) return CURID_INVALID_ARG;
+  handle->spin = cycles > 0 ? cycles : kSpinBudget;
   return CURID_OK;
 }
 

@@ -16,6 +16,7 @@ struct Ctx {
   size_t smem_optin;
   StatusBlock* status;          // device
   long long* launches = nullptr;  // host counter of kernel launches (profiling)
+  long long spin = kSpinBudget;   // bound of inter-block waits, SM clock cycles
 };
 
 // After a kernel launch: report a launch error, count the launch.

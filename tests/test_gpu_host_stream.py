@@ -3,7 +3,8 @@ matrix overlapped with the current decomposition.  Its results must be the
 ones the plain device call gives on the same matrices and seeds (the same
 kernels on the same inputs), and the copy-in of a buffer must not overtake
 the decomposition still reading it (checked by alternating distinct
-matrices through the two buffers)."""
+matrices through the buffers), with one decomposition in flight and with
+three on three streams."""
 import pytest
 import torch
 
@@ -13,14 +14,14 @@ import synthetic as syn
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("tf32", [False, True])
-def test_host_stream_matches_device_calls(tf32):
+@pytest.mark.parametrize("tf32,inflight", [(False, 1), (True, 1), (True, 3)])
+def test_host_stream_matches_device_calls(tf32, inflight):
     m, n, k, p, q = 1500, 1100, 60, 10, 1
     mats = [syn.spectrum_matrix(m, n, syn.power_decay(n), 1412 + i, torch.float32, "cpu")
             for i in range(5)]
     hosts = [a.pin_memory() for a in mats]
     seeds = [9000 + i for i in range(5)]
-    hs = curid.HostStream(m, n, k, torch.float32, 0, p=p, q=q, tf32=tf32)
+    hs = curid.HostStream(m, n, k, torch.float32, 0, p=p, q=q, tf32=tf32, inflight=inflight)
     res = hs.host_results(5)
     hs.run(hosts, res, seeds)
     torch.cuda.synchronize()

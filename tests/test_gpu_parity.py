@@ -230,6 +230,7 @@ def test_randomized_cur_moderate(dtype):
     else:
         assert abs(eg - e_same) <= 1e-5, (eg, e_same)
         assert eg <= 1.05 * eo, (eg, eo)
+        assert abs(eg - eo) <= 1e-5, (eg, eo)
 
 
 @pytest.mark.parametrize("dtype,k,p", [(torch.float32, 246, 10), (torch.float64, 182, 10),
@@ -406,6 +407,7 @@ def test_tensor_core_randomized_cur():
     eg = O.rel_err_fro(Ah, C, U, R)
     eo = O.rel_err_fro(Ah, o.C, o.U, o.R)
     assert eg <= 1.05 * eo, (eg, eo)
+    assert abs(eg - eo) <= 1e-5, (eg, eo)
     assert id_residual(Ah, J, T, k) <= 1.05 * id_residual(Ah, o.J, o.T, k)
     Uo = O.cur_middle(R, O.vstar(J, T, n))
     assert abs(eg - O.rel_err_fro(Ah, C, Uo, R)) <= 1e-5
