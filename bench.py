@@ -228,6 +228,7 @@ def run_ours(args, ws, rank, local):
 
     # ---- 1. one decomposition at a time: latency, per-phase times and the
     # launch durations the roofline uses (kernels timed in isolation) --------
+    curid.set_concurrency(1, local)
     for i in range(args.warmup):
         step(i, 0)
     check_status("warm-up", 1)
@@ -248,6 +249,9 @@ def run_ours(args, ws, rank, local):
     err_gpu = rel_err_gpu(A, outs[0].J, outs[0].I, outs[0].U, args.k)
 
     # ---- 2. throughput: kin decompositions in flight, K timed steps ---------
+    for s in range(kin):
+        with torch.cuda.stream(streams[s]), curid.inflight(s):
+            curid.set_concurrency(kin, local)
     for i in range(max(args.warmup, 2 * kin)):
         step(1000 + i)
     torch.cuda.synchronize(dev)
@@ -480,6 +484,7 @@ def measure_c1(dev, reps=20, inflight=8, steps=64):
     outs = []
     for s in range(inflight):
         with torch.cuda.stream(streams[s]), curid.inflight(s):
+            curid.set_concurrency(inflight, dev.index or 0)
             outs.append(curid.cur_outputs(A, k))
 
     def call(s):
@@ -491,12 +496,15 @@ def measure_c1(dev, reps=20, inflight=8, steps=64):
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     lat = []
+    curid.set_concurrency(1, dev.index or 0)
+    call(0)
     for _ in range(reps):
         e0.record(main)
         call(0)
         e1.record(main)
         torch.cuda.synchronize(dev)
         lat.append(e0.elapsed_time(e1))
+    curid.set_concurrency(inflight, dev.index or 0)
     e0.record(main)
     for st in streams[1:]:
         st.wait_event(e0)

@@ -105,6 +105,16 @@ curid_status curid_set_workspace(curid_handle* handle, void* ptr, size_t bytes);
  * usable.  Not part of the paper's method (failure handling for the
  * persistent kernels).  Errors: INVALID_ARG (null handle, cycles < 0). */
 curid_status curid_set_timeout(curid_handle* handle, long long cycles);
+/* How many decompositions the caller keeps in flight on this GPU at once
+ * (each with its own handle, stream and workspace; default 1).  With 1 the
+ * persistent CPQR kernel runs one block per SM, the lowest latency per
+ * factorization; with more it runs on the fewest SMs that hold the matrix
+ * (about a third for the sample matrix of an 8000 x 6000 decomposition at
+ * k = 200), a little slower on its own but leaving the other SMs to the
+ * other decompositions.  Results do not depend on it beyond rounding.
+ * Set it before sizing the workspace.  Errors: INVALID_ARG (null handle,
+ * inflight < 1). */
+curid_status curid_set_concurrency(curid_handle* handle, int inflight);
 
 /* Workspace bytes needed by curid_cur / curid_tsid / curid_id_col /
  * curid_id_row for an m x n matrix of dtype `dtype` at rank k with sketch

@@ -6,7 +6,7 @@ C ABI of ``include/curid.h``); this package is its thin Python binding.
 """
 from ._binding import (  # noqa: F401
     BatchedID, CURFunction, CuridError, HostStream, LIB_PATH, PHASES, Result, STATUS_NAMES, cpqr,
-    inflight, set_timeout,
+    inflight, set_concurrency, set_timeout,
     cur, cur_adjoint, cur_complex, cur_differentiable, cur_outputs, cur_sparse, gaussian, id_col, id_row,
     interp_tikhonov, interp_tsvd, last_status, load_library, profile, profile_read, sketch_matrix,
     sparse_operand, srft_draw, srft_omega, tsid,

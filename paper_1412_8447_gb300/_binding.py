@@ -48,6 +48,7 @@ SIGNATURES = {
     "curid_set_stream": [_vp, _vp],
     "curid_set_workspace": [_vp, _vp, ctypes.c_size_t],
     "curid_set_timeout": [_vp, ctypes.c_longlong],
+    "curid_set_concurrency": [_vp, _int],
     "curid_workspace_size": [_vp, _int, _i64, _i64, _int, Sketch, ctypes.POINTER(ctypes.c_size_t)],
     "curid_last_status": [_vp, ctypes.POINTER(_int)],
     "curid_profile": [_vp, _int],
@@ -272,6 +273,13 @@ def status_block(device=0):
     h = handle(device)
     torch.cuda.synchronize(device)
     return h.ws[:20].view(torch.int32).cpu().tolist() if h.ws is not None else None
+
+
+def set_concurrency(inflight, device=0):
+    """Tell the library how many decompositions are kept in flight on
+    ``device`` (applies to the current ``inflight`` slot's handle)."""
+    h = handle(device)
+    _check(h.lib.curid_set_concurrency(h.h, int(inflight)), "curid_set_concurrency")
 
 
 def set_timeout(cycles, device=0):
@@ -823,6 +831,9 @@ class HostStream:
                 self.A[b].copy_(A_hosts[i], non_blocking=True)
                 self.ready[b].record(self.copy_stream)
 
+        for slot in range(self.inflight):
+            with torch.cuda.stream(streams[slot]), inflight(slot):
+                set_concurrency(self.inflight, self.device.index)
         for i in range(min(count, self.inflight)):
             copy_in(i)
         for i in range(count):

@@ -194,11 +194,11 @@ curid_status adjoint_run(const Ctx& ctx0, const real* A, int64_t m, int64_t n, i
   CURID_TRY(gather_rows<real>(ctx, A, m, n, lda, I, k, Rraw, n));
   CURID_TRY(mm(false, true, k, k, n, one, Rraw, n, Qr, n, zero, P.Lr, k));
   // C^T = L_C Q_C^T; L_C = C^T Q_C; C^T itself is kept (gathered again)
-  CURID_TRY(gather_cols<real>(ctx, A, m, lda, J, k, P.C1, m, true));
+  CURID_TRY(gather_cols<real>(ctx, A, m, n, lda, J, k, P.C1, m, true));
   real* Qc = P.C1;
   real* Craw = P.C2;
   CURID_TRY(chol_qr_rows<real>(ctx, &Qc, &Craw, k, m, m, P.G, P.partial, P.partial_cap));
-  CURID_TRY(gather_cols<real>(ctx, A, m, lda, J, k, Craw, m, true));
+  CURID_TRY(gather_cols<real>(ctx, A, m, n, lda, J, k, Craw, m, true));
   CURID_TRY(mm(false, true, k, k, m, one, Craw, m, Qc, m, zero, P.Lc, k));
   CURID_TRY(tri_solve<real>(ctx, k, P.Lr, k, false, false, nullptr, 0, P.Lri, k, k, nullptr));
   CURID_TRY(tri_solve<real>(ctx, k, P.Lc, k, false, false, nullptr, 0, P.Lci, k, k, nullptr));
@@ -262,6 +262,8 @@ curid_status adjoint_check(curid_handle* h, curid_dtype dt, int64_t m, int64_t n
   if (m <= 0 || n <= 0 || m > INT32_MAX || n > INT32_MAX) return CURID_INVALID_ARG;
   if (k < 1 || k > std::min(m, n)) return CURID_INVALID_ARG;
   Ctx ctx{nullptr, h->num_sms, h->smem_optin, nullptr};
+  ctx.spin = h->spin;
+  ctx.concurrency = h->concurrency;
   const bool fits = dt == CURID_F64
                         ? (tri_solve_fits<double>(ctx, k) && chol_inverse_fits<double>(ctx, k))
                         : (tri_solve_fits<float>(ctx, k) && chol_inverse_fits<float>(ctx, k));
@@ -277,6 +279,8 @@ curid_status curid_cur_adjoint_workspace_size(curid_handle* handle, curid_dtype 
   if (!bytes) return CURID_INVALID_ARG;
   CURID_TRY(adjoint_check(handle, dtype, m, n, k));
   Ctx ctx{nullptr, handle->num_sms, handle->smem_optin, nullptr};
+  ctx.spin = handle->spin;
+  ctx.concurrency = handle->concurrency;
   if (dtype == CURID_F64) {
     AdjPlan<double> P;
     adj_plan<double>(ctx, m, n, k, nullptr, &P);
@@ -301,6 +305,8 @@ curid_status curid_cur_adjoint(curid_handle* handle, curid_dtype dtype, const vo
   if (prev != handle->device && cudaSetDevice(handle->device) != cudaSuccess)
     return CURID_CUDA_ERROR;
   Ctx ctx{handle->stream, handle->num_sms, handle->smem_optin, nullptr};
+  ctx.spin = handle->spin;
+  ctx.concurrency = handle->concurrency;
   ctx.launches = handle->profiling ? &handle->launches : nullptr;
   curid_status st;
   if (dtype == CURID_F64)

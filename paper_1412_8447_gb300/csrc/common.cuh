@@ -96,6 +96,8 @@ struct curid_handle {
   int batch_shape[2] = {-1, -1};
   // bound of every inter-block wait in SM clock cycles (curid_set_timeout)
   long long spin = curid::kSpinBudget;
+  // decompositions the caller keeps in flight on this GPU (curid_set_concurrency)
+  int concurrency = 1;
 };
 
 #define CURID_CUDA(call)                                \

@@ -306,22 +306,36 @@ size_t cpqr_smem_bytes(int ncs, int nc, int ldl) {
          (size_t)nc * sizeof(int) + 64;
 }
 
-// Grid, columns per CTA and how many of them fit in shared memory.
+// Grid, columns per CTA, how many of them fit in shared memory, and the warps
+// per CTA of the register-resident kernel.
+//
+// One decomposition at a time (the handle's concurrency 1): one CTA per SM,
+// the lowest latency per factorization.  With several in flight: the fewest
+// CTAs whose registers hold the matrix (eight columns per warp).  The pivot
+// exchange gets cheaper with fewer CTAs (records of 38-64 CTAs meet in about
+// 2.4K cycles on GB300, of 152 in about twice that), the update gets longer,
+// and the SMs left free run the other decompositions: the factorization
+// takes about 1.2x as long on a third of the SMs.  Cooperative grids are
+// gang-scheduled, so grids of concurrent factorizations queue whole.
+// CURID_CPQR_CTAS in the environment overrides the choice for comparisons:
+// "all" (one per SM) or "fewest".  (Eight-warp CTAs, two per SM, so that two
+// concurrent factorizations share SMs, measured slower: 549/s against 613/s
+// with four decompositions in flight.)
 template <typename real>
 curid_status cpqr_layout(const Ctx& ctx, int64_t l, int64_t n, int* G_out, int* nc_out,
-                         int* ncs_out) {
+                         int* ncs_out, int* warps_out = nullptr) {
   if (l <= 0 || n <= 0) return CURID_INVALID_ARG;
   const int gmax = std::min(ctx.num_sms, 32 * kMaxSlotsPerLane);
   int G = (int)std::min<int64_t>(gmax, n);
-  // register-resident slabs: the fewest CTAs whose registers hold the matrix.
-  // The pivot exchange gets cheaper with fewer CTAs (records of 38-64 CTAs
-  // meet in about 2.4K cycles on GB300, of 152 in about twice that) while
-  // the update has work to spare, and the SMs left free serve other streams.
-  // CURID_CPQR_CTAS=all keeps one CTA per SM (for comparisons).
-  const int64_t rc = cpqr_reg_cols<real>((int)std::min<int64_t>(l, INT32_MAX));
+  int warps = 16;
   const char* env = std::getenv("CURID_CPQR_CTAS");
-  const bool all = env && std::strcmp(env, "all") == 0;
-  if (rc > 0 && !all && (n + rc - 1) / rc <= gmax) G = (int)((n + rc - 1) / rc);
+  bool fewest = ctx.concurrency > 1;
+  if (env && std::strcmp(env, "all") == 0) fewest = false;
+  if (env && std::strcmp(env, "fewest") == 0) fewest = true;
+  if (fewest) {
+    const int64_t rc = cpqr_reg_cols<real>((int)std::min<int64_t>(l, INT32_MAX), warps);
+    if (rc > 0 && (n + rc - 1) / rc <= gmax) G = (int)((n + rc - 1) / rc);
+  }
   const int nc = (int)((n + G - 1) / G);
   G = (int)((n + nc - 1) / nc);
   const int ldl = (int)(l | 1);
@@ -332,6 +346,7 @@ curid_status cpqr_layout(const Ctx& ctx, int64_t l, int64_t n, int* G_out, int* 
   *G_out = G;
   *nc_out = nc;
   *ncs_out = ncs;
+  if (warps_out) *warps_out = warps;
   return CURID_OK;
 }
 
@@ -362,8 +377,8 @@ template <typename real>
 curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64_t ldy, int k_max,
                       double tol, int32_t* J, real* S, int64_t lds, const CpqrScratch& s,
                       int which) {
-  int G, nc, ncs;
-  CURID_TRY(cpqr_layout<real>(ctx, l, n, &G, &nc, &ncs));
+  int G, nc, ncs, warps;
+  CURID_TRY(cpqr_layout<real>(ctx, l, n, &G, &nc, &ncs, &warps));
   if (G != s.grid || (nc > ncs && !s.overflow)) return CURID_INVALID_ARG;
   const size_t smem = cpqr_smem_bytes<real>(ncs, nc, (int)(l | 1));
   CpqrParams<real> P;
@@ -392,9 +407,10 @@ curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64
   P.status = ctx.status;
   P.which = which;
   P.spin = ctx.spin;
+  P.warps = warps;
   CURID_CUDA(cudaMemsetAsync(s.slots, 0, 2 * (size_t)G * sizeof(Rec), ctx.stream));
   CURID_CUDA(cudaMemsetAsync(s.abort_flag, 0, sizeof(int), ctx.stream));
-  if (cpqr_reg_fits<real>(ctx, (int)l, nc)) return cpqr_reg_launch<real>(ctx, P, G);
+  if (cpqr_reg_fits<real>(ctx, (int)l, nc, warps)) return cpqr_reg_launch<real>(ctx, P, G);
   auto fn = nc > ncs ? cpqr_kernel<real, true> : cpqr_kernel<real, false>;
   CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   void* args[] = {&P};

@@ -43,6 +43,7 @@ struct CpqrParams {
   int which;
   unsigned gen;                  // launch generation, high bits of every tag
   long long spin;                // bound of every inter-block wait, SM clock cycles
+  int warps;                     // warps per CTA of the register-resident kernel
 };
 
 // Published candidate columns are tagged word by word like the records, so a
@@ -179,7 +180,7 @@ __device__ bool gather_records(const CpqrParams<real>& P, int bf, unsigned epoch
     if (lane + 32 * r < G) pending |= 1u << r;
   bool ok = true;
   const long long t0 = clock64();
-  while (pending) {
+  for (int round = 0; pending; ++round) {
 #pragma unroll
     for (int r = 0; r < kMaxSlotsPerLane; ++r) {
       if (!(pending & (1u << r))) continue;
@@ -202,12 +203,14 @@ __device__ bool gather_records(const CpqrParams<real>& P, int bf, unsigned epoch
       if (fresh) pending &= ~(1u << r);
     }
     if (!pending) break;
-    if (ld_volatile_i32(P.abort_flag)) { ok = false; break; }
+    // the clock every round (no memory access), the abort flag every 16th
+    // (a load that would otherwise lengthen every polling round)
     if (clock64() - t0 > P.spin) {
       atomicExch(P.abort_flag, 1);
       ok = false;
       break;
     }
+    if ((round & 15) == 15 && ld_volatile_i32(P.abort_flag)) { ok = false; break; }
   }
   ok = __all_sync(0xffffffffu, ok);
   return ok;
@@ -399,10 +402,12 @@ __device__ __forceinline__ void reflector(real alpha, real nu, real* beta, real*
 // The register-resident kernel (cpqr_reg.cu): whether it takes an l-row
 // factorization with nc columns per CTA, and its launch (scratch already
 // reset by the caller).
+// most columns of a register-resident slab of CTAs with `warps` warps (0: l
+// too large), and whether an nc-column slab fits
 template <typename real>
-int cpqr_reg_cols(int l);  // most columns of a register-resident slab (0: l too large)
+int cpqr_reg_cols(int l, int warps);
 template <typename real>
-bool cpqr_reg_fits(const Ctx& ctx, int l, int nc);
+bool cpqr_reg_fits(const Ctx& ctx, int l, int nc, int warps);
 template <typename real>
 curid_status cpqr_reg_launch(const Ctx& ctx, const CpqrParams<real>& P, int G);
 

@@ -81,7 +81,7 @@ struct WarpBest {
 // columns (lane t holds the squared norm of column 4 g + ((t >> 3) & 3) in
 // qg[g]): post the warp's best unselected column, the sum of its squared
 // norms and whether one is not finite.
-template <int KC, typename real>
+template <int KC, int NW, typename real>
 __device__ __forceinline__ void post_warp_best(const real (&qg)[KC / 4], unsigned act, int lane,
                                                int warp, WarpBest<real>& wb) {
   const int cs = (lane >> 3) & 3;
@@ -94,7 +94,7 @@ __device__ __forceinline__ void post_warp_best(const real (&qg)[KC / 4], unsigne
     const real nv = sqrt(qg[g]);
     ss += nv * nv;
     if (!isfinite(nv)) nf = 1;
-    else if (local_better(nv, warp + kWarps * c, bn, bi)) { bn = nv; bi = warp + kWarps * c; }
+    else if (local_better(nv, warp + NW * c, bn, bi)) { bn = nv; bi = warp + NW * c; }
   }
 #pragma unroll
   for (int o = 8; o <= 16; o <<= 1) {
@@ -117,15 +117,15 @@ __device__ __forceinline__ void post_warp_best(const real (&qg)[KC / 4], unsigne
 // warp holding the candidate writes its rows r0..l-1 to the CTA's data slot
 // as tagged words (readers check every word's tag, so the two writes need no
 // order between them).
-template <int RPL, int KC, typename real>
+template <int RPL, int KC, int NW, typename real>
 __device__ __forceinline__ void publish_reg(const CpqrParams<real>& P, const WarpBest<real>& wb,
                                             const real (&y)[KC][RPL], int c0, int r0, int bf,
                                             unsigned epoch, int lane, int warp) {
-  real bn = lane < kWarps ? wb.bn[lane] : real(-1);
-  int bi = lane < kWarps ? wb.bi[lane] : -1;
-  int nf = lane < kWarps ? wb.nf[lane] : 0;
+  real bn = lane < NW ? wb.bn[lane] : real(-1);
+  int bi = lane < NW ? wb.bi[lane] : -1;
+  int nf = lane < NW ? wb.nf[lane] : 0;
 #pragma unroll
-  for (int o = 1; o < kWarps; o <<= 1) {
+  for (int o = 1; o < NW; o <<= 1) {
     const real on = __shfl_xor_sync(0xffffffffu, bn, o);
     const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
     if (local_better(on, oi, bn, bi)) { bn = on; bi = oi; }
@@ -137,9 +137,9 @@ __device__ __forceinline__ void publish_reg(const CpqrParams<real>& P, const War
   nf = __shfl_sync(0xffffffffu, nf, 0);
   const unsigned tag = tag_of(P.gen, (int)epoch);
   if (warp == 0) {
-    real ss = lane < kWarps ? wb.ss[lane] : real(0);
+    real ss = lane < NW ? wb.ss[lane] : real(0);
 #pragma unroll
-    for (int o = 1; o < kWarps; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    for (int o = 1; o < NW; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if (lane == 0) {
       unsigned hi, lo;
       norm_words<real>(bi >= 0 ? bn : real(0), &hi, &lo);
@@ -148,10 +148,10 @@ __device__ __forceinline__ void publish_reg(const CpqrParams<real>& P, const War
              pack(tag, lo), pack(tag, __float_as_uint((float)ss)));
     }
   }
-  if (bi >= 0 && !nf && bi % kWarps == warp) {
+  if (bi >= 0 && !nf && bi % NW == warp) {
     constexpr int W = Words<real>::W;
     unsigned long long* dst = slot_of(P, bf, blockIdx.x);
-    const int cb = bi / kWarps;
+    const int cb = bi / NW;
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       if (c != cb) continue;
@@ -164,8 +164,8 @@ __device__ __forceinline__ void publish_reg(const CpqrParams<real>& P, const War
   }
 }
 
-template <typename real, int RPL, int KC>
-__global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> P) {
+template <typename real, int RPL, int KC, int NW>
+__global__ void __launch_bounds__(NW * 32, 16 / NW) cpqr_reg_kernel(CpqrParams<real> P) {
   constexpr int NG = KC / 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -181,11 +181,11 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> 
   const int c0 = b * nc;
   const int ncl = max(0, min(nc, P.n - c0));
 
-  for (int64_t e = tid; e < (int64_t)l * ncl; e += kThreads) {
+  for (int64_t e = tid; e < (int64_t)l * ncl; e += NW * 32) {
     const int r = (int)(e / ncl), lc = (int)(e % ncl);
     ys[(int64_t)lc * ldl + r] = P.Y[(int64_t)r * P.ldy + c0 + lc];
   }
-  for (int lc = tid; lc < nc; lc += kThreads) active[lc] = lc < ncl ? 1 : 0;
+  for (int lc = tid; lc < nc; lc += NW * 32) active[lc] = lc < ncl ? 1 : 0;
   __syncthreads();
 
   real y[KC][RPL];
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> 
     real q[KC];
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      const int lc = warp + kWarps * c;
+      const int lc = warp + NW * c;
       if (lc < ncl) act |= 1u << c;
       q[c] = real(0);
 #pragma unroll
@@ -208,10 +208,10 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> 
 #pragma unroll
     for (int g = 0; g < NG; ++g)
       qg[g] = reduce4(q[4 * g], q[4 * g + 1], q[4 * g + 2], q[4 * g + 3], lane);
-    post_warp_best<KC>(qg, act, lane, warp, wb);
+    post_warp_best<KC, NW>(qg, act, lane, warp, wb);
   }
   __syncthreads();
-  publish_reg<RPL, KC>(P, wb, y, c0, 0, 0, 1u, lane, warp);
+  publish_reg<RPL, KC, NW>(P, wb, y, c0, 0, 0, 1u, lane, warp);
 
   real normY = real(-1), nu_first = real(0);
   int k_eff = -1;
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> 
     const int owner = st.owner, pcol = st.col;
     const real nu = st.nu;
     note_rank(P, j, nu, nu_first, k_eff);
-    if (!fetch_pivot<kThreads>(P, j, owner, xv, st)) break;
+    if (!fetch_pivot<NW * 32>(P, j, owner, xv, st)) break;
     real beta, tau, scale;
     reflector(xv[j], nu, &beta, &tau, &scale);
     // v of this lane's rows: 0 above j, 1 at j, scale x(r) below
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> 
       dg[g] = reduce4(d[4 * g], d[4 * g + 1], d[4 * g + 2], d[4 * g + 3], lane);
     // the warp holding the pivot column retires it: beta at row j, zeros below
     const int pl = pcol - c0;
-    const int pc = (pl >= 0 && pl < ncl && pl % kWarps == warp) ? pl / kWarps : -1;
+    const int pc = (pl >= 0 && pl < ncl && pl % NW == warp) ? pl / NW : -1;
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       if (c == pc) {
@@ -287,16 +287,16 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> 
 #pragma unroll
     for (int g = 0; g < NG; ++g)
       qg[g] = reduce4(q[4 * g], q[4 * g + 1], q[4 * g + 2], q[4 * g + 3], lane);
-    post_warp_best<KC>(qg, act, lane, warp, wb);
+    post_warp_best<KC, NW>(qg, act, lane, warp, wb);
     __syncthreads();
-    publish_reg<RPL, KC>(P, wb, y, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2), lane, warp);
+    publish_reg<RPL, KC, NW>(P, wb, y, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2), lane, warp);
   }
   const int k_done = j;
   if (st.stop == 2) return;  // timed out: leave without further waits
   // S rows 0..k_done-1 in original column order, staged through shared memory
 #pragma unroll
   for (int c = 0; c < KC; ++c) {
-    const int lc = warp + kWarps * c;
+    const int lc = warp + NW * c;
     if (lc < ncl) {
 #pragma unroll
       for (int u = 0; u < RPL; ++u) {
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_reg_kernel(CpqrParams<real> 
     }
   }
   __syncthreads();
-  for (int64_t e = tid; e < (int64_t)k_done * ncl; e += kThreads) {
+  for (int64_t e = tid; e < (int64_t)k_done * ncl; e += NW * 32) {
     const int i = (int)(e / ncl), lc = (int)(e % ncl);
     P.S[(int64_t)i * P.lds + c0 + lc] = ys[(int64_t)lc * ldl + i];
   }
@@ -324,50 +324,60 @@ size_t reg_smem_bytes(int nc, int ldl) {
 // Eight columns per warp fit the registers without spilling up to 224 rows
 // in float32 and 64 in float64; four up to 256 / 128 rows.
 template <typename real>
-int cpqr_reg_cols(int l) {
+int cpqr_reg_cols(int l, int warps) {
   if (l < 1 || l > max_reg_rows<real>()) return 0;
   const int wide_rows = sizeof(real) == 4 ? 224 : 64;
-  return kWarps * (l <= wide_rows ? 8 : 4);
+  return warps * (l <= wide_rows ? 8 : 4);
 }
 
 template <typename real>
-bool cpqr_reg_fits(const Ctx& ctx, int l, int nc) {
+bool cpqr_reg_fits(const Ctx& ctx, int l, int nc, int warps) {
   // the kernel's static shared variables share the per-block limit
-  return nc >= 1 && nc <= cpqr_reg_cols<real>(l) &&
+  return nc >= 1 && nc <= cpqr_reg_cols<real>(l, warps) &&
          reg_smem_bytes<real>(nc, l | 1) + 1024 <= ctx.smem_optin;
 }
 
-template <typename real>
-curid_status cpqr_reg_launch(const Ctx& ctx, const CpqrParams<real>& P, int G) {
-  if (!cpqr_reg_fits<real>(ctx, P.l, P.nc)) return CURID_UNSUPPORTED;
-  const size_t smem = reg_smem_bytes<real>(P.nc, P.ldl);
-  // rows per lane from l; four columns per warp when the slab has at most
-  // 64 columns, else eight
-  const bool wide = P.nc > kWarps * 4;
-  void (*fn)(CpqrParams<real>) = nullptr;
-  if (P.l <= 64) fn = wide ? cpqr_reg_kernel<real, 2, 8> : cpqr_reg_kernel<real, 2, 4>;
-  else if (P.l <= 128) {
-    if constexpr (sizeof(real) == 4) fn = wide ? cpqr_reg_kernel<real, 4, 8> : cpqr_reg_kernel<real, 4, 4>;
-    else fn = cpqr_reg_kernel<real, 4, 4>;
+namespace {
+
+template <typename real, int NW>
+void (*reg_kernel_for(int l, int nc))(CpqrParams<real>) {
+  const bool wide = nc > NW * 4;
+  if (l <= 64) return wide ? cpqr_reg_kernel<real, 2, 8, NW> : cpqr_reg_kernel<real, 2, 4, NW>;
+  if (l <= 128) {
+    if constexpr (sizeof(real) == 4)
+      return wide ? cpqr_reg_kernel<real, 4, 8, NW> : cpqr_reg_kernel<real, 4, 4, NW>;
+    else
+      return cpqr_reg_kernel<real, 4, 4, NW>;
   }
   if constexpr (sizeof(real) == 4) {
-    if (P.l > 128 && P.l <= 224) fn = wide ? cpqr_reg_kernel<real, 7, 8> : cpqr_reg_kernel<real, 7, 4>;
-    else if (P.l > 224) fn = cpqr_reg_kernel<real, 8, 4>;
+    if (l <= 224) return wide ? cpqr_reg_kernel<real, 7, 8, NW> : cpqr_reg_kernel<real, 7, 4, NW>;
+    return cpqr_reg_kernel<real, 8, 4, NW>;
   }
+  return nullptr;
+}
+
+}  // namespace
+
+template <typename real>
+curid_status cpqr_reg_launch(const Ctx& ctx, const CpqrParams<real>& P, int G) {
+  const int warps = kWarps;
+  if (P.warps != warps || !cpqr_reg_fits<real>(ctx, P.l, P.nc, warps)) return CURID_UNSUPPORTED;
+  const size_t smem = reg_smem_bytes<real>(P.nc, P.ldl);
+  void (*fn)(CpqrParams<real>) = reg_kernel_for<real, kWarps>(P.l, P.nc);
   if (!fn) return CURID_UNSUPPORTED;
   CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CpqrParams<real> Pc = P;
   void* args[] = {&Pc};
-  CURID_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(G), dim3(kThreads), args, smem,
+  CURID_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(G), dim3(warps * 32), args, smem,
                                          ctx.stream));
   if (ctx.launches) ++*ctx.launches;
   return CURID_OK;
 }
 
-template int cpqr_reg_cols<float>(int);
-template int cpqr_reg_cols<double>(int);
-template bool cpqr_reg_fits<float>(const Ctx&, int, int);
-template bool cpqr_reg_fits<double>(const Ctx&, int, int);
+template int cpqr_reg_cols<float>(int, int);
+template int cpqr_reg_cols<double>(int, int);
+template bool cpqr_reg_fits<float>(const Ctx&, int, int, int);
+template bool cpqr_reg_fits<double>(const Ctx&, int, int, int);
 template curid_status cpqr_reg_launch<float>(const Ctx&, const CpqrParams<float>&, int);
 template curid_status cpqr_reg_launch<double>(const Ctx&, const CpqrParams<double>&, int);
 

@@ -57,10 +57,19 @@ struct PhaseScope {
   }
 };
 
+// Context for sizing (no stream): the handle's settings that shape plans.
+Ctx host_ctx(curid_handle* h) {
+  Ctx c{nullptr, h->num_sms, h->smem_optin, nullptr};
+  c.spin = h->spin;
+  c.concurrency = h->concurrency;
+  return c;
+}
+
 Ctx make_ctx(curid_handle* h) {
   Ctx c{h->stream, h->num_sms, h->smem_optin, nullptr};
   c.launches = h->profiling ? &h->launches : nullptr;
   c.spin = h->spin;
+  c.concurrency = h->concurrency;
   return c;
 }
 
@@ -462,10 +471,10 @@ curid_status run(curid_handle* h, Op op, const void* Araw, const Dims& d, double
     PhaseScope ps(h, CURID_PHASE_GATHER);
     if constexpr (sizeof(real) == 4) {
       if (d.bf16) {
-        CURID_TRY((gather_cols_as<__nv_bfloat16, real>(ctx, Ab, m, lda, o.J, k, P.Ct, m, true)));
+        CURID_TRY((gather_cols_as<__nv_bfloat16, real>(ctx, Ab, m, n, lda, o.J, k, P.Ct, m, true)));
         if (o.C)
           CURID_TRY((gather_cols_as<__nv_bfloat16, __nv_bfloat16>(
-              ctx, Ab, m, lda, o.J, k, static_cast<__nv_bfloat16*>(o.C), k, false)));
+              ctx, Ab, m, n, lda, o.J, k, static_cast<__nv_bfloat16*>(o.C), k, false)));
       }
     }
     if (d.sp) {
@@ -473,9 +482,9 @@ curid_status run(curid_handle* h, Op op, const void* Araw, const Dims& d, double
                                     static_cast<const real*>(d.sp->col_val), m, P.Ct, m,
                                     static_cast<real*>(o.C), k));
     } else if (!d.bf16) {
-      CURID_TRY(gather_cols<real>(ctx, A, m, lda, o.J, k, P.Ct, m, true));
+      CURID_TRY(gather_cols<real>(ctx, A, m, n, lda, o.J, k, P.Ct, m, true));
       if (o.C)
-        CURID_TRY(gather_cols<real>(ctx, A, m, lda, o.J, k, static_cast<real*>(o.C), k, false));
+        CURID_TRY(gather_cols<real>(ctx, A, m, n, lda, o.J, k, static_cast<real*>(o.C), k, false));
     }
   }
   {
@@ -632,7 +641,7 @@ curid_status adaptive_rank(curid_handle* h, curid_dtype dt, const void* A, int64
                            int64_t lda, double tol, int32_t* J, int* k_out) {
   const int64_t kmax = std::min(m, n);
   const size_t esz = dt == CURID_F64 ? 8 : 4;
-  Ctx ctx{nullptr, h->num_sms, h->smem_optin, nullptr};
+  Ctx ctx = host_ctx(h);
   Carver cv(nullptr);
   cv.take<StatusBlock>(1);
   CpqrScratch cs;
@@ -1029,6 +1038,12 @@ curid_status curid_set_timeout(curid_handle* handle, long long cycles) {
   return CURID_OK;
 }
 
+curid_status curid_set_concurrency(curid_handle* handle, int inflight) {
+  if (!handle || inflight < 1) return CURID_INVALID_ARG;
+  handle->concurrency = inflight;
+  return CURID_OK;
+}
+
 curid_status curid_set_workspace(curid_handle* handle, void* ptr, size_t bytes) {
   if (!handle) return CURID_INVALID_ARG;
   if (ptr && (reinterpret_cast<uintptr_t>(ptr) & 255)) return CURID_INVALID_ARG;
@@ -1056,7 +1071,7 @@ curid_status curid_workspace_size(curid_handle* handle, curid_dtype dtype, int64
   Dims d;
   int dummy = 1;
   CURID_TRY(check_common(handle, dtype, &dummy, m, n, n, k, 0.0, sk, &d));
-  Ctx ctx{nullptr, handle->num_sms, handle->smem_optin, nullptr};
+  Ctx ctx = host_ctx(handle);
   const bool gen = d.randomized && sk.omega == nullptr;
   Dims dt;
   const bool row_ok = check_common(handle, dtype, &dummy, n, m, m, k, 0.0, sk, &dt) == CURID_OK;
@@ -1352,7 +1367,7 @@ curid_status curid_sparse_workspace_size(curid_handle* handle, curid_dtype dtype
   SparseA sa;
   Dims d;
   CURID_TRY(sparse_dims(handle, dtype, m, n, &dummy, k, sk, &sa, &d));
-  Ctx ctx{nullptr, handle->num_sms, handle->smem_optin, nullptr};
+  Ctx ctx = host_ctx(handle);
   const bool gen = sk.omega == nullptr;
   if (dtype == CURID_F64) {
     Plan<double> P;
@@ -1402,7 +1417,7 @@ curid_status curid_complex_workspace_size(curid_handle* handle, curid_dtype dtyp
                                           int64_t n, int k, curid_sketch sk, size_t* bytes) {
   if (!bytes) return CURID_INVALID_ARG;
   CURID_TRY(complex_check(handle, dtype, m, n, k, sk));
-  Ctx ctx{nullptr, handle->num_sms, handle->smem_optin, nullptr};
+  Ctx ctx = host_ctx(handle);
   if (dtype == CURID_F64) {
     ComplexPlan<double> P;
     CURID_TRY(complex_plan<double>(ctx, m, n, k, sk, nullptr, &P));
@@ -1433,7 +1448,7 @@ curid_status curid_cur_complex(curid_handle* handle, curid_dtype dtype, const vo
 curid_status curid_interp_tsvd_workspace_size(curid_handle* handle, curid_dtype dtype, int64_t n,
                                               int k, size_t* bytes) {
   if (!handle || !bytes || n < 1 || k < 1 || k > n) return CURID_INVALID_ARG;
-  Ctx ctx{nullptr, handle->num_sms, handle->smem_optin, nullptr};
+  Ctx ctx = host_ctx(handle);
   if (dtype == CURID_F64) {
     TsvdPlan<double> P;
     tsvd_plan<double>(ctx, n, k, nullptr, &P);
@@ -1468,7 +1483,7 @@ curid_status curid_interp_tsvd(curid_handle* handle, curid_dtype dtype, const vo
 curid_status curid_interp_tikhonov_workspace_size(curid_handle* handle, curid_dtype dtype,
                                                   int64_t n, int k, size_t* bytes) {
   if (!handle || !bytes || n < 1 || k < 1 || k > n) return CURID_INVALID_ARG;
-  Ctx ctx{nullptr, handle->num_sms, handle->smem_optin, nullptr};
+  Ctx ctx = host_ctx(handle);
   if (dtype == CURID_F64) {
     TikPlan<double> P;
     tik_plan<double>(ctx, n, k, nullptr, &P);

@@ -3,6 +3,8 @@
 // Memory-bound; all writes are coalesced, reads are coalesced wherever the
 // index set allows (rows of R are contiguous; a column of C is a stride-lda
 // walk, so each warp reads 32 rows of one skeleton column).
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace curid {
@@ -28,22 +30,35 @@ __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, __nv_bfloat16>(__nv_
   return x;
 }
 
-// out^T layout (transpose == true): out[i*ldo + r] = A[r*lda + J[i]]
+// out^T layout (transpose == true): out[i*ldo + r] = A[r*lda + J[i]].  A
+// column is a stride-lda walk, so every element costs one 32-byte sector;
+// each thread keeps four of them in flight.
 template <typename S, typename D>
-__global__ void gather_cols_t_kernel(const S* __restrict__ A, int64_t m, int64_t lda,
+__global__ void gather_cols_t_kernel(const S* __restrict__ A, int64_t m, int64_t n, int64_t lda,
                                      const int32_t* __restrict__ J, int k,
                                      D* __restrict__ out, int64_t ldo) {
   const int i = blockIdx.y;
   int64_t col = J[i];
-  if (col < 0 || col >= lda) col = 0;  // indices come from the device; never read out of range
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
-       r += (int64_t)gridDim.x * blockDim.x)
-    out[(int64_t)i * ldo + r] = cvt<D>(A[r * lda + col]);
+  if (col < 0 || col >= n) col = 0;  // indices come from the device; never read out of range
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r0 < m; r0 += 4 * stride) {
+    S v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t r = r0 + u * stride;
+      v[u] = r < m ? A[r * lda + col] : S(0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t r = r0 + u * stride;
+      if (r < m) out[(int64_t)i * ldo + r] = cvt<D>(v[u]);
+    }
+  }
 }
 
 // out[r*ldo + i] = A[r*lda + J[i]] through a 32 x 32 shared tile
 template <typename S, typename D>
-__global__ void gather_cols_kernel(const S* __restrict__ A, int64_t m, int64_t lda,
+__global__ void gather_cols_kernel(const S* __restrict__ A, int64_t m, int64_t n, int64_t lda,
                                    const int32_t* __restrict__ J, int k,
                                    D* __restrict__ out, int64_t ldo) {
   __shared__ D tile[32][33];
@@ -54,7 +69,7 @@ __global__ void gather_cols_kernel(const S* __restrict__ A, int64_t m, int64_t l
     const int i = i0 + yy;
     const int64_t r = r0 + tx;
     int64_t col = i < k ? (int64_t)J[i] : 0;
-    if (col < 0 || col >= lda) col = 0;
+    if (col < 0 || col >= n) col = 0;
     tile[yy][tx] = (i < k && r < m) ? cvt<D>(A[r * lda + col]) : cvt<D>(0.f);
   }
   __syncthreads();
@@ -77,6 +92,22 @@ __global__ void gather_rows_kernel(const S* __restrict__ A, int64_t m, int64_t n
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x)
     dst[c] = cvt<D>(src[c]);
+}
+
+// Rows of one element type copied as 16-byte vectors V (rows, leading
+// dimensions and n in whole vectors; checked by the launcher).
+template <typename V>
+__global__ void gather_rows_vec_kernel(const V* __restrict__ A, int64_t m, int64_t nv,
+                                       int64_t ldav, const int32_t* __restrict__ I,
+                                       V* __restrict__ out, int64_t ldov) {
+  const int i = blockIdx.y;
+  int64_t row = I[i];
+  if (row < 0 || row >= m) row = 0;
+  const V* src = A + row * ldav;
+  V* dst = out + (int64_t)i * ldov;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nv;
+       c += (int64_t)gridDim.x * blockDim.x)
+    dst[c] = src[c];
 }
 
 template <typename real>
@@ -184,15 +215,16 @@ inline unsigned blocks_for(int64_t work, int num_sms) {
 }  // namespace
 
 template <typename S, typename D>
-curid_status gather_cols_as(const Ctx& ctx, const S* A, int64_t m, int64_t lda, const int32_t* J,
-                            int k, D* out, int64_t ldo, bool transpose) {
+curid_status gather_cols_as(const Ctx& ctx, const S* A, int64_t m, int64_t n, int64_t lda,
+                            const int32_t* J, int k, D* out, int64_t ldo, bool transpose) {
   if (k <= 0 || m <= 0) return CURID_OK;
   if (transpose) {
-    dim3 grid((unsigned)std::min<int64_t>((m + 255) / 256, 64), (unsigned)k);
-    gather_cols_t_kernel<S, D><<<grid, 256, 0, ctx.stream>>>(A, m, lda, J, k, out, ldo);
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 1023) / 1024, 64)),
+              (unsigned)k);
+    gather_cols_t_kernel<S, D><<<grid, 256, 0, ctx.stream>>>(A, m, n, lda, J, k, out, ldo);
   } else {
     dim3 grid((unsigned)((m + 31) / 32), (unsigned)((k + 31) / 32));
-    gather_cols_kernel<S, D><<<grid, dim3(32, 8), 0, ctx.stream>>>(A, m, lda, J, k, out, ldo);
+    gather_cols_kernel<S, D><<<grid, dim3(32, 8), 0, ctx.stream>>>(A, m, n, lda, J, k, out, ldo);
   }
   CURID_LAUNCHED(ctx);
   return CURID_OK;
@@ -202,6 +234,19 @@ template <typename S, typename D>
 curid_status gather_rows_as(const Ctx& ctx, const S* A, int64_t m, int64_t n, int64_t lda,
                             const int32_t* I, int k, D* out, int64_t ldo) {
   if (k <= 0 || n <= 0) return CURID_OK;
+  constexpr int64_t w = 16 / sizeof(S);  // elements per 16-byte vector
+  if constexpr (std::is_same<S, D>::value && 16 % sizeof(S) == 0) {
+    if (n % w == 0 && lda % w == 0 && ldo % w == 0 &&
+        (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+      const int64_t nv = n / w;
+      dim3 grid((unsigned)std::min<int64_t>((nv + 255) / 256, 64), (unsigned)k);
+      gather_rows_vec_kernel<uint4><<<grid, 256, 0, ctx.stream>>>(
+          reinterpret_cast<const uint4*>(A), m, nv, lda / w, I, reinterpret_cast<uint4*>(out),
+          ldo / w);
+      CURID_LAUNCHED(ctx);
+      return CURID_OK;
+    }
+  }
   dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)k);
   gather_rows_kernel<S, D><<<grid, 256, 0, ctx.stream>>>(A, m, n, lda, I, out, ldo);
   CURID_LAUNCHED(ctx);
@@ -219,9 +264,9 @@ curid_status convert2d(const Ctx& ctx, const S* src, int64_t lds, D* dst, int64_
 }
 
 template <typename real>
-curid_status gather_cols(const Ctx& ctx, const real* A, int64_t m, int64_t lda, const int32_t* J,
-                         int k, real* out, int64_t ldo, bool transpose) {
-  return gather_cols_as<real, real>(ctx, A, m, lda, J, k, out, ldo, transpose);
+curid_status gather_cols(const Ctx& ctx, const real* A, int64_t m, int64_t n, int64_t lda,
+                         const int32_t* J, int k, real* out, int64_t ldo, bool transpose) {
+  return gather_cols_as<real, real>(ctx, A, m, n, lda, J, k, out, ldo, transpose);
 }
 
 template <typename real>
@@ -296,7 +341,7 @@ curid_status transpose2d(const Ctx& ctx, const real* src, int64_t lds, real* dst
 }
 
 #define CURID_INST(real)                                                                       \
-  template curid_status gather_cols<real>(const Ctx&, const real*, int64_t, int64_t,           \
+  template curid_status gather_cols<real>(const Ctx&, const real*, int64_t, int64_t, int64_t,  \
                                           const int32_t*, int, real*, int64_t, bool);          \
   template curid_status gather_rows<real>(const Ctx&, const real*, int64_t, int64_t, int64_t,  \
                                           const int32_t*, int, real*, int64_t);                \
@@ -318,10 +363,11 @@ CURID_INST(double)
 
 using bf16_t = __nv_bfloat16;
 template curid_status gather_cols_as<bf16_t, float>(const Ctx&, const bf16_t*, int64_t, int64_t,
-                                                    const int32_t*, int, float*, int64_t, bool);
+                                                    int64_t, const int32_t*, int, float*, int64_t,
+                                                    bool);
 template curid_status gather_cols_as<bf16_t, bf16_t>(const Ctx&, const bf16_t*, int64_t,
-                                                     int64_t, const int32_t*, int, bf16_t*,
-                                                     int64_t, bool);
+                                                     int64_t, int64_t, const int32_t*, int,
+                                                     bf16_t*, int64_t, bool);
 template curid_status gather_rows_as<bf16_t, float>(const Ctx&, const bf16_t*, int64_t, int64_t,
                                                     int64_t, const int32_t*, int, float*,
                                                     int64_t);

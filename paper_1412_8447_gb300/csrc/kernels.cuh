@@ -17,6 +17,7 @@ struct Ctx {
   StatusBlock* status;          // device
   long long* launches = nullptr;  // host counter of kernel launches (profiling)
   long long spin = kSpinBudget;   // bound of inter-block waits, SM clock cycles
+  int concurrency = 1;            // decompositions the caller keeps in flight
 };
 
 // After a kernel launch: report a launch error, count the launch.
@@ -134,7 +135,7 @@ curid_status gemm_nt_f64acc(const Ctx& ctx, int64_t M, int64_t N, int64_t K, con
 
 // ---- gathers and copies (gather.cu) ------------------------------------------
 template <typename real>
-curid_status gather_cols(const Ctx& ctx, const real* A, int64_t m, int64_t lda,
+curid_status gather_cols(const Ctx& ctx, const real* A, int64_t m, int64_t n, int64_t lda,
                          const int32_t* J, int k, real* out, int64_t ldo, bool transpose);
 template <typename real>
 curid_status gather_rows(const Ctx& ctx, const real* A, int64_t m, int64_t n, int64_t lda,
@@ -142,8 +143,8 @@ curid_status gather_rows(const Ctx& ctx, const real* A, int64_t m, int64_t n, in
 // the same gathers and a 2-D copy with a change of element type (instantiated
 // for bfloat16 -> float / bfloat16, float -> bfloat16 / double, double -> float)
 template <typename S, typename D>
-curid_status gather_cols_as(const Ctx& ctx, const S* A, int64_t m, int64_t lda, const int32_t* J,
-                            int k, D* out, int64_t ldo, bool transpose);
+curid_status gather_cols_as(const Ctx& ctx, const S* A, int64_t m, int64_t n, int64_t lda,
+                            const int32_t* J, int k, D* out, int64_t ldo, bool transpose);
 template <typename S, typename D>
 curid_status gather_rows_as(const Ctx& ctx, const S* A, int64_t m, int64_t n, int64_t lda,
                             const int32_t* I, int k, D* out, int64_t ldo);
