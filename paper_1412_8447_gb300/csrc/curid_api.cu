@@ -3,6 +3,7 @@
 // Every step of the method runs in this library's kernels; the host only
 // validates, carves the caller's workspace and enqueues launches.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -83,6 +84,7 @@ struct Plan {
   real* B[3] = {nullptr, nullptr, nullptr};  // sample-matrix buffers, l x max(m, n)
   real* G = nullptr;      // l x l  (Gram)
   real* Linv = nullptr;   // l x l
+  real* Li = nullptr;     // 2 x l x pad4(l) (l <= 256, tensor-core orth)
   // column CPQR and T
   CpqrScratch cs{};
   real* S = nullptr;      // k x n
@@ -177,9 +179,14 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
       for (int b = 0; b < 3; ++b) P->B[b] = cv.take<real>((size_t)l * pad4(std::max(m, n)));
       P->G = cv.take<real>((size_t)l * l);
       P->Linv = cv.take<real>((size_t)l * l);
-      if (sizeof(real) == 4 && (d.tf32 || d.bf16) && !d.sp && l > 256)
+      if (sizeof(real) == 4 && (d.tf32 || d.bf16) && !d.sp)
         part = std::max(part, gemm_tf32_partial_elems(std::min<int64_t>(l, 256), l,
                                                       std::max(m, n), ctx.num_sms));
+      if (sizeof(real) == 4 && (d.tf32 || d.bf16) && !d.sp && l <= 256) {
+        // L^{-1} split for the tensor-core apply of the small-sample orth
+        P->Li = cv.take<real>(2 * (size_t)l * pad4(l));
+        part = std::max(part, gemm_tf32_partial_elems(l, std::max(m, n), l, ctx.num_sms));
+      }
       upd(l, l, n);
       upd(l, l, m);
       upd(l, n, l);
@@ -303,16 +310,25 @@ curid_status a_product(const Ctx& ctx, bool tf32, bool bf16, bool tb, int64_t M,
 // than 256 rows the Gram matrices go to the TF32 tensor cores too, at
 // float32 accuracy (gram_tf32), with `spare` (a free sample buffer) for the
 // TF32 part and Linv as scratch: l = 520 rows of 20000, orth 13 -> 10 ms
-// per decomposition.  At l = 210 the split and the two products cost more
-// than the one FMA product they replace (orth 0.77 -> 0.80 ms), so smaller
-// samples keep it.
+// per decomposition.  Samples of up to 256 rows go to the tensor cores as a
+// whole (Gram and the apply X <- L^{-1} X through an explicit L^{-1}) when
+// several decompositions are in flight, where the SIMT products' SM time is
+// what limits throughput; one at a time they keep the SIMT Gram and the
+// triangular solve.  CURID_ORTH_TC=1 / 0 in the environment forces either
+// (for comparisons).
 template <typename real>
 curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
                        const Plan<real>& P, bool final_orth, bool tc, real* spare) {
-  const bool use_tc = sizeof(real) == 4 && tc && r > 256 && spare && P.Linv && !P.sp;
+  const bool tc_ok = sizeof(real) == 4 && tc && spare && P.Linv && !P.sp;
+  bool small_tc = tc_ok && r <= 256 && P.Li && ctx.concurrency > 1;
+  if (const char* env = std::getenv("CURID_ORTH_TC")) {
+    if (std::strcmp(env, "1") == 0) small_tc = tc_ok && r <= 256 && P.Li;
+    if (std::strcmp(env, "0") == 0) small_tc = false;
+  }
+  const bool use_tc = tc_ok && (r > 256 || small_tc);
   return chol_qr_rows<real>(ctx, X, tmp, r, c, ld, P.G, P.partial, P.partial_cap,
                             final_orth ? 3 : 2, use_tc ? spare : nullptr,
-                            use_tc ? P.Linv : nullptr);
+                            use_tc ? P.Linv : nullptr, small_tc ? P.Li : nullptr);
 }
 
 // Sample matrix of Algorithm 4 with the power scheme of Section 5.3:

@@ -511,13 +511,13 @@ curid_status gemm_nt_f64acc(const Ctx& ctx, int64_t M, int64_t N, int64_t K, con
 template <typename real>
 curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
                           real* G, real* partial, size_t partial_cap, int passes, real* xh,
-                          real* g2) {
+                          real* g2, real* li) {
   const double shift = sizeof(real) == 4 ? 1e-5 : 1e-13;
   for (int pass = 0; pass < passes; ++pass) {
     bool tc = false;
     if constexpr (sizeof(real) == 4) {
       if (xh && g2) {
-        // the remainder goes to *tmp, which the triangular solve overwrites
+        // the remainder goes to *tmp, which the triangular apply overwrites
         CURID_TRY(gram_tf32(ctx, *X, r, c, ld, xh, *tmp, G, g2, partial, partial_cap));
         tc = true;
       }
@@ -526,7 +526,29 @@ curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64
       CURID_TRY(gemm<real>(ctx, false, true, r, r, c, real(1), *X, ld, *X, ld, real(0), G, r,
                            partial, partial_cap));
     CURID_TRY(cholesky<real>(ctx, G, (int)r, pass == 0 ? shift : 0.0));
-    CURID_TRY(tri_solve<real>(ctx, (int)r, G, r, false, false, *X, ld, *tmp, ld, c, nullptr));
+    bool applied = false;
+    if constexpr (sizeof(real) == 4) {
+      if (tc && li && r <= 256) {
+        // X <- L^{-1} X as tensor-core products: L^{-1} explicitly (a
+        // triangular solve with the identity), split into its TF32 part and
+        // remainder; each product splits X inside, so the sum carries
+        // float32 accuracy.
+        const int64_t ldp = (r + 3) & ~int64_t(3);  // 16-byte rows for the tensor-core loads
+        float* lhi = li;
+        float* llo = li + r * ldp;
+        CURID_TRY(tri_solve<float>(ctx, (int)r, G, r, false, false, nullptr, 0, lhi, ldp, r,
+                                   nullptr));
+        CURID_TRY(split_tf32(ctx, lhi, ldp, lhi, ldp, llo, ldp, r, r));
+        CURID_TRY(gemm_tf32(ctx, false, false, r, c, r, lhi, ldp, *X, ld, *tmp, ld, partial,
+                            partial_cap));
+        CURID_TRY(gemm_tf32(ctx, false, false, r, c, r, llo, ldp, *X, ld, xh, ld, partial,
+                            partial_cap));
+        CURID_TRY(add2d<float>(ctx, xh, ld, *tmp, ld, r, c));
+        applied = true;
+      }
+    }
+    if (!applied)
+      CURID_TRY(tri_solve<real>(ctx, (int)r, G, r, false, false, *X, ld, *tmp, ld, c, nullptr));
     std::swap(*X, *tmp);
   }
   return CURID_OK;
@@ -551,10 +573,10 @@ curid_status gram_tf32(const Ctx& ctx, const float* X, int64_t r, int64_t c, int
 }
 
 template curid_status chol_qr_rows<float>(const Ctx&, float**, float**, int64_t, int64_t, int64_t,
-                                          float*, float*, size_t, int, float*, float*);
+                                          float*, float*, size_t, int, float*, float*, float*);
 template curid_status chol_qr_rows<double>(const Ctx&, double**, double**, int64_t, int64_t,
                                            int64_t, double*, double*, size_t, int, double*,
-                                           double*);
+                                           double*, double*);
 template curid_status gemm_nt_f64acc<float>(const Ctx&, int64_t, int64_t, int64_t, const float*,
                                             int64_t, const float*, int64_t, double*, int64_t);
 template curid_status gemm_nt_f64acc<double>(const Ctx&, int64_t, int64_t, int64_t,

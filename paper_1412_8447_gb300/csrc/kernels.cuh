@@ -117,11 +117,13 @@ bool chol_inverse_fits(const Ctx& ctx, int l);
 // dimension ld; each pass writes out of place, and on return *X points at
 // the result and *tmp at the other buffer.  G: r x r scratch.
 // With xh and g2 (float32 only: r x ld and r x r scratch), each Gram matrix
-// is formed on the TF32 tensor cores at float32 accuracy (gram_tf32).
+// is formed on the TF32 tensor cores at float32 accuracy (gram_tf32); with li
+// as well (2 r x pad4(r) scratch, r <= 256) the apply X <- L^{-1} X runs on
+// the tensor cores too, through L^{-1} split into its TF32 part and remainder.
 template <typename real>
 curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
                           real* G, real* partial, size_t partial_cap, int passes = 3,
-                          real* xh = nullptr, real* g2 = nullptr);
+                          real* xh = nullptr, real* g2 = nullptr, real* li = nullptr);
 // G (r x r, leading dimension r) = X X^T on the TF32 tensor cores: X =
 // X_hi + X_lo (TF32 part and float32 remainder, into xh and xl), G = X_hi X^T
 // + X_lo X^T with X split hi + lo inside each product; g2: r x r scratch.
