@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
     note_rank(P, j, nu, nu_first, k_eff);
     if (!fetch_pivot<kThreads>(P, j, owner, xv, st)) break;
     real beta, tau, scale;
-    reflector(xv[j], nu, &beta, &tau, &scale);
+    step_reflector(xv, j, nu, st, &beta, &tau, &scale);
     // apply H to every unselected local column, recompute its residual norm
     // from rows j+1..l-1; the owner retires the pivot column.  Warp w owns
     // columns w, w + 16, w + 32, w + 48 and updates them in one interleaved

@@ -226,6 +226,7 @@ struct StepState {
   int prefix;  // closing exchange: unselected columns of lower CTAs
   int stale;   // a tagged word of the pivot column never became fresh
   real nu;     // pivot norm
+  real beta, tau, scale;  // the step's reflector (float64: formed once per CTA)
 };
 
 // Warp 0 of step j: gather the G records of the step, pick the global pivot
@@ -396,6 +397,24 @@ __device__ __forceinline__ void reflector(real alpha, real nu, real* beta, real*
   if (nu > real(0)) {
     *tau = (*beta - alpha) / *beta;
     *scale = real(1) / (alpha - *beta);
+  }
+}
+
+// Every thread of a CTA, after the barrier that ends fetch_pivot: the
+// reflector of step j.  In float64 its two divisions run at a 64th of the
+// float32 rate on GB300, so one thread forms it and the CTA shares it
+// (one more barrier); in float32 every thread forms its own copy.
+template <typename real>
+__device__ __forceinline__ void step_reflector(const real* xv, int j, real nu, StepState<real>& st,
+                                               real* beta, real* tau, real* scale) {
+  if constexpr (sizeof(real) == 8) {
+    if (threadIdx.x == 0) reflector(xv[j], nu, &st.beta, &st.tau, &st.scale);
+    __syncthreads();
+    *beta = st.beta;
+    *tau = st.tau;
+    *scale = st.scale;
+  } else {
+    reflector(xv[j], nu, beta, tau, scale);
   }
 }
 

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) cpqr_reg_kernel(CpqrParams<r
     note_rank(P, j, nu, nu_first, k_eff);
     if (!fetch_pivot<NW * 32>(P, j, owner, xv, st)) break;
     real beta, tau, scale;
-    reflector(xv[j], nu, &beta, &tau, &scale);
+    step_reflector(xv, j, nu, st, &beta, &tau, &scale);
     // v of this lane's rows: 0 above j, 1 at j, scale x(r) below
     real v[RPL];
 #pragma unroll

@@ -148,9 +148,12 @@ template <typename real>
 int gemm_splits(int64_t M, int64_t N, int64_t K, int num_sms) {
   using Tl = GemmTile<real>;
   const int64_t tiles = ((M + Tl::BM - 1) / Tl::BM) * ((N + Tl::BN - 1) / Tl::BN);
-  if (tiles >= num_sms || K < 512) return 1;
+  // K chunks of at least 256 (float32) / 64 (float64: a 64th of the float32
+  // rate per SM on GB300, so even short products need more than one SM)
+  const int64_t kmin = sizeof(real) == 8 ? 64 : 256;
+  if (tiles >= num_sms || K < 2 * kmin) return 1;
   int64_t s = (2 * num_sms + tiles - 1) / tiles;
-  s = std::min<int64_t>(s, K / 256);
+  s = std::min<int64_t>(s, K / kmin);
   return (int)std::max<int64_t>(1, s);
 }
 
