@@ -2,9 +2,21 @@
 // first line of Algorithms 1 and 4; the full-rank ID of C^* in Algorithm 2).
 //
 // GB300 design: one persistent CTA per SM (cooperative launch, so all CTAs
-// are co-resident).  CTA b owns a contiguous slab of columns, held in shared
-// memory for the whole factorization, column-major with an odd stride so a
-// warp walking down a column is bank-conflict free.  A step j is:
+// are co-resident).  CTA b owns a contiguous slab of columns for the whole
+// factorization, cut into groups of four neighbouring columns stored row by
+// row: one 16-byte vector holds the four columns of a row in float32, so a
+// warp reads or writes a group's rows with one vector access per lane and 32
+// lanes on 32 consecutive rows touch 512 contiguous bytes (no bank
+// conflicts at any row count).  Group g belongs to warp (g + 1) mod 16.  In
+// float32 the first group of warps 1..15 stays in their registers (lane t
+// holds rows t, t + 32, ...; up to 544 rows), the other groups in shared
+// memory, and groups beyond shared memory in a global overflow area of the
+// same layout: registers and shared memory together hold about 360 KB per
+// SM, the 20000 columns of 520 rows of the 20000 x 20000 randomized CUR on
+// 152 SMs without overflow.  Warp 0 gathers the pivot records and holds no
+// register group, so no warp carries both the records in flight and a
+// register group (128 registers per thread, no spills).
+// A step j is:
 //   1. warp 0 of every CTA reads the G candidate records of step j (one per
 //      CTA: its largest residual column norm, that column's index, the sum
 //      of its squared residual norms), all loads in flight together, and
@@ -12,20 +24,24 @@
 //      records double as the grid barrier;
 //   2. every CTA reads the pivot column (rows j..l-1) that its owner
 //      published and forms the same Householder reflector
-//      H = I - tau v v^T (v(j) = 1), mapping it to beta e_j;
-//   3. each warp applies H to one of the CTA's unselected columns and
-//      recomputes that column's residual norm from rows j+1..l-1 (no norm
-//      downdating, hence no cancellation to guard against);
-//   4. warp 0 publishes the CTA's new local candidate for step j+1: the
-//      record first, then the candidate column; every 64-bit word of both
-//      carries the step's tag, so no fence is needed and a reader checks
-//      each word for freshness.
+//      H = I - tau v v^T (v(j) = 1, v(r) = scale x(r) below row j), mapping
+//      it to beta e_j;
+//   3. each warp applies H to its groups: the four dot products of a group
+//      are summed by one transpose-and-reduce butterfly, the update touches
+//      rows j..l-1 only, and the residual norms are recomputed from rows
+//      j+1..l-1 (no norm downdating, hence no cancellation to guard
+//      against); the warp holding the pivot column retires it (beta at row
+//      j, zeros below) and every warp posts its best unselected column;
+//   4. warp 0 publishes the CTA's record for step j+1 and the warp holding
+//      the CTA's best column copies it to the CTA's slot; every 64-bit word
+//      of both carries the step's tag, so no fence is needed and a reader
+//      checks each word for freshness.
 // One grid-wide exchange and three CTA barriers per pivot step; no host
 // round trip until the end.  The exchange (records, tags, pivot decision,
 // pivot-column read, closing count exchange) lives in cpqr_exchange.cuh and
 // is shared with the register-resident variant in cpqr_reg.cu, which
-// cpqr_run launches instead when the slab fits in registers (at most 256
-// rows, 128 in float64, and 64 columns per CTA).
+// cpqr_run launches instead when the whole slab fits in registers (at most
+// 256 rows, 128 in float64, and 64 or 128 columns per CTA).
 // After the last step row i of S holds S1(i, c) for every original column c,
 // J lists the pivots and then the unselected columns in ascending order.
 #include <atomic>
@@ -40,234 +56,360 @@ namespace {
 
 using namespace cpqr_x;
 
-constexpr int kColsPerWarp = 4;  // columns a warp updates in one interleaved pass
+// Rows per lane of the register-resident groups (float32 only: four columns
+// of 17 rows are 68 registers): matrices of up to 544 rows.
+constexpr int kGroupRegRows = 17;
 
-// Column lc of this CTA's slab: shared memory for lc < ncs, else the CTA's
-// part of the global overflow area (same column-major layout).
-template <bool OV, typename real>
-__device__ __forceinline__ real* slab_col(const CpqrParams<real>& P, real* ys, int lc) {
-  if constexpr (!OV) return ys + (int64_t)lc * P.ldl;
-  return lc < P.ncs ? ys + (int64_t)lc * P.ldl
-                    : P.gys + ((int64_t)blockIdx.x * (P.nc - P.ncs) + (lc - P.ncs)) * P.ldl;
+template <typename real>
+constexpr int group_reg_rows(int64_t l) {
+  return (sizeof(real) == 4 && l <= 32 * kGroupRegRows) ? kGroupRegRows : 0;
 }
 
-// Warp 0: pick the CTA's candidate (largest residual norm among its
-// unselected columns, smallest index on ties), publish the record of `epoch`
-// in buffer `bf`, then copy the candidate's rows r0..l-1 to the CTA's data
-// slot (tagged words; a reader waits for the fresh tag of each word).
-template <bool OV, typename real>
-__device__ void publish(const CpqrParams<real>& P, real* ys, const real* nrm,
-                        const int* active, int ncl, int c0, int r0, int bf, unsigned epoch) {
-  const int lane = threadIdx.x & 31;
-  const int G = gridDim.x;
-  real bn = real(-1), ss = real(0);
-  int bi = -1, nf = 0;
-  for (int lc = lane; lc < ncl; lc += 32) {
-    if (!active[lc]) continue;
-    const real v = nrm[lc];
-    if (!isfinite(v)) nf = 1;
-    ss += v * v;
-    if (bi < 0 || v > bn) { bn = v; bi = lc; }
+// Four neighbouring columns of one row.
+template <typename real>
+struct alignas(4 * sizeof(real)) Quad {
+  real x, y, z, w;
+};
+
+template <typename real>
+__device__ __forceinline__ Quad<real> ldq(const Quad<real>* p) {
+  if constexpr (sizeof(real) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    return {t.x, t.y, t.z, t.w};
+  } else {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    return {a.x, a.y, b.x, b.y};
   }
+}
+
+template <typename real>
+__device__ __forceinline__ void stq(Quad<real>* p, const Quad<real>& q) {
+  if constexpr (sizeof(real) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(q.x, q.y, q.z, q.w);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(q.x, q.y);
+    reinterpret_cast<double2*>(p)[1] = make_double2(q.z, q.w);
+  }
+}
+
+// Component c of q, c known only at run time (selects, no local memory).
+template <typename real>
+__device__ __forceinline__ real comp(const Quad<real>& q, int c) {
+  return c == 0 ? q.x : c == 1 ? q.y : c == 2 ? q.z : q.w;
+}
+
+template <typename real>
+__device__ __forceinline__ void set_comp(Quad<real>& q, int c, real v) {
+  if (c == 0) q.x = v;
+  else if (c == 1) q.y = v;
+  else if (c == 2) q.z = v;
+  else q.w = v;
+}
+
+// Unselected columns of group g as a 4-bit mask.
+__device__ __forceinline__ unsigned act_of(const int* active, int g) {
+  const int4 a = *reinterpret_cast<const int4*>(active + 4 * g);
+  return (a.x ? 1u : 0u) | (a.y ? 2u : 0u) | (a.z ? 4u : 0u) | (a.w ? 8u : 0u);
+}
+
+// Rows of group g >= NR (NR: register groups per CTA): shared memory for the
+// first P.ncs, then the CTA's part of the global overflow area.
+template <int NR, bool OV, typename real>
+__device__ __forceinline__ Quad<real>* group_rows(const CpqrParams<real>& P, Quad<real>* ys, int g) {
+  const int s = g - NR;
+  if (!OV || s < P.ncs) return ys + (int64_t)s * P.l;
+  const int ngo = P.nc / 4 - NR - P.ncs;
+  return reinterpret_cast<Quad<real>*>(P.gys) + ((int64_t)blockIdx.x * ngo + (s - P.ncs)) * P.l;
+}
+
+// A lane's running best over the columns it sees: after reduce4 the lanes of
+// one eighth of the warp hold the same column, so the warp's best is merged
+// over the lanes 8 and 16 apart only.
+template <typename real>
+struct LaneBest {
+  real bn, ss;
+  int bi, nf;
+  __device__ __forceinline__ void reset() {
+    bn = real(-1);
+    ss = real(0);
+    bi = -1;
+    nf = 0;
+  }
+  // an unselected local column lc with squared residual norm q2
+  __device__ __forceinline__ void add(real q2, int lc) {
+    const real nv = sqrt(q2);
+    ss += q2;
+    if (!isfinite(nv)) nf = 1;
+    else if (local_better(nv, lc, bn, bi)) {
+      bn = nv;
+      bi = lc;
+    }
+  }
+};
+
+template <typename real>
+__device__ __forceinline__ void post_best(LaneBest<real> b, int lane, int warp, WarpBest<real>& wb) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = 8; o <= 16; o <<= 1) {
+    const real on = __shfl_xor_sync(0xffffffffu, b.bn, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, b.bi, o);
+    if (local_better(on, oi, b.bn, b.bi)) {
+      b.bn = on;
+      b.bi = oi;
+    }
+    b.ss += __shfl_xor_sync(0xffffffffu, b.ss, o);
+    b.nf |= __shfl_xor_sync(0xffffffffu, b.nf, o);
+  }
+  if (lane == 0) {
+    wb.bn[warp] = b.bn;
+    wb.bi[warp] = b.bi;
+    wb.ss[warp] = b.ss;
+    wb.nf[warp] = b.nf;
+  }
+}
+
+// Group g belongs to warp (g + 1) mod 16: warp 0, which also gathers the
+// records, gets groups 15, 31, ... and no register group.
+__device__ __forceinline__ int group_owner(int g) { return (g + 1) % kWarps; }
+__device__ __forceinline__ int first_group(int warp) { return (warp + kWarps - 1) % kWarps; }
+
+// Every warp, after the barrier that follows post_best: the CTA's candidate
+// for epoch `epoch`.  Warp 0 publishes the record in buffer bf; the warp that
+// owns the candidate's group copies its rows r0..l-1 to the CTA's data slot
+// as tagged words, from its registers or from the group's rows (readers check
+// every word's tag, so the two writes need no order between them).
+template <int RPL, bool REGS, int NR, bool OV, typename real>
+__device__ __forceinline__ void publish(const CpqrParams<real>& P, Quad<real>* ys,
+                                        const WarpBest<real>& wb, const Quad<real> (&yr)[RPL],
+                                        int c0, int r0, int bf, unsigned epoch, int lane,
+                                        int warp) {
+  real bn = lane < kWarps ? wb.bn[lane] : real(-1);
+  int bi = lane < kWarps ? wb.bi[lane] : -1;
+  int nf = lane < kWarps ? wb.nf[lane] : 0;
+#pragma unroll
+  for (int o = 1; o < kWarps; o <<= 1) {
     const real on = __shfl_xor_sync(0xffffffffu, bn, o);
     const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (oi >= 0 && (bi < 0 || on > bn || (on == bn && oi < bi))) { bn = on; bi = oi; }
-    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (local_better(on, oi, bn, bi)) {
+      bn = on;
+      bi = oi;
+    }
     nf |= __shfl_xor_sync(0xffffffffu, nf, o);
   }
+  // lanes 0..15 agree; take lane 0's view everywhere
+  bn = __shfl_sync(0xffffffffu, bn, 0);
+  bi = __shfl_sync(0xffffffffu, bi, 0);
+  nf = __shfl_sync(0xffffffffu, nf, 0);
   const unsigned tag = tag_of(P.gen, (int)epoch);
-  // the record first: readers validate every word of the column by its tag,
-  // so the column copy below overlaps the record's way to the other CTAs
-  if (lane == 0) {
-    unsigned hi, lo;
-    norm_words<real>(bi >= 0 ? bn : real(0), &hi, &lo);
-    const unsigned col = nf ? kNonFinite : (bi >= 0 ? (unsigned)(c0 + bi) : kNoCol);
-    st_rec(P.recs + (size_t)bf * G + blockIdx.x, pack(tag, col), pack(tag, hi), pack(tag, lo),
-           pack(tag, __float_as_uint((float)ss)));
-  }
-  if (bi >= 0 && !nf) {
-    constexpr int W = Words<real>::W;
-    unsigned long long* dst = slot_of(P, bf, blockIdx.x);
-    if (!OV || bi < P.ncs) {
-      const real* src = ys + (int64_t)bi * P.ldl;
-      for (int r = r0 + lane; r < P.l; r += 32) put_tagged<real>(dst + (int64_t)r * W, tag, src[r]);
-    } else {
-      const real* src = slab_col<OV>(P, ys, bi);
-      for (int r = r0 + lane; r < P.l; r += 32) put_tagged<real>(dst + (int64_t)r * W, tag, src[r]);
-    }
-  }
-}
-
-// One interleaved pass of a warp over columns base, base + kWarps, ... of
-// its slab (see the step loop).  SH: all of them are in shared memory, so
-// their pointers come straight from the shared array and the accesses
-// compile to shared-memory loads and stores.
-template <bool SH, typename real>
-__device__ __forceinline__ void update_group(const CpqrParams<real>& P, real* ys, const real* xv,
-                                             real* nrm, int* active, int ncl, int c0, int j,
-                                             int pcol, real beta, real tau, real scale, int base,
-                                             int lane) {
-  const int l = P.l;
-  bool v[kColsPerWarp];
-  real* y[kColsPerWarp];
+  if (warp == 0) {
+    real ss = lane < kWarps ? wb.ss[lane] : real(0);
 #pragma unroll
-  for (int c = 0; c < kColsPerWarp; ++c) {
-    const int lc = base + c * kWarps;
-    v[c] = lc < ncl && active[lc] != 0;
-    y[c] = SH ? ys + (int64_t)(lc < ncl ? lc : base) * P.ldl
-              : slab_col<true>(P, ys, lc < ncl ? lc : base);
-    if (v[c] && c0 + lc == pcol) {
-      for (int r = j + lane; r < l; r += 32) y[c][r] = r == j ? beta : real(0);
-      if (lane == 0) {
-        active[lc] = 0;
-        P.J[j] = pcol;
-      }
-      v[c] = false;
-    }
-  }
-  bool any = false;
-#pragma unroll
-  for (int c = 0; c < kColsPerWarp; ++c) any |= v[c];
-  if (!any) return;
-  constexpr int RB = sizeof(real) == 4 ? 4 : 2;  // rows per lane held in registers
-  real d[kColsPerWarp];
-#pragma unroll
-  for (int c = 0; c < kColsPerWarp; ++c) d[c] = real(0);
-  real wj[kColsPerWarp], ws[kColsPerWarp], q[kColsPerWarp];
-  if (l - j - 1 <= 32 * RB) {
-    // every row this lane touches fits in registers: one load of the
-    // column part, dot products, reflector update and new norms from the
-    // registers, one store
-    real xr[RB], yr[kColsPerWarp][RB];
-#pragma unroll
-    for (int u = 0; u < RB; ++u) {
-      const int r = j + 1 + lane + 32 * u;
-      const bool ok = r < l;
-      xr[u] = ok ? xv[r] : real(0);
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c) yr[c][u] = (ok && v[c]) ? y[c][r] : real(0);
-    }
-#pragma unroll
-    for (int u = 0; u < RB; ++u)
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c) d[c] += xr[u] * yr[c][u];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
-#pragma unroll
-    for (int c = 0; c < kColsPerWarp; ++c) {
-      wj[c] = v[c] ? tau * (y[c][j] + scale * d[c]) : real(0);
-      ws[c] = wj[c] * scale;
-      q[c] = real(0);
-    }
+    for (int o = 1; o < kWarps; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if (lane == 0) {
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c)
-        if (v[c]) y[c][j] -= wj[c];
+      unsigned hi, lo;
+      norm_words<real>(bi >= 0 ? bn : real(0), &hi, &lo);
+      const unsigned col = nf ? kNonFinite : (bi >= 0 ? (unsigned)(c0 + bi) : kNoCol);
+      st_rec(P.recs + (size_t)bf * gridDim.x + blockIdx.x, pack(tag, col), pack(tag, hi),
+             pack(tag, lo), pack(tag, __float_as_uint((float)ss)));
     }
+  }
+  if (bi < 0 || nf || group_owner(bi >> 2) != warp) return;
+  constexpr int W = Words<real>::W;
+  unsigned long long* dst = slot_of(P, bf, blockIdx.x);
+  const int g = bi >> 2, c = bi & 3;
+  if (REGS && g < NR) {
 #pragma unroll
-    for (int u = 0; u < RB; ++u) {
-      const int r = j + 1 + lane + 32 * u;
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c) {
-        const real nv = yr[c][u] - ws[c] * xr[u];
-        q[c] += nv * nv;  // rows past l hold zeros
-        if (v[c] && r < l) y[c][r] = nv;
-      }
+    for (int u = 0; u < RPL; ++u) {
+      const int r = lane + 32 * u;
+      if (r >= r0 && r < P.l) put_tagged<real>(dst + (int64_t)r * W, tag, comp(yr[u], c));
     }
   } else {
-    for (int r = j + 1 + lane; r < l; r += 32) {
-      const real x = xv[r];
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c)
-        if (v[c]) d[c] += x * y[c][r];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
-#pragma unroll
-    for (int c = 0; c < kColsPerWarp; ++c) {
-      wj[c] = v[c] ? tau * (y[c][j] + scale * d[c]) : real(0);
-      ws[c] = wj[c] * scale;
-      q[c] = real(0);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c)
-        if (v[c]) y[c][j] -= wj[c];
-    }
-    for (int r = j + 1 + lane; r < l; r += 32) {
-      const real x = xv[r];
-#pragma unroll
-      for (int c = 0; c < kColsPerWarp; ++c) {
-        if (!v[c]) continue;
-        const real nv = y[c][r] - ws[c] * x;
-        y[c][r] = nv;
-        q[c] += nv * nv;
-      }
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int c = 0; c < kColsPerWarp; ++c) q[c] += __shfl_xor_sync(0xffffffffu, q[c], o);
-  if (lane == 0) {
-#pragma unroll
-    for (int c = 0; c < kColsPerWarp; ++c)
-      if (v[c]) nrm[base + c * kWarps] = sqrt(q[c]);
+    const real* src = reinterpret_cast<const real*>(group_rows<NR, OV>(P, ys, g)) + c;
+    for (int r = r0 + lane; r < P.l; r += 32) put_tagged<real>(dst + (int64_t)r * W, tag, src[4 * (int64_t)r]);
   }
 }
 
-template <typename real, bool OV>
-__global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int b = blockIdx.x;
-  const int nc = P.nc, ldl = P.ldl, l = P.l;
-  real* ys = reinterpret_cast<real*>(smem_raw);
-  real* xv = ys + (int64_t)P.ncs * ldl;
-  real* nrm = xv + ldl;
-  int* active = reinterpret_cast<int*>(nrm + nc);
-
-  __shared__ StepState<real> st;
-
-  const int c0 = b * nc;
-  const int ncl = max(0, min(nc, P.n - c0));
-
-  // load the slab, column-major in shared memory
-  for (int64_t e = tid; e < (int64_t)l * ncl; e += kThreads) {
-    const int r = (int)(e / ncl), lc = (int)(e % ncl);
-    const real yv = P.Y[(int64_t)r * P.ldy + c0 + lc];
-    if (!OV || lc < P.ncs) ys[(int64_t)lc * ldl + r] = yv;
-    else slab_col<true>(P, ys, lc)[r] = yv;
+// H applied to a register-resident group (rows lane + 32 u).  act: the
+// group's unselected columns other than the pivot; pc: the pivot's column in
+// the group, or -1.  v = 0 above row j and v(j) = 1 take the place of row
+// masks; row blocks of 32 above j or past l are skipped (warp-uniform).
+template <int RPL, typename real>
+__device__ __forceinline__ void update_reg_group(Quad<real> (&y)[RPL], const real* xv, int l, int j,
+                                                 real tau, real scale, real beta, unsigned act,
+                                                 int pc, int lane, int g, LaneBest<real>& best) {
+  real d0 = real(0), d1 = real(0), d2 = real(0), d3 = real(0);
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    if (32 * u + 31 < j || 32 * u >= l) continue;
+    const int r = lane + 32 * u;
+    const real v = r > j ? (r < l ? scale * xv[r] : real(0)) : (r == j ? real(1) : real(0));
+    d0 += v * y[u].x;
+    d1 += v * y[u].y;
+    d2 += v * y[u].z;
+    d3 += v * y[u].w;
   }
-  for (int lc = tid; lc < nc; lc += kThreads) active[lc] = lc < ncl ? 1 : 0;
-  __syncthreads();
-  for (int lc = warp; lc < ncl; lc += kWarps) {
-    real s2 = real(0);
-    if (!OV || lc < P.ncs) {
-      const real* y = ys + (int64_t)lc * ldl;
-      for (int r = lane; r < l; r += 32) s2 += y[r] * y[r];
-    } else {
-      const real* y = slab_col<true>(P, ys, lc);
-      for (int r = lane; r < l; r += 32) s2 += y[r] * y[r];
+  const int cs = (lane >> 3) & 3;
+  const bool on = (act >> cs) & 1u;
+  const real dg = reduce4(d0, d1, d2, d3, lane);  // every lane: full-warp shuffles
+  const real w = on ? tau * dg : real(0);
+  const real w0 = __shfl_sync(0xffffffffu, w, 0), w1 = __shfl_sync(0xffffffffu, w, 8);
+  const real w2 = __shfl_sync(0xffffffffu, w, 16), w3 = __shfl_sync(0xffffffffu, w, 24);
+  real q0 = real(0), q1 = real(0), q2 = real(0), q3 = real(0);
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    if (32 * u + 31 < j || 32 * u >= l) continue;
+    const int r = lane + 32 * u;
+    const real v = r > j ? (r < l ? scale * xv[r] : real(0)) : (r == j ? real(1) : real(0));
+    y[u].x -= w0 * v;
+    y[u].y -= w1 * v;
+    y[u].z -= w2 * v;
+    y[u].w -= w3 * v;
+    if (r > j) {
+      q0 += y[u].x * y[u].x;
+      q1 += y[u].y * y[u].y;
+      q2 += y[u].z * y[u].z;
+      q3 += y[u].w * y[u].w;
     }
-    s2 = warp_sum(s2);
-    if (lane == 0) nrm[lc] = sqrt(s2);
   }
-  __syncthreads();
-  if (warp == 0) publish<OV>(P, ys, nrm, active, ncl, c0, 0, 0, 1u);
+  if (pc >= 0) {
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) {
+      if (32 * u + 31 < j || 32 * u >= l) continue;
+      const int r = lane + 32 * u;
+      if (r >= j) set_comp(y[u], pc, r == j ? beta : real(0));
+    }
+  }
+  const real qg = reduce4(q0, q1, q2, q3, lane);
+  if (on) best.add(qg, 4 * g + cs);
+}
+
+// H applied to a group in shared or global memory (yg: its rows), with the
+// pivot column x = xv in place of v: w = tau (y(j) + scale x(j+1:)^T y(j+1:)),
+// y(j) -= w, y(r) -= w scale x(r) below.  Rows above j are not touched.
+template <int UNROLL, typename real>
+__device__ __forceinline__ void update_mem_group(Quad<real>* yg, const real* xv, int l, int j,
+                                                 real tau, real scale, real beta, unsigned act,
+                                                 int pc, int lane, int g, LaneBest<real>& best) {
+  real d0 = real(0), d1 = real(0), d2 = real(0), d3 = real(0);
+#pragma unroll UNROLL
+  for (int r = j + 1 + lane; r < l; r += 32) {
+    const real x = xv[r];
+    const Quad<real> t = ldq(yg + r);
+    d0 += x * t.x;
+    d1 += x * t.y;
+    d2 += x * t.z;
+    d3 += x * t.w;
+  }
+  const int cs = (lane >> 3) & 3;
+  const bool on = (act >> cs) & 1u;
+  const real yj = comp(ldq(yg + j), cs);
+  const real dg = reduce4(d0, d1, d2, d3, lane);
+  const real w = on ? tau * (yj + scale * dg) : real(0);
+  const real ws = w * scale;
+  const real s0 = __shfl_sync(0xffffffffu, ws, 0), s1 = __shfl_sync(0xffffffffu, ws, 8);
+  const real s2 = __shfl_sync(0xffffffffu, ws, 16), s3 = __shfl_sync(0xffffffffu, ws, 24);
+  __syncwarp();  // every lane has read row j
+  if ((lane & 7) == 0 && (on || cs == pc))
+    reinterpret_cast<real*>(yg + j)[cs] = cs == pc ? beta : yj - w;
+  real q0 = real(0), q1 = real(0), q2 = real(0), q3 = real(0);
+#pragma unroll UNROLL
+  for (int r = j + 1 + lane; r < l; r += 32) {
+    const real x = xv[r];
+    Quad<real> t = ldq(yg + r);
+    t.x -= s0 * x;
+    t.y -= s1 * x;
+    t.z -= s2 * x;
+    t.w -= s3 * x;
+    q0 += t.x * t.x;
+    q1 += t.y * t.y;
+    q2 += t.z * t.z;
+    q3 += t.w * t.w;
+    if (pc >= 0) set_comp(t, pc, real(0));
+    stq(yg + r, t);
+  }
+  const real qg = reduce4(q0, q1, q2, q3, lane);
+  if (on) best.add(qg, 4 * g + cs);
+}
+
+// Squared norms of the columns of a group in memory, all rows.
+template <typename real>
+__device__ __forceinline__ real mem_group_norms(const Quad<real>* yg, int l, int lane) {
+  real q0 = real(0), q1 = real(0), q2 = real(0), q3 = real(0);
+  for (int r = lane; r < l; r += 32) {
+    const Quad<real> t = ldq(yg + r);
+    q0 += t.x * t.x;
+    q1 += t.y * t.y;
+    q2 += t.z * t.z;
+    q3 += t.w * t.w;
+  }
+  return reduce4(q0, q1, q2, q3, lane);
+}
+
+// The steps of the factorization as one warp runs them (every warp calls it
+// once; all take the same CTA barriers, as cta_sync: warp 0 reaches them
+// from its own copy of this function).  LEAD: warp 0, which gathers the
+// records and holds no register group, so its registers never carry both
+// the records in flight and a register group.  Returns the steps taken.
+template <typename real, int RPL, bool OV, bool LEAD>
+__device__ __forceinline__ int cpqr_steps(const CpqrParams<real>& P, Quad<real>* ys, real* xv,
+                                          int* active, StepState<real>& st, WarpBest<real>& wb,
+                                          int c0, int ncl, int ng, int* k_eff_out) {
+  constexpr int NR = RPL > 0 ? kWarps - 1 : 0;  // register groups of a CTA
+  constexpr bool REGS = RPL > 0 && !LEAD;        // this warp holds one
+  constexpr int RR = REGS ? RPL : 1;
+  constexpr int UN = 4;  // rows in flight per lane in the memory groups' loops
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int l = P.l;
+  const int g0 = first_group(warp);
+  const int cs = (lane >> 3) & 3;
+  Quad<real> yr[RR];
+#pragma unroll
+  for (int u = 0; u < RR; ++u) yr[u] = Quad<real>{real(0), real(0), real(0), real(0)};
+  const bool has_reg = REGS && g0 < ng;
+  if (has_reg) {
+    const int lc = 4 * g0;
+#pragma unroll
+    for (int u = 0; u < RR; ++u) {
+      const int r = lane + 32 * u;
+      if (r < l) {
+        const real* row = P.Y + (int64_t)r * P.ldy + c0 + lc;
+        yr[u].x = lc < ncl ? row[0] : real(0);
+        yr[u].y = lc + 1 < ncl ? row[1] : real(0);
+        yr[u].z = lc + 2 < ncl ? row[2] : real(0);
+        yr[u].w = lc + 3 < ncl ? row[3] : real(0);
+      }
+    }
+  }
+  cta_sync();  // groups in memory loaded, active flags set
+  LaneBest<real> best;
+  best.reset();
+  if (has_reg) {
+    real q0 = real(0), q1 = real(0), q2 = real(0), q3 = real(0);
+#pragma unroll
+    for (int u = 0; u < RR; ++u) {
+      q0 += yr[u].x * yr[u].x;
+      q1 += yr[u].y * yr[u].y;
+      q2 += yr[u].z * yr[u].z;
+      q3 += yr[u].w * yr[u].w;
+    }
+    const real qg = reduce4(q0, q1, q2, q3, lane);
+    if ((act_of(active, g0) >> cs) & 1u) best.add(qg, 4 * g0 + cs);
+  }
+  for (int g = REGS ? g0 + kWarps : g0; g < ng; g += kWarps) {
+    const real qg = mem_group_norms(group_rows<NR, OV>(P, ys, g), l, lane);
+    if ((act_of(active, g) >> cs) & 1u) best.add(qg, 4 * g + cs);
+  }
+  post_best(best, lane, warp, wb);
+  cta_sync();
+  publish<RR, REGS, NR, OV>(P, ys, wb, yr, c0, 0, 0, 1u, lane, warp);
 
   real normY = real(-1), nu_first = real(0);
   int k_eff = -1;
   int j = 0;
   for (;; ++j) {
-    if (warp == 0) decide_pivot(P, j, normY, st);
-    __syncthreads();
+    if (LEAD) decide_pivot(P, j, normY, st);
+    cta_sync();
     if (st.stop) break;
     const int owner = st.owner, pcol = st.col;
     const real nu = st.nu;
@@ -275,39 +417,116 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
     if (!fetch_pivot<kThreads>(P, j, owner, xv, st)) break;
     real beta, tau, scale;
     step_reflector(xv, j, nu, st, &beta, &tau, &scale);
-    // apply H to every unselected local column, recompute its residual norm
-    // from rows j+1..l-1; the owner retires the pivot column.  Warp w owns
-    // columns w, w + 16, w + 32, w + 48 and updates them in one interleaved
-    // pass so their reductions overlap.
-    for (int base = warp; base < ncl; base += kColsPerWarp * kWarps) {
-      // columns past ncl are unused (their pointer falls back to column base)
-      if (!OV || min(ncl - 1, base + (kColsPerWarp - 1) * kWarps) < P.ncs)
-        update_group<true>(P, ys, xv, nrm, active, ncl, c0, j, pcol, beta, tau, scale, base, lane);
-      else
-        update_group<false>(P, ys, xv, nrm, active, ncl, c0, j, pcol, beta, tau, scale, base, lane);
+    const int pl = pcol - c0;                             // local pivot column
+    const int pg = (pl >= 0 && pl < ncl) ? pl >> 2 : -1;  // its group, if here
+    best.reset();
+    if (has_reg) {
+      const int pc = pg == g0 ? pl & 3 : -1;
+      const unsigned act = act_of(active, g0) & ~(pc >= 0 ? 1u << pc : 0u);
+      if (act || pc >= 0)
+        update_reg_group<RR>(yr, xv, l, j, tau, scale, beta, act, pc, lane, g0, best);
     }
-    __syncthreads();
-    if (warp == 0) publish<OV>(P, ys, nrm, active, ncl, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2));
+    for (int g = REGS ? g0 + kWarps : g0; g < ng; g += kWarps) {
+      const int pc = pg == g ? pl & 3 : -1;
+      const unsigned act = act_of(active, g) & ~(pc >= 0 ? 1u << pc : 0u);
+      if (!act && pc < 0) continue;
+      const int s = g - NR;
+      if (!OV || s < P.ncs)
+        update_mem_group<UN>(ys + (int64_t)s * l, xv, l, j, tau, scale, beta, act, pc, lane, g,
+                             best);
+      else
+        update_mem_group<UN>(group_rows<NR, true>(P, ys, g), xv, l, j, tau, scale, beta, act, pc,
+                             lane, g, best);
+    }
+    if (pg >= 0 && group_owner(pg) == warp && lane == 0) {
+      active[pl] = 0;
+      P.J[j] = pcol;
+    }
+    post_best(best, lane, warp, wb);
+    cta_sync();
+    publish<RR, REGS, NR, OV>(P, ys, wb, yr, c0, j + 1, (j + 1) & 1, (unsigned)(j + 2), lane, warp);
   }
-  const int k_done = j;
+  *k_eff_out = k_eff;
+  // rows 0..j-1 of S from the register group
+  if (has_reg && st.stop != 2) {
+#pragma unroll
+    for (int u = 0; u < RR; ++u) {
+      const int r = lane + 32 * u;
+      if (r >= j) continue;
+      real* row = P.S + (int64_t)r * P.lds + c0 + 4 * g0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (4 * g0 + c < ncl) row[c] = comp(yr[u], c);
+    }
+  }
+  return j;
+}
+
+// RPL > 0: the first group of warps 1..15 is register-resident (RPL rows
+// per lane).  OV: some groups live in the global overflow area.
+template <typename real, int RPL, bool OV>
+__global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
+  constexpr int NR = RPL > 0 ? kWarps - 1 : 0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int b = blockIdx.x;
+  const int nc = P.nc, l = P.l;
+  Quad<real>* ys = reinterpret_cast<Quad<real>*>(smem_raw);  // P.ncs groups of l rows
+  real* xv = reinterpret_cast<real*>(ys + (int64_t)P.ncs * l);  // pivot column of the step
+  int* active = reinterpret_cast<int*>(xv + P.ldl);             // nc flags (P.ldl: l rounded up to 4)
+
+  __shared__ StepState<real> st;
+  __shared__ WarpBest<real> wb;
+
+  const int c0 = b * nc;
+  const int ncl = max(0, min(nc, P.n - c0));
+  const int ng = (ncl + 3) >> 2;  // groups holding this CTA's columns
+
+  for (int lc = tid; lc < nc; lc += kThreads) active[lc] = lc < ncl ? 1 : 0;
+  // groups in memory, read along the rows of Y; the columns past ncl of the
+  // last group are zero
+  const int cm0 = min(4 * ng, 4 * NR), ncm = 4 * ng - cm0;
+  for (int64_t e = tid; e < (int64_t)l * ncm; e += kThreads) {
+    const int r = (int)(e / ncm), lc = cm0 + (int)(e % ncm);
+    const real yv = lc < ncl ? P.Y[(int64_t)r * P.ldy + c0 + lc] : real(0);
+    reinterpret_cast<real*>(group_rows<NR, OV>(P, ys, lc >> 2) + r)[lc & 3] = yv;
+  }
+  int k_eff = -1;
+  const int k_done = warp == 0
+                         ? cpqr_steps<real, RPL, OV, true>(P, ys, xv, active, st, wb, c0, ncl, ng, &k_eff)
+                         : cpqr_steps<real, RPL, OV, false>(P, ys, xv, active, st, wb, c0, ncl, ng, &k_eff);
   if (st.stop == 2) return;  // timed out: leave without further waits
-  // S rows 0..k_done-1 in original column order
-  for (int64_t e = tid; e < (int64_t)k_done * ncl; e += kThreads) {
-    const int i = (int)(e / ncl), lc = (int)(e % ncl);
-    P.S[(int64_t)i * P.lds + c0 + lc] =
-        (!OV || lc < P.ncs) ? ys[(int64_t)lc * ldl + i] : slab_col<true>(P, ys, lc)[i];
+  // S rows 0..k_done-1 of the groups in memory, in original column order
+  for (int64_t e = tid; e < (int64_t)k_done * ncm; e += kThreads) {
+    const int i = (int)(e / ncm), lc = cm0 + (int)(e % ncm);
+    if (lc < ncl)
+      P.S[(int64_t)i * P.lds + c0 + lc] =
+          reinterpret_cast<const real*>(group_rows<NR, OV>(P, ys, lc >> 2) + i)[lc & 3];
   }
   finish_order(P, active, ncl, c0, k_done, k_eff, st);
 }
 
+// Shape of one factorization: grid, columns per CTA (a multiple of four),
+// which kernel, and for the grouped kernel its register rows, groups in
+// shared memory and overflow groups per CTA.
+struct Layout {
+  int G = 1, nc = 4, warps = kWarps;
+  bool reg = false;  // the register-resident kernel (cpqr_reg.cu)
+  int rpl = 0;       // grouped kernel: rows per lane of the register groups
+  int ncs = 0;       // grouped kernel: groups in shared memory
+  int ngo = 0;       // grouped kernel: overflow groups per CTA
+  int ldl = 1;
+  size_t smem = 0;
+};
+
 template <typename real>
-size_t cpqr_smem_bytes(int ncs, int nc, int ldl) {
-  return (size_t)ncs * ldl * sizeof(real) + (size_t)ldl * sizeof(real) + (size_t)nc * sizeof(real) +
-         (size_t)nc * sizeof(int) + 64;
+size_t grouped_smem_bytes(int ncs, int nc, int64_t l) {
+  const int64_t xl = (l + 3) & ~int64_t(3);
+  return (size_t)ncs * l * 4 * sizeof(real) + (size_t)xl * sizeof(real) + (size_t)nc * sizeof(int) +
+         64;
 }
 
-// Grid, columns per CTA, how many of them fit in shared memory, and the warps
-// per CTA of the register-resident kernel.
+// Grid, columns per CTA and kernel of an l x n factorization.
 //
 // One decomposition at a time (the handle's concurrency 1): one CTA per SM,
 // the lowest latency per factorization.  With several in flight: the fewest
@@ -322,75 +541,95 @@ size_t cpqr_smem_bytes(int ncs, int nc, int ldl) {
 // concurrent factorizations share SMs, measured slower: 549/s against 613/s
 // with four decompositions in flight.)
 template <typename real>
-curid_status cpqr_layout(const Ctx& ctx, int64_t l, int64_t n, int* G_out, int* nc_out,
-                         int* ncs_out, int* warps_out = nullptr) {
+curid_status cpqr_layout(const Ctx& ctx, int64_t l, int64_t n, Layout* L) {
   if (l <= 0 || n <= 0) return CURID_INVALID_ARG;
+  if (l > (1 << 24) || n > INT32_MAX / 2) return CURID_UNSUPPORTED;
   const int gmax = std::min(ctx.num_sms, 32 * kMaxSlotsPerLane);
   int G = (int)std::min<int64_t>(gmax, n);
-  int warps = 16;
   const char* env = std::getenv("CURID_CPQR_CTAS");
   bool fewest = ctx.concurrency > 1;
   if (env && std::strcmp(env, "all") == 0) fewest = false;
   if (env && std::strcmp(env, "fewest") == 0) fewest = true;
   if (fewest) {
-    const int64_t rc = cpqr_reg_cols<real>((int)std::min<int64_t>(l, INT32_MAX), warps);
+    const int64_t rc = cpqr_reg_cols<real>((int)l, kWarps);
     if (rc > 0 && (n + rc - 1) / rc <= gmax) G = (int)((n + rc - 1) / rc);
   }
-  const int nc = (int)((n + G - 1) / G);
+  int nc = (int)((n + G - 1) / G);
+  nc = (nc + 3) & ~3;
   G = (int)((n + nc - 1) / nc);
-  const int ldl = (int)(l | 1);
+  L->G = G;
+  L->nc = nc;
+  L->warps = kWarps;
+  L->reg = cpqr_reg_fits<real>(ctx, (int)l, nc, kWarps);
+  if (L->reg) {
+    L->ldl = (int)(l | 1);
+    L->rpl = L->ncs = L->ngo = 0;
+    L->smem = 0;  // cpqr_reg_launch sizes its own
+    return CURID_OK;
+  }
+  L->rpl = group_reg_rows<real>(l);
+  const int nr = L->rpl > 0 ? kWarps - 1 : 0;
+  const int rest = std::max(0, nc / 4 - nr);
   // the kernel's static shared variables share the per-block limit
-  const size_t fixed = cpqr_smem_bytes<real>(0, nc, ldl) + 1024;
+  const size_t fixed = grouped_smem_bytes<real>(0, nc, l) + 1024;
   if (fixed > ctx.smem_optin) return CURID_UNSUPPORTED;
-  const int ncs = (int)std::min<size_t>(nc, (ctx.smem_optin - fixed) / ((size_t)ldl * sizeof(real)));
-  *G_out = G;
-  *nc_out = nc;
-  *ncs_out = ncs;
-  if (warps_out) *warps_out = warps;
+  L->ncs = (int)std::min<size_t>(rest, (ctx.smem_optin - fixed) / ((size_t)l * 4 * sizeof(real)));
+  L->ngo = rest - L->ncs;
+  L->ldl = (int)((l + 3) & ~int64_t(3));
+  L->smem = grouped_smem_bytes<real>(L->ncs, nc, l);
   return CURID_OK;
+}
+
+template <typename real>
+void (*grouped_kernel(const Layout& L))(CpqrParams<real>) {
+  if constexpr (sizeof(real) == 4) {
+    if (L.rpl == kGroupRegRows)
+      return L.ngo > 0 ? cpqr_kernel<real, kGroupRegRows, true> : cpqr_kernel<real, kGroupRegRows, false>;
+  }
+  if (L.rpl != 0) return nullptr;
+  return L.ngo > 0 ? cpqr_kernel<real, 0, true> : cpqr_kernel<real, 0, false>;
 }
 
 }  // namespace
 
 template <typename real>
 curid_status cpqr_plan(const Ctx& ctx, int64_t l, int64_t n, int* grid, size_t* smem) {
-  int G, nc, ncs;
-  CURID_TRY(cpqr_layout<real>(ctx, l, n, &G, &nc, &ncs));
-  *grid = G;
-  *smem = cpqr_smem_bytes<real>(ncs, nc, (int)(l | 1));
+  Layout L;
+  CURID_TRY(cpqr_layout<real>(ctx, l, n, &L));
+  *grid = L.G;
+  *smem = L.smem;
   return CURID_OK;
 }
 
 template <typename real>
 void cpqr_carve(Carver& cv, const Ctx& ctx, int64_t l, int64_t n, CpqrScratch* s) {
-  int G = 1, nc = 1, ncs = 1;
-  if (cpqr_layout<real>(ctx, l, n, &G, &nc, &ncs) != CURID_OK) G = nc = ncs = 1;
-  s->grid = G;
-  s->slots = cv.take<Rec>(2 * (size_t)G);
-  s->slot_data = cv.take<unsigned long long>(2 * (size_t)G * slot_words<real>(l));
-  s->counts = cv.take<int>(G);
+  Layout L;
+  if (cpqr_layout<real>(ctx, l, n, &L) != CURID_OK) L = Layout();
+  s->grid = L.G;
+  s->slots = cv.take<Rec>(2 * (size_t)L.G);
+  s->slot_data = cv.take<unsigned long long>(2 * (size_t)L.G * slot_words<real>(l));
+  s->counts = cv.take<int>(L.G);
   s->abort_flag = cv.take<int>(1);
-  s->overflow = nc > ncs ? cv.take<real>((size_t)G * (nc - ncs) * (size_t)(l | 1)) : nullptr;
+  s->overflow = L.ngo > 0 ? cv.take<real>((size_t)L.G * L.ngo * (size_t)l * 4) : nullptr;
 }
 
 template <typename real>
 curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64_t ldy, int k_max,
                       double tol, int32_t* J, real* S, int64_t lds, const CpqrScratch& s,
                       int which) {
-  int G, nc, ncs, warps;
-  CURID_TRY(cpqr_layout<real>(ctx, l, n, &G, &nc, &ncs, &warps));
-  if (G != s.grid || (nc > ncs && !s.overflow)) return CURID_INVALID_ARG;
-  const size_t smem = cpqr_smem_bytes<real>(ncs, nc, (int)(l | 1));
+  Layout L;
+  CURID_TRY(cpqr_layout<real>(ctx, l, n, &L));
+  if (L.G != s.grid || (L.ngo > 0 && !s.overflow)) return CURID_INVALID_ARG;
   CpqrParams<real> P;
   P.Y = Y;
   P.ldy = ldy;
   P.l = (int)l;
   P.n = (int)n;
   P.k_max = k_max;
-  P.nc = nc;
-  P.ncs = ncs;
+  P.nc = L.nc;
+  P.ncs = L.ncs;
   P.gys = static_cast<real*>(s.overflow);
-  P.ldl = (int)(l | 1);
+  P.ldl = L.ldl;
   P.tol = (real)tol;
   // a pivot norm at or below 2 sqrt(l) eps nu_1 is rounding noise (Section 2.3's
   // singular S11): k_eff stops there
@@ -407,14 +646,15 @@ curid_status cpqr_run(const Ctx& ctx, const real* Y, int64_t l, int64_t n, int64
   P.status = ctx.status;
   P.which = which;
   P.spin = ctx.spin;
-  P.warps = warps;
-  CURID_CUDA(cudaMemsetAsync(s.slots, 0, 2 * (size_t)G * sizeof(Rec), ctx.stream));
+  P.warps = L.warps;
+  CURID_CUDA(cudaMemsetAsync(s.slots, 0, 2 * (size_t)L.G * sizeof(Rec), ctx.stream));
   CURID_CUDA(cudaMemsetAsync(s.abort_flag, 0, sizeof(int), ctx.stream));
-  if (cpqr_reg_fits<real>(ctx, (int)l, nc, warps)) return cpqr_reg_launch<real>(ctx, P, G);
-  auto fn = nc > ncs ? cpqr_kernel<real, true> : cpqr_kernel<real, false>;
-  CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (L.reg) return cpqr_reg_launch<real>(ctx, P, L.G);
+  auto fn = grouped_kernel<real>(L);
+  if (!fn) return CURID_UNSUPPORTED;
+  CURID_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
   void* args[] = {&P};
-  CURID_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(G), dim3(kThreads), args, smem,
+  CURID_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(L.G), dim3(kThreads), args, L.smem,
                                          ctx.stream));
   if (ctx.launches) ++*ctx.launches;
   return CURID_OK;

@@ -29,8 +29,8 @@ struct CpqrParams {
   const real* Y;
   int64_t ldy;
   int l, n, k_max, nc, ldl;
-  int ncs;                       // columns of a slab held in shared memory (the rest: gys)
-  real* gys;                     // [G][nc - ncs][ldl] overflow columns, column-major
+  int ncs;                       // grouped kernel: column groups in shared memory
+  real* gys;                     // grouped kernel: [G][overflow groups][l][4] the rest
   real tol;
   real rank_rtol;
   int32_t* J;
@@ -67,6 +67,12 @@ template <typename real>
 __device__ __forceinline__ unsigned long long* slot_of(const CpqrParams<real>& P, int bf, int cta) {
   return P.slot_data + ((int64_t)bf * gridDim.x + cta) * slot_words<real>(P.l);
 }
+
+// CTA barrier that may be reached from different instructions by different
+// warps (PTX barrier.sync without .aligned): the grouped kernel runs warp 0
+// and the other warps through two copies of the step loop.  Same memory
+// ordering as __syncthreads().
+__device__ __forceinline__ void cta_sync() { asm volatile("barrier.sync 0;" ::: "memory"); }
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
@@ -311,7 +317,7 @@ __device__ __forceinline__ bool fetch_pivot(const CpqrParams<real>& P, int j, in
     }
     xv[r] = v;
   }
-  __syncthreads();
+  cta_sync();
   if (st.stale) {
     if (tid == 0) {
       atomicExch(P.abort_flag, 1);
@@ -386,6 +392,42 @@ __device__ __forceinline__ void note_rank(const CpqrParams<real>& P, int j, real
   }
 }
 
+// On return lane t holds the warp-wide sum of a_c for c = (t >> 3) & 3:
+// the exchange at offset 16 splits the columns {0,1} / {2,3} between the
+// lane halves, the one at offset 8 splits each pair, and three xor rounds
+// finish each sum inside its group of 8 lanes.
+template <typename real>
+__device__ __forceinline__ real reduce4(real a0, real a1, real a2, real a3, int lane) {
+  const bool hi = (lane & 16) != 0;
+  const real k0 = (hi ? a2 : a0) + __shfl_xor_sync(0xffffffffu, hi ? a0 : a2, 16);
+  const real k1 = (hi ? a3 : a1) + __shfl_xor_sync(0xffffffffu, hi ? a1 : a3, 16);
+  const bool mid = (lane & 8) != 0;
+  real m = (mid ? k1 : k0) + __shfl_xor_sync(0xffffffffu, mid ? k0 : k1, 8);
+  m += __shfl_xor_sync(0xffffffffu, m, 4);
+  m += __shfl_xor_sync(0xffffffffu, m, 2);
+  m += __shfl_xor_sync(0xffffffffu, m, 1);
+  return m;
+}
+
+// (na, ia) beats (nb, ib) among local columns: ib < 0 is no column; larger
+// norm, then smaller index.  A NaN norm never beats a column (the record
+// flags it as non-finite instead).
+template <typename real>
+__device__ __forceinline__ bool local_better(real na, int ia, real nb, int ib) {
+  if (ia < 0) return false;
+  if (ib < 0) return true;
+  if (na > nb) return true;
+  return na == nb && ia < ib;
+}
+
+template <typename real>
+struct WarpBest {
+  real bn[kWarps];
+  real ss[kWarps];
+  int bi[kWarps];
+  int nf[kWarps];
+};
+
 // Householder reflector of step j from the pivot column x (rows j..l-1) and
 // its norm nu: H = I - tau v v^T, v(j) = 1, v(r) = scale x(r) for r > j,
 // H x = beta e_j with beta = -sign(x(j)) nu.  nu = 0 gives H = I.
@@ -409,7 +451,7 @@ __device__ __forceinline__ void step_reflector(const real* xv, int j, real nu, S
                                                real* beta, real* tau, real* scale) {
   if constexpr (sizeof(real) == 8) {
     if (threadIdx.x == 0) reflector(xv[j], nu, &st.beta, &st.tau, &st.scale);
-    __syncthreads();
+    cta_sync();
     *beta = st.beta;
     *tau = st.tau;
     *scale = st.scale;

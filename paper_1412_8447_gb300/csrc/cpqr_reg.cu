@@ -41,42 +41,6 @@ constexpr int max_reg_rows() {
   return sizeof(real) == 4 ? 256 : 128;
 }
 
-// On return lane t holds the warp-wide sum of a_c for c = (t >> 3) & 3:
-// the exchange at offset 16 splits the columns {0,1} / {2,3} between the
-// lane halves, the one at offset 8 splits each pair, and three xor rounds
-// finish each sum inside its group of 8 lanes.
-template <typename real>
-__device__ __forceinline__ real reduce4(real a0, real a1, real a2, real a3, int lane) {
-  const bool hi = (lane & 16) != 0;
-  const real k0 = (hi ? a2 : a0) + __shfl_xor_sync(0xffffffffu, hi ? a0 : a2, 16);
-  const real k1 = (hi ? a3 : a1) + __shfl_xor_sync(0xffffffffu, hi ? a1 : a3, 16);
-  const bool mid = (lane & 8) != 0;
-  real m = (mid ? k1 : k0) + __shfl_xor_sync(0xffffffffu, mid ? k0 : k1, 8);
-  m += __shfl_xor_sync(0xffffffffu, m, 4);
-  m += __shfl_xor_sync(0xffffffffu, m, 2);
-  m += __shfl_xor_sync(0xffffffffu, m, 1);
-  return m;
-}
-
-// (na, ia) beats (nb, ib) among local columns: ib < 0 is no column; larger
-// norm, then smaller index.  A NaN norm never beats a column (the record
-// flags it as non-finite instead).
-template <typename real>
-__device__ __forceinline__ bool local_better(real na, int ia, real nb, int ib) {
-  if (ia < 0) return false;
-  if (ib < 0) return true;
-  if (na > nb) return true;
-  return na == nb && ia < ib;
-}
-
-template <typename real>
-struct WarpBest {
-  real bn[kWarps];
-  real ss[kWarps];
-  int bi[kWarps];
-  int nf[kWarps];
-};
-
 // Each warp, after its residual norms are summed by reduce4 per group of four
 // columns (lane t holds the squared norm of column 4 g + ((t >> 3) & 3) in
 // qg[g]): post the warp's best unselected column, the sum of its squared

@@ -58,7 +58,7 @@ curid_status gemm_bf16(const Ctx& ctx, bool tb, int64_t M, int64_t N, int64_t K,
 struct CpqrScratch {
   void* slots;       // 2 * G slot records
   void* slot_data;   // 2 * G * l reals
-  void* overflow;    // columns beyond shared memory: G * (nc - ncs) * ldl reals
+  void* overflow;    // column groups beyond shared memory and registers (or null)
   int* counts;       // G
   int* abort_flag;   // 1
   int grid;          // G

@@ -267,12 +267,17 @@ def test_order_beyond_limit_is_unsupported():
 
 
 @pytest.mark.parametrize("dtype,l,n,k", [(torch.float32, 520, 20000, 64),
+                                         (torch.float32, 520, 30000, 64),
+                                         (torch.float32, 600, 20000, 64),
                                          (torch.float64, 300, 40000, 48)])
 def test_cpqr_overflow_columns(dtype, l, n, k):
-    """Slabs larger than one SM's shared memory (520 x 134 float32 columns,
-    300 x 264 float64): the columns that do not fit live in global memory;
-    the planted pivot order must come out exactly, and S must match the
-    oracle's rows up to sign."""
+    """Large slabs of the grouped shared-memory kernel.  520 x 20000 float32
+    (132 columns of a CTA): 15 register groups and 18 groups in shared
+    memory.  520 x 30000 (200 columns): register groups, shared memory and 8
+    overflow groups in global memory.  600 x 20000 (rows beyond the register
+    groups) and 300 x 40000 float64: shared memory and overflow only.  The
+    planted pivot order must come out exactly, and S must match the oracle's
+    rows up to sign."""
     Y, perm = syn.planted_pivots(l, n, k, 44, decay=0.85 if dtype == torch.float32 else 2 ** -0.5,
                                  dtype=dtype)
     r = curid.cpqr(cuda(Y), k=k)
