@@ -7,15 +7,15 @@
 // row: one 16-byte vector holds the four columns of a row in float32, so a
 // warp reads or writes a group's rows with one vector access per lane and 32
 // lanes on 32 consecutive rows touch 512 contiguous bytes (no bank
-// conflicts at any row count).  Group g belongs to warp (g + 1) mod 16.  In
-// float32 the first group of warps 1..15 stays in their registers (lane t
-// holds rows t, t + 32, ...; up to 544 rows), the other groups in shared
-// memory, and groups beyond shared memory in a global overflow area of the
-// same layout: registers and shared memory together hold about 360 KB per
-// SM, the 20000 columns of 520 rows of the 20000 x 20000 randomized CUR on
-// 152 SMs without overflow.  Warp 0 gathers the pivot records and holds no
-// register group, so no warp carries both the records in flight and a
-// register group (128 registers per thread, no spills).
+// conflicts at any row count).  In float32 warps 1..15 each keep one group
+// in their registers (lane t holds rows t, t + 32, ...; up to 544 rows), the
+// other groups live in shared memory, and groups beyond shared memory in a
+// global overflow area of the same layout: registers and shared memory
+// together hold about 360 KB per SM, the 20000 columns of 520 rows of the
+// 20000 x 20000 randomized CUR on 152 SMs without overflow.  Warp 0 gathers
+// the pivot records and holds no register group (no warp carries both the
+// records in flight and a register group: 128 registers per thread, no
+// spills); it takes two memory groups in its place.
 // A step j is:
 //   1. warp 0 of every CTA reads the G candidate records of step j (one per
 //      CTA: its largest residual column norm, that column's index, the sum
@@ -169,10 +169,29 @@ __device__ __forceinline__ void post_best(LaneBest<real> b, int lane, int warp, 
   }
 }
 
-// Group g belongs to warp (g + 1) mod 16: warp 0, which also gathers the
-// records, gets groups 15, 31, ... and no register group.
-__device__ __forceinline__ int group_owner(int g) { return (g + 1) % kWarps; }
-__device__ __forceinline__ int first_group(int warp) { return (warp + kWarps - 1) % kWarps; }
+// Owner warp of group g.  With register groups (NR = 15): group g < 15 is
+// the register group of warp g + 1; memory group m = g - 15 belongs to warp
+// 0 for m = 0, 1 and then to warps 1, 2, ..., 15, 0, 1, ... in turn: warp 0,
+// which gathers the records and holds no register group, takes two memory
+// groups in its place (a register group costs about as much as two).
+// Without register groups: warp (g + 1) mod 16.
+template <int NR>
+__device__ __forceinline__ int group_owner(int g) {
+  if (NR == 0) return (g + 1) % kWarps;
+  if (g < NR) return g + 1;
+  const int m = g - NR;
+  return m < 2 ? 0 : (m - 1) % kWarps;
+}
+
+// A warp's memory groups in the order it updates them: first, next.
+template <int NR>
+__device__ __forceinline__ int first_mem_group(int warp) {
+  return NR == 0 ? (warp + kWarps - 1) % kWarps : NR + (warp ? warp + 1 : 0);
+}
+template <int NR>
+__device__ __forceinline__ int next_mem_group(int g) {
+  return (NR > 0 && g == NR) ? NR + 1 : g + kWarps;
+}
 
 // Every warp, after the barrier that follows post_best: the CTA's candidate
 // for epoch `epoch`.  Warp 0 publishes the record in buffer bf; the warp that
@@ -214,7 +233,7 @@ __device__ __forceinline__ void publish(const CpqrParams<real>& P, Quad<real>* y
              pack(tag, lo), pack(tag, __float_as_uint((float)ss)));
     }
   }
-  if (bi < 0 || nf || group_owner(bi >> 2) != warp) return;
+  if (bi < 0 || nf || group_owner<NR>(bi >> 2) != warp) return;
   constexpr int W = Words<real>::W;
   unsigned long long* dst = slot_of(P, bf, blockIdx.x);
   const int g = bi >> 2, c = bi & 3;
@@ -230,20 +249,81 @@ __device__ __forceinline__ void publish(const CpqrParams<real>& P, Quad<real>* y
   }
 }
 
-// H applied to a register-resident group (rows lane + 32 u).  act: the
-// group's unselected columns other than the pivot; pc: the pivot's column in
-// the group, or -1.  v = 0 above row j and v(j) = 1 take the place of row
-// masks; row blocks of 32 above j or past l are skipped (warp-uniform).
+// All threads of step j, after the barrier that follows decide_pivot: the
+// pivot column x that its owner published (tagged words), its norm nu, and
+// the step's reflector (beta, tau, scale).  Float32: xv receives the
+// Householder vector itself, v(r) = 0 above row j (row j - 1 is cleared
+// here, the rows above it in earlier steps), v(j) = 1, v(r) = scale x(r)
+// below; every thread reads x(j) and forms the reflector, so one barrier ends
+// the fetch.  Float64 (divisions and products at a 64th of the float32 rate):
+// xv receives x itself (rows j..l-1), thread 0 forms the reflector and a
+// second barrier shares it; the update folds scale into its sums.  False
+// (st.stop = 2, the abort flag raised) if a word never became fresh.
+template <typename real>
+__device__ __forceinline__ bool fetch_v(const CpqrParams<real>& P, int j, int owner, real nu,
+                                        real* xv, StepState<real>& st, real* beta, real* tau,
+                                        real* scale) {
+  constexpr int W = Words<real>::W;
+  const int tid = threadIdx.x, l = P.l;
+  const unsigned long long* src = slot_of(P, j & 1, owner);
+  const unsigned tag = tag_of(P.gen, j + 1);
+  bool ok = true;
+  if constexpr (sizeof(real) == 4) {
+    real alpha = real(0);
+    if (!get_tagged<real>(src + (int64_t)j * W, tag, &alpha, P.abort_flag, P.spin)) ok = false;
+    reflector(alpha, nu, beta, tau, scale);
+    for (int r = j + tid; r < l; r += kThreads) {
+      real x = alpha;
+      if (r > j && !get_tagged<real>(src + (int64_t)r * W, tag, &x, P.abort_flag, P.spin)) {
+        ok = false;
+        x = real(0);
+      }
+      xv[r] = r == j ? real(1) : *scale * x;
+    }
+    if (j > 0 && tid == kThreads - 1) xv[j - 1] = real(0);
+    if (!ok) st.stale = 1;
+    cta_sync();
+  } else {
+    for (int r = j + tid; r < l; r += kThreads) {
+      real x;
+      if (!get_tagged<real>(src + (int64_t)r * W, tag, &x, P.abort_flag, P.spin)) {
+        ok = false;
+        x = real(0);
+      }
+      xv[r] = x;
+    }
+    if (!ok) st.stale = 1;
+    cta_sync();
+    if (tid == 0) reflector(xv[j], nu, &st.beta, &st.tau, &st.scale);
+    cta_sync();
+    *beta = st.beta;
+    *tau = st.tau;
+    *scale = st.scale;
+  }
+  if (st.stale) {
+    if (tid == 0) {
+      atomicExch(P.abort_flag, 1);
+      set_flag(&P.status->flags, FLAG_TIMEOUT);
+    }
+    st.stop = 2;
+    return false;
+  }
+  return true;
+}
+
+// H applied to a register-resident group (rows lane + 32 u), v = xv (zero
+// above row j and past l, so neither pass needs a row mask but the norms';
+// every row block is processed: skipping the blocks above j, a branch per
+// block, measured slower).  act: the group's unselected columns other than
+// the pivot; pc: the pivot's column in the group, or -1.
 template <int RPL, typename real>
-__device__ __forceinline__ void update_reg_group(Quad<real> (&y)[RPL], const real* xv, int l, int j,
-                                                 real tau, real scale, real beta, unsigned act,
-                                                 int pc, int lane, int g, LaneBest<real>& best) {
+__device__ __forceinline__ void update_reg_group(Quad<real> (&y)[RPL], const real* xv, int j,
+                                                 real tau, real beta, unsigned act, int pc,
+                                                 int lane, int g, LaneBest<real>& best) {
   real d0 = real(0), d1 = real(0), d2 = real(0), d3 = real(0);
 #pragma unroll
   for (int u = 0; u < RPL; ++u) {
-    if (32 * u + 31 < j || 32 * u >= l) continue;
-    const int r = lane + 32 * u;
-    const real v = r > j ? (r < l ? scale * xv[r] : real(0)) : (r == j ? real(1) : real(0));
+    const real v = xv[lane + 32 * u];
     d0 += v * y[u].x;
     d1 += v * y[u].y;
     d2 += v * y[u].z;
@@ -258,9 +338,8 @@ __device__ __forceinline__ void update_reg_group(Quad<real> (&y)[RPL], const rea
   real q0 = real(0), q1 = real(0), q2 = real(0), q3 = real(0);
 #pragma unroll
   for (int u = 0; u < RPL; ++u) {
-    if (32 * u + 31 < j || 32 * u >= l) continue;
     const int r = lane + 32 * u;
-    const real v = r > j ? (r < l ? scale * xv[r] : real(0)) : (r == j ? real(1) : real(0));
+    const real v = xv[r];
     y[u].x -= w0 * v;
     y[u].y -= w1 * v;
     y[u].z -= w2 * v;
@@ -275,7 +354,7 @@ __device__ __forceinline__ void update_reg_group(Quad<real> (&y)[RPL], const rea
   if (pc >= 0) {
 #pragma unroll
     for (int u = 0; u < RPL; ++u) {
-      if (32 * u + 31 < j || 32 * u >= l) continue;
+      if (32 * u + 31 < j) continue;
       const int r = lane + 32 * u;
       if (r >= j) set_comp(y[u], pc, r == j ? beta : real(0));
     }
@@ -284,49 +363,66 @@ __device__ __forceinline__ void update_reg_group(Quad<real> (&y)[RPL], const rea
   if (on) best.add(qg, 4 * g + cs);
 }
 
-// H applied to a group in shared or global memory (yg: its rows), with the
-// pivot column x = xv in place of v: w = tau (y(j) + scale x(j+1:)^T y(j+1:)),
-// y(j) -= w, y(r) -= w scale x(r) below.  Rows above j are not touched.
+// H applied to a group in shared or global memory (yg: its rows); rows
+// above j are not touched.  Float32, v = xv: w = tau v^T y over rows
+// j..l-1, y -= w v.  Float64, x = xv: w = tau (y(j) + scale x^T y over rows
+// j+1..l-1), y(j) -= w, y -= (w scale) x below.  Lane 0 updates row j, whose
+// new values do not enter the residual norms.
 template <int UNROLL, typename real>
 __device__ __forceinline__ void update_mem_group(Quad<real>* yg, const real* xv, int l, int j,
-                                                 real tau, real scale, real beta, unsigned act,
+                                                 real tau, real beta, real scale, unsigned act,
                                                  int pc, int lane, int g, LaneBest<real>& best) {
+  constexpr bool RAW = sizeof(real) == 8;
   real d0 = real(0), d1 = real(0), d2 = real(0), d3 = real(0);
 #pragma unroll UNROLL
-  for (int r = j + 1 + lane; r < l; r += 32) {
-    const real x = xv[r];
+  for (int r = j + (RAW ? 1 : 0) + lane; r < l; r += 32) {
+    const real v = xv[r];
     const Quad<real> t = ldq(yg + r);
-    d0 += x * t.x;
-    d1 += x * t.y;
-    d2 += x * t.z;
-    d3 += x * t.w;
+    d0 += v * t.x;
+    d1 += v * t.y;
+    d2 += v * t.z;
+    d3 += v * t.w;
   }
   const int cs = (lane >> 3) & 3;
   const bool on = (act >> cs) & 1u;
-  const real yj = comp(ldq(yg + j), cs);
+  Quad<real> yj;
+  if (RAW) yj = ldq(yg + j);  // every lane, before the shuffles below
   const real dg = reduce4(d0, d1, d2, d3, lane);
-  const real w = on ? tau * (yj + scale * dg) : real(0);
-  const real ws = w * scale;
-  const real s0 = __shfl_sync(0xffffffffu, ws, 0), s1 = __shfl_sync(0xffffffffu, ws, 8);
-  const real s2 = __shfl_sync(0xffffffffu, ws, 16), s3 = __shfl_sync(0xffffffffu, ws, 24);
-  __syncwarp();  // every lane has read row j
-  if ((lane & 7) == 0 && (on || cs == pc))
-    reinterpret_cast<real*>(yg + j)[cs] = cs == pc ? beta : yj - w;
+  const real w = on ? (RAW ? tau * (comp(yj, cs) + scale * dg) : tau * dg) : real(0);
+  const real w0 = __shfl_sync(0xffffffffu, w, 0), w1 = __shfl_sync(0xffffffffu, w, 8);
+  const real w2 = __shfl_sync(0xffffffffu, w, 16), w3 = __shfl_sync(0xffffffffu, w, 24);
+  // every lane's reads of row j are done (they fed the w it shuffled)
+  if (lane == 0) {
+    Quad<real> t = ldq(yg + j);
+    t.x -= w0;
+    t.y -= w1;
+    t.z -= w2;
+    t.w -= w3;
+    stq(yg + j, t);
+  }
+  const real s0 = RAW ? w0 * scale : w0, s1 = RAW ? w1 * scale : w1;
+  const real s2 = RAW ? w2 * scale : w2, s3 = RAW ? w3 * scale : w3;
   real q0 = real(0), q1 = real(0), q2 = real(0), q3 = real(0);
 #pragma unroll UNROLL
   for (int r = j + 1 + lane; r < l; r += 32) {
-    const real x = xv[r];
+    const real v = xv[r];
     Quad<real> t = ldq(yg + r);
-    t.x -= s0 * x;
-    t.y -= s1 * x;
-    t.z -= s2 * x;
-    t.w -= s3 * x;
+    t.x -= s0 * v;
+    t.y -= s1 * v;
+    t.z -= s2 * v;
+    t.w -= s3 * v;
     q0 += t.x * t.x;
     q1 += t.y * t.y;
     q2 += t.z * t.z;
     q3 += t.w * t.w;
-    if (pc >= 0) set_comp(t, pc, real(0));
     stq(yg + r, t);
+  }
+  if (pc >= 0) {
+    // the pivot column: beta at row j, zeros below (its w is zero, so the
+    // passes above left it as it was); each lane rewrites rows it stored
+    real* col = reinterpret_cast<real*>(yg) + pc;
+    if (lane == 0) col[4 * (int64_t)j] = beta;
+    for (int r = j + 1 + lane; r < l; r += 32) col[4 * (int64_t)r] = real(0);
   }
   const real qg = reduce4(q0, q1, q2, q3, lane);
   if (on) best.add(qg, 4 * g + cs);
@@ -361,12 +457,12 @@ __device__ __forceinline__ int cpqr_steps(const CpqrParams<real>& P, Quad<real>*
   constexpr int UN = 4;  // rows in flight per lane in the memory groups' loops
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int l = P.l;
-  const int g0 = first_group(warp);
+  const int g0 = warp - 1;  // the register group, for warps 1..15
   const int cs = (lane >> 3) & 3;
   Quad<real> yr[RR];
 #pragma unroll
   for (int u = 0; u < RR; ++u) yr[u] = Quad<real>{real(0), real(0), real(0), real(0)};
-  const bool has_reg = REGS && g0 < ng;
+  const bool has_reg = REGS && g0 >= 0 && g0 < ng;
   if (has_reg) {
     const int lc = 4 * g0;
 #pragma unroll
@@ -396,7 +492,7 @@ __device__ __forceinline__ int cpqr_steps(const CpqrParams<real>& P, Quad<real>*
     const real qg = reduce4(q0, q1, q2, q3, lane);
     if ((act_of(active, g0) >> cs) & 1u) best.add(qg, 4 * g0 + cs);
   }
-  for (int g = REGS ? g0 + kWarps : g0; g < ng; g += kWarps) {
+  for (int g = first_mem_group<NR>(warp); g < ng; g = next_mem_group<NR>(g)) {
     const real qg = mem_group_norms(group_rows<NR, OV>(P, ys, g), l, lane);
     if ((act_of(active, g) >> cs) & 1u) best.add(qg, 4 * g + cs);
   }
@@ -414,9 +510,8 @@ __device__ __forceinline__ int cpqr_steps(const CpqrParams<real>& P, Quad<real>*
     const int owner = st.owner, pcol = st.col;
     const real nu = st.nu;
     note_rank(P, j, nu, nu_first, k_eff);
-    if (!fetch_pivot<kThreads>(P, j, owner, xv, st)) break;
     real beta, tau, scale;
-    step_reflector(xv, j, nu, st, &beta, &tau, &scale);
+    if (!fetch_v(P, j, owner, nu, xv, st, &beta, &tau, &scale)) break;
     const int pl = pcol - c0;                             // local pivot column
     const int pg = (pl >= 0 && pl < ncl) ? pl >> 2 : -1;  // its group, if here
     best.reset();
@@ -424,21 +519,21 @@ __device__ __forceinline__ int cpqr_steps(const CpqrParams<real>& P, Quad<real>*
       const int pc = pg == g0 ? pl & 3 : -1;
       const unsigned act = act_of(active, g0) & ~(pc >= 0 ? 1u << pc : 0u);
       if (act || pc >= 0)
-        update_reg_group<RR>(yr, xv, l, j, tau, scale, beta, act, pc, lane, g0, best);
+        update_reg_group<RR>(yr, xv, j, tau, beta, act, pc, lane, g0, best);
     }
-    for (int g = REGS ? g0 + kWarps : g0; g < ng; g += kWarps) {
+    for (int g = first_mem_group<NR>(warp); g < ng; g = next_mem_group<NR>(g)) {
       const int pc = pg == g ? pl & 3 : -1;
       const unsigned act = act_of(active, g) & ~(pc >= 0 ? 1u << pc : 0u);
       if (!act && pc < 0) continue;
       const int s = g - NR;
       if (!OV || s < P.ncs)
-        update_mem_group<UN>(ys + (int64_t)s * l, xv, l, j, tau, scale, beta, act, pc, lane, g,
+        update_mem_group<UN>(ys + (int64_t)s * l, xv, l, j, tau, beta, scale, act, pc, lane, g,
                              best);
       else
-        update_mem_group<UN>(group_rows<NR, true>(P, ys, g), xv, l, j, tau, scale, beta, act, pc,
+        update_mem_group<UN>(group_rows<NR, true>(P, ys, g), xv, l, j, tau, beta, scale, act, pc,
                              lane, g, best);
     }
-    if (pg >= 0 && group_owner(pg) == warp && lane == 0) {
+    if (pg >= 0 && group_owner<NR>(pg) == warp && lane == 0) {
       active[pl] = 0;
       P.J[j] = pcol;
     }
@@ -473,7 +568,8 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
   const int nc = P.nc, l = P.l;
   Quad<real>* ys = reinterpret_cast<Quad<real>*>(smem_raw);  // P.ncs groups of l rows
   real* xv = reinterpret_cast<real*>(ys + (int64_t)P.ncs * l);  // pivot column of the step
-  int* active = reinterpret_cast<int*>(xv + P.ldl);             // nc flags (P.ldl: l rounded up to 4)
+  int* active = reinterpret_cast<int*>(xv + P.ldl);             // nc flags
+  // (P.ldl: l rounded up to 4, at least the rows of the register groups)
 
   __shared__ StepState<real> st;
   __shared__ WarpBest<real> wb;
@@ -483,6 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1) cpqr_kernel(CpqrParams<real> P) {
   const int ng = (ncl + 3) >> 2;  // groups holding this CTA's columns
 
   for (int lc = tid; lc < nc; lc += kThreads) active[lc] = lc < ncl ? 1 : 0;
+  for (int r = tid; r < P.ldl; r += kThreads) xv[r] = real(0);
   // groups in memory, read along the rows of Y; the columns past ncl of the
   // last group are zero
   const int cm0 = min(4 * ng, 4 * NR), ncm = 4 * ng - cm0;
@@ -519,11 +616,16 @@ struct Layout {
   size_t smem = 0;
 };
 
+// rows of the step's Householder vector in shared memory: l rounded up to a
+// multiple of 4, at least the rows of the register groups
+inline int64_t grouped_v_rows(int64_t l, int rpl) {
+  return std::max<int64_t>((l + 3) & ~int64_t(3), 32 * (int64_t)rpl);
+}
+
 template <typename real>
-size_t grouped_smem_bytes(int ncs, int nc, int64_t l) {
-  const int64_t xl = (l + 3) & ~int64_t(3);
-  return (size_t)ncs * l * 4 * sizeof(real) + (size_t)xl * sizeof(real) + (size_t)nc * sizeof(int) +
-         64;
+size_t grouped_smem_bytes(int ncs, int nc, int64_t l, int rpl) {
+  return (size_t)ncs * l * 4 * sizeof(real) + (size_t)grouped_v_rows(l, rpl) * sizeof(real) +
+         (size_t)nc * sizeof(int) + 64;
 }
 
 // Grid, columns per CTA and kernel of an l x n factorization.
@@ -571,12 +673,12 @@ curid_status cpqr_layout(const Ctx& ctx, int64_t l, int64_t n, Layout* L) {
   const int nr = L->rpl > 0 ? kWarps - 1 : 0;
   const int rest = std::max(0, nc / 4 - nr);
   // the kernel's static shared variables share the per-block limit
-  const size_t fixed = grouped_smem_bytes<real>(0, nc, l) + 1024;
+  const size_t fixed = grouped_smem_bytes<real>(0, nc, l, L->rpl) + 1024;
   if (fixed > ctx.smem_optin) return CURID_UNSUPPORTED;
   L->ncs = (int)std::min<size_t>(rest, (ctx.smem_optin - fixed) / ((size_t)l * 4 * sizeof(real)));
   L->ngo = rest - L->ncs;
-  L->ldl = (int)((l + 3) & ~int64_t(3));
-  L->smem = grouped_smem_bytes<real>(L->ncs, nc, l);
+  L->ldl = (int)grouped_v_rows(l, L->rpl);
+  L->smem = grouped_smem_bytes<real>(L->ncs, nc, l, L->rpl);
   return CURID_OK;
 }
 
