@@ -84,7 +84,7 @@ struct Plan {
   real* B[3] = {nullptr, nullptr, nullptr};  // sample-matrix buffers, l x max(m, n)
   real* G = nullptr;      // l x l  (Gram)
   real* Linv = nullptr;   // l x l
-  real* Li = nullptr;     // 2 x l x pad4(l) (l <= 256, tensor-core orth)
+  real* Li = nullptr;     // 2 x l x pad4(l) (tensor-core orth apply)
   // column CPQR and T
   CpqrScratch cs{};
   real* S = nullptr;      // k x n
@@ -182,10 +182,11 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
       if (sizeof(real) == 4 && (d.tf32 || d.bf16) && !d.sp)
         part = std::max(part, gemm_tf32_partial_elems(std::min<int64_t>(l, 256), l,
                                                       std::max(m, n), ctx.num_sms));
-      if (sizeof(real) == 4 && (d.tf32 || d.bf16) && !d.sp && l <= 256) {
-        // L^{-1} split for the tensor-core apply of the small-sample orth
+      if (sizeof(real) == 4 && (d.tf32 || d.bf16) && !d.sp) {
+        // L^{-1} split for the tensor-core apply of the orth
         P->Li = cv.take<real>(2 * (size_t)l * pad4(l));
-        part = std::max(part, gemm_tf32_partial_elems(l, std::max(m, n), l, ctx.num_sms));
+        part = std::max(part, gemm_tf32_partial_elems(std::min<int64_t>(l, 256), std::max(m, n),
+                                                      l, ctx.num_sms));
       }
       upd(l, l, n);
       upd(l, l, m);
@@ -307,14 +308,15 @@ curid_status a_product(const Ctx& ctx, bool tf32, bool bf16, bool tb, int64_t M,
 // whose Q forms the Y that is pivoted, takes all three.
 //
 // With tensor-core products (TF32, or BF16 storage of A) and samples of more
-// than 256 rows the Gram matrices go to the TF32 tensor cores too, at
-// float32 accuracy (gram_tf32), with `spare` (a free sample buffer) for the
-// TF32 part and Linv as scratch: l = 520 rows of 20000, orth 13 -> 10 ms
-// per decomposition.  Samples of up to 256 rows go to the tensor cores as a
-// whole (Gram and the apply X <- L^{-1} X through an explicit L^{-1}) when
-// several decompositions are in flight, where the SIMT products' SM time is
-// what limits throughput; one at a time they keep the SIMT Gram and the
-// triangular solve.  CURID_ORTH_TC=1 / 0 in the environment forces either
+// than 256 rows the orth runs on the TF32 tensor cores at float32 accuracy:
+// the Gram matrices (gram_tf32, with `spare`, a free sample buffer, for the
+// TF32 part and Linv as scratch) and the apply X <- L^{-1} X through an
+// explicit L^{-1} split into its TF32 part and remainder (l = 520 rows of
+// 20000: orth 13 -> 10 ms per decomposition with the Gram alone).  Samples
+// of up to 256 rows go to the tensor cores when several decompositions are
+// in flight, where the SIMT products' SM time is what limits throughput;
+// one at a time they keep the SIMT Gram and the triangular solve.
+// CURID_ORTH_TC=1 / 0 in the environment forces either for small samples
 // (for comparisons).
 template <typename real>
 curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
@@ -328,7 +330,7 @@ curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t 
   const bool use_tc = tc_ok && (r > 256 || small_tc);
   return chol_qr_rows<real>(ctx, X, tmp, r, c, ld, P.G, P.partial, P.partial_cap,
                             final_orth ? 3 : 2, use_tc ? spare : nullptr,
-                            use_tc ? P.Linv : nullptr, small_tc ? P.Li : nullptr);
+                            use_tc ? P.Linv : nullptr, use_tc ? P.Li : nullptr);
 }
 
 // Sample matrix of Algorithm 4 with the power scheme of Section 5.3:

@@ -528,21 +528,28 @@ curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64
     CURID_TRY(cholesky<real>(ctx, G, (int)r, pass == 0 ? shift : 0.0));
     bool applied = false;
     if constexpr (sizeof(real) == 4) {
-      if (tc && li && r <= 256) {
+      if (tc && li) {
         // X <- L^{-1} X as tensor-core products: L^{-1} explicitly (a
         // triangular solve with the identity), split into its TF32 part and
         // remainder; each product splits X inside, so the sum carries
-        // float32 accuracy.
+        // float32 accuracy.  The products take at most 256 rows of L^{-1}
+        // at a time (the MMA's N); rows r0..r0+mr-1 of a lower triangular
+        // L^{-1} need only the first r0 + mr rows of X.
         const int64_t ldp = (r + 3) & ~int64_t(3);  // 16-byte rows for the tensor-core loads
         float* lhi = li;
         float* llo = li + r * ldp;
         CURID_TRY(tri_solve<float>(ctx, (int)r, G, r, false, false, nullptr, 0, lhi, ldp, r,
                                    nullptr));
         CURID_TRY(split_tf32(ctx, lhi, ldp, lhi, ldp, llo, ldp, r, r));
-        CURID_TRY(gemm_tf32(ctx, false, false, r, c, r, lhi, ldp, *X, ld, *tmp, ld, partial,
-                            partial_cap));
-        CURID_TRY(gemm_tf32(ctx, false, false, r, c, r, llo, ldp, *X, ld, xh, ld, partial,
-                            partial_cap));
+        const int64_t chunks = (r + 255) / 256;
+        const int64_t rows = ((r + chunks - 1) / chunks + 15) / 16 * 16;
+        for (int64_t r0 = 0; r0 < r; r0 += rows) {
+          const int64_t mr = std::min(rows, r - r0), kk = r0 + mr;
+          CURID_TRY(gemm_tf32(ctx, false, false, mr, c, kk, lhi + r0 * ldp, ldp, *X, ld,
+                              *tmp + r0 * ld, ld, partial, partial_cap));
+          CURID_TRY(gemm_tf32(ctx, false, false, mr, c, kk, llo + r0 * ldp, ldp, *X, ld,
+                              xh + r0 * ld, ld, partial, partial_cap));
+        }
         CURID_TRY(add2d<float>(ctx, xh, ld, *tmp, ld, r, c));
         applied = true;
       }

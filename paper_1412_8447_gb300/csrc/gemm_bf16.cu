@@ -12,12 +12,15 @@
 //
 // Tiling as in the TF32 kernel: D = C^T, the MMA's M = 128 output columns of
 // C, its N = a chunk of the sample's rows (<= 256; l > 256 is cut into
-// equal chunks, one per grid row, since a 128-lane accumulator holds at most
-// 512 FP32 columns of TMEM).  Operands are K-major with the 128-byte swizzle:
-// for C = X A^T the rows of A are K-major already and come by TMA; for
-// C = X A the TMA brings MN-major 64 x 64 boxes and four converter warps
-// transpose them.  Warp 0 issues TMA, warp 1 the MMAs, warps 4-7 convert
-// and run the epilogue.  Every mbarrier wait is bounded.
+// equal chunks, since a 128-lane accumulator holds at most 512 FP32 columns
+// of TMEM).  The chunks of one column tile are neighbouring CTAs (the chunk
+// is the grid's fastest index), so they stream the same A tiles at the same
+// time and A comes from HBM about once.  Operands use the 128-byte swizzle:
+// for C = X A^T the rows of A are K-major and come by TMA as they are; for
+// C = X A the TMA brings MN-major 64 x 64 boxes and the MMA reads them as an
+// MN-major operand (kind::f16 allows either major-ness for 16-bit types), so
+// no thread touches A.  Warp 0 issues TMA, warp 1 the MMAs, warps 4-7 run
+// the epilogue.  Every mbarrier wait is bounded.
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -47,12 +50,10 @@ struct Bf16Params {
   uint32_t idesc;
 };
 
-size_t bf16_stage_bytes(int chunk, bool mn) {
-  return (size_t)kATile * (mn ? 2 : 1) + 2 * (size_t)chunk * 128;
-}
+size_t bf16_stage_bytes(int chunk) { return (size_t)kATile + 2 * (size_t)chunk * 128; }
 
-size_t bf16_smem(int chunk, bool mn, int stages) {
-  return 1024 + (size_t)stages * bf16_stage_bytes(chunk, mn) + (3 * kMaxStages + 1) * 8 + 16;
+size_t bf16_smem(int chunk, int stages) {
+  return 1024 + (size_t)stages * bf16_stage_bytes(chunk) + (2 * kMaxStages + 1) * 8 + 16;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -63,37 +64,32 @@ tc_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const bool mn = P.mn_major != 0;
   const int S = P.stages;
   const uint32_t xbytes = (uint32_t)P.chunk * 128u;
-  unsigned char* Ak[kMaxStages];
-  unsigned char* Ar[kMaxStages];
+  unsigned char* Ak[kMaxStages];  // A tile: K-major 128 rows, or two MN-major 64 x 64 boxes
   unsigned char* Xh[kMaxStages];
   unsigned char* Xl[kMaxStages];
   unsigned char* p = reinterpret_cast<unsigned char*>(base);
   for (int s = 0; s < S; ++s) {
     Ak[s] = p;
     p += kATile;
-    Ar[s] = p;
-    if (mn) p += kATile;
     Xh[s] = p;
     Xl[s] = p + xbytes;
     p += 2 * xbytes;
   }
-  uint64_t* bars = reinterpret_cast<uint64_t*>(p);  // full[S], conv[S], empty[S], acc
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kMaxStages + 1);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(p);  // full[S], empty[S], acc
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kMaxStages + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto full = [&](int s) { return smem_u32(bars + s); };
-  auto conv = [&](int s) { return smem_u32(bars + kMaxStages + s); };
-  auto empty = [&](int s) { return smem_u32(bars + 2 * kMaxStages + s); };
-  const uint32_t acc_bar = smem_u32(bars + 3 * kMaxStages);
+  auto empty = [&](int s) { return smem_u32(bars + kMaxStages + s); };
+  const uint32_t acc_bar = smem_u32(bars + 2 * kMaxStages);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * kBM;
-  const int row0 = blockIdx.y * P.chunk;
+  const int row0 = blockIdx.x * P.chunk;  // chunk fastest: a column tile's chunks run together
+  const int n0 = blockIdx.y * kBM;
   const int nk = (P.K + kBK - 1) / kBK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(full(s), 1);
-      mbar_init(conv(s), 128);
       mbar_init(empty(s), 1);
     }
     mbar_init(acc_bar, 1);
@@ -131,8 +127,8 @@ tc_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       mbar_expect_tx(full(s), (uint32_t)kATile + 2 * xbytes);
       const int k = i * kBK;
       if (mn) {
-        tma_load_2d(smem_u32(Ar[s]), &tmA, n0, k, full(s));
-        tma_load_2d(smem_u32(Ar[s] + kATile / 2), &tmA, n0 + 64, k, full(s));
+        tma_load_2d(smem_u32(Ak[s]), &tmA, n0, k, full(s));
+        tma_load_2d(smem_u32(Ak[s] + kATile / 2), &tmA, n0 + 64, k, full(s));
       } else {
         tma_load_2d(smem_u32(Ak[s]), &tmA, k, n0, full(s));
       }
@@ -149,7 +145,7 @@ tc_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     for (int i = 0; i < nk; ++i) {
       const int s = i % S;
       const uint32_t ph = (uint32_t)(i / S) & 1u;
-      if (!mbar_wait(mn ? conv(s) : full(s), ph) || *abort_flag) {
+      if (!mbar_wait(full(s), ph) || *abort_flag) {
         *abort_flag = 1;
         atomicCAS(&P.status->timeout_site, 0, (6 << 24) | (s << 16) | i);
         break;
@@ -158,7 +154,11 @@ tc_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const uint32_t a = smem_u32(Ak[s]), xh = smem_u32(Xh[s]), xl = smem_u32(Xl[s]);
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk) {
-        const uint64_t da = smem_desc(a + kk * 32, 16, 1024);
+        // K-major: 16 K values are 32 bytes along each 128-byte row; MN-major:
+        // two 8-row K groups (1024 bytes apart, the stride byte offset), the
+        // second 64 columns 8 KB on (the leading byte offset)
+        const uint64_t da = mn ? smem_desc(a + kk * 2048, kATile / 2, 1024)
+                               : smem_desc(a + kk * 32, 16, 1024);
         const uint64_t dh = smem_desc(xh + kk * 32, 16, 1024);
         const uint64_t dl = smem_desc(xl + kk * 32, 16, 1024);
         mma_f16(tmem, da, dh, P.idesc, (i > 0 || kk > 0) ? 1u : 0u);
@@ -168,41 +168,6 @@ tc_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
     mma_commit(acc_bar);
   } else if (warp >= 4) {
-    const int t = threadIdx.x - 128;
-    if (mn) {
-      // ---- transpose the MN-major boxes into the K-major tile ----
-      // box j = t / 64 holds columns 64j..64j+63 as 64 K rows of 128 bytes
-      // (16-byte chunks swizzled by the row); thread t gathers column t over
-      // the 64 K values and writes row t of the K-major tile.
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % S;
-        const uint32_t ph = (uint32_t)(i / S) & 1u;
-        if (!mbar_wait(full(s), ph) || *abort_flag) {
-          *abort_flag = 1;
-          atomicCAS(&P.status->timeout_site, 0, (7 << 24) | (s << 16) | i);
-          break;
-        }
-        const unsigned char* raw = Ar[s] + (t >> 6) * (kATile / 2);
-        const int c = t & 63;
-        uint32_t w[32];
-#pragma unroll
-        for (int k = 0; k < kBK; k += 2) {
-          const int o0 = k * 128 + ((((c >> 3) ^ (k & 7))) << 4) + ((c & 7) << 1);
-          const int o1 = (k + 1) * 128 + ((((c >> 3) ^ ((k + 1) & 7))) << 4) + ((c & 7) << 1);
-          const uint32_t lo = *reinterpret_cast<const unsigned short*>(raw + o0);
-          const uint32_t hi = *reinterpret_cast<const unsigned short*>(raw + o1);
-          w[k >> 1] = lo | (hi << 16);
-        }
-#pragma unroll
-        for (int cc = 0; cc < 8; ++cc) {
-          const int off = t * 128 + ((cc ^ (t & 7)) << 4);
-          *reinterpret_cast<uint4*>(Ak[s] + off) =
-              make_uint4(w[4 * cc], w[4 * cc + 1], w[4 * cc + 2], w[4 * cc + 3]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(conv(s));
-      }
-    }
     // ---- epilogue: TMEM -> registers -> C ----
     int ok = 0;
     if (lane == 0) {
@@ -319,7 +284,7 @@ curid_status gemm_bf16(const Ctx& ctx, bool tb, int64_t M, int64_t N, int64_t K,
       !make_map_bf16(&mapL, lo, (uint64_t)kpad, (uint64_t)rows_pad, kpad, (uint32_t)chunk))
     return CURID_CUDA_ERROR;
   int stages = kMaxStages;
-  while (stages > 1 && bf16_smem(chunk, mn, stages) > ctx.smem_optin) --stages;
+  while (stages > 1 && bf16_smem(chunk, stages) > ctx.smem_optin) --stages;
   if (stages < 2) return CURID_UNSUPPORTED;
   Bf16Params P;
   P.M = (int)M;
@@ -331,14 +296,14 @@ curid_status gemm_bf16(const Ctx& ctx, bool tb, int64_t M, int64_t N, int64_t K,
   P.C = C;
   P.ldc = ldc;
   P.status = ctx.status;
-  // instruction descriptor (kind::f16): FP32 accumulator, BF16 A and B, both
-  // K-major, N >> 3, M >> 4
-  P.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(chunk >> 3) << 17) |
-            ((uint32_t)(kBM >> 4) << 24);
-  const size_t smem = bf16_smem(chunk, mn, stages);
+  // instruction descriptor (kind::f16): FP32 accumulator, BF16 A and B, A
+  // MN-major (bit 15) for C = X A else K-major, B K-major, N >> 3, M >> 4
+  P.idesc = (1u << 4) | (1u << 7) | (1u << 10) | (mn ? 1u << 15 : 0u) |
+            ((uint32_t)(chunk >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+  const size_t smem = bf16_smem(chunk, stages);
   CURID_CUDA(cudaFuncSetAttribute(tc_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-  dim3 grid((unsigned)((N + kBM - 1) / kBM), (unsigned)nch);
+  dim3 grid((unsigned)nch, (unsigned)((N + kBM - 1) / kBM));
   tc_bf16_kernel<<<grid, kThreads, smem, ctx.stream>>>(mapA, mapH, mapL, P);
   CURID_LAUNCHED(ctx);
   return CURID_OK;
