@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--p", type=int, default=P)
     ap.add_argument("--q", type=int, default=Q)
     ap.add_argument("--tf32", type=int, default=1)
-    ap.add_argument("--inflight", type=int, default=4,
+    ap.add_argument("--inflight", type=int, default=8,
                     help="decompositions in flight (one stream and workspace each)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -44,7 +44,13 @@ __global__ void extract_pivots_kernel(const int32_t* __restrict__ Jp, int k, int
                                       int32_t* __restrict__ J, StatusBlock* status,
                                       bool halve_ranks) {
   if (halve_ranks && blockIdx.x == 0 && threadIdx.x == 0) {
-    // the status block's ranks count real steps: two per complex pivot
+    // the status block's ranks count real steps: two per complex pivot.  The
+    // embedding's rank is even in exact arithmetic; an odd count means the
+    // rank cut-off or the tolerance stop fell between the two members of a
+    // pair (one fell below the threshold within rounding of the other): the
+    // complex rank is rounded down and flagged.
+    if ((status->k_eff | status->k_row) & 1) set_flag(&status->flags, FLAG_RANK_DEFICIENT);
+    if (status->k_done & 1) set_flag(&status->flags, FLAG_BREAKDOWN);
     status->k_done >>= 1;
     status->k_eff >>= 1;
     status->k_row >>= 1;

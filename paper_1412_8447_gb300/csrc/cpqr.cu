@@ -57,12 +57,16 @@ namespace {
 using namespace cpqr_x;
 
 // Rows per lane of the register-resident groups (float32 only: four columns
-// of 17 rows are 68 registers): matrices of up to 544 rows.
+// of 17 rows are 68 registers): matrices of up to 544 rows; up to 224 rows
+// take 7 rows per lane, so no register row block lies past the matrix.
 constexpr int kGroupRegRows = 17;
+constexpr int kGroupRegRowsShort = 7;
 
 template <typename real>
 constexpr int group_reg_rows(int64_t l) {
-  return (sizeof(real) == 4 && l <= 32 * kGroupRegRows) ? kGroupRegRows : 0;
+  if (sizeof(real) != 4) return 0;
+  if (l <= 32 * kGroupRegRowsShort) return kGroupRegRowsShort;
+  return l <= 32 * kGroupRegRows ? kGroupRegRows : 0;
 }
 
 // Four neighbouring columns of one row.
@@ -125,10 +129,12 @@ __device__ __forceinline__ Quad<real>* group_rows(const CpqrParams<real>& P, Qua
 
 // A lane's running best over the columns it sees: after reduce4 the lanes of
 // one eighth of the warp hold the same column, so the warp's best is merged
-// over the lanes 8 and 16 apart only.
+// over the lanes 8 and 16 apart only.  Columns are compared by their squared
+// residual norms (the same order); the square root is taken once, for the
+// CTA's record.
 template <typename real>
 struct LaneBest {
-  real bn, ss;
+  real bn, ss;  // best squared norm, sum of squared norms
   int bi, nf;
   __device__ __forceinline__ void reset() {
     bn = real(-1);
@@ -138,11 +144,10 @@ struct LaneBest {
   }
   // an unselected local column lc with squared residual norm q2
   __device__ __forceinline__ void add(real q2, int lc) {
-    const real nv = sqrt(q2);
     ss += q2;
-    if (!isfinite(nv)) nf = 1;
-    else if (local_better(nv, lc, bn, bi)) {
-      bn = nv;
+    if (!isfinite(q2)) nf = 1;
+    else if (local_better(q2, lc, bn, bi)) {
+      bn = q2;
       bi = lc;
     }
   }
@@ -193,9 +198,10 @@ __device__ __forceinline__ int next_mem_group(int g) {
   return (NR > 0 && g == NR) ? NR + 1 : g + kWarps;
 }
 
-// Every warp, after the barrier that follows post_best: the CTA's candidate
-// for epoch `epoch`.  Warp 0 publishes the record in buffer bf; the warp that
-// owns the candidate's group copies its rows r0..l-1 to the CTA's data slot
+// Every warp, after the barrier that follows post_best (wb holds squared
+// norms): the CTA's candidate for epoch `epoch`.  Warp 0 publishes the
+// record in buffer bf; the warp that owns the candidate's group copies its
+// rows r0..l-1 to the CTA's data slot
 // as tagged words, from its registers or from the group's rows (readers check
 // every word's tag, so the two writes need no order between them).
 template <int RPL, bool REGS, int NR, bool OV, typename real>
@@ -227,7 +233,7 @@ __device__ __forceinline__ void publish(const CpqrParams<real>& P, Quad<real>* y
     for (int o = 1; o < kWarps; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if (lane == 0) {
       unsigned hi, lo;
-      norm_words<real>(bi >= 0 ? bn : real(0), &hi, &lo);
+      norm_words<real>(bi >= 0 ? sqrt(bn) : real(0), &hi, &lo);
       const unsigned col = nf ? kNonFinite : (bi >= 0 ? (unsigned)(c0 + bi) : kNoCol);
       st_rec(P.recs + (size_t)bf * gridDim.x + blockIdx.x, pack(tag, col), pack(tag, hi),
              pack(tag, lo), pack(tag, __float_as_uint((float)ss)));
@@ -428,6 +434,137 @@ __device__ __forceinline__ void update_mem_group(Quad<real>* yg, const real* xv,
   if (on) best.add(qg, 4 * g + cs);
 }
 
+// For short columns (the 7-row register groups) a group's fixed costs -- two
+// shuffle reductions, the w broadcast, the best-column bookkeeping -- outweigh
+// its row work, so the update is split in two halves and a warp runs its
+// memory groups two at a time (their reductions overlap):
+//   dots:  lane-partial sums of v^T y for the four columns;
+//   apply: y -= w v with the w of the four columns, lane-partial squared
+//          norms of rows j+1..l-1, and the pivot column retired (beta at row
+//          j, zeros below; its w is zero, so the update leaves it as it was).
+// Register groups hold rows lane + 32 u; v = xv is zero above row j and past
+// l, so they need no row mask but the norms' (Section 2.2's residual norms
+// over rows j+1..l-1).  Groups in shared or global memory (yg: their rows)
+// are not touched above row j.  Float32: xv holds v, w = tau v^T y over rows
+// j..l-1.  Float64: xv holds the pivot column x, w = tau (y(j) + scale x^T y
+// over rows j+1..l-1), y(j) -= w and y -= (w scale) x below.
+
+template <int RPL, typename real>
+__device__ __forceinline__ void reg_dots(const Quad<real> (&y)[RPL], const real* xv, int lane,
+                                         real (&d)[4]) {
+  d[0] = d[1] = d[2] = d[3] = real(0);
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    const real v = xv[lane + 32 * u];
+    d[0] += v * y[u].x;
+    d[1] += v * y[u].y;
+    d[2] += v * y[u].z;
+    d[3] += v * y[u].w;
+  }
+}
+
+template <int RPL, typename real>
+__device__ __forceinline__ void reg_apply(Quad<real> (&y)[RPL], const real* xv, int j,
+                                          const real (&w)[4], int pc, real beta, int lane,
+                                          real (&q)[4]) {
+  q[0] = q[1] = q[2] = q[3] = real(0);
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    const int r = lane + 32 * u;
+    const real v = xv[r];
+    y[u].x -= w[0] * v;
+    y[u].y -= w[1] * v;
+    y[u].z -= w[2] * v;
+    y[u].w -= w[3] * v;
+    if (r > j) {
+      q[0] += y[u].x * y[u].x;
+      q[1] += y[u].y * y[u].y;
+      q[2] += y[u].z * y[u].z;
+      q[3] += y[u].w * y[u].w;
+    }
+  }
+  if (pc >= 0) {
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) {
+      if (32 * u + 31 < j) continue;
+      const int r = lane + 32 * u;
+      if (r >= j) set_comp(y[u], pc, r == j ? beta : real(0));
+    }
+  }
+}
+
+template <int UNROLL, typename real>
+__device__ __forceinline__ void mem_dots(const Quad<real>* yg, const real* xv, int l, int j,
+                                         int lane, real (&d)[4]) {
+  constexpr bool RAW = sizeof(real) == 8;
+  d[0] = d[1] = d[2] = d[3] = real(0);
+#pragma unroll UNROLL
+  for (int r = j + (RAW ? 1 : 0) + lane; r < l; r += 32) {
+    const real v = xv[r];
+    const Quad<real> t = ldq(yg + r);
+    d[0] += v * t.x;
+    d[1] += v * t.y;
+    d[2] += v * t.z;
+    d[3] += v * t.w;
+  }
+}
+
+// w of the lane's column cs from its reduced dot product dg (zero unless on)
+template <typename real>
+__device__ __forceinline__ real mem_w(const Quad<real>* yg, int j, real dg, real tau, real scale,
+                                      bool on, int cs) {
+  if constexpr (sizeof(real) == 8) return on ? tau * (comp(ldq(yg + j), cs) + scale * dg) : real(0);
+  return on ? tau * dg : real(0);
+}
+
+template <int UNROLL, typename real>
+__device__ __forceinline__ void mem_apply(Quad<real>* yg, const real* xv, int l, int j,
+                                          const real (&w)[4], real scale, int pc, real beta,
+                                          int lane, real (&q)[4]) {
+  constexpr bool RAW = sizeof(real) == 8;
+  // every lane's reads of row j are done (they fed the w it shuffled)
+  if (lane == 0) {
+    Quad<real> t = ldq(yg + j);
+    t.x -= w[0];
+    t.y -= w[1];
+    t.z -= w[2];
+    t.w -= w[3];
+    stq(yg + j, t);
+  }
+  const real s0 = RAW ? w[0] * scale : w[0], s1 = RAW ? w[1] * scale : w[1];
+  const real s2 = RAW ? w[2] * scale : w[2], s3 = RAW ? w[3] * scale : w[3];
+  q[0] = q[1] = q[2] = q[3] = real(0);
+#pragma unroll UNROLL
+  for (int r = j + 1 + lane; r < l; r += 32) {
+    const real v = xv[r];
+    Quad<real> t = ldq(yg + r);
+    t.x -= s0 * v;
+    t.y -= s1 * v;
+    t.z -= s2 * v;
+    t.w -= s3 * v;
+    q[0] += t.x * t.x;
+    q[1] += t.y * t.y;
+    q[2] += t.z * t.z;
+    q[3] += t.w * t.w;
+    stq(yg + r, t);
+  }
+  if (pc >= 0) {
+    // each lane rewrites rows it stored
+    real* col = reinterpret_cast<real*>(yg) + pc;
+    if (lane == 0) col[4 * (int64_t)j] = beta;
+    for (int r = j + 1 + lane; r < l; r += 32) col[4 * (int64_t)r] = real(0);
+  }
+}
+
+// The four columns' values of lane 8 c (c = 0..3) to every lane.
+template <typename real>
+__device__ __forceinline__ void bcast4(real x, real (&w)[4]) {
+  w[0] = __shfl_sync(0xffffffffu, x, 0);
+  w[1] = __shfl_sync(0xffffffffu, x, 8);
+  w[2] = __shfl_sync(0xffffffffu, x, 16);
+  w[3] = __shfl_sync(0xffffffffu, x, 24);
+}
+
 // Squared norms of the columns of a group in memory, all rows.
 template <typename real>
 __device__ __forceinline__ real mem_group_norms(const Quad<real>* yg, int l, int lane) {
@@ -515,23 +652,73 @@ __device__ __forceinline__ int cpqr_steps(const CpqrParams<real>& P, Quad<real>*
     const int pl = pcol - c0;                             // local pivot column
     const int pg = (pl >= 0 && pl < ncl) ? pl >> 2 : -1;  // its group, if here
     best.reset();
-    if (has_reg) {
-      const int pc = pg == g0 ? pl & 3 : -1;
-      const unsigned act = act_of(active, g0) & ~(pc >= 0 ? 1u << pc : 0u);
-      if (act || pc >= 0)
-        update_reg_group<RR>(yr, xv, j, tau, beta, act, pc, lane, g0, best);
-    }
-    for (int g = first_mem_group<NR>(warp); g < ng; g = next_mem_group<NR>(g)) {
-      const int pc = pg == g ? pl & 3 : -1;
-      const unsigned act = act_of(active, g) & ~(pc >= 0 ? 1u << pc : 0u);
-      if (!act && pc < 0) continue;
-      const int s = g - NR;
-      if (!OV || s < P.ncs)
-        update_mem_group<UN>(ys + (int64_t)s * l, xv, l, j, tau, beta, scale, act, pc, lane, g,
-                             best);
-      else
-        update_mem_group<UN>(group_rows<NR, true>(P, ys, g), xv, l, j, tau, beta, scale, act, pc,
-                             lane, g, best);
+    if constexpr (RPL != kGroupRegRowsShort) {
+      if (has_reg) {
+        const int pc = pg == g0 ? pl & 3 : -1;
+        const unsigned act = act_of(active, g0) & ~(pc >= 0 ? 1u << pc : 0u);
+        if (act || pc >= 0)
+          update_reg_group<RR>(yr, xv, j, tau, beta, act, pc, lane, g0, best);
+      }
+      for (int g = first_mem_group<NR>(warp); g < ng; g = next_mem_group<NR>(g)) {
+        const int pc = pg == g ? pl & 3 : -1;
+        const unsigned act = act_of(active, g) & ~(pc >= 0 ? 1u << pc : 0u);
+        if (!act && pc < 0) continue;
+        const int s = g - NR;
+        if (!OV || s < P.ncs)
+          update_mem_group<UN>(ys + (int64_t)s * l, xv, l, j, tau, beta, scale, act, pc, lane, g,
+                               best);
+        else
+          update_mem_group<UN>(group_rows<NR, true>(P, ys, g), xv, l, j, tau, beta, scale, act, pc,
+                               lane, g, best);
+      }
+    } else {
+      // the register group, then the memory groups two by two: each pair's
+      // dots, their reductions, the w's, the updates, the norms' reductions
+      // (retired columns get w = 0)
+      int g = first_mem_group<NR>(warp);
+      auto mem_rows = [&](int gg) -> Quad<real>* {
+        const int s = gg - NR;
+        return (!OV || s < P.ncs) ? ys + (int64_t)s * l : group_rows<NR, true>(P, ys, gg);
+      };
+      auto pivot_in = [&](int gg) { return pg == gg ? pl & 3 : -1; };
+      auto act_in = [&](int gg, int pc) {
+        return act_of(active, gg) & ~(pc >= 0 ? 1u << pc : 0u);
+      };
+      if (has_reg) {
+        const int pcA = pivot_in(g0);
+        const bool onA = (act_in(g0, pcA) >> cs) & 1u;
+        real dA[4], wA[4];
+        reg_dots<RR>(yr, xv, lane, dA);
+        const real rA = reduce4(dA[0], dA[1], dA[2], dA[3], lane);
+        bcast4(onA ? tau * rA : real(0), wA);
+        reg_apply<RR>(yr, xv, j, wA, pcA, beta, lane, dA);
+        const real qA = reduce4(dA[0], dA[1], dA[2], dA[3], lane);
+        if (onA) best.add(qA, 4 * g0 + cs);
+      }
+      while (g < ng) {
+        const int g2 = next_mem_group<NR>(g);
+        const bool B = g2 < ng;
+        Quad<real>* yA = mem_rows(g);
+        Quad<real>* yB = B ? mem_rows(g2) : yA;
+        const int pcA = pivot_in(g), pcB = B ? pivot_in(g2) : -1;
+        const bool onA = (act_in(g, pcA) >> cs) & 1u;
+        const bool onB = B && ((act_in(g2, pcB) >> cs) & 1u);
+        real dA[4], dB[4];
+        mem_dots<UN>(yA, xv, l, j, lane, dA);
+        if (B) mem_dots<UN>(yB, xv, l, j, lane, dB);
+        const real rA = reduce4(dA[0], dA[1], dA[2], dA[3], lane);
+        const real rB = B ? reduce4(dB[0], dB[1], dB[2], dB[3], lane) : real(0);
+        real wA[4], wB[4];
+        bcast4(mem_w(yA, j, rA, tau, scale, onA, cs), wA);
+        if (B) bcast4(mem_w(yB, j, rB, tau, scale, onB, cs), wB);
+        mem_apply<UN>(yA, xv, l, j, wA, scale, pcA, beta, lane, dA);
+        if (B) mem_apply<UN>(yB, xv, l, j, wB, scale, pcB, beta, lane, dB);
+        const real qA = reduce4(dA[0], dA[1], dA[2], dA[3], lane);
+        const real qB = B ? reduce4(dB[0], dB[1], dB[2], dB[3], lane) : real(0);
+        if (onA) best.add(qA, 4 * g + cs);
+        if (onB) best.add(qB, 4 * g2 + cs);
+        g = B ? next_mem_group<NR>(g2) : g2;
+      }
     }
     if (pg >= 0 && group_owner<NR>(pg) == warp && lane == 0) {
       active[pl] = 0;
@@ -631,17 +818,23 @@ size_t grouped_smem_bytes(int ncs, int nc, int64_t l, int rpl) {
 // Grid, columns per CTA and kernel of an l x n factorization.
 //
 // One decomposition at a time (the handle's concurrency 1): one CTA per SM,
-// the lowest latency per factorization.  With several in flight: the fewest
-// CTAs whose registers hold the matrix (eight columns per warp).  The pivot
-// exchange gets cheaper with fewer CTAs (records of 38-64 CTAs meet in about
-// 2.4K cycles on GB300, of 152 in about twice that), the update gets longer,
-// and the SMs left free run the other decompositions: the factorization
-// takes about 1.2x as long on a third of the SMs.  Cooperative grids are
-// gang-scheduled, so grids of concurrent factorizations queue whole.
-// CURID_CPQR_CTAS in the environment overrides the choice for comparisons:
-// "all" (one per SM) or "fewest".  (Eight-warp CTAs, two per SM, so that two
-// concurrent factorizations share SMs, measured slower: 549/s against 613/s
-// with four decompositions in flight.)
+// the lowest latency per factorization.  With two to seven in flight: the
+// fewest CTAs whose registers hold the matrix (eight columns per warp of the
+// register-resident kernel).  The pivot exchange gets cheaper with fewer
+// CTAs (records of 38-64 CTAs meet in about 2.4K cycles on GB300, of 152 in
+// about twice that), the update gets longer, and the SMs left free run the
+// other decompositions: the factorization takes about 1.2x as long on a
+// third of the SMs.  With eight or more in flight (float32): the grouped
+// kernel on the fewest CTAs whose registers and shared memory hold the
+// matrix (about 330 columns of 210 rows per CTA): about twice as long again
+// on a third of those SMs, which pays once enough decompositions share the
+// GPU (8000 x 6000, k = 200: 766/s with eight in flight against 653/s for
+// the register kernel; 528/s against 617/s with four).  Cooperative grids
+// are gang-scheduled, so grids of concurrent factorizations queue whole.
+// In the environment, for comparisons: CURID_CPQR_CTAS = "all" (one per SM),
+// "fewest" or a number of CTAs; CURID_CPQR_KERNEL = "grouped" or "reg".
+// (Eight-warp CTAs, two per SM, so that two concurrent factorizations share
+// SMs, measured slower: 549/s against 613/s with four in flight.)
 template <typename real>
 curid_status cpqr_layout(const Ctx& ctx, int64_t l, int64_t n, Layout* L) {
   if (l <= 0 || n <= 0) return CURID_INVALID_ARG;
@@ -652,7 +845,29 @@ curid_status cpqr_layout(const Ctx& ctx, int64_t l, int64_t n, Layout* L) {
   bool fewest = ctx.concurrency > 1;
   if (env && std::strcmp(env, "all") == 0) fewest = false;
   if (env && std::strcmp(env, "fewest") == 0) fewest = true;
-  if (fewest) {
+  const char* kenv = std::getenv("CURID_CPQR_KERNEL");
+  const int rpl = group_reg_rows<real>(l);
+  // eight or more in flight (float32): the grouped kernel on the fewest CTAs
+  bool force_grouped = fewest && ctx.concurrency >= 8 && rpl > 0;
+  if (kenv && std::strcmp(kenv, "grouped") == 0) force_grouped = true;
+  if (kenv && std::strcmp(kenv, "reg") == 0) force_grouped = false;
+  const int forced_g = env ? std::atoi(env) : 0;  // a number: that many CTAs (comparisons)
+  if (forced_g > 0) {
+    G = (int)std::min<int64_t>(std::min(forced_g, gmax), n);
+  } else if (fewest && force_grouped) {
+    // fewest CTAs whose registers and shared memory hold the matrix
+    const int64_t nr = rpl > 0 ? kWarps - 1 : 0;
+    for (int g = 1; g <= gmax; ++g) {
+      const int64_t ncg = (((n + g - 1) / g) + 3) & ~int64_t(3);
+      const size_t fixed = grouped_smem_bytes<real>(0, (int)ncg, l, rpl) + 1024;
+      if (fixed > ctx.smem_optin) continue;
+      const int64_t cap = nr + (int64_t)((ctx.smem_optin - fixed) / ((size_t)l * 4 * sizeof(real)));
+      if (ncg / 4 <= cap) {
+        G = g;
+        break;
+      }
+    }
+  } else if (fewest) {
     const int64_t rc = cpqr_reg_cols<real>((int)l, kWarps);
     if (rc > 0 && (n + rc - 1) / rc <= gmax) G = (int)((n + rc - 1) / rc);
   }
@@ -662,14 +877,14 @@ curid_status cpqr_layout(const Ctx& ctx, int64_t l, int64_t n, Layout* L) {
   L->G = G;
   L->nc = nc;
   L->warps = kWarps;
-  L->reg = cpqr_reg_fits<real>(ctx, (int)l, nc, kWarps);
+  L->reg = !force_grouped && cpqr_reg_fits<real>(ctx, (int)l, nc, kWarps);
   if (L->reg) {
     L->ldl = (int)(l | 1);
     L->rpl = L->ncs = L->ngo = 0;
     L->smem = 0;  // cpqr_reg_launch sizes its own
     return CURID_OK;
   }
-  L->rpl = group_reg_rows<real>(l);
+  L->rpl = rpl;
   const int nr = L->rpl > 0 ? kWarps - 1 : 0;
   const int rest = std::max(0, nc / 4 - nr);
   // the kernel's static shared variables share the per-block limit
@@ -687,6 +902,9 @@ void (*grouped_kernel(const Layout& L))(CpqrParams<real>) {
   if constexpr (sizeof(real) == 4) {
     if (L.rpl == kGroupRegRows)
       return L.ngo > 0 ? cpqr_kernel<real, kGroupRegRows, true> : cpqr_kernel<real, kGroupRegRows, false>;
+    if (L.rpl == kGroupRegRowsShort)
+      return L.ngo > 0 ? cpqr_kernel<real, kGroupRegRowsShort, true>
+                       : cpqr_kernel<real, kGroupRegRowsShort, false>;
   }
   if (L.rpl != 0) return nullptr;
   return L.ngo > 0 ? cpqr_kernel<real, 0, true> : cpqr_kernel<real, 0, false>;

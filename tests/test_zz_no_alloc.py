@@ -51,7 +51,30 @@ def test_static_cpqr_matches_workspace_cpqr(dtype):
         np.testing.assert_allclose(S[:kk].cpu().numpy(), Sr, atol=tol_fp * np.abs(Sr).max(),
                                    rtol=0)
         flags, steps, rank = info.cpu().tolist()
-        assert flags == 0 and rank == kk
+        assert flags == 0 and rank == kk and steps == kk
+
+
+@pytest.mark.parametrize("dtype,l,n,k", [(torch.float32, 520, 26144, 64),
+                                         (torch.float64, 8000, 8, 8)])
+def test_static_cpqr_overflow_groups(dtype, l, n, k):
+    """Slabs that spill past registers and shared memory into the carved
+    overflow area of the static scratch (on a 152-SM GPU with 227 KB of
+    shared memory per CTA): 520 x 26144 float32 is 172 columns per CTA, one
+    four-column group more than registers and shared memory hold; 8000 x 8
+    float64 runs on two CTAs whose one group (256 KB) fits no shared memory.
+    Same J, S and step count as the workspace-based call."""
+    torch.cuda.set_device(0)
+    Y = syn.spectrum_matrix(l, n, syn.power_decay(min(l, n)), 71, dtype, "cuda:0")
+    st, J, S, info = cpqr_static(Y, k)
+    torch.cuda.synchronize()
+    assert st == 0
+    ref = curid.cpqr(Y, k=k)
+    assert torch.equal(J, ref.J)
+    Sr = ref.S[:k].cpu().numpy()
+    tol_fp = 1e-11 if dtype == torch.float64 else 2e-5
+    np.testing.assert_allclose(S[:k].cpu().numpy(), Sr, atol=tol_fp * np.abs(Sr).max(), rtol=0)
+    flags, steps, rank = info.cpu().tolist()
+    assert flags == 0 and steps == k and rank == ref.k
 
 
 def test_static_cpqr_rejects_oversized_request():
