@@ -58,14 +58,22 @@ __device__ __forceinline__ real warp_sum(real v) {
   return v;
 }
 
-__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
-  return *reinterpret_cast<const volatile unsigned long long*>(p);
+// Loads and stores between CTAs of one GPU: relaxed at GPU scope (performed
+// in L2, never from a stale L1 line).  Volatile accesses would be
+// system-scope, which on a GPU whose memory the CPU caches coherently costs
+// more per access.
+__device__ __forceinline__ unsigned long long ld_gpu_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
-__device__ __forceinline__ int ld_volatile_i32(const int* p) {
-  return *reinterpret_cast<const volatile int*>(p);
+__device__ __forceinline__ int ld_gpu_i32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
-__device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned long long v) {
-  *reinterpret_cast<volatile unsigned long long*>(p) = v;
+__device__ __forceinline__ void st_gpu_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 }  // namespace curid

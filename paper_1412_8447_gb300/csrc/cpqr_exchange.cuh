@@ -92,10 +92,10 @@ template <typename real>
 __device__ __forceinline__ void put_tagged(unsigned long long* dst, unsigned tag, real v) {
   if (sizeof(real) == 8) {
     const unsigned long long b = (unsigned long long)__double_as_longlong((double)v);
-    st_volatile_u64(dst, pack(tag, (unsigned)(b >> 32)));
-    st_volatile_u64(dst + 1, pack(tag, (unsigned)(b & 0xffffffffull)));
+    st_gpu_u64(dst, pack(tag, (unsigned)(b >> 32)));
+    st_gpu_u64(dst + 1, pack(tag, (unsigned)(b & 0xffffffffull)));
   } else {
-    st_volatile_u64(dst, pack(tag, __float_as_uint((float)v)));
+    st_gpu_u64(dst, pack(tag, __float_as_uint((float)v)));
   }
 }
 
@@ -106,20 +106,20 @@ __device__ __forceinline__ bool get_tagged(const unsigned long long* src, unsign
   const long long t0 = clock64();
   while (true) {
     if (sizeof(real) == 8) {
-      const unsigned long long a = ld_volatile_u64(src), b = ld_volatile_u64(src + 1);
+      const unsigned long long a = ld_gpu_u64(src), b = ld_gpu_u64(src + 1);
       if ((unsigned)(a >> 32) == tag && (unsigned)(b >> 32) == tag) {
         *v = (real)__longlong_as_double((long long)(((a & 0xffffffffull) << 32) |
                                                      (b & 0xffffffffull)));
         return true;
       }
     } else {
-      const unsigned long long a = ld_volatile_u64(src);
+      const unsigned long long a = ld_gpu_u64(src);
       if ((unsigned)(a >> 32) == tag) {
         *v = (real)__uint_as_float((unsigned)(a & 0xffffffffull));
         return true;
       }
     }
-    if (ld_volatile_i32(abort_flag) || clock64() - t0 > spin) return false;
+    if (ld_gpu_i32(abort_flag) || clock64() - t0 > spin) return false;
   }
 }
 
@@ -144,17 +144,17 @@ __device__ __forceinline__ real words_norm(unsigned hi, unsigned lo) {
 
 __device__ __forceinline__ void st_rec(Rec* r, unsigned long long a, unsigned long long b,
                                        unsigned long long c, unsigned long long d) {
-  asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(&r->w[0]), "l"(a), "l"(b)
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(&r->w[0]), "l"(a), "l"(b)
                : "memory");
-  asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(&r->w[2]), "l"(c), "l"(d)
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(&r->w[2]), "l"(c), "l"(d)
                : "memory");
 }
 
 __device__ __forceinline__ void ld_rec(const Rec* r, unsigned long long* w) {
-  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];"
                : "=l"(w[0]), "=l"(w[1])
                : "l"(&r->w[0]));
-  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];"
                : "=l"(w[2]), "=l"(w[3])
                : "l"(&r->w[2]));
 }
@@ -194,7 +194,7 @@ __device__ bool gather_records(const CpqrParams<real>& P, int bf, unsigned epoch
       if (full) {
         ld_rec(rec, w[r]);
       } else {
-        asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
+        asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];"
                      : "=l"(w[r][0]), "=l"(w[r][1])
                      : "l"(&rec->w[0]));
         w[r][2] = w[r][3] = (unsigned long long)epoch << 32;
@@ -216,7 +216,7 @@ __device__ bool gather_records(const CpqrParams<real>& P, int bf, unsigned epoch
       ok = false;
       break;
     }
-    if ((round & 15) == 15 && ld_volatile_i32(P.abort_flag)) { ok = false; break; }
+    if ((round & 15) == 15 && ld_gpu_i32(P.abort_flag)) { ok = false; break; }
   }
   ok = __all_sync(0xffffffffu, ok);
   return ok;
