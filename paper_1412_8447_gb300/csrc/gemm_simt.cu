@@ -179,7 +179,9 @@ curid_status gemm(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N,
     }
     return CURID_UNSUPPORTED;
   }
-  int splits = gemm_splits<real>(M, N, K, ctx.num_sms);
+  // K is split to fill the SMs this caller's decomposition can expect to
+  // have: all of them one at a time, a share of them with several in flight
+  int splits = gemm_splits<real>(M, N, K, std::max(1, ctx.num_sms / std::max(1, ctx.concurrency)));
   if (splits > 1 && (partial == nullptr || (size_t)splits * M * N > partial_cap)) {
     splits = partial ? (int)std::max<size_t>(1, partial_cap / (size_t)(M * N)) : 1;
   }

@@ -325,7 +325,9 @@ curid_status gemm_tf32(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, i
            : make_map(&mapA, A, (uint64_t)K, (uint64_t)N, lda, kBM)))
     return CURID_CUDA_ERROR;
   if (!make_map(&mapX, X, (uint64_t)K, (uint64_t)M, ldx, (uint32_t)NP)) return CURID_CUDA_ERROR;
-  int splits = tc_splits(N, K, ctx.num_sms);
+  // K is split to fill the SMs this caller's decomposition can expect to
+  // have: all of them one at a time, a share of them with several in flight
+  int splits = tc_splits(N, K, std::max(1, ctx.num_sms / std::max(1, ctx.concurrency)));
   if (splits > 1 && (!partial || (size_t)splits * M * N > partial_cap)) splits = 1;
   const int kchunk = (int)(((K + splits - 1) / splits + kBK - 1) / kBK * kBK);
   splits = (int)((K + kchunk - 1) / kchunk);
