@@ -7,7 +7,12 @@
 //
 // One persistent launch: each CTA takes blocks from a global counter (in the
 // caller's order; largest first balances the tail) and factors one block at
-// a time.  The block is copied row-major into the CTA's scratch; thread t
+// a time.  The block is copied row-major into the CTA's shared memory when
+// it fits there (the launch gives each CTA its share of the SM's shared
+// memory: blocks of up to about 52K float32 elements at one CTA per SM),
+// else into the CTA's global scratch (L2); the two cases are instantiations
+// of their own, so an on-chip block uses shared-memory addressing only.
+// Thread t
 // owns columns t, t + blockDim, ... (at most kColsPerThread), so applying a
 // reflector is two coalesced sweeps down the rows: w = v^T X for every
 // column, then X -= tau v w^T fused with the new column norms, recomputed
@@ -45,6 +50,8 @@ struct BatchParams {
   int* block_status;  // nullable
   real* scratch;      // gridDim.x x scratch_stride
   int64_t scratch_stride;
+  int64_t xcap;       // elements of a block that fit the CTA's shared memory
+  int max_n;
   int max_m;
   int* counter;
   StatusBlock* status;
@@ -111,7 +118,189 @@ __device__ real cta_sum(real v, real* s_red) {
 template <typename real>
 size_t batched_smem(int max_m, int max_n, int k_max) {
   return ((size_t)((max_m + 3) & ~3) + (size_t)k_max * k_max) * sizeof(real) +
-         (size_t)max_n * sizeof(int);
+         (size_t)((max_n + 3) & ~3) * sizeof(int);
+}
+
+// Factor block b (m x n), row-major with leading dimension n, held whole in
+// the CTA's shared memory (SH: X points there) or in its global scratch.
+// (Holding the first rows on chip and the rest in L2 measured no faster than
+// the whole block in L2: the L2 rows set the pace of every sweep.)  Every
+// thread of the CTA calls it.
+template <typename real, bool SH>
+__device__ __forceinline__ void factor_block(const BatchParams<real>& P, int b, int m, int n,
+                                             real* X, real* v, real* S11, int* active,
+                                             real* s_val, int* s_idx) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int kk = P.k_max;
+  const real eps = sizeof(real) == 8 ? real(DBL_EPSILON) : real(FLT_EPSILON);
+  const int64_t lda = P.lda[b];
+  const real* A = P.A[b];
+  const int kcap = min(min(m, n), kk);
+  int32_t* Jb = P.J[b];
+
+  // copy A_b into X (row-major, leading dimension n)
+  for (int r = tid / 32; r < m; r += nt / 32)
+    for (int c = tid & 31; c < n; c += 32) X[(int64_t)r * n + c] = A[r * lda + c];
+  for (int c = tid; c < n; c += nt) active[c] = 1;
+  __syncthreads();
+  // column norms of the owned columns
+  real nu2[kColsPerThread];
+  real local2 = real(0);
+#pragma unroll
+  for (int u = 0; u < kColsPerThread; ++u) {
+    nu2[u] = real(0);
+    const int c = tid + u * nt;
+    if (c < n) {
+      for (int r0 = 0; r0 < m; r0 += kRowBatch) {
+        real xv[kRowBatch];
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q)
+          xv[q] = r0 + q < m ? X[(int64_t)(r0 + q) * n + c] : real(0);
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q) nu2[u] += xv[q] * xv[q];
+      }
+    }
+    local2 += nu2[u];
+  }
+  const real norm2 = cta_sum(local2, s_val);
+  const real normA = sqrt(norm2);
+  real resid2 = norm2;
+  bool nonfinite = !isfinite(norm2);
+  int k = 0, k_eff = -1;
+  real nu_first = real(0);
+
+  while (!nonfinite && k < kcap) {
+    if (P.tol > real(0) && sqrt(resid2) <= P.tol * normA) break;
+    // (1) pivot: the largest residual norm among the active columns
+    real best = real(-1);
+    int bi = INT_MAX;
+#pragma unroll
+    for (int u = 0; u < kColsPerThread; ++u) {
+      const int c = tid + u * nt;
+      if (c < n && active[c]) {
+        const real nu = sqrt(nu2[u]);
+        if (nu > best || (nu == best && c < bi)) {
+          best = nu;
+          bi = c;
+        }
+      }
+    }
+    real pnu;
+    int p;
+    cta_argmax<real>(best, bi, s_val, s_idx, &pnu, &p);
+    if (p < 0 || p >= n) break;
+    if (k == 0) nu_first = pnu;
+    if (k_eff < 0 && (pnu == real(0) || pnu <= real(2) * sqrt(real(m)) * eps * nu_first))
+      k_eff = k;
+    // (2) Householder reflector H = I - tau v v^T of X[k:m, p], v(k) = 1,
+    // H X[k:m, p] = beta e_k
+    for (int r = k + tid; r < m; r += nt) v[r] = X[(int64_t)r * n + p];
+    __syncthreads();
+    const real alpha = v[k];
+    real sig = real(0);
+    for (int r = k + 1 + tid; r < m; r += nt) sig += v[r] * v[r];
+    sig = cta_sum(sig, s_val);
+    real beta, tau, scale;
+    if (sig == real(0)) {
+      beta = alpha;
+      tau = real(0);
+      scale = real(0);
+    } else {
+      const real nrm = sqrt(alpha * alpha + sig);
+      beta = alpha >= real(0) ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      scale = real(1) / (alpha - beta);
+    }
+    for (int r = k + 1 + tid; r < m; r += nt) v[r] *= scale;
+    if (tid == 0) {
+      v[k] = real(1);
+      X[(int64_t)k * n + p] = beta;
+      Jb[k] = p;
+      active[p] = 0;
+    }
+    __syncthreads();
+    // (3) w = tau v^T X[k:m, c]; X[k:m, c] -= w v; norm of rows k+1..m-1.
+    // Rows go in batches of kRowBatch loads issued before their use, so
+    // each thread keeps that many L2 requests in flight.
+    real loc = real(0);
+#pragma unroll
+    for (int u = 0; u < kColsPerThread; ++u) {
+      const int c = tid + u * nt;
+      if (c < n && active[c]) {
+        real w = real(0);
+        for (int r0 = k; r0 < m; r0 += kRowBatch) {
+          real xv[kRowBatch];
+#pragma unroll
+          for (int q = 0; q < kRowBatch; ++q) {
+            const int r = r0 + q;
+            xv[q] = r < m ? X[(int64_t)r * n + c] : real(0);
+          }
+#pragma unroll
+          for (int q = 0; q < kRowBatch; ++q)
+            if (r0 + q < m) w += v[r0 + q] * xv[q];
+        }
+        w *= tau;
+        real s2 = real(0);
+        for (int r0 = k; r0 < m; r0 += kRowBatch) {
+          real xv[kRowBatch];
+#pragma unroll
+          for (int q = 0; q < kRowBatch; ++q) {
+            const int r = r0 + q;
+            xv[q] = r < m ? X[(int64_t)r * n + c] : real(0);
+          }
+#pragma unroll
+          for (int q = 0; q < kRowBatch; ++q) {
+            const int r = r0 + q;
+            if (r < m) {
+              const real x = xv[q] - w * v[r];
+              X[(int64_t)r * n + c] = x;
+              if (r > k) s2 += x * x;
+            }
+          }
+        }
+        nu2[u] = s2;
+        loc += s2;
+      }
+    }
+    resid2 = cta_sum(loc, s_val);
+    if (!isfinite(resid2)) nonfinite = true;
+    ++k;
+  }
+  // J[k:] = the unselected columns in ascending order
+  if (tid == 0) {
+    int pos = k;
+    for (int c = 0; c < n; ++c)
+      if (active[c]) Jb[pos++] = c;
+  }
+  __syncthreads();
+  const int ke = k_eff < 0 ? k : k_eff;
+  for (int e = tid; e < ke * ke; e += nt) {
+    const int i = e / ke, t = e % ke;
+    S11[i * kk + t] = i <= t ? X[(int64_t)i * n + Jb[t]] : real(0);
+  }
+  __syncthreads();
+  // T (k x (n - k), leading dimension n), one column per thread; rows at
+  // and after the numerical rank are zero (Section 2.3)
+  real* Tb = P.T[b];
+  for (int c = tid; c < n - k; c += nt) {
+    const int col = Jb[k + c];
+    for (int i = k - 1; i >= ke; --i) Tb[(int64_t)i * n + c] = real(0);
+    for (int i = ke - 1; i >= 0; --i) {
+      real s = X[(int64_t)i * n + col];
+      for (int t = i + 1; t < ke; ++t) s -= S11[i * kk + t] * Tb[(int64_t)t * n + c];
+      Tb[(int64_t)i * n + c] = s / S11[i * kk + i];
+    }
+  }
+  if (tid == 0) {
+    P.k_out[b] = k;
+    int st = CURID_OK;
+    if (nonfinite) st = CURID_NONFINITE;
+    else if (k_eff >= 0) st = CURID_RANK_DEFICIENT;
+    else if (P.tol > real(0) && k == kcap && sqrt(resid2) > P.tol * normA) st = CURID_TOL_NOT_MET;
+    if (P.block_status) P.block_status[b] = st;
+    if (st == CURID_NONFINITE) set_flag(&P.status->flags, FLAG_NONFINITE);
+    if (st == CURID_RANK_DEFICIENT) set_flag(&P.status->flags, FLAG_RANK_DEFICIENT);
+  }
 }
 
 template <typename real>
@@ -120,13 +309,12 @@ __global__ void __launch_bounds__(kMaxBlockDim) batched_id_kernel(BatchParams<re
   real* v = reinterpret_cast<real*>(smem_raw);                 // reflector, max_m
   real* S11 = v + ((P.max_m + 3) & ~3);                         // k_max x k_max
   int* active = reinterpret_cast<int*>(S11 + (size_t)P.k_max * P.k_max);  // max_n
+  real* Xs = reinterpret_cast<real*>(active + ((P.max_n + 3) & ~3));     // xcap elements
   __shared__ real s_val[32];
   __shared__ int s_idx[32];
   __shared__ int s_blk;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int kk = P.k_max;
-  real* X = P.scratch + (int64_t)blockIdx.x * P.scratch_stride;
-  const real eps = sizeof(real) == 8 ? real(DBL_EPSILON) : real(FLT_EPSILON);
+  const int tid = threadIdx.x;
+  real* Xg = P.scratch + (int64_t)blockIdx.x * P.scratch_stride;
 
   for (;;) {
     if (tid == 0) s_blk = atomicAdd(P.counter, 1);
@@ -136,174 +324,10 @@ __global__ void __launch_bounds__(kMaxBlockDim) batched_id_kernel(BatchParams<re
     if (b >= P.nb) break;
     if (P.order) b = P.order[b];
     const int m = P.m[b], n = P.n[b];
-    const int64_t lda = P.lda[b];
-    const real* A = P.A[b];
-    const int kcap = min(min(m, n), kk);
-    int32_t* Jb = P.J[b];
-
-    // copy A_b into X (row-major, leading dimension n)
-    for (int r = tid / 32; r < m; r += nt / 32)
-      for (int c = tid & 31; c < n; c += 32) X[(int64_t)r * n + c] = A[r * lda + c];
-    for (int c = tid; c < n; c += nt) active[c] = 1;
-    __syncthreads();
-    // column norms of the owned columns
-    real nu2[kColsPerThread];
-    real local2 = real(0);
-#pragma unroll
-    for (int u = 0; u < kColsPerThread; ++u) {
-      nu2[u] = real(0);
-      const int c = tid + u * nt;
-      if (c < n) {
-        for (int r0 = 0; r0 < m; r0 += kRowBatch) {
-          real xv[kRowBatch];
-#pragma unroll
-          for (int q = 0; q < kRowBatch; ++q)
-            xv[q] = r0 + q < m ? X[(int64_t)(r0 + q) * n + c] : real(0);
-#pragma unroll
-          for (int q = 0; q < kRowBatch; ++q) nu2[u] += xv[q] * xv[q];
-        }
-      }
-      local2 += nu2[u];
-    }
-    const real norm2 = cta_sum(local2, s_val);
-    const real normA = sqrt(norm2);
-    real resid2 = norm2;
-    bool nonfinite = !isfinite(norm2);
-    int k = 0, k_eff = -1;
-    real nu_first = real(0);
-
-    while (!nonfinite && k < kcap) {
-      if (P.tol > real(0) && sqrt(resid2) <= P.tol * normA) break;
-      // (1) pivot: the largest residual norm among the active columns
-      real best = real(-1);
-      int bi = INT_MAX;
-#pragma unroll
-      for (int u = 0; u < kColsPerThread; ++u) {
-        const int c = tid + u * nt;
-        if (c < n && active[c]) {
-          const real nu = sqrt(nu2[u]);
-          if (nu > best || (nu == best && c < bi)) {
-            best = nu;
-            bi = c;
-          }
-        }
-      }
-      real pnu;
-      int p;
-      cta_argmax<real>(best, bi, s_val, s_idx, &pnu, &p);
-      if (p < 0 || p >= n) break;
-      if (k == 0) nu_first = pnu;
-      if (k_eff < 0 && (pnu == real(0) || pnu <= real(2) * sqrt(real(m)) * eps * nu_first))
-        k_eff = k;
-      // (2) Householder reflector H = I - tau v v^T of X[k:m, p], v(k) = 1,
-      // H X[k:m, p] = beta e_k
-      for (int r = k + tid; r < m; r += nt) v[r] = X[(int64_t)r * n + p];
-      __syncthreads();
-      const real alpha = v[k];
-      real sig = real(0);
-      for (int r = k + 1 + tid; r < m; r += nt) sig += v[r] * v[r];
-      sig = cta_sum(sig, s_val);
-      real beta, tau, scale;
-      if (sig == real(0)) {
-        beta = alpha;
-        tau = real(0);
-        scale = real(0);
-      } else {
-        const real nrm = sqrt(alpha * alpha + sig);
-        beta = alpha >= real(0) ? -nrm : nrm;
-        tau = (beta - alpha) / beta;
-        scale = real(1) / (alpha - beta);
-      }
-      for (int r = k + 1 + tid; r < m; r += nt) v[r] *= scale;
-      if (tid == 0) {
-        v[k] = real(1);
-        X[(int64_t)k * n + p] = beta;
-        Jb[k] = p;
-        active[p] = 0;
-      }
-      __syncthreads();
-      // (3) w = tau v^T X[k:m, c]; X[k:m, c] -= w v; norm of rows k+1..m-1.
-      // Rows go in batches of kRowBatch loads issued before their use, so
-      // each thread keeps that many L2 requests in flight.
-      real loc = real(0);
-#pragma unroll
-      for (int u = 0; u < kColsPerThread; ++u) {
-        const int c = tid + u * nt;
-        if (c < n && active[c]) {
-          real w = real(0);
-          for (int r0 = k; r0 < m; r0 += kRowBatch) {
-            real xv[kRowBatch];
-#pragma unroll
-            for (int q = 0; q < kRowBatch; ++q) {
-              const int r = r0 + q;
-              xv[q] = r < m ? X[(int64_t)r * n + c] : real(0);
-            }
-#pragma unroll
-            for (int q = 0; q < kRowBatch; ++q)
-              if (r0 + q < m) w += v[r0 + q] * xv[q];
-          }
-          w *= tau;
-          real s2 = real(0);
-          for (int r0 = k; r0 < m; r0 += kRowBatch) {
-            real xv[kRowBatch];
-#pragma unroll
-            for (int q = 0; q < kRowBatch; ++q) {
-              const int r = r0 + q;
-              xv[q] = r < m ? X[(int64_t)r * n + c] : real(0);
-            }
-#pragma unroll
-            for (int q = 0; q < kRowBatch; ++q) {
-              const int r = r0 + q;
-              if (r < m) {
-                const real x = xv[q] - w * v[r];
-                X[(int64_t)r * n + c] = x;
-                if (r > k) s2 += x * x;
-              }
-            }
-          }
-          nu2[u] = s2;
-          loc += s2;
-        }
-      }
-      resid2 = cta_sum(loc, s_val);
-      if (!isfinite(resid2)) nonfinite = true;
-      ++k;
-    }
-    // J[k:] = the unselected columns in ascending order
-    if (tid == 0) {
-      int pos = k;
-      for (int c = 0; c < n; ++c)
-        if (active[c]) Jb[pos++] = c;
-    }
-    __syncthreads();
-    const int ke = k_eff < 0 ? k : k_eff;
-    for (int e = tid; e < ke * ke; e += nt) {
-      const int i = e / ke, t = e % ke;
-      S11[i * kk + t] = i <= t ? X[(int64_t)i * n + Jb[t]] : real(0);
-    }
-    __syncthreads();
-    // T (k x (n - k), leading dimension n), one column per thread; rows at
-    // and after the numerical rank are zero (Section 2.3)
-    real* Tb = P.T[b];
-    for (int c = tid; c < n - k; c += nt) {
-      const int col = Jb[k + c];
-      for (int i = k - 1; i >= ke; --i) Tb[(int64_t)i * n + c] = real(0);
-      for (int i = ke - 1; i >= 0; --i) {
-        real s = X[(int64_t)i * n + col];
-        for (int t = i + 1; t < ke; ++t) s -= S11[i * kk + t] * Tb[(int64_t)t * n + c];
-        Tb[(int64_t)i * n + c] = s / S11[i * kk + i];
-      }
-    }
-    if (tid == 0) {
-      P.k_out[b] = k;
-      int st = CURID_OK;
-      if (nonfinite) st = CURID_NONFINITE;
-      else if (k_eff >= 0) st = CURID_RANK_DEFICIENT;
-      else if (P.tol > real(0) && k == kcap && sqrt(resid2) > P.tol * normA) st = CURID_TOL_NOT_MET;
-      if (P.block_status) P.block_status[b] = st;
-      if (st == CURID_NONFINITE) set_flag(&P.status->flags, FLAG_NONFINITE);
-      if (st == CURID_RANK_DEFICIENT) set_flag(&P.status->flags, FLAG_RANK_DEFICIENT);
-    }
+    if ((int64_t)m * n <= P.xcap)
+      factor_block<real, true>(P, b, m, n, Xs, v, S11, active, s_val, s_idx);
+    else
+      factor_block<real, false>(P, b, m, n, Xg, v, S11, active, s_val, s_idx);
     __syncthreads();
   }
 }
@@ -328,20 +352,39 @@ struct BatchArgs {
 constexpr int kShapes[][2] = {{512, 1}, {256, 1}, {256, 2}, {128, 2}, {128, 4}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
+// A launch shape's grid, dynamic shared memory and on-chip block capacity:
+// each CTA gets its share of the SM's shared memory for a block.
 template <typename real>
-bool shape_ok(const curid_handle* h, const BatchArgs& a, int s, int* grid) {
+bool shape_ok(const curid_handle* h, const BatchArgs& a, int s, int* grid, size_t* smem_out,
+              int64_t* xcap_out) {
   const int threads = kShapes[s][0], per_sm = kShapes[s][1];
   if (a.max_n > kColsPerThread * threads) return false;
-  const size_t smem = batched_smem<real>(a.max_m, a.max_n, a.k_max);
-  if (smem > h->smem_optin) return false;
-  if (cudaFuncSetAttribute(batched_id_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
+  const size_t base = batched_smem<real>(a.max_m, a.max_n, a.k_max);
+  if (base > h->smem_optin) return false;
+  int per_sm_bytes = 0;
+  if (cudaDeviceGetAttribute(&per_sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                             h->device) != cudaSuccess)
     return false;
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_id_kernel<real>, threads,
-                                                    smem) != cudaSuccess)
-    return false;
-  if (occ < per_sm) return false;
+  // per CTA: 1 KB reserved by the system and the kernel's static variables
+  const int64_t share = (int64_t)per_sm_bytes / per_sm - 2048;
+  int64_t xbytes = std::min<int64_t>(share - (int64_t)base, (int64_t)h->smem_optin - (int64_t)base);
+  xbytes = std::max<int64_t>(0, xbytes) & ~int64_t(1023);
+  for (;; xbytes -= 1024) {
+    if (xbytes < 0) return false;
+    const size_t smem = base + (size_t)xbytes;
+    if (cudaFuncSetAttribute(batched_id_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return false;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_id_kernel<real>, threads,
+                                                      smem) != cudaSuccess)
+      return false;
+    if (occ >= per_sm) {
+      *smem_out = smem;
+      *xcap_out = xbytes / (int64_t)sizeof(real);
+      break;
+    }
+  }
   *grid = h->num_sms * per_sm;
   return true;
 }
@@ -360,7 +403,9 @@ size_t batched_ws(const curid_handle* h, const BatchArgs& a) {
 template <typename real>
 curid_status batched_launch(curid_handle* h, const BatchArgs& a, int shape) {
   int grid = 0;
-  if (!shape_ok<real>(h, a, shape, &grid)) return CURID_UNSUPPORTED;
+  size_t smem = 0;
+  int64_t xcap = 0;
+  if (!shape_ok<real>(h, a, shape, &grid, &smem, &xcap)) return CURID_UNSUPPORTED;
   if (!h->ws || batched_ws<real>(h, a) > h->ws_bytes) return CURID_NO_WORKSPACE;
   Carver cv(h->ws);
   StatusBlock* st = cv.take<StatusBlock>(1);
@@ -385,9 +430,10 @@ curid_status batched_launch(curid_handle* h, const BatchArgs& a, int shape) {
   P.scratch = scratch;
   P.scratch_stride = stride;
   P.max_m = a.max_m;
+  P.max_n = a.max_n;
+  P.xcap = xcap;
   P.counter = counter;
   P.status = st;
-  const size_t smem = batched_smem<real>(a.max_m, a.max_n, a.k_max);
   batched_id_kernel<real><<<grid, kShapes[shape][0], smem, h->stream>>>(P);
   CURID_CUDA(cudaGetLastError());
   if (h->profiling) ++h->launches;
@@ -416,8 +462,10 @@ curid_status batched_default(curid_handle* h, curid_dtype dt, const BatchArgs& a
   int s = tuned_shape(h, dt);
   if (s >= 0) return batched_launch<real>(h, a, s);
   int grid;
+  size_t smem;
+  int64_t xcap;
   for (s = 0; s < kNumShapes; ++s)
-    if (shape_ok<real>(h, a, s, &grid)) return batched_launch<real>(h, a, s);
+    if (shape_ok<real>(h, a, s, &grid, &smem, &xcap)) return batched_launch<real>(h, a, s);
   return CURID_UNSUPPORTED;
 }
 
@@ -433,7 +481,9 @@ curid_status batched_tune(curid_handle* h, curid_dtype dt, const BatchArgs& a, i
   curid_status result = CURID_OK;
   for (int s = 0; s < kNumShapes && result == CURID_OK; ++s) {
     int grid;
-    if (!shape_ok<real>(h, a, s, &grid)) continue;
+    size_t smem;
+    int64_t xcap;
+    if (!shape_ok<real>(h, a, s, &grid, &smem, &xcap)) continue;
     for (int rep = 0; rep < 2 && result == CURID_OK; ++rep) {
       if (cudaEventRecord(e0, h->stream) != cudaSuccess) { result = CURID_CUDA_ERROR; break; }
       result = batched_launch<real>(h, a, s);
