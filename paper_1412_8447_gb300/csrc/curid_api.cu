@@ -280,17 +280,9 @@ curid_status a_product(const Ctx& ctx, bool tf32, bool bf16, bool tb, int64_t M,
   if constexpr (sizeof(real) == 4) {
     if (bf16)
       return gemm_bf16(ctx, tb, M, N, K, X, ldx, A, lda, out, ldo, P.xsplit, P.xsplit_elems);
-    if (tf32) {
-      // the sample is the MMA's N (<= 256): larger samples run in row chunks
-      // of equal size (multiples of 16), each reading A once
-      const int64_t chunks = (M + 255) / 256;
-      const int64_t rows = ((M + chunks - 1) / chunks + 15) / 16 * 16;
-      for (int64_t r0 = 0; r0 < M; r0 += rows)
-        CURID_TRY(gemm_tf32(ctx, false, tb, std::min(rows, M - r0), N, K, X + r0 * ldx, ldx,
-                            static_cast<const real*>(A), lda, out + r0 * ldo, ldo, P.partial,
-                            P.partial_cap));
-      return CURID_OK;
-    }
+    if (tf32)
+      return gemm_tf32(ctx, false, tb, M, N, K, X, ldx, static_cast<const real*>(A), lda, out,
+                       ldo, P.partial, P.partial_cap);
   }
   return gemm<real>(ctx, false, tb, M, N, K, real(1), X, ldx, static_cast<const real*>(A), lda,
                     real(0), out, ldo, P.partial, P.partial_cap);

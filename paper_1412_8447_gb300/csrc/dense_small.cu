@@ -565,17 +565,8 @@ curid_status gram_tf32(const Ctx& ctx, const float* X, int64_t r, int64_t c, int
                        float* xh, float* xl, float* G, float* g2, float* partial,
                        size_t partial_cap) {
   CURID_TRY(split_tf32(ctx, X, ld, xh, ld, xl, ld, r, c));
-  // the left operand is the MMA's N (<= 256 rows): equal row chunks of a
-  // multiple of 16
-  const int64_t chunks = (r + 255) / 256;
-  const int64_t rows = ((r + chunks - 1) / chunks + 15) / 16 * 16;
-  for (int64_t r0 = 0; r0 < r; r0 += rows) {
-    const int64_t mr = std::min(rows, r - r0);
-    CURID_TRY(gemm_tf32(ctx, false, true, mr, r, c, xh + r0 * ld, ld, X, ld, G + r0 * r, r,
-                        partial, partial_cap));
-    CURID_TRY(gemm_tf32(ctx, false, true, mr, r, c, xl + r0 * ld, ld, X, ld, g2 + r0 * r, r,
-                        partial, partial_cap));
-  }
+  CURID_TRY(gemm_tf32(ctx, false, true, r, r, c, xh, ld, X, ld, G, r, partial, partial_cap));
+  CURID_TRY(gemm_tf32(ctx, false, true, r, r, c, xl, ld, X, ld, g2, r, partial, partial_cap));
   return add2d<float>(ctx, g2, r, G, r, r, r);
 }
 

@@ -15,9 +15,11 @@
 // Tiling: the transposed product D = C^T is computed, so the MMA's M = 128
 // rows are 128 output columns and its N = l (<= 256, rounded up to 16) is
 // the whole sample: one CTA holds a 128 x l accumulator in TMEM and streams
-// its 128 columns of A exactly once over its K range.  K is split across
-// CTAs when the column tiles alone cannot fill the GPU; partial tiles are
-// summed in a fixed order.  Warp 0 issues TMA loads, warp 1 the MMAs,
+// its 128 columns of A exactly once over its K range.  Larger samples run in
+// equal row chunks of at most 256, one per CTA, the chunks of a column tile
+// neighbouring CTAs so that they stream the same tiles of A together.  K is
+// split across CTAs when the tiles alone cannot fill the SMs the caller can
+// expect; partial tiles are summed in a fixed order.  Warp 0 issues TMA loads, warp 1 the MMAs,
 // warps 4-7 split A into hi/lo per stage and run the epilogue
 // (TMEM -> registers -> coalesced stores of C).  Both MMA operands are
 // K-major: for C = X A, where A's rows run along K, the TMA brings an
@@ -44,8 +46,9 @@ constexpr int kAtileBytes = kBM * kBK * 4;  // 16 KB
 constexpr int kTmemCols = 256;
 
 struct TcParams {
-  int M;         // rows of C (= l), MMA N before rounding
-  int NP;        // M rounded up to 16
+  int M;         // rows of C (= l)
+  int NP;        // rows of a chunk of C (<= 256, a multiple of 16): the MMA's N
+  int nch;       // chunks of rows; chunk = blockIdx.x % nch (neighbouring CTAs)
   int N;         // columns of C
   int K;
   int kchunk;    // K per split, multiple of kBK
@@ -82,7 +85,10 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
   const uint32_t acc_bar = smem_u32(bars + 3 * kStages);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * kBM;
+  // the row chunks of one column tile are neighbouring CTAs: they stream the
+  // same tiles of A at the same time, so A comes from HBM about once
+  const int row0 = (int)(blockIdx.x % P.nch) * P.NP;
+  const int n0 = (int)(blockIdx.x / P.nch) * kBM;
   const int kbeg = blockIdx.y * P.kchunk;
   const int kend = min(P.K, kbeg + P.kchunk);
   const int nk = (kend - kbeg + kBK - 1) / kBK;
@@ -135,7 +141,7 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
       } else {
         tma_load_2d(smem_u32(Ahi[s]), &tmA, k, n0, full(s));
       }
-      tma_load_2d(smem_u32(Xs[s]), &tmX, k, 0, full(s));
+      tma_load_2d(smem_u32(Xs[s]), &tmX, k, row0, full(s));
       issued = i + 1;
     }
     if (*abort_flag) {
@@ -243,13 +249,14 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
       const int col = n0 + q * 32 + lane;  // output column of this thread
       float* dst = P.partial ? P.partial + (size_t)blockIdx.y * P.M * P.N : P.C;
       const int64_t ld = P.partial ? P.N : P.ldc;
+      const int rows = min(P.NP, P.M - row0);
       for (int c0 = 0; c0 < P.NP; c0 += 32) {
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
         if (col < P.N) {
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            if (c0 + j < P.M) dst[(int64_t)(c0 + j) * ld + col] = __uint_as_float(r[j]);
+            if (c0 + j < rows) dst[(int64_t)(row0 + c0 + j) * ld + col] = __uint_as_float(r[j]);
         }
       }
     }
@@ -311,12 +318,14 @@ size_t gemm_tf32_partial_elems(int64_t M, int64_t N, int64_t K, int num_sms) {
 curid_status gemm_tf32(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
                        const float* X, int64_t ldx, const float* A, int64_t lda, float* C,
                        int64_t ldc, float* partial, size_t partial_cap) {
-  if (ta || M <= 0 || M > 256 || N <= 0 || K <= 0) return CURID_UNSUPPORTED;
+  if (ta || M <= 0 || N <= 0 || K <= 0 || M > (int64_t)INT32_MAX / 2) return CURID_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(A) & 15) ||
       (ldx & 3) || (lda & 3))
     return CURID_UNSUPPORTED;
   if (!tma_encoder()) return CURID_CUDA_ERROR;
-  const int NP = (int)((M + 15) / 16 * 16);
+  // rows in chunks of at most 256 (the MMA's N), equal up to rounding to 16
+  const int nch = (int)((M + 255) / 256);
+  const int NP = (int)(((M + nch - 1) / nch + 15) / 16 * 16);
   CUtensorMap mapA, mapX;
   const bool mn = !tb;
   // C = X A: A is K x N (rows k, columns n), box {32 columns, 32 rows};
@@ -327,13 +336,14 @@ curid_status gemm_tf32(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, i
   if (!make_map(&mapX, X, (uint64_t)K, (uint64_t)M, ldx, (uint32_t)NP)) return CURID_CUDA_ERROR;
   // K is split to fill the SMs this caller's decomposition can expect to
   // have: all of them one at a time, a share of them with several in flight
-  int splits = tc_splits(N, K, std::max(1, ctx.num_sms / std::max(1, ctx.concurrency)));
+  int splits = tc_splits(N, K, std::max(1, ctx.num_sms / std::max(1, ctx.concurrency) / nch));
   if (splits > 1 && (!partial || (size_t)splits * M * N > partial_cap)) splits = 1;
   const int kchunk = (int)(((K + splits - 1) / splits + kBK - 1) / kBK * kBK);
   splits = (int)((K + kchunk - 1) / kchunk);
   TcParams P;
   P.M = (int)M;
   P.NP = NP;
+  P.nch = nch;
   P.N = (int)N;
   P.K = (int)K;
   P.kchunk = kchunk;
@@ -350,7 +360,7 @@ curid_status gemm_tf32(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, i
   if (smem > ctx.smem_optin) return CURID_UNSUPPORTED;
   CURID_CUDA(cudaFuncSetAttribute(tc_sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-  dim3 grid((unsigned)((N + kBM - 1) / kBM), (unsigned)splits);
+  dim3 grid((unsigned)(nch * ((N + kBM - 1) / kBM)), (unsigned)splits);
   tc_sketch_kernel<<<grid, kTcThreads, smem, ctx.stream>>>(mapA, mapX, P);
   CURID_LAUNCHED(ctx);
   if (splits > 1) {
