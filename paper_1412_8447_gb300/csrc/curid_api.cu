@@ -84,7 +84,7 @@ struct Plan {
   real* B[3] = {nullptr, nullptr, nullptr};  // sample-matrix buffers, l x max(m, n)
   real* G = nullptr;      // l x l  (Gram)
   real* Linv = nullptr;   // l x l
-  real* Li = nullptr;     // 2 x l x pad4(l) (tensor-core orth apply)
+  real* Li = nullptr;     // l x pad4(l) (tensor-core orth apply)
   // column CPQR and T
   CpqrScratch cs{};
   real* S = nullptr;      // k x n
@@ -183,8 +183,8 @@ curid_status make_plan(const Ctx& ctx, Op op, const Dims& d, bool gen_omega, boo
         part = std::max(part, gemm_tf32_partial_elems(std::min<int64_t>(l, 256), l,
                                                       std::max(m, n), ctx.num_sms));
       if (sizeof(real) == 4 && (d.tf32 || d.bf16) && !d.sp) {
-        // L^{-1} split for the tensor-core apply of the orth
-        P->Li = cv.take<real>(2 * (size_t)l * pad4(l));
+        // explicit L^{-1} for the tensor-core apply of the orth
+        P->Li = cv.take<real>((size_t)l * pad4(l));
         part = std::max(part, gemm_tf32_partial_elems(std::min<int64_t>(l, 256), std::max(m, n),
                                                       l, ctx.num_sms));
       }
@@ -301,10 +301,10 @@ curid_status a_product(const Ctx& ctx, bool tf32, bool bf16, bool tb, int64_t M,
 //
 // With tensor-core products (TF32, or BF16 storage of A) and samples of more
 // than 256 rows the orth runs on the TF32 tensor cores at float32 accuracy:
-// the Gram matrices (gram_tf32, with `spare`, a free sample buffer, for the
-// TF32 part and Linv as scratch) and the apply X <- L^{-1} X through an
-// explicit L^{-1} split into its TF32 part and remainder (l = 520 rows of
-// 20000: orth 13 -> 10 ms per decomposition with the Gram alone).  Samples
+// the Gram matrices (gram_tf32) and the apply X <- L^{-1} X through an
+// explicit L^{-1}, each one launch that splits both operands into TF32 parts
+// in shared memory (l = 520 rows of 20000: orth 13 -> 10 ms per
+// decomposition with the Gram alone).  Samples
 // of up to 256 rows go to the tensor cores when several decompositions are
 // in flight, where the SIMT products' SM time is what limits throughput;
 // one at a time they keep the SIMT Gram and the triangular solve.
@@ -312,8 +312,8 @@ curid_status a_product(const Ctx& ctx, bool tf32, bool bf16, bool tb, int64_t M,
 // (for comparisons).
 template <typename real>
 curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
-                       const Plan<real>& P, bool final_orth, bool tc, real* spare) {
-  const bool tc_ok = sizeof(real) == 4 && tc && spare && P.Linv && !P.sp;
+                       const Plan<real>& P, bool final_orth, bool tc) {
+  const bool tc_ok = sizeof(real) == 4 && tc && P.Li && !P.sp;
   bool small_tc = tc_ok && r <= 256 && P.Li && ctx.concurrency > 1;
   if (const char* env = std::getenv("CURID_ORTH_TC")) {
     if (std::strcmp(env, "1") == 0) small_tc = tc_ok && r <= 256 && P.Li;
@@ -321,8 +321,7 @@ curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t 
   }
   const bool use_tc = tc_ok && (r > 256 || small_tc);
   return chol_qr_rows<real>(ctx, X, tmp, r, c, ld, P.G, P.partial, P.partial_cap,
-                            final_orth ? 3 : 2, use_tc ? spare : nullptr,
-                            use_tc ? P.Linv : nullptr, use_tc ? P.Li : nullptr);
+                            final_orth ? 3 : 2, use_tc, use_tc ? P.Li : nullptr);
 }
 
 // Sample matrix of Algorithm 4 with the power scheme of Section 5.3:
@@ -348,8 +347,7 @@ curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const 
     real* t = other(cur, nullptr);
     {
       PhaseScope ps(h, CURID_PHASE_ORTH);
-      CURID_TRY(orth_rows<real>(ctx, &cur, &t, l, n, ldy, P, false, tf32 || bf16,
-                                other(cur, t)));
+      CURID_TRY(orth_rows<real>(ctx, &cur, &t, l, n, ldy, P, false, tf32 || bf16));
     }
     real* z = other(cur, nullptr);
     {
@@ -359,8 +357,7 @@ curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const 
     real* zt = other(z, nullptr);
     {
       PhaseScope ps(h, CURID_PHASE_ORTH);
-      CURID_TRY(orth_rows<real>(ctx, &z, &zt, l, m, ldz, P, i == q - 1, tf32 || bf16,
-                                other(z, zt)));
+      CURID_TRY(orth_rows<real>(ctx, &z, &zt, l, m, ldz, P, i == q - 1, tf32 || bf16));
     }
     real* y = other(z, nullptr);
     {

@@ -510,15 +510,14 @@ curid_status gemm_nt_f64acc(const Ctx& ctx, int64_t M, int64_t N, int64_t K, con
 
 template <typename real>
 curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
-                          real* G, real* partial, size_t partial_cap, int passes, real* xh,
-                          real* g2, real* li) {
+                          real* G, real* partial, size_t partial_cap, int passes, bool tc_gram,
+                          real* li) {
   const double shift = sizeof(real) == 4 ? 1e-5 : 1e-13;
   for (int pass = 0; pass < passes; ++pass) {
     bool tc = false;
     if constexpr (sizeof(real) == 4) {
-      if (xh && g2) {
-        // the remainder goes to *tmp, which the triangular apply overwrites
-        CURID_TRY(gram_tf32(ctx, *X, r, c, ld, xh, *tmp, G, g2, partial, partial_cap));
+      if (tc_gram) {
+        CURID_TRY(gram_tf32(ctx, *X, r, c, ld, G, partial, partial_cap));
         tc = true;
       }
     }
@@ -530,27 +529,21 @@ curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64
     if constexpr (sizeof(real) == 4) {
       if (tc && li) {
         // X <- L^{-1} X as tensor-core products: L^{-1} explicitly (a
-        // triangular solve with the identity), split into its TF32 part and
-        // remainder; each product splits X inside, so the sum carries
-        // float32 accuracy.  The products take at most 256 rows of L^{-1}
-        // at a time (the MMA's N); rows r0..r0+mr-1 of a lower triangular
-        // L^{-1} need only the first r0 + mr rows of X.
+        // triangular solve with the identity); the product splits both
+        // operands into TF32 parts and remainders in shared memory, so it
+        // carries float32 accuracy.  The products take at most 256 rows of
+        // L^{-1} at a time (the MMA's N); rows r0..r0+mr-1 of a lower
+        // triangular L^{-1} need only the first r0 + mr rows of X.
         const int64_t ldp = (r + 3) & ~int64_t(3);  // 16-byte rows for the tensor-core loads
-        float* lhi = li;
-        float* llo = li + r * ldp;
-        CURID_TRY(tri_solve<float>(ctx, (int)r, G, r, false, false, nullptr, 0, lhi, ldp, r,
+        CURID_TRY(tri_solve<float>(ctx, (int)r, G, r, false, false, nullptr, 0, li, ldp, r,
                                    nullptr));
-        CURID_TRY(split_tf32(ctx, lhi, ldp, lhi, ldp, llo, ldp, r, r));
         const int64_t chunks = (r + 255) / 256;
         const int64_t rows = ((r + chunks - 1) / chunks + 15) / 16 * 16;
         for (int64_t r0 = 0; r0 < r; r0 += rows) {
           const int64_t mr = std::min(rows, r - r0), kk = r0 + mr;
-          CURID_TRY(gemm_tf32(ctx, false, false, mr, c, kk, lhi + r0 * ldp, ldp, *X, ld,
-                              *tmp + r0 * ld, ld, partial, partial_cap));
-          CURID_TRY(gemm_tf32(ctx, false, false, mr, c, kk, llo + r0 * ldp, ldp, *X, ld,
-                              xh + r0 * ld, ld, partial, partial_cap));
+          CURID_TRY(gemm_tf32(ctx, false, false, mr, c, kk, li + r0 * ldp, ldp, *X, ld,
+                              *tmp + r0 * ld, ld, partial, partial_cap, true));
         }
-        CURID_TRY(add2d<float>(ctx, xh, ld, *tmp, ld, r, c));
         applied = true;
       }
     }
@@ -561,20 +554,16 @@ curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64
   return CURID_OK;
 }
 
-curid_status gram_tf32(const Ctx& ctx, const float* X, int64_t r, int64_t c, int64_t ld,
-                       float* xh, float* xl, float* G, float* g2, float* partial,
-                       size_t partial_cap) {
-  CURID_TRY(split_tf32(ctx, X, ld, xh, ld, xl, ld, r, c));
-  CURID_TRY(gemm_tf32(ctx, false, true, r, r, c, xh, ld, X, ld, G, r, partial, partial_cap));
-  CURID_TRY(gemm_tf32(ctx, false, true, r, r, c, xl, ld, X, ld, g2, r, partial, partial_cap));
-  return add2d<float>(ctx, g2, r, G, r, r, r);
+curid_status gram_tf32(const Ctx& ctx, const float* X, int64_t r, int64_t c, int64_t ld, float* G,
+                       float* partial, size_t partial_cap) {
+  return gemm_tf32(ctx, false, true, r, r, c, X, ld, X, ld, G, r, partial, partial_cap, true);
 }
 
 template curid_status chol_qr_rows<float>(const Ctx&, float**, float**, int64_t, int64_t, int64_t,
-                                          float*, float*, size_t, int, float*, float*, float*);
+                                          float*, float*, size_t, int, bool, float*);
 template curid_status chol_qr_rows<double>(const Ctx&, double**, double**, int64_t, int64_t,
-                                           int64_t, double*, double*, size_t, int, double*,
-                                           double*, double*);
+                                           int64_t, double*, double*, size_t, int, bool,
+                                           double*);
 template curid_status gemm_nt_f64acc<float>(const Ctx&, int64_t, int64_t, int64_t, const float*,
                                             int64_t, const float*, int64_t, double*, int64_t);
 template curid_status gemm_nt_f64acc<double>(const Ctx&, int64_t, int64_t, int64_t,

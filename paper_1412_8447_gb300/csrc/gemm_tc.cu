@@ -10,7 +10,10 @@
 // every singular direction and costs the skeleton up to 8 % in residual on
 // the sigma_j = j^-2 workload; the split keeps the sample matrix at FP32
 // quality (an orthonormal or Gaussian X rounded to TF32 only perturbs
-// directions that the sample already spans).
+// directions that the sample already spans).  Where X is not a sketch
+// operand (the Gram matrices and the L^{-1} apply of the orthonormalisation,
+// split_x) X is split the same way in shared memory and a third MMA,
+// X_lo A_hi, joins each K step: both operands at FP32 accuracy in one launch.
 //
 // Tiling: the transposed product D = C^T is computed, so the MMA's M = 128
 // rows are 128 output columns and its N = l (<= 256, rounded up to 16) is
@@ -53,6 +56,8 @@ struct TcParams {
   int K;
   int kchunk;    // K per split, multiple of kBK
   int mn_major;  // 1: C = X A (A read MN-major); 0: C = X A^T (K-major)
+  int split_x;   // 1: X split in shared memory too (X_hi A_hi + X_hi A_lo + X_lo A_hi)
+  int stages;    // pipeline stages (<= kStages)
   float* C;
   int64_t ldc;
   float* partial;  // [splits][M][N] when K is split
@@ -66,15 +71,18 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
   const int xbytes = ((P.NP * 128 + 1023) / 1024) * 1024;
+  const int S = P.stages;
   unsigned char* Ahi[kStages];
   unsigned char* Alo[kStages];
   unsigned char* Xs[kStages];
+  unsigned char* Xl[kStages];
   unsigned char* p = reinterpret_cast<unsigned char*>(base);
-  for (int s = 0; s < kStages; ++s) {
+  for (int s = 0; s < S; ++s) {
     Ahi[s] = p;
     Alo[s] = p + kAtileBytes;
     Xs[s] = p + 2 * kAtileBytes;
-    p += 2 * kAtileBytes + xbytes;
+    Xl[s] = Xs[s] + xbytes;
+    p += 2 * kAtileBytes + (P.split_x ? 2 : 1) * xbytes;
   }
   uint64_t* bars = reinterpret_cast<uint64_t*>(p);  // full[S], conv[S], empty[S], acc
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 1);
@@ -123,9 +131,9 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
     int issued = 0;
     for (int i = 0; i < nk; ++i) {
-      const int s = i % kStages;
-      const uint32_t ph = (uint32_t)(i / kStages) & 1u;
-      if (i >= kStages && !mbar_wait(empty(s), ph ^ 1u)) {
+      const int s = i % S;
+      const uint32_t ph = (uint32_t)(i / S) & 1u;
+      if (i >= S && !mbar_wait(empty(s), ph ^ 1u)) {
         *abort_flag = 1;
         atomicCAS(&P.status->timeout_site, 0, (1 << 24) | (s << 16) | i);
         break;
@@ -146,14 +154,14 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     }
     if (*abort_flag) {
       // let every load this thread issued land before the CTA can exit
-      for (int i = max(0, issued - kStages); i < issued; ++i)
-        mbar_wait(full(i % kStages), (uint32_t)(i / kStages) & 1u);
+      for (int i = max(0, issued - S); i < issued; ++i)
+        mbar_wait(full(i % S), (uint32_t)(i / S) & 1u);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
     for (int i = 0; i < nk; ++i) {
-      const int s = i % kStages;
-      const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+      const int s = i % S;
+      const uint32_t ph = (uint32_t)(i / S) & 1u;
       if (!mbar_wait(conv(s), ph) || *abort_flag) {
         *abort_flag = 1;
         atomicCAS(&P.status->timeout_site, 0, (2 << 24) | (s << 16) | i);
@@ -161,6 +169,7 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t ah = smem_u32(Ahi[s]), al = smem_u32(Alo[s]), xb = smem_u32(Xs[s]);
+      const uint32_t xlb = smem_u32(Xl[s]);
 #pragma unroll
       for (int kk = 0; kk < kBK / 8; ++kk) {
         // K-major tiles: 128 rows of 128 bytes, 8 K elements = 32 bytes per MMA
@@ -169,6 +178,7 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         const uint64_t dx = smem_desc(xb + kk * 32, 16, 1024);
         mma_tf32(tmem, dh, dx, P.idesc, (i > 0 || kk > 0) ? 1u : 0u);
         mma_tf32(tmem, dl, dx, P.idesc, 1u);
+        if (P.split_x) mma_tf32(tmem, dh, smem_desc(xlb + kk * 32, 16, 1024), P.idesc, 1u);
       }
       mma_commit(empty(s));
     }
@@ -177,8 +187,8 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     // ---- split A into hi / lo, then the epilogue ----
     const int t = threadIdx.x - 128;
     for (int i = 0; i < nk; ++i) {
-      const int s = i % kStages;
-      const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+      const int s = i % S;
+      const uint32_t ph = (uint32_t)(i / S) & 1u;
       if (!mbar_wait(full(s), ph) || *abort_flag) {
         *abort_flag = 1;
         atomicCAS(&P.status->timeout_site, 0, (3 << 24) | (s << 16) | i);
@@ -226,6 +236,23 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
           h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
           hi[idx] = h;
           lo[idx] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        }
+      }
+      if (P.split_x) {
+        // the X tile: NP rows of 128 bytes, split elementwise in place (the
+        // swizzle is a permutation within each 1024-byte atom, the same for
+        // the low buffer)
+        float4* xh = reinterpret_cast<float4*>(Xs[s]);
+        float4* xl = reinterpret_cast<float4*>(Xl[s]);
+        for (int idx = t; idx < P.NP * 8; idx += 128) {
+          const float4 v = xh[idx];
+          float4 h;
+          h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+          h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+          h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+          h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+          xh[idx] = h;
+          xl[idx] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -303,9 +330,10 @@ int tc_splits(int64_t N, int64_t K, int num_sms) {
   return (int)s;
 }
 
-size_t tc_smem(int NP) {
+size_t tc_smem(int NP, int stages, bool split_x) {
   const int xbytes = ((NP * 128 + 1023) / 1024) * 1024;
-  return 1024 + (size_t)kStages * (2 * kAtileBytes + xbytes) + (3 * kStages + 1) * 8 + 16;
+  return 1024 + (size_t)stages * (2 * kAtileBytes + (split_x ? 2 : 1) * xbytes) +
+         (3 * kStages + 1) * 8 + 16;
 }
 
 }  // namespace
@@ -317,7 +345,7 @@ size_t gemm_tf32_partial_elems(int64_t M, int64_t N, int64_t K, int num_sms) {
 
 curid_status gemm_tf32(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
                        const float* X, int64_t ldx, const float* A, int64_t lda, float* C,
-                       int64_t ldc, float* partial, size_t partial_cap) {
+                       int64_t ldc, float* partial, size_t partial_cap, bool split_x) {
   if (ta || M <= 0 || N <= 0 || K <= 0 || M > (int64_t)INT32_MAX / 2) return CURID_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(A) & 15) ||
       (ldx & 3) || (lda & 3))
@@ -348,6 +376,7 @@ curid_status gemm_tf32(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, i
   P.K = (int)K;
   P.kchunk = kchunk;
   P.mn_major = mn ? 1 : 0;
+  P.split_x = split_x ? 1 : 0;
   P.C = C;
   P.ldc = ldc;
   P.partial = splits > 1 ? partial : nullptr;
@@ -356,8 +385,11 @@ curid_status gemm_tf32(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, i
   // N >> 3, M >> 4
   P.idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NP >> 3) << 17) |
             ((uint32_t)(kBM >> 4) << 24);
-  const size_t smem = tc_smem(NP);
+  int stages = kStages;
+  while (stages > 2 && tc_smem(NP, stages, split_x) > ctx.smem_optin) --stages;
+  const size_t smem = tc_smem(NP, stages, split_x);
   if (smem > ctx.smem_optin) return CURID_UNSUPPORTED;
+  P.stages = stages;
   CURID_CUDA(cudaFuncSetAttribute(tc_sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
   dim3 grid((unsigned)(nch * ((N + kBM - 1) / kBM)), (unsigned)splits);

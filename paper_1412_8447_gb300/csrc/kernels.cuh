@@ -40,9 +40,11 @@ curid_status gemm(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, int64_
 // ---- tensor-core products (gemm_tc.cu): TF32 inputs, FP32 accumulation ----
 // C[M x N] = op(A) op(B) with the same op convention as gemm(); returns
 // CURID_UNSUPPORTED for shapes or alignments the kernel does not take.
+// split_x: the left operand is split into TF32 high and low parts too (three
+// MMAs per K step, float32 accuracy for both operands).
 curid_status gemm_tf32(const Ctx& ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
                        const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
-                       int64_t ldc, float* partial, size_t partial_cap);
+                       int64_t ldc, float* partial, size_t partial_cap, bool split_x = false);
 size_t gemm_tf32_partial_elems(int64_t M, int64_t N, int64_t K, int num_sms);
 // BF16 A (gemm_bf16.cu): C[M x N] = X A (tb false; A K x N) or X A^T (tb
 // true; A N x K), X float32 (M x K) split into BF16 high and low parts in
@@ -116,20 +118,18 @@ bool chol_inverse_fits(const Ctx& ctx, int l);
 // whose result is orthonormalised again needs.  X is r x c with leading
 // dimension ld; each pass writes out of place, and on return *X points at
 // the result and *tmp at the other buffer.  G: r x r scratch.
-// With xh and g2 (float32 only: r x ld and r x r scratch), each Gram matrix
-// is formed on the TF32 tensor cores at float32 accuracy (gram_tf32); with li
-// as well (2 r x pad4(r) scratch, r <= 256) the apply X <- L^{-1} X runs on
-// the tensor cores too, through L^{-1} split into its TF32 part and remainder.
+// With tc_gram (float32 only) each Gram matrix is formed on the TF32 tensor
+// cores at float32 accuracy (gram_tf32); with li as well (r x pad4(r)
+// scratch) the apply X <- L^{-1} X runs on the tensor cores too, through an
+// explicit L^{-1}.
 template <typename real>
 curid_status chol_qr_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t c, int64_t ld,
                           real* G, real* partial, size_t partial_cap, int passes = 3,
-                          real* xh = nullptr, real* g2 = nullptr, real* li = nullptr);
-// G (r x r, leading dimension r) = X X^T on the TF32 tensor cores: X =
-// X_hi + X_lo (TF32 part and float32 remainder, into xh and xl), G = X_hi X^T
-// + X_lo X^T with X split hi + lo inside each product; g2: r x r scratch.
-curid_status gram_tf32(const Ctx& ctx, const float* X, int64_t r, int64_t c, int64_t ld,
-                       float* xh, float* xl, float* G, float* g2, float* partial,
-                       size_t partial_cap);
+                          bool tc_gram = false, real* li = nullptr);
+// G (r x r, leading dimension r) = X X^T on the TF32 tensor cores, both
+// operands split into TF32 parts and float32 remainders in shared memory.
+curid_status gram_tf32(const Ctx& ctx, const float* X, int64_t r, int64_t c, int64_t ld, float* G,
+                       float* partial, size_t partial_cap);
 // C (float64) = A B^T with float64 accumulation; A M x K, B N x K.
 template <typename real>
 curid_status gemm_nt_f64acc(const Ctx& ctx, int64_t M, int64_t N, int64_t K, const real* A,
