@@ -380,6 +380,11 @@ def run_ours(args, ws, rank, local):
     err_oracle = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu, err_oracle = cpu_baseline(args, A, curid)
+    # the forms below run one decomposition at a time: put back the handles'
+    # concurrency (the in-flight passes set it on every slot)
+    for s in range(kin):
+        with torch.cuda.stream(streams[s]), curid.inflight(s):
+            curid.set_concurrency(1, local)
     forms = None
     if rank == 0 and ws == 1 and not args.no_forms:
         forms = {"adjoint": measure_adjoint(dev), "batched": measure_batched(dev),

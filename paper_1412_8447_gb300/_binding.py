@@ -773,7 +773,8 @@ class HostStream:
     ``inflight`` decompositions run at once, each on its own stream and
     library handle (``inflight`` slots); inflight + 1 device buffers for A
     rotate, so the copy of the next matrix runs while ``inflight``
-    decompositions use the others.  The copies of A run on a side stream,
+    decompositions use the others.  The copies of A run on two side streams
+    (consecutive matrices alternate),
     each waiting until the decomposition that last read its buffer has
     finished; the copies of (J, I, U) back to the host run on the stream of
     their decomposition.  Host matrices should be pinned
@@ -790,7 +791,9 @@ class HostStream:
         nbuf = self.inflight + 1
         self.A = [torch.empty((m, n), dtype=dtype, device=dev) for _ in range(nbuf)]
         self.out = [cur_outputs(self.A[0], k) for _ in range(self.inflight)]
-        self.copy_stream = torch.cuda.Stream(dev)
+        # two copy streams: host-to-device copies of consecutive matrices can
+        # use two copy engines at once
+        self.copy_streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
         self.streams = [None] + [torch.cuda.Stream(dev) for _ in range(self.inflight - 1)]
         self.ready = [torch.cuda.Event() for _ in range(nbuf)]
         self.free = [torch.cuda.Event() for _ in range(nbuf)]
@@ -817,19 +820,21 @@ class HostStream:
             raise ValueError("one (J, I, U) result triple per matrix is needed")
         # no copy or decomposition may start before work already queued on
         # the current stream
-        self.copy_stream.wait_stream(cur_s)
+        for cs in self.copy_streams:
+            cs.wait_stream(cur_s)
         for st in streams[1:]:
             st.wait_stream(cur_s)
         first = [True] * nbuf
 
         def copy_in(i):
             b = i % nbuf
-            with torch.cuda.stream(self.copy_stream):
+            cs = self.copy_streams[i % 2]
+            with torch.cuda.stream(cs):
                 if not first[b]:
-                    self.copy_stream.wait_event(self.free[b])
+                    cs.wait_event(self.free[b])
                 first[b] = False
                 self.A[b].copy_(A_hosts[i], non_blocking=True)
-                self.ready[b].record(self.copy_stream)
+                self.ready[b].record(cs)
 
         for slot in range(self.inflight):
             with torch.cuda.stream(streams[slot]), inflight(slot):
@@ -853,6 +858,7 @@ class HostStream:
                 U.copy_(self.out[slot].U, non_blocking=True)
         # the A buffers must not be reused by a later run before these copies,
         # and the current stream ends after every decomposition
-        cur_s.wait_stream(self.copy_stream)
+        for cs in self.copy_streams:
+            cur_s.wait_stream(cs)
         for st in streams[1:]:
             cur_s.wait_stream(st)

@@ -294,6 +294,36 @@ def test_cpqr_overflow_columns(dtype, l, n, k):
         assert np.max(np.abs(sgn * S[i] - So[i])) <= tol * np.max(np.abs(So[i]))
 
 
+@pytest.mark.parametrize("l,n,k,ctas", [(210, 6000, 120, None), (200, 3000, 80, "3")])
+def test_cpqr_grouped_throughput_layout(monkeypatch, l, n, k, ctas):
+    """The layout the library picks with eight or more decompositions in
+    flight: the grouped kernel with 7-row register groups on the fewest CTAs
+    that hold the sample (210 x 6000 float32: 19 CTAs).  With the grid forced
+    down to three CTAs (200 x 3000: 1000 columns per CTA) most groups live in
+    the global overflow area.  The planted pivot order must come out exactly,
+    S must match the oracle's rows up to sign, and the concurrency is put
+    back afterwards."""
+    Y, perm = syn.planted_pivots(l, n, k, 45, decay=0.9, dtype=torch.float32)
+    if ctas:
+        monkeypatch.setenv("CURID_CPQR_KERNEL", "grouped")
+        monkeypatch.setenv("CURID_CPQR_CTAS", ctas)
+    curid.set_concurrency(8)
+    try:
+        r = curid.cpqr(cuda(Y), k=k)
+    finally:
+        curid.set_concurrency(1)
+    J = npi(r.J)
+    assert list(J[:k]) == list(perm[:k])
+    assert sorted(J.tolist()) == list(range(n)) and list(J[k:]) == sorted(J[k:].tolist())
+    o = O.cpqr(np64(Y), k=k)
+    S = np64(r.S)
+    So = np.zeros((k, n))
+    So[:, o.J] = o.S1
+    for i in range(k):
+        sgn = np.sign(S[i, J[i]]) * np.sign(So[i, J[i]])
+        assert np.max(np.abs(sgn * S[i] - So[i])) <= 1e-4 * np.max(np.abs(So[i]))
+
+
 def test_random_omega_generated_on_device():
     m, n, k, p = 900, 700, 30, 10
     A = syn.spectrum_matrix(m, n, syn.exp_decay(min(m, n), 6.0), 33)
