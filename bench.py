@@ -36,7 +36,7 @@ FP32_FMA_PER_SM_CLK = 128          # FP32 lanes per SM
 # dram__bytes_read.sum + dram__bytes_write.sum of one cpqr_reg_kernel launch on
 # this workload from the ncu capture named below (empty: no capture of the
 # current kernel yet)
-CPQR_DRAM_BYTES = {"cpqr_col": 5.160e6 + 7.7e3, "cpqr_row": 6.504e6}
+CPQR_DRAM_BYTES = {"cpqr_col": 5.142e6 + 18.4e3, "cpqr_row": 6.695e6 + 24.3e3}
 CPQR_DRAM_SOURCE = ("profiles/cpqr_reg_kernel_randomized_cur_f32_8000x6000_k200.md "
                     "(ncu dram__bytes_read.sum + dram__bytes_write.sum of the one-at-a-time "
                     "cpqr_reg_kernel<float, 7, 4, 16> launches)")
