@@ -1,5 +1,5 @@
-"""Failure statuses driven on the GPU without faulting it (SURVEY's failure
-handling; Section 2.3 for rank deficiency): a wait between the blocks of the
+"""Failure statuses driven on the GPU without faulting it (Section 2.3 for
+rank deficiency): a wait between the blocks of the
 persistent CPQR kernel that runs out (a one-cycle bound set on the handle),
 a non-finite input, an exactly rank-deficient input, and a zero sample whose
 row orthonormalisation (Section 5.3) cannot proceed.  After each, the same
