@@ -312,7 +312,7 @@ def run_ours(args, ws, rank, local):
                "d2h_bytes_per_step": (args.n + args.m) * 4 + args.k * args.k * 8,
                "steps": ke,
                "how": f"HostStream: {kin} decompositions in flight on {kin} streams, the copy "
-                      "of the next matrices on two side streams"}
+                      "of the next matrices on three side streams"}
         del hs
 
     pk, pk_kind = peaks()
