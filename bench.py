@@ -670,10 +670,14 @@ def measure_mixed(dev, steps=3, size=20000, q=None, with_f64=True):
 def measure_srft(dev, steps=10, m=M, n=N, k=K):
     """Accelerated randomized scheme (Section 5.2): the structured Omega of
     Eq. (5.2) (real form: DCT-II rows with random signs, rows and signs drawn
-    on the device each step), l = 2k, no power step, TF32 product, on the
-    benchmark matrix, with U = V* R^+ and with the error-corrected U of
-    Eq. (4.3); against the Gaussian Omega with the same l and q = 0.  Errors
-    ||A - CUR||_F / ||A||_F in float64 on the GPU."""
+    on the device each step), l = 2k, no power step, on the benchmark matrix.
+    "srft": Omega A by the fast transform (Omega never formed), U = V* R^+;
+    "srft_corrected_u": the same with the error-corrected U of Eq. (4.3);
+    "srft_explicit": Omega formed and applied by the TF32 tensor-core product;
+    "gaussian_same_l": a Gaussian Omega with the same l, TF32 product.
+    "sample_ms": the sample Y = Omega A alone, fast transform against the
+    formed Omega's TF32 product.  Errors ||A - CUR||_F / ||A||_F in float64
+    on the GPU."""
     import paper_1412_8447_gb300 as curid
     import synthetic as syn
     l = 2 * k
@@ -689,14 +693,18 @@ def measure_srft(dev, steps=10, m=M, n=N, k=K):
 
     def srft_step(i):
         rows, signs = curid.srft_draw(m, l, 5000 + i, device=dev.index or 0)
-        Om = curid.srft_omega(rows, signs, torch.float32)
-        curid.cur(A, k, p=l - k, q=0, omega=Om, tf32=True, out=out, check=False)
+        curid.cur(A, k, p=l - k, q=0, omega=curid.Srft(rows, signs), tf32=True, out=out,
+                  check=False)
 
     def srft_corrected_step(i):
         rows, signs = curid.srft_draw(m, l, 5000 + i, device=dev.index or 0)
+        curid.cur(A, k, p=l - k, q=0, omega=curid.Srft(rows, signs), tf32=True, out=out,
+                  check=False, corrected=True)
+
+    def srft_explicit_step(i):
+        rows, signs = curid.srft_draw(m, l, 5000 + i, device=dev.index or 0)
         Om = curid.srft_omega(rows, signs, torch.float32)
-        curid.cur(A, k, p=l - k, q=0, omega=Om, tf32=True, out=out, check=False,
-                  corrected=True)
+        curid.cur(A, k, p=l - k, q=0, omega=Om, tf32=True, out=out, check=False)
 
     def gauss_step(i):
         curid.cur(A, k, p=l - k, q=0, seed=6000 + i, tf32=True, out=out, check=False)
@@ -705,7 +713,7 @@ def measure_srft(dev, steps=10, m=M, n=N, k=K):
                        f"l = 2k = {l}, q = 0, TF32 products",
            "unit": "decompositions/s"}
     for name, fn in (("srft", srft_step), ("srft_corrected_u", srft_corrected_step),
-                     ("gaussian_same_l", gauss_step)):
+                     ("srft_explicit", srft_explicit_step), ("gaussian_same_l", gauss_step)):
         for i in range(3):
             fn(i)
         torch.cuda.synchronize(dev)
@@ -718,6 +726,23 @@ def measure_srft(dev, steps=10, m=M, n=N, k=K):
         st, _ = curid.last_status(dev.index or 0)
         res[name] = {"value": 1e3 / ms, "ms_per_step": ms, "status": curid.STATUS_NAMES[st],
                      "rel_err_fro": err()}
+    # the sample alone: the fast transform against the formed Omega's product
+    rows, signs = curid.srft_draw(m, l, 7000, device=dev.index or 0)
+    Om = curid.srft_omega(rows, signs, torch.float32)
+    sample = {}
+    for name, fn in (("fast", lambda: curid.srft_sketch(A, rows, signs)),
+                     ("explicit_tf32", lambda: curid.sketch_matrix(A, Om, q=0, tf32=True))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sample[name] = e0.elapsed_time(e1) / steps
+    sample["fast_hbm_gbs"] = m * n * 4 / (sample["fast"] * 1e-3) / 1e9
+    res["sample_ms"] = sample
     del A, out
     torch.cuda.empty_cache()
     return res

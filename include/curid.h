@@ -77,13 +77,24 @@ typedef enum { CURID_F64 = 0, CURID_F32 = 1, CURID_BF16 = 2 } curid_dtype;
  *           same dtype as A) used as Omega; when NULL the library draws
  *           Omega from its Philox4x32-10 + Box-Muller generator with `seed`.
  *   tf32  : for CURID_F32 only: 1 = the three kinds of sketch product run on
- *           the tensor cores in TF32 with FP32 accumulation; 0 = FP32 FMA. */
+ *           the tensor cores in TF32 with FP32 accumulation; 0 = FP32 FMA.
+ *   srft_rows, srft_signs : optional DEVICE arrays (int32 [l], int8 [m]):
+ *           Omega is the structured matrix of Section 5.2, Eq. (5.2), with
+ *           these sampled rows and signs (see curid_srft_omega), and the
+ *           first product Omega A is the fast transform of curid_srft_sketch
+ *           (Omega is never formed; the power steps, if any, are the usual
+ *           products).  Both or neither; omega must then be NULL and p >= 0;
+ *           dtype CURID_F32 or CURID_F64 (BF16: CURID_UNSUPPORTED), and m
+ *           within curid_srft_sketch's limits.  Not for the sparse and
+ *           complex decompositions nor the adaptive rank (UNSUPPORTED). */
 typedef struct {
   int p;
   int q;
   uint64_t seed;
   const void* omega;
   int tf32;
+  const int32_t* srft_rows;
+  const int8_t* srft_signs;
 } curid_sketch;
 
 typedef struct curid_handle curid_handle;
@@ -185,6 +196,26 @@ curid_status curid_gaussian(curid_handle* handle, curid_dtype dtype,
 curid_status curid_srft_omega(curid_handle* handle, curid_dtype dtype,
                               int64_t m, int64_t l, const int32_t* rows,
                               const int8_t* signs, void* omega, int64_t ldo);
+
+/* Y = Omega A for the structured Omega of curid_srft_omega (Section 5.2,
+ * Eq. (5.2), same reading, rows and signs) without forming Omega: the fast
+ * application the paper gives the structured matrix for.  Each column of
+ * D A is transformed by a DCT-II computed through a mixed-radix FFT in
+ * shared memory (cost O(m log m) per column, A read once), and the l rows
+ * listed in `rows` are kept and scaled; a row outside [0, m) is read from
+ * the periodic extension of F as in curid_srft_omega.  A is m x n (lda, row
+ * major), Y is l x n (ldy), both device memory of dtype CURID_F32 or
+ * CURID_F64 owned by the caller; rows (int32, [l]) and signs (int8, [m])
+ * are device arrays; nothing is allocated.  Agrees with curid_srft_omega
+ * followed by the product Omega A up to rounding (float32: about 1e-6 of
+ * the largest |Y|).  Errors: INVALID_ARG for null pointers, m, n or l < 1,
+ * lda < n or ldy < n; UNSUPPORTED for another dtype, for m with a prime
+ * factor above 7, or for m beyond one SM's shared memory (m complex values:
+ * m <= 29000 in float32, 14500 in float64 on a GPU with 227 KB per CTA). */
+curid_status curid_srft_sketch(curid_handle* handle, curid_dtype dtype,
+                               const void* A, int64_t m, int64_t n,
+                               int64_t lda, int64_t l, const int32_t* rows,
+                               const int8_t* signs, void* Y, int64_t ldy);
 
 /* The random choices of Eq. (5.2) drawn on the device from `seed`: signs
  * (int8, [m], each -1 or +1) for D and rows (int32, [l]) for R, l distinct

@@ -31,7 +31,20 @@ class CuridError(RuntimeError):
 
 class Sketch(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("q", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("omega", ctypes.c_void_p), ("tf32", ctypes.c_int)]
+                ("omega", ctypes.c_void_p), ("tf32", ctypes.c_int),
+                ("srft_rows", ctypes.c_void_p), ("srft_signs", ctypes.c_void_p)]
+
+
+class Srft:
+    """The structured Omega of Eq. (5.2) given by its sampled rows (int32)
+    and signs (int8), both on the device.  Passed as ``omega`` to the
+    decompositions, it is applied by the fast transform (curid_srft_sketch)
+    instead of being formed."""
+
+    def __init__(self, rows, signs):
+        if rows.dtype != torch.int32 or signs.dtype != torch.int8:
+            raise ValueError("rows must be int32 and signs int8")
+        self.rows, self.signs = rows.contiguous(), signs.contiguous()
 
 
 class Sparse(ctypes.Structure):
@@ -57,6 +70,7 @@ SIGNATURES = {
     "curid_gaussian": [_vp, _int, _i64, _i64, ctypes.c_uint64, _vp],
     "curid_srft_omega": [_vp, _int, _i64, _i64, _vp, _vp, _vp, _i64],
     "curid_srft_draw": [_vp, _i64, _i64, ctypes.c_uint64, _vp, _vp],
+    "curid_srft_sketch": [_vp, _int, _vp, _i64, _i64, _i64, _i64, _vp, _vp, _vp, _i64],
     "curid_sketch_matrix": [_vp, _int, _vp, _i64, _i64, _i64, _int, _int, _int, _vp, _vp],
     "curid_cpqr": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, _vp, _vp],
     "curid_cpqr_static": [_vp, _int, _vp, _i64, _i64, _i64, _int, _dbl, _vp, _vp, _vp],
@@ -210,9 +224,13 @@ def _mat(A):
 
 
 def _sketch(p, q, seed, omega, tf32):
+    if isinstance(omega, Srft):
+        return Sketch(int(p), int(q), int(seed) & ((1 << 64) - 1), None, 1 if tf32 else 0,
+                      ctypes.c_void_p(omega.rows.data_ptr()),
+                      ctypes.c_void_p(omega.signs.data_ptr()))
     return Sketch(int(p), int(q), int(seed) & ((1 << 64) - 1),
                   ctypes.c_void_p(omega.data_ptr()) if omega is not None else None,
-                  1 if tf32 else 0)
+                  1 if tf32 else 0, None, None)
 
 
 def workspace_bytes(h, dt, m, n, k, sk):
@@ -335,6 +353,27 @@ def srft_omega(rows, signs, dtype=torch.float32):
     _check(h.lib.curid_srft_omega(h.h, _dtype_code(out.dtype), m, l, _ptr(rows), _ptr(signs),
                                   _ptr(out), m), "curid_srft_omega")
     return out
+
+
+def srft_sketch(A, rows, signs):
+    """Y = Omega A (l x n) for the structured Omega of Eq. (5.2) given by
+    ``rows`` and ``signs``, by the fast transform, without forming Omega
+    (curid_srft_sketch).  A float32 or float64, row-major, on the device."""
+    A = _mat(A)
+    if rows.dtype != torch.int32 or signs.dtype != torch.int8:
+        raise ValueError("rows must be int32 and signs int8")
+    rows, signs = rows.contiguous(), signs.contiguous()
+    m, n = A.shape
+    if signs.numel() != m:
+        raise ValueError("signs must have one entry per row of A")
+    dev = _dev(A)
+    h = handle(dev)
+    h.prepare(0)
+    l = rows.numel()
+    Y = torch.empty((l, n), dtype=A.dtype, device=A.device)
+    _check(h.lib.curid_srft_sketch(h.h, _dtype_code(A.dtype), _ptr(A), m, n, A.stride(0), l,
+                                   _ptr(rows), _ptr(signs), _ptr(Y), n), "curid_srft_sketch")
+    return Y
 
 
 def sketch_matrix(A, omega, q=0, tf32=False):

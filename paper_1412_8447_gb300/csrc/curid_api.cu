@@ -331,7 +331,8 @@ curid_status orth_rows(const Ctx& ctx, real** X, real** tmp, int64_t r, int64_t 
 template <typename real>
 curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const void* A,
                     int64_t m, int64_t n, int64_t lda, int l, int q, bool tf32, bool bf16,
-                    const real* Om, int64_t ldo, real** Yout) {
+                    const real* Om, int64_t ldo, real** Yout, const int32_t* srft_rows = nullptr,
+                    const int8_t* srft_signs = nullptr) {
   const int64_t ldy = pad4(n), ldz = pad4(m);
   auto other = [&](const real* a, const real* b) -> real* {
     for (int i = 0; i < 3; ++i)
@@ -341,7 +342,14 @@ curid_status sketch(curid_handle* h, const Ctx& ctx, const Plan<real>& P, const 
   real* cur = P.B[0];
   {
     PhaseScope ps(h, CURID_PHASE_SKETCH);
-    CURID_TRY(a_product<real>(ctx, tf32, bf16, false, l, n, m, Om, ldo, A, lda, cur, ldy, P));
+    if (srft_rows) {
+      // structured Omega of Eq. (5.2) applied by the fast transform
+      if (bf16) return CURID_UNSUPPORTED;
+      CURID_TRY(srft_apply<real>(ctx, static_cast<const real*>(A), m, n, lda, l, srft_rows,
+                                 srft_signs, cur, ldy));
+    } else {
+      CURID_TRY(a_product<real>(ctx, tf32, bf16, false, l, n, m, Om, ldo, A, lda, cur, ldy, P));
+    }
   }
   for (int i = 0; i < q; ++i) {
     real* t = other(cur, nullptr);
@@ -418,7 +426,8 @@ curid_status run(curid_handle* h, Op op, const void* Araw, const Dims& d, double
   if (d.bf16 && (reinterpret_cast<uintptr_t>(Araw) & 15)) return CURID_UNSUPPORTED;
   Ctx ctx = make_ctx(h);
   Plan<real> P;
-  const bool gen_omega = d.randomized && sk.omega == nullptr;
+  const bool structured = d.randomized && sk.srft_rows != nullptr;
+  const bool gen_omega = d.randomized && sk.omega == nullptr && !structured;
   const bool need_I = o.I == nullptr;
   CURID_TRY(make_plan<real>(ctx, op, d, gen_omega, need_I, nullptr, &P));
   if (ws == nullptr || P.bytes > ws_bytes) return CURID_NO_WORKSPACE;
@@ -439,14 +448,15 @@ curid_status run(curid_handle* h, Op op, const void* Araw, const Dims& d, double
       CURID_TRY(gaussian_fill<real>(ctx, l, m, sk.seed, P.omega, pad4(m)));
       Om = P.omega;
       ldo = pad4(m);
-    } else if (P.omega) {
+    } else if (P.omega && !structured) {
       CURID_TRY(copy2d<real>(ctx, Om, m, P.omega, pad4(m), l, m));
       Om = P.omega;
       ldo = pad4(m);
     }
     real* Yr;
     CURID_TRY(sketch<real>(h, ctx, P, Araw, m, n, lda, l, d.q, sk.tf32 != 0, d.bf16, Om, ldo,
-                           &Yr));
+                           &Yr, structured ? sk.srft_rows : nullptr,
+                           structured ? sk.srft_signs : nullptr));
     Y = Yr;
     ly = l;
     ldy = pad4(n);
@@ -611,6 +621,11 @@ curid_status check_common(curid_handle* h, curid_dtype dt, const void* A, int64_
   if (k > std::min(m, n)) return CURID_INVALID_ARG;
   if (sk.q < 0) return CURID_INVALID_ARG;
   if (sk.tf32 && dt != CURID_F32) return CURID_INVALID_ARG;
+  if (sk.srft_rows || sk.srft_signs) {
+    // the structured Omega replaces omega and seed; it needs both arrays
+    if (!sk.srft_rows || !sk.srft_signs || sk.omega || sk.p < 0) return CURID_INVALID_ARG;
+    if (dt == CURID_BF16) return CURID_UNSUPPORTED;
+  }
   if (dt == CURID_BF16) {
     // the randomized method only: the products run on the tensor cores from
     // 16-byte aligned rows of A
@@ -694,7 +709,8 @@ inline int64_t adaptive_l_cap(int64_t m, int64_t n) {
 curid_status adaptive_rank_randomized(curid_handle* h, curid_dtype dt, const void* A, int64_t m,
                                       int64_t n, int64_t lda, double tol, curid_sketch* sk,
                                       int32_t* J, int* k_out) {
-  if (sk->omega) return CURID_UNSUPPORTED;  // the sample grows: Omega comes from the seed
+  // the sample grows: Omega comes from the seed
+  if (sk->omega || sk->srft_rows || sk->srft_signs) return CURID_UNSUPPORTED;
   const int64_t cap = adaptive_l_cap(m, n);
   if (sk->p < 0 || sk->p >= cap) return CURID_INVALID_ARG;
   int64_t l = std::min<int64_t>(cap, std::max<int64_t>(kAdaptiveL0, sk->p + 1));
@@ -1066,7 +1082,7 @@ curid_status curid_workspace_size(curid_handle* handle, curid_dtype dtype, int64
   // sketch for the largest sample the search may reach (l = min(m, n, 4096))
   if (k == 0 && m > 0 && n > 0) {
     if (sk.p >= 0) {
-      if (sk.omega) return CURID_UNSUPPORTED;
+      if (sk.omega || sk.srft_rows || sk.srft_signs) return CURID_UNSUPPORTED;
       const int64_t cap = adaptive_l_cap(m, n);
       if (sk.p >= cap) return CURID_INVALID_ARG;
       k = (int)(cap - sk.p);
@@ -1079,7 +1095,7 @@ curid_status curid_workspace_size(curid_handle* handle, curid_dtype dtype, int64
   int dummy = 1;
   CURID_TRY(check_common(handle, dtype, &dummy, m, n, n, k, 0.0, sk, &d));
   Ctx ctx = host_ctx(handle);
-  const bool gen = d.randomized && sk.omega == nullptr;
+  const bool gen = d.randomized && sk.omega == nullptr && sk.srft_rows == nullptr;
   Dims dt;
   const bool row_ok = check_common(handle, dtype, &dummy, n, m, m, k, 0.0, sk, &dt) == CURID_OK;
   auto size_for = [&](auto tag) -> curid_status {
@@ -1152,6 +1168,27 @@ curid_status curid_srft_draw(curid_handle* handle, int64_t m, int64_t l, uint64_
     Ctx ctx = make_ctx(handle);
     PhaseScope ps(handle, CURID_PHASE_OMEGA);
     return srft_draw(ctx, m, l, seed, rows, signs);
+  });
+}
+
+curid_status curid_srft_sketch(curid_handle* handle, curid_dtype dtype, const void* A,
+                               int64_t m, int64_t n, int64_t lda, int64_t l,
+                               const int32_t* rows, const int8_t* signs, void* Y, int64_t ldy) {
+  if (!handle || !A || !rows || !signs || !Y || m < 1 || n < 1 || l < 1 || lda < n || ldy < n)
+    return CURID_INVALID_ARG;
+  return dispatch(handle, [&]() -> curid_status {
+    Ctx ctx = make_ctx(handle);
+    PhaseScope ps(handle, CURID_PHASE_SKETCH);
+    switch (dtype) {
+      case CURID_F64:
+        return srft_apply<double>(ctx, static_cast<const double*>(A), m, n, lda, l, rows, signs,
+                                  static_cast<double*>(Y), ldy);
+      case CURID_F32:
+        return srft_apply<float>(ctx, static_cast<const float*>(A), m, n, lda, l, rows, signs,
+                                 static_cast<float*>(Y), ldy);
+      default:
+        return CURID_UNSUPPORTED;
+    }
   });
 }
 
@@ -1352,6 +1389,7 @@ static curid_status sparse_dims(curid_handle* h, curid_dtype dt, int64_t m, int6
     return CURID_INVALID_ARG;
   if (sk.p < 0 || sk.q < 0 || k < 1 || k + (int64_t)sk.p > std::min(m, n))
     return CURID_INVALID_ARG;
+  if (sk.srft_rows || sk.srft_signs) return CURID_UNSUPPORTED;
   *sa = SparseA{A->nnz, A->row_ptr, A->col_idx, A->row_val, A->col_ptr, A->row_idx, A->col_val};
   d->m = m;
   d->n = n;
@@ -1416,7 +1454,8 @@ static curid_status complex_check(curid_handle* h, curid_dtype dt, int64_t m, in
   if (sk.p >= 0 && k + (int64_t)sk.p > std::min(m, n)) return CURID_INVALID_ARG;
   if (sk.p < 0 && sk.q > 0) return CURID_INVALID_ARG;
   if (sk.tf32 && dt != CURID_F32) return CURID_INVALID_ARG;
-  if (sk.omega) return CURID_UNSUPPORTED;  // the sample is drawn from the seed
+  // the sample is drawn from the seed
+  if (sk.omega || sk.srft_rows || sk.srft_signs) return CURID_UNSUPPORTED;
   return CURID_OK;
 }
 

@@ -258,5 +258,12 @@ curid_status srft_draw(const Ctx& ctx, int64_t m, int64_t l, uint64_t seed, int3
 template <typename real>
 curid_status srft_fill(const Ctx& ctx, int64_t m, int64_t l, const int32_t* rows,
                        const int8_t* signs, real* out, int64_t ld);
+// Y = Omega A (l x n, leading dimension ldy) for the same Omega without
+// forming it: one pass over A, a fast DCT of its columns in shared memory.
+// UNSUPPORTED when m has a prime factor above 7 or its columns do not fit.
+template <typename real>
+curid_status srft_apply(const Ctx& ctx, const real* A, int64_t m, int64_t n, int64_t lda,
+                        int64_t l, const int32_t* rows, const int8_t* signs, real* Y,
+                        int64_t ldy);
 
 }  // namespace curid
