@@ -74,6 +74,19 @@ def test_null_handle_rejected_on_host(lib):
         == B.INVALID_ARG
     assert lib.curid_cur_complex(None, 0, vp(1), 10, 10, 10, 2, sk, vp(1), vp(1), vp(1), None,
                                  0) == B.INVALID_ARG
+    assert lib.curid_srft_sketch(None, 1, vp(1), 10, 10, 10, 4, vp(1), vp(1), vp(1), 10) \
+        == B.INVALID_ARG
+
+
+def test_sketch_struct_matches_header():
+    """The binding's curid_sketch has the header's fields in the header's
+    order (the structure is passed by value through the C ABI)."""
+    txt = open(os.path.join(ROOT, "include", "curid.h")).read()
+    body = re.search(r"typedef struct \{([^}]*)\} curid_sketch;", txt).group(1)
+    names = re.findall(r"(\w+)\s*;", body)
+    assert names == [f[0] for f in B.Sketch._fields_]
+    # int, int, uint64, pointer, int (+ padding), pointer, pointer on LP64
+    assert ctypes.sizeof(B.Sketch) == 48
 
 
 def test_philox_known_answers():
