@@ -361,7 +361,8 @@ curid_status curid_id_col(curid_handle* handle, curid_dtype dtype,
 
 /* Row ID (Remark 2.1): A ~ W A(I[:k], :), W = P [I; T_W^*], computed as
  * the column ID of A^*.  Outputs I (m), TW (k x (m-k), leading dimension
- * ldtw). */
+ * ldtw).  With a sketch, Omega is that of the column ID of A^*: sk.omega
+ * is l x n, and sk.srft_signs has n entries. */
 curid_status curid_id_row(curid_handle* handle, curid_dtype dtype,
                           const void* A, int64_t m, int64_t n, int64_t lda,
                           int k, double tol, curid_sketch sk, int32_t* I,
